@@ -1,0 +1,91 @@
+/*
+ * hydro_oracle.h -- C interface of the plain FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle is the slow, obviously-correct
+ * reference that the GPU library is checked against.  Only the tests, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or helper with the CUDA library: the enum
+ * values below are restated here (they are part of the public interface
+ * contract, not shared code).
+ *
+ * Method (HERACLES++, arXiv:2503.04428):
+ *   Euler equations with gravity, heating and passive scalars  -- Sect. 2.1, Eq. 1
+ *   gravity: uniform / point mass / monopole                    -- Sect. 2.2, Eq. 2-4
+ *   ideal-gas EoS                                               -- Sect. 2.3, Eq. 5
+ *   heating/cooling, Ni-56 decay chain                          -- Sect. 2.4, Eq. 8-9
+ *   mesh, dS and dV per geometry                                -- Sect. 3.1.1
+ *   spherical geometric momentum sources                        -- Sect. 3.1.2, Eq. 13-16
+ *   MUSCL-Hancock: limited primitive reconstruction (Eq. 17),
+ *   Hancock half-step predictor (Eq. 18), Godunov update (Eq. 19),
+ *   HLL / HLLC Riemann solvers, three boundary conditions       -- Sect. 3.2
+ *   exact Riemann solution (the "analytical" Sod comparison)    -- App. C.1
+ *   Sedov self-similar shock radius                             -- Sect. 4.3, Eq. 25
+ *
+ * Every array is structure-of-arrays, interior cells only, variable-major:
+ *   U[v][k][j][i], i fastest, v in (rho, m_1..m_dim, E, rho f_1..rho f_S).
+ * All functions return 0 on success, a negative status on error.
+ */
+#ifndef HYDRO_ORACLE_H
+#define HYDRO_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_NEGATIVE_STATE = -3, ORC_ERR_NONFINITE = -4,
+       ORC_ERR_NEWTON = -5, ORC_ERR_VACUUM = -8 };
+enum { ORC_PERIODIC = 0, ORC_TRANSMISSIVE = 1, ORC_REFLECTIVE = 2 };
+enum { ORC_CARTESIAN = 0, ORC_SPHERICAL = 1 };
+enum { ORC_HLL = 0, ORC_HLLC = 1, ORC_EXACT = 2 };
+enum { ORC_FIRST_ORDER = 0, ORC_MINMOD = 1, ORC_VANLEER = 2, ORC_VANALBADA = 3 };
+enum { ORC_GRAV_NONE = 0, ORC_GRAV_UNIFORM = 1, ORC_GRAV_POINT = 2, ORC_GRAV_POINT_MONOPOLE = 3 };
+enum { ORC_HEAT_NONE = 0, ORC_HEAT_CONST = 1, ORC_HEAT_NI56 = 2 };
+enum { ORC_GUESS_TORO = 0, ORC_GUESS_MLP = 1 };
+
+typedef struct orc_ctx* orc_t;
+
+/* n[3]: cells per axis (inactive axes 1); faces: the n[d]+1 face coordinates of
+ * every active axis, concatenated; bc[6]: (lo,hi) per axis. */
+int  orc_create(int dim, const int* n, const double* faces, const int* bc, int coords,
+                double gamma, int n_scalars, int riemann, int limiter, orc_t* out);
+void orc_destroy(orc_t h);
+int  orc_set_sources(orc_t h, int gravity, const double* g0, double G, double Mc,
+                     int heating, const double* heat_params);
+int  orc_set_guess(orc_t h, int guess, const float* mlp_weights);
+int  orc_set_state(orc_t h, const double* U);
+int  orc_get_state(orc_t h, double* U);
+int  orc_set_time(orc_t h, double t);
+int  orc_cfl_dt(orc_t h, double cfl, double* dt);
+int  orc_step(orc_t h, double dt);
+int  orc_totals(orc_t h, double* out);
+/* out[0]=Riemann faces solved, [1]=Newton iterations, [2]=first-order fallbacks,
+ * [3]=faces that used the MLP guess */
+int  orc_stats(orc_t h, long long* out);
+int  orc_shell_mass(orc_t h, double* M_out);   /* enclosed mass per radial cell (monopole) */
+
+/* Batched 1D tubes on [0,1], transmissive ends, each advanced nsteps at its own
+ * CFL time step.  U is (3 x total cells), tubes concatenated per variable. */
+int  orc_batch_run(const int* lengths, int ntubes, double* U, double gamma, int riemann,
+                   int limiter, double cfl, int nsteps, int guess, const float* mlp_weights,
+                   int nthreads, long long* stats_out);
+
+/* Point-wise pieces, exposed for the pins. */
+double orc_limiter(int kind, double dm, double dp);
+int  orc_flux_1d(int riemann, double gamma, int n_scalars, int dim, const double* UL,
+                 const double* UR, double* F);
+int  orc_exact_star(double gamma, const double* WL, const double* WR, int guess,
+                    const float* mlp_weights, double* pstar, double* ustar, int* iters);
+int  orc_exact_sample(double gamma, const double* WL, const double* WR, double xi, double* W);
+double orc_guess_toro(double gamma, const double* WL, const double* WR, int* kind);
+int  orc_mlp_features(double gamma, const double* WL, const double* WR, double* x6, double* pref);
+int  orc_mlp_forward(const float* w, const double* x6, long n, double* y);
+double orc_mlp_loss_grad(const float* w, const double* x6, const double* t, long n, double* grad);
+int  orc_adam_step(float* w, float* m, float* v, const double* grad, int nparam, int step,
+                   double lr, double beta1, double beta2, double eps);
+double orc_sedov_xi0(double gamma);
+double orc_heating_rate(int heating, const double* heat_params, double t, double rho_f_ni);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
