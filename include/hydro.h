@@ -1,0 +1,192 @@
+/*
+ * hydro.h -- C ABI of the GB300 (sm_103a) Godunov cell-update library.
+ *
+ * The library advances the Euler equations with gravity, heating and passive
+ * scalars (HERACLES++, arXiv:2503.04428, Sect. 2.1 Eq. 1) by one
+ * MUSCL-Hancock time step per call (Sect. 3.2, Eq. 17-19): primitive recovery
+ * through the ideal-gas EoS (Sect. 2.3 Eq. 5), limited reconstruction, the
+ * Hancock half-step predictor, an HLL/HLLC/exact Riemann solve at every face,
+ * the conservative update with Cartesian or spherical geometric sources
+ * (Sect. 3.1.2, Eq. 13-16), gravity (Sect. 2.2, Eq. 2-4) and heating
+ * (Sect. 2.4, Eq. 8-9), and the CFL time step.  All of it runs in the
+ * library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a hydro_status (0 = HYDRO_OK, negative = error)
+ *     unless stated otherwise; hydro_last_error() returns a thread-local text
+ *     describing the last failure on the calling thread.
+ *   - A hydro_t is opaque and owns all of its device memory: a double-buffered
+ *     state and small scratch arrays.  It is not thread-safe: one host thread
+ *     at a time per handle.
+ *   - Caller pointers are borrowed for the duration of the call only.  Where
+ *     an argument `where` is HYDRO_DEVICE the pointer is a device address in
+ *     the current CUDA context (for example a torch tensor's data_ptr()); with
+ *     HYDRO_HOST it is ordinary (ideally pinned) host memory.
+ *   - All kernels and copies are issued on the CUDA stream given at creation
+ *     (NULL = legacy default stream).  Calls that return data to the host
+ *     synchronise that stream.
+ *   - State layout: structure of arrays over interior cells, variable-major,
+ *     U[v][k][j][i] with i fastest; v runs over (rho, rho u_1..rho u_dim, E,
+ *     rho f_1..rho f_S).  In spherical coordinates axes (0,1,2) are
+ *     (r, theta, phi) and velocities (u_r, u_theta, u_phi).  Elements are
+ *     double for precision 64 and float for precision 32.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hydro_ctx* hydro_t;
+
+typedef enum {
+  HYDRO_OK = 0,
+  HYDRO_ERR_ARG = -1,             /* invalid argument (message says which) */
+  HYDRO_ERR_CUDA = -2,            /* a CUDA runtime call failed */
+  HYDRO_ERR_NEGATIVE_STATE = -3,  /* a cell reached rho <= 0 or P <= 0 */
+  HYDRO_ERR_NONFINITE = -4,       /* NaN or Inf in the state */
+  HYDRO_ERR_NEWTON = -5,          /* exact-solver Newton did not converge in 100 iterations */
+  HYDRO_ERR_TIMEOUT = -6,         /* reserved: a bounded device wait expired */
+  HYDRO_ERR_OOM = -7,             /* device allocation failed */
+  HYDRO_ERR_VACUUM = -8,          /* exact solver: the data generate vacuum */
+  HYDRO_ERR_UNSUPPORTED = -9      /* combination not built (see message) */
+} hydro_status;
+
+enum { HYDRO_PERIODIC = 0, HYDRO_TRANSMISSIVE = 1, HYDRO_REFLECTIVE = 2 };  /* Sect. 3.2 */
+enum { HYDRO_CARTESIAN = 0, HYDRO_SPHERICAL = 1 };                          /* Sect. 3.1.1 */
+enum { HYDRO_HLL = 0, HYDRO_HLLC = 1, HYDRO_EXACT = 2 };                    /* Sect. 3.2, App. C.1 */
+enum { HYDRO_FIRST_ORDER = 0, HYDRO_MINMOD = 1, HYDRO_VANLEER = 2, HYDRO_VANALBADA = 3 }; /* Eq. 17 */
+enum { HYDRO_GRAV_NONE = 0, HYDRO_GRAV_UNIFORM = 1, HYDRO_GRAV_POINT = 2,
+       HYDRO_GRAV_POINT_MONOPOLE = 3 };                                     /* Eq. 2-4 */
+enum { HYDRO_HEAT_NONE = 0, HYDRO_HEAT_CONST = 1, HYDRO_HEAT_NI56 = 2 };    /* Sect. 2.4 */
+enum { HYDRO_HOST = 0, HYDRO_DEVICE = 1 };
+enum { HYDRO_GUESS_TORO = 0, HYDRO_GUESS_MLP = 1 };
+
+#define HYDRO_MAX_SCALARS 3
+#define HYDRO_MLP_NPARAM 4673  /* 6->64->64->1: W1[64][6] b1[64] W2[64][64] b2[64] w3[64] b3 */
+
+/* Grid (Sect. 3.1.1): logically Cartesian, 1-3 active axes.  faces[d] holds
+ * the n[d]+1 increasing face coordinates of axis d (regular, logarithmic or
+ * custom spacing; radians for angles); axes >= dim are ignored.  bc[d] gives
+ * the (low, high) boundary kind.  Absent angular axes of a spherical grid
+ * span the full sphere.  Every active axis needs n[d] >= 2. */
+typedef struct {
+  int dim;
+  int n[3];
+  const double* faces[3];
+  int bc[3][2];
+} hydro_grid;
+
+/* Ideal-gas EoS (Eq. 5) with n_scalars passive scalars (Eq. 1d), 0..3. */
+typedef struct {
+  double gamma;
+  int n_scalars;
+} hydro_eos;
+
+typedef struct {
+  long long steps;         /* steps completed on this handle */
+  long long faces;         /* Riemann problems solved (owned faces) */
+  long long newton_iters;  /* exact solver: Newton iterations summed over faces */
+  long long fallbacks;     /* predicted face states replaced by the cell average */
+  long long mlp_faces;     /* exact solver: faces whose guess came from the MLP */
+  double t;                /* simulation time (grid handles) */
+  double last_dt;
+  int tile_x, tile_y, zchunk, threads;  /* launch shape chosen by the autotuner */
+  double tuned_us_per_step;            /* autotuner's best measured step time */
+} hydro_stats_t;
+
+/* Create a grid solver.  precision: 64 (FP64 throughout) or 32 (FP32 bulk
+ * arithmetic; FP64 CFL reduction, conserved totals and hard Newton solves).
+ * riemann: HYDRO_HLL / HYDRO_HLLC / HYDRO_EXACT.  limiter: Eq. 17 options.
+ * stream: a cudaStream_t (NULL allowed).  The state is zero until set. */
+int hydro_create(const hydro_grid* grid, int coords, const hydro_eos* eos, int riemann,
+                 int limiter, int precision, void* stream, hydro_t* out);
+
+/* Source terms.  gravity (Eq. 2-4): UNIFORM uses g0 (components along the
+ * grid axes); POINT uses -G Mc / r^2 e_r; POINT_MONOPOLE adds the enclosed
+ * mass M(r) of the current state (spherically symmetric approximation,
+ * Eq. 4), both spherical only.  Sources enter as +rho g and +rho u.g with g
+ * the acceleration.  heating (Sect. 2.4): CONST adds heat_params[0] per unit
+ * volume and time; NI56 adds Eq. 8 in CGS units with heat_params[0] the index
+ * of the scalar holding the Ni-56 mass fraction.  Evaluated at t^n. */
+int hydro_set_sources(hydro_t h, int gravity, const double g0[3], double G, double Mc,
+                      int heating, const double* heat_params);
+
+/* Copy a state in (validated on the device: rho > 0, P > 0, finite; on
+ * failure the previous state is kept) and compute its CFL signal speed. */
+int hydro_set_state(hydro_t h, const void* U, int where);
+int hydro_get_state(hydro_t h, void* U_out, int where);
+int hydro_set_time(hydro_t h, double t);
+
+/* dt = cfl / max_cells sum_d (|u_d| + c)/h_d for the current state (FP64). */
+int hydro_cfl_dt(hydro_t h, double cfl, double* dt_out);
+
+/* One time step of size dt (Eq. 19 plus sources).  Synchronises the stream
+ * to read the device status; on error the state is left as before the call. */
+int hydro_step(hydro_t h, double dt);
+
+/* nsteps time steps with the time step computed on the device from the CFL
+ * condition (dt = cfl/smax, clipped so that t does not pass t_end when
+ * t_end > 0), without host round trips (captured as one CUDA graph after
+ * the first call).  On error the state rolls back to the last good step.
+ * *t_out (may be NULL) receives the time reached. */
+int hydro_run(hydro_t h, int nsteps, double cfl, double t_end, double* t_out);
+
+/* Conserved totals sum_cells U dV, FP64, deterministic order; out has nv entries. */
+int hydro_totals(hydro_t h, double* out_nv);
+int hydro_stats(hydro_t h, hydro_stats_t* out);
+
+/* Batched form: ntubes independent 1D tubes on [0,1] with lengths[b] uniform
+ * cells each, transmissive ends, no scalars.  The state is (3 x sum lengths),
+ * tubes concatenated per variable.  Every tube takes its own CFL time step. */
+int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int riemann,
+                       int limiter, int precision, void* stream, hydro_t* out);
+
+/* nsteps steps of every tube in one persistent launch per step (replayed as a
+ * CUDA graph); the first call runs the launch-shape autotuner on a scratch
+ * copy of the state. */
+int hydro_batch_run(hydro_t h, int nsteps, double cfl);
+
+/* Record (with probability keep_prob, counter-based per face and step) the
+ * left/right primitive states (rho,u,P)x2 of faces whose Toro guess is not
+ * the PVRS one, during later hydro_batch_run calls; capacity faces at most. */
+int hydro_harvest_begin(hydro_t h, long capacity, double keep_prob, unsigned long long seed);
+/* Copy up to cap harvested faces (6 doubles each) to host memory; *n = count. */
+int hydro_harvest_get(hydro_t h, double* faces6, long cap, long* n);
+
+/* MLP initial guess for the exact solver (6->64->64->1, SiLU, FP32 weights,
+ * output ln(p_star/p_ref) with p_ref = sqrt(P_L P_R)).  It is consulted only
+ * on faces whose Toro guess is not PVRS; Newton still runs to 1e-10 relative
+ * and polishes once.  weights: HYDRO_MLP_NPARAM floats (host). */
+int hydro_mlp_set(hydro_t h, const float* weights, int enable);
+int hydro_mlp_get(hydro_t h, float* weights_out);
+
+/* Train the handle's MLP on the GPU (own forward, backward and Adam
+ * kernels): faces6 holds n samples (rho_L,u_L,P_L,rho_R,u_R,P_R), log_pstar
+ * their ln(p_star); MSE on ln(p_star/p_ref); minibatches of `batch`, Adam
+ * (beta 0.9/0.999) with learning rate lr, shuffled by `seed`.  Host arrays.
+ * *loss_out (may be NULL) receives the last epoch's mean loss. */
+int hydro_mlp_train(hydro_t h, const double* faces6, const double* log_pstar, long n, int epochs,
+                    int batch, float lr, unsigned long long seed, double* loss_out);
+
+/* GPU forward + backward of the MSE loss for given features x6 (n x 6) and
+ * targets (n): gradient (HYDRO_MLP_NPARAM doubles) and loss.  Host arrays. */
+int hydro_mlp_loss_grad(const float* weights, const double* x6, const double* target, long n,
+                        double* grad_out, double* loss_out);
+
+/* Exact Riemann star states on the GPU for n independent faces (host arrays
+ * WL, WR of n x (rho,u,P)): p_star, u_star and Newton iterations per face.
+ * precision 64 or 32; guess HYDRO_GUESS_TORO or HYDRO_GUESS_MLP (weights
+ * required then).  Same Newton rule as the solver (App. C.1; Toro ch. 4). */
+int hydro_exact_solve(const double* WL, const double* WR, long n, double gamma, int guess,
+                      const float* weights, int precision, double* pstar, double* ustar,
+                      int* iters);
+
+const char* hydro_last_error(void);
+void hydro_destroy(hydro_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

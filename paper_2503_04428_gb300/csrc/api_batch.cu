@@ -1,0 +1,718 @@
+// api_batch.cu -- C ABI of the batched-tube form, the MLP guess network and
+// the standalone exact Riemann solver (include/hydro.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "batched.cuh"
+#include "mlp.cuh"
+#include "runtime.h"
+
+namespace hydro {
+
+static const int BATCH_CH[] = {128, 256, 512};
+
+struct BatchState {
+  int ntubes = 0;
+  long long total = 0;
+  long long faces_per_step = 0;
+  long long* off_d = nullptr;
+  std::vector<long long> off;
+  double* smax_cur = nullptr;
+  unsigned long long* smax_next = nullptr;
+  double* t_tube = nullptr;
+  BatchCtrl* bctrl = nullptr;
+  BatchCtrl* bctrl_host = nullptr;
+  // work items of the chosen chunk size
+  int ch = 256, grid = 0;
+  int* item_tube = nullptr;
+  int* item_start = nullptr;
+  int nitems = 0;
+  // MLP
+  float* w = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  bool w_set = false;
+  int mlp_on = 0;
+  // harvesting
+  double* harvest = nullptr;
+  unsigned long long* harvest_n = nullptr;
+  long long harvest_cap = 0;
+  unsigned long long harvest_thresh = 0, harvest_seed = 0;
+  // graph of one step
+  cudaGraphExec_t graph = nullptr;
+  double graph_cfl = -1.0;
+  bool tuned = false;
+  double tuned_us = 0.0;
+  int limiter = 1;
+};
+
+static int berr(const std::string& m) {
+  set_error(m);
+  return HYDRO_ERR_ARG;
+}
+
+template <typename T>
+static size_t batch_smem(int ch) {
+  switch (ch) {
+    case 128: return sizeof(BatchSmem<T, 128>);
+    case 256: return sizeof(BatchSmem<T, 256>);
+    default: return sizeof(BatchSmem<T, 512>);
+  }
+}
+
+template <typename T, int CH>
+static int launch_batch_ch(hydro_ctx* h, const BatchArgs<T>& a, int grid) {
+  static bool attr = false;
+  const size_t sm = sizeof(BatchSmem<T, CH>);
+  if (!attr) {
+    HCK(cudaFuncSetAttribute(batched_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  batched_kernel<T, CH><<<grid, CH, sm, h->stream>>>(a);
+  HCK(cudaGetLastError());
+  return HYDRO_OK;
+}
+
+template <typename T, int CH>
+static int occupancy(int* blocks) {
+  static bool attr = false;
+  const size_t sm = sizeof(BatchSmem<T, CH>);
+  if (!attr) {
+    HCK(cudaFuncSetAttribute(batched_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  HCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batched_kernel<T, CH>, CH, sm));
+  return HYDRO_OK;
+}
+
+template <typename T>
+static int occupancy_ch(int ch, int* blocks) {
+  switch (ch) {
+    case 128: return occupancy<T, 128>(blocks);
+    case 256: return occupancy<T, 256>(blocks);
+    default: return occupancy<T, 512>(blocks);
+  }
+}
+
+// Work items (tube, first cell) for chunk size ch.
+static int make_items(hydro_ctx* h, int ch) {
+  BatchState* bs = h->bs;
+  std::vector<int> tube, start;
+  for (int b = 0; b < bs->ntubes; ++b) {
+    const int nb = (int)(bs->off[b + 1] - bs->off[b]);
+    for (int s = 0; s < nb; s += ch) {
+      tube.push_back(b);
+      start.push_back(s);
+    }
+  }
+  if (bs->item_tube) {
+    cudaFree(bs->item_tube);
+    cudaFree(bs->item_start);
+  }
+  HCK(cudaMalloc(&bs->item_tube, sizeof(int) * tube.size()));
+  HCK(cudaMalloc(&bs->item_start, sizeof(int) * start.size()));
+  HCK(cudaMemcpy(bs->item_tube, tube.data(), sizeof(int) * tube.size(), cudaMemcpyHostToDevice));
+  HCK(cudaMemcpy(bs->item_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
+  bs->nitems = (int)tube.size();
+  bs->ch = ch;
+  return HYDRO_OK;
+}
+
+template <typename T>
+static BatchArgs<T> batch_args(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const double* smax_cur,
+                               unsigned long long* smax_next, double* t_tube) {
+  BatchState* bs = h->bs;
+  BatchArgs<T> a;
+  a.A = (const T*)h->buf[0];
+  a.Aw = (T*)h->buf[0];
+  a.B = (T*)h->buf[1];
+  a.total = bs->total;
+  a.off = bs->off_d;
+  a.item_tube = bs->item_tube;
+  a.item_start = bs->item_start;
+  a.nitems = bs->nitems;
+  a.ntubes = bs->ntubes;
+  a.smax_cur = smax_cur;
+  a.smax_next = smax_next;
+  a.t_tube = t_tube;
+  a.cfl = cfl;
+  a.gas = make_gas<T>(h->gamma);
+  a.limiter = bs->limiter;
+  a.mlp_w = bs->w;
+  a.mlp_on = bs->mlp_on && bs->w_set;
+  a.harvest = bs->harvest;
+  a.harvest_n = bs->harvest_n;
+  a.harvest_cap = bs->harvest_cap;
+  a.harvest_thresh = bs->harvest_thresh;
+  a.harvest_seed = bs->harvest_seed;
+  a.ctrl = ctrl;
+  return a;
+}
+
+template <typename T>
+static int launch_batch_t(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const double* smax_cur,
+                          unsigned long long* smax_next, double* t_tube) {
+  BatchArgs<T> a = batch_args<T>(h, cfl, ctrl, smax_cur, smax_next, t_tube);
+  switch (h->bs->ch) {
+    case 128: return launch_batch_ch<T, 128>(h, a, h->bs->grid);
+    case 256: return launch_batch_ch<T, 256>(h, a, h->bs->grid);
+    default: return launch_batch_ch<T, 512>(h, a, h->bs->grid);
+  }
+}
+
+static int launch_batch(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const double* smax_cur,
+                        unsigned long long* smax_next, double* t_tube) {
+  return h->precision == 64 ? launch_batch_t<double>(h, cfl, ctrl, smax_cur, smax_next, t_tube)
+                            : launch_batch_t<float>(h, cfl, ctrl, smax_cur, smax_next, t_tube);
+}
+
+static int read_bctrl(hydro_ctx* h) {
+  HCK(cudaMemcpyAsync(h->bs->bctrl_host, h->bs->bctrl, sizeof(BatchCtrl), cudaMemcpyDeviceToHost, h->stream));
+  HCK(cudaStreamSynchronize(h->stream));
+  return HYDRO_OK;
+}
+
+static int write_bctrl(hydro_ctx* h) {
+  HCK(cudaMemcpyAsync(h->bs->bctrl, h->bs->bctrl_host, sizeof(BatchCtrl), cudaMemcpyHostToDevice, h->stream));
+  HCK(cudaStreamSynchronize(h->stream));
+  return HYDRO_OK;
+}
+
+static void drop_graph(BatchState* bs) {
+  if (bs->graph) {
+    cudaGraphExecDestroy(bs->graph);
+    bs->graph = nullptr;
+  }
+}
+
+// Autotuner of the batched launch: chunk size (= threads per CTA) and the
+// number of persistent CTAs per SM, each candidate timed with CUDA events on
+// scratch copies of the per-tube arrays and control block (the committed
+// state is untouched; outputs land in the non-current buffer).
+static int autotune_batch(hydro_ctx* h, double cfl) {
+  BatchState* bs = h->bs;
+  if (bs->tuned) return HYDRO_OK;
+  bs->tuned = true;
+  std::ostringstream key;
+  key << "batch_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
+      << device_key();
+  int cached;
+  double us;
+  if (tune_cache_get(key.str(), &cached, &us)) {
+    int st = make_items(h, cached / 1000);
+    if (st) return st;
+    bs->grid = h->num_sms * (cached % 1000);
+    bs->tuned_us = us;
+    return HYDRO_OK;
+  }
+  int st = read_bctrl(h);
+  if (st) return st;
+  BatchCtrl base = *bs->bctrl_host;
+  base.c.status = 0;
+  base.c.done = 0;
+  base.next_item = 0;
+  BatchCtrl* sc = nullptr;
+  double* s_cur = nullptr;
+  unsigned long long* s_next = nullptr;
+  double* s_t = nullptr;
+  HCK(cudaMalloc(&sc, sizeof(BatchCtrl)));
+  HCK(cudaMalloc(&s_cur, sizeof(double) * bs->ntubes));
+  HCK(cudaMalloc(&s_next, sizeof(unsigned long long) * bs->ntubes));
+  HCK(cudaMalloc(&s_t, sizeof(double) * bs->ntubes));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e300;
+  int best_ch = 256, best_mult = 1;
+  auto reset = [&]() {
+    cudaMemcpyAsync(sc, &base, sizeof(BatchCtrl), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(s_cur, bs->smax_cur, sizeof(double) * bs->ntubes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemsetAsync(s_next, 0, sizeof(unsigned long long) * bs->ntubes, h->stream);
+  };
+  for (int ch : BATCH_CH) {
+    if ((st = make_items(h, ch))) break;
+    int occ = 1;
+    st = h->precision == 64 ? occupancy_ch<double>(ch, &occ) : occupancy_ch<float>(ch, &occ);
+    if (st) break;
+    for (int mult = 1; mult <= occ; mult *= 2) {
+      bs->grid = h->num_sms * mult;
+      const int reps = 2;
+      float ms = 0.f;
+      reset();
+      if ((st = launch_batch(h, cfl, sc, s_cur, s_next, s_t))) break;
+      for (int r = 0; r < reps; ++r) {
+        reset();
+        cudaEventRecord(e0, h->stream);
+        if ((st = launch_batch(h, cfl, sc, s_cur, s_next, s_t))) break;
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float m1 = 0.f;
+        cudaEventElapsedTime(&m1, e0, e1);
+        ms += m1;
+      }
+      if (st) break;
+      const double t = 1000.0 * ms / reps;
+      if (t < best) {
+        best = t;
+        best_ch = ch;
+        best_mult = mult;
+      }
+    }
+    if (st) break;
+  }
+  cudaStreamSynchronize(h->stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sc);
+  cudaFree(s_cur);
+  cudaFree(s_next);
+  cudaFree(s_t);
+  if (st) return st;
+  if ((st = make_items(h, best_ch))) return st;
+  bs->grid = h->num_sms * best_mult;
+  bs->tuned_us = best;
+  tune_cache_put(key.str(), best_ch * 1000 + best_mult, best);
+  return HYDRO_OK;
+}
+
+template <typename T>
+static int batch_speed(hydro_ctx* h, int slot, int* status) {
+  BatchState* bs = h->bs;
+  int* d_status = nullptr;
+  HCK(cudaMalloc(&d_status, sizeof(int)));
+  HCK(cudaMemsetAsync(d_status, 0, sizeof(int), h->stream));
+  HCK(cudaMemsetAsync(bs->smax_next, 0, sizeof(unsigned long long) * bs->ntubes, h->stream));
+  batch_speed_kernel<T><<<bs->ntubes, 256, 0, h->stream>>>((const T*)h->buf[slot], bs->total, bs->off_d,
+                                                            bs->ntubes, make_gas<T>(h->gamma), bs->smax_next,
+                                                            d_status);
+  HCK(cudaGetLastError());
+  HCK(cudaMemcpyAsync(status, d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  HCK(cudaStreamSynchronize(h->stream));
+  cudaFree(d_status);
+  return HYDRO_OK;
+}
+
+// Glorot-uniform initial weights from SplitMix64 (zero biases).
+static void init_weights(std::vector<float>& w, unsigned long long seed) {
+  w.assign(MLP_NPARAM, 0.f);
+  unsigned long long state = seed;
+  auto next = [&]() {
+    state += 0x9E3779B97F4A7C15ull;
+    unsigned long long z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  auto fill = [&](int off, int n, int fan_in, int fan_out) {
+    const double a = std::sqrt(6.0 / (fan_in + fan_out));
+    for (int i = 0; i < n; ++i) w[off + i] = (float)(a * (2.0 * next() - 1.0));
+  };
+  fill(MW1, MLP_H * MLP_IN, MLP_IN, MLP_H);
+  fill(MW2, MLP_H * MLP_H, MLP_H, MLP_H);
+  fill(MW3, MLP_H, MLP_H, 1);
+}
+
+static int ensure_mlp(hydro_ctx* h) {
+  BatchState* bs = h->bs;
+  if (!bs->w) {
+    HCK(cudaMalloc(&bs->w, sizeof(float) * MLP_NPARAM));
+    HCK(cudaMalloc(&bs->m, sizeof(float) * MLP_NPARAM));
+    HCK(cudaMalloc(&bs->v, sizeof(float) * MLP_NPARAM));
+  }
+  return HYDRO_OK;
+}
+
+// Gradient of the MSE over `count` samples (rows idx[first..] of X/Y) into grad.
+static int mlp_gradient(cudaStream_t s, const float* W, const float* X, const float* Y, const int* idx,
+                        long long first, long long count, float* partial, double* loss_partial,
+                        double* grad, double* loss_acc) {
+  static bool attr = false;
+  if (!attr) {
+    HCK(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
+    attr = true;
+  }
+  const int nblocks = (int)((count + MLP_SB - 1) / MLP_SB);
+  mlp_grad_kernel<<<nblocks, 256, sizeof(MlpSmem), s>>>(W, X, Y, idx, first, count, (float)(1.0 / count),
+                                                        partial, loss_partial);
+  HCK(cudaGetLastError());
+  mlp_reduce_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(partial, nblocks, grad, loss_partial, loss_acc);
+  HCK(cudaGetLastError());
+  return HYDRO_OK;
+}
+
+}  // namespace hydro
+
+using namespace hydro;
+
+int hydro_batch_set_state_impl(hydro_ctx* h, const void* U, int where) {
+  BatchState* bs = h->bs;
+  int st = read_bctrl(h);
+  if (st) return st;
+  const int slot = bs->bctrl_host->c.cur ^ 1;
+  HCK(cudaMemcpyAsync(h->buf[slot], U, (size_t)3 * bs->total * h->esize,
+                      where == HYDRO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  int status = 0;
+  st = h->precision == 64 ? batch_speed<double>(h, slot, &status) : batch_speed<float>(h, slot, &status);
+  if (st) return st;
+  if (status) {
+    set_error(status == HYDRO_ERR_NONFINITE ? "hydro_set_state: non-finite value in the state"
+                                            : "hydro_set_state: density or pressure not positive");
+    return status;
+  }
+  HCK(cudaMemcpyAsync(bs->smax_cur, bs->smax_next, sizeof(double) * bs->ntubes, cudaMemcpyDeviceToDevice,
+                      h->stream));
+  HCK(cudaMemsetAsync(bs->smax_next, 0, sizeof(unsigned long long) * bs->ntubes, h->stream));
+  HCK(cudaMemsetAsync(bs->t_tube, 0, sizeof(double) * bs->ntubes, h->stream));
+  bs->bctrl_host->c.cur = slot;
+  bs->bctrl_host->c.status = 0;
+  bs->bctrl_host->c.done = 0;
+  bs->bctrl_host->c.err_step = -1;
+  bs->bctrl_host->next_item = 0;
+  return write_bctrl(h);
+}
+
+int hydro_batch_get_state_impl(hydro_ctx* h, void* U, int where) {
+  int st = read_bctrl(h);
+  if (st) return st;
+  HCK(cudaMemcpyAsync(U, h->buf[h->bs->bctrl_host->c.cur], (size_t)3 * h->bs->total * h->esize,
+                      where == HYDRO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  HCK(cudaStreamSynchronize(h->stream));
+  return HYDRO_OK;
+}
+
+int hydro_batch_stats_impl(hydro_ctx* h, hydro_stats_t* out) {
+  int st = read_bctrl(h);
+  if (st) return st;
+  const Ctrl& c = h->bs->bctrl_host->c;
+  std::memset(out, 0, sizeof(*out));
+  out->steps = c.step;
+  out->faces = c.step * h->bs->faces_per_step;
+  out->newton_iters = (long long)c.iters;
+  out->fallbacks = (long long)c.fallbacks;
+  out->mlp_faces = (long long)c.mlp;
+  out->tile_x = h->bs->ch;
+  out->tile_y = 1;
+  out->zchunk = h->bs->grid;
+  out->threads = h->bs->ch;
+  out->tuned_us_per_step = h->bs->tuned_us;
+  return HYDRO_OK;
+}
+
+void hydro_batch_free_impl(hydro_ctx* h) {
+  BatchState* bs = h->bs;
+  drop_graph(bs);
+  cudaFree(bs->off_d);
+  cudaFree(bs->smax_cur);
+  cudaFree(bs->smax_next);
+  cudaFree(bs->t_tube);
+  cudaFree(bs->bctrl);
+  cudaFreeHost(bs->bctrl_host);
+  cudaFree(bs->item_tube);
+  cudaFree(bs->item_start);
+  cudaFree(bs->w);
+  cudaFree(bs->m);
+  cudaFree(bs->v);
+  cudaFree(bs->harvest);
+  cudaFree(bs->harvest_n);
+  delete bs;
+  h->bs = nullptr;
+}
+
+extern "C" {
+
+int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int riemann, int limiter,
+                       int precision, void* stream, hydro_t* out) {
+  if (!lengths || !eos || !out || ntubes < 1) return berr("hydro_batch_create: bad argument");
+  *out = nullptr;
+  if (riemann != HYDRO_EXACT)
+    return set_error("hydro_batch_create: the batched form uses the exact Riemann solver"), HYDRO_ERR_UNSUPPORTED;
+  if (eos->n_scalars != 0) return berr("hydro_batch_create: tubes carry no passive scalars");
+  if (!(eos->gamma > 1.0)) return berr("hydro_batch_create: gamma must exceed 1");
+  if (limiter < HYDRO_FIRST_ORDER || limiter > HYDRO_VANALBADA) return berr("hydro_batch_create: bad limiter");
+  long long total = 0;
+  for (int b = 0; b < ntubes; ++b) {
+    if (lengths[b] < 2) return berr("hydro_batch_create: every tube needs >= 2 cells");
+    total += lengths[b];
+  }
+  if (total > 0x7fffffffLL) return berr("hydro_batch_create: more than 2^31 cells in total");
+  hydro_ctx* h = new hydro_ctx();
+  h->batched = true;
+  int st = hydro_common_init(h, precision, stream);
+  if (st) { hydro_destroy(h); return st; }
+  h->gamma = eos->gamma;
+  h->riemann = riemann;
+  h->limiter = limiter;
+  h->dim = 1;
+  h->nv = 3;
+  h->ncell = total;
+  BatchState* bs = new BatchState();
+  h->bs = bs;
+  bs->ntubes = ntubes;
+  bs->total = total;
+  bs->limiter = limiter;
+  bs->faces_per_step = total + ntubes;
+  bs->off.assign(ntubes + 1, 0);
+  for (int b = 0; b < ntubes; ++b) bs->off[b + 1] = bs->off[b] + lengths[b];
+  const size_t bytes = (size_t)3 * total * h->esize;
+  for (int b = 0; b < 2; ++b)
+    if ((st = h->arena.alloc(&h->buf[b], bytes))) { hydro_destroy(h); return st; }
+  if (cudaMalloc(&bs->off_d, sizeof(long long) * (ntubes + 1)) != cudaSuccess ||
+      cudaMalloc(&bs->smax_cur, sizeof(double) * ntubes) != cudaSuccess ||
+      cudaMalloc(&bs->smax_next, sizeof(unsigned long long) * ntubes) != cudaSuccess ||
+      cudaMalloc(&bs->t_tube, sizeof(double) * ntubes) != cudaSuccess ||
+      cudaMalloc(&bs->bctrl, sizeof(BatchCtrl)) != cudaSuccess ||
+      cudaMallocHost(&bs->bctrl_host, sizeof(BatchCtrl)) != cudaSuccess) {
+    set_error("hydro_batch_create: device allocation failed");
+    hydro_destroy(h);
+    return HYDRO_ERR_OOM;
+  }
+  cudaMemcpy(bs->off_d, bs->off.data(), sizeof(long long) * (ntubes + 1), cudaMemcpyHostToDevice);
+  cudaMemset(bs->smax_cur, 0, sizeof(double) * ntubes);
+  cudaMemset(bs->smax_next, 0, sizeof(unsigned long long) * ntubes);
+  cudaMemset(bs->t_tube, 0, sizeof(double) * ntubes);
+  std::memset(bs->bctrl_host, 0, sizeof(BatchCtrl));
+  bs->bctrl_host->c.err_step = -1;
+  if ((st = write_bctrl(h)) || (st = make_items(h, 256))) { hydro_destroy(h); return st; }
+  bs->grid = h->num_sms;
+  *out = h;
+  return HYDRO_OK;
+}
+
+int hydro_batch_run(hydro_t h, int nsteps, double cfl) {
+  if (!h || !h->batched) return berr("hydro_batch_run: batched handle required");
+  if (nsteps < 0 || !(cfl > 0.0)) return berr("hydro_batch_run: bad nsteps or cfl");
+  BatchState* bs = h->bs;
+  int st;
+  if ((st = autotune_batch(h, cfl))) return st;
+  if (!bs->graph || bs->graph_cfl != cfl) {
+    drop_graph(bs);
+    cudaGraph_t g;
+    HCK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+    st = launch_batch(h, cfl, bs->bctrl, bs->smax_cur, bs->smax_next, bs->t_tube);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&bs->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    bs->graph_cfl = cfl;
+  }
+  for (int s = 0; s < nsteps; ++s) HCK(cudaGraphLaunch(bs->graph, h->stream));
+  if ((st = read_bctrl(h))) return st;
+  const int code = bs->bctrl_host->c.status;
+  if (code == 0) return HYDRO_OK;
+  std::ostringstream m;
+  m << "hydro_batch_run: device status " << code << " at step " << bs->bctrl_host->c.err_step;
+  bs->bctrl_host->c.status = 0;
+  bs->bctrl_host->c.done = 0;
+  bs->bctrl_host->c.err_step = -1;
+  bs->bctrl_host->next_item = 0;
+  HCK(cudaMemsetAsync(bs->smax_next, 0, sizeof(unsigned long long) * bs->ntubes, h->stream));
+  if ((st = write_bctrl(h))) return st;
+  set_error(m.str());
+  return code;
+}
+
+int hydro_harvest_begin(hydro_t h, long capacity, double keep_prob, unsigned long long seed) {
+  if (!h || !h->batched || capacity < 0 || !(keep_prob >= 0.0 && keep_prob <= 1.0))
+    return berr("hydro_harvest_begin: bad argument");
+  BatchState* bs = h->bs;
+  cudaFree(bs->harvest);
+  cudaFree(bs->harvest_n);
+  bs->harvest = nullptr;
+  bs->harvest_n = nullptr;
+  bs->harvest_cap = capacity;
+  if (capacity > 0) {
+    HCK(cudaMalloc(&bs->harvest, sizeof(double) * 6 * capacity));
+    HCK(cudaMalloc(&bs->harvest_n, sizeof(unsigned long long)));
+    HCK(cudaMemset(bs->harvest_n, 0, sizeof(unsigned long long)));
+  }
+  bs->harvest_thresh = keep_prob >= 1.0 ? ~0ull : (unsigned long long)(keep_prob * 18446744073709551616.0);
+  bs->harvest_seed = seed;
+  drop_graph(bs);
+  return HYDRO_OK;
+}
+
+int hydro_harvest_get(hydro_t h, double* faces6, long cap, long* n) {
+  if (!h || !h->batched || !n) return berr("hydro_harvest_get: bad argument");
+  BatchState* bs = h->bs;
+  *n = 0;
+  if (!bs->harvest) return HYDRO_OK;
+  unsigned long long cnt = 0;
+  HCK(cudaStreamSynchronize(h->stream));
+  HCK(cudaMemcpy(&cnt, bs->harvest_n, sizeof(cnt), cudaMemcpyDeviceToHost));
+  long long m = std::min<long long>((long long)cnt, bs->harvest_cap);
+  m = std::min<long long>(m, cap);
+  if (m > 0 && faces6) HCK(cudaMemcpy(faces6, bs->harvest, sizeof(double) * 6 * m, cudaMemcpyDeviceToHost));
+  *n = (long)m;
+  return HYDRO_OK;
+}
+
+int hydro_mlp_set(hydro_t h, const float* weights, int enable) {
+  if (!h || !h->batched) return berr("hydro_mlp_set: batched handle required");
+  BatchState* bs = h->bs;
+  int st = ensure_mlp(h);
+  if (st) return st;
+  if (weights) {
+    HCK(cudaMemcpy(bs->w, weights, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice));
+    bs->w_set = true;
+  }
+  if (enable && !bs->w_set) return berr("hydro_mlp_set: no weights to enable");
+  bs->mlp_on = enable ? 1 : 0;
+  drop_graph(bs);
+  bs->tuned = bs->tuned && true;
+  return HYDRO_OK;
+}
+
+int hydro_mlp_get(hydro_t h, float* weights_out) {
+  if (!h || !h->batched || !weights_out) return berr("hydro_mlp_get: bad argument");
+  if (!h->bs->w_set) return berr("hydro_mlp_get: the network has no weights yet");
+  HCK(cudaMemcpy(weights_out, h->bs->w, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost));
+  return HYDRO_OK;
+}
+
+int hydro_mlp_train(hydro_t h, const double* faces6, const double* log_pstar, long n, int epochs, int batch,
+                    float lr, unsigned long long seed, double* loss_out) {
+  if (!h || !h->batched || !faces6 || !log_pstar || n < 1 || epochs < 0 || batch < 1 || !(lr > 0.f))
+    return berr("hydro_mlp_train: bad argument");
+  BatchState* bs = h->bs;
+  int st = ensure_mlp(h);
+  if (st) return st;
+  if (!bs->w_set) {
+    std::vector<float> w0;
+    init_weights(w0, seed);
+    HCK(cudaMemcpy(bs->w, w0.data(), sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice));
+    bs->w_set = true;
+  }
+  HCK(cudaMemset(bs->m, 0, sizeof(float) * MLP_NPARAM));
+  HCK(cudaMemset(bs->v, 0, sizeof(float) * MLP_NPARAM));
+  const long long bsz = std::min<long long>(batch, n);
+  const int nblocks = (int)((bsz + MLP_SB - 1) / MLP_SB);
+  double *f6 = nullptr, *lp = nullptr, *grad = nullptr, *lpart = nullptr, *lacc = nullptr;
+  float *X = nullptr, *Y = nullptr, *part = nullptr;
+  int* idx = nullptr;
+  cudaStream_t s = h->stream;
+  auto cleanup = [&]() {
+    cudaFree(f6); cudaFree(lp); cudaFree(grad); cudaFree(lpart); cudaFree(lacc);
+    cudaFree(X); cudaFree(Y); cudaFree(part); cudaFree(idx);
+  };
+  if (cudaMalloc(&f6, sizeof(double) * 6 * n) || cudaMalloc(&lp, sizeof(double) * n) ||
+      cudaMalloc(&X, sizeof(float) * 6 * n) || cudaMalloc(&Y, sizeof(float) * n) ||
+      cudaMalloc(&idx, sizeof(int) * n) || cudaMalloc(&part, sizeof(float) * MLP_NPARAM * nblocks) ||
+      cudaMalloc(&lpart, sizeof(double) * nblocks) || cudaMalloc(&grad, sizeof(double) * MLP_NPARAM) ||
+      cudaMalloc(&lacc, sizeof(double))) {
+    cleanup();
+    set_error("hydro_mlp_train: device allocation failed");
+    return HYDRO_ERR_OOM;
+  }
+  cudaMemcpyAsync(f6, faces6, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(lp, log_pstar, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  mlp_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f6, lp, n, h->gamma, X, Y);
+  std::vector<int> perm(n);
+  unsigned long long state = seed ^ 0xD1B54A32D192ED03ull;
+  auto next = [&]() {
+    state += 0x9E3779B97F4A7C15ull;
+    unsigned long long z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  int step = 0;
+  double loss = 0.0;
+  for (int ep = 0; ep < epochs && st == 0; ++ep) {
+    for (long i = 0; i < n; ++i) perm[i] = (int)i;
+    for (long i = n - 1; i > 0; --i) std::swap(perm[i], perm[next() % (unsigned long long)(i + 1)]);
+    cudaMemcpyAsync(idx, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(lacc, 0, sizeof(double), s);
+    for (long long first = 0; first + bsz <= n; first += bsz) {
+      if ((st = mlp_gradient(s, bs->w, X, Y, idx, first, bsz, part, lpart, grad, lacc))) break;
+      ++step;
+      adam_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(bs->w, bs->m, bs->v, grad, step, (double)lr, 0.9,
+                                                           0.999, 1e-8);
+      if (cudaGetLastError() != cudaSuccess) { st = HYDRO_ERR_CUDA; break; }
+    }
+    cudaMemcpyAsync(&loss, lacc, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    loss /= (double)((n / bsz) * bsz);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cleanup();
+  if (st) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_mlp_train");
+  if (loss_out) *loss_out = loss;
+  drop_graph(bs);
+  return HYDRO_OK;
+}
+
+int hydro_mlp_loss_grad(const float* weights, const double* x6, const double* target, long n, double* grad_out,
+                        double* loss_out) {
+  if (!weights || !x6 || !target || n < 1 || !grad_out) return berr("hydro_mlp_loss_grad: bad argument");
+  std::vector<float> xf(6 * n), yf(n);
+  for (long i = 0; i < 6 * n; ++i) xf[i] = (float)x6[i];
+  for (long i = 0; i < n; ++i) yf[i] = (float)target[i];
+  const int nblocks = (int)((n + MLP_SB - 1) / MLP_SB);
+  float *W = nullptr, *X = nullptr, *Y = nullptr, *part = nullptr;
+  double *grad = nullptr, *lpart = nullptr, *lacc = nullptr;
+  HCK(cudaMalloc(&W, sizeof(float) * MLP_NPARAM));
+  HCK(cudaMalloc(&X, sizeof(float) * 6 * n));
+  HCK(cudaMalloc(&Y, sizeof(float) * n));
+  HCK(cudaMalloc(&part, sizeof(float) * MLP_NPARAM * nblocks));
+  HCK(cudaMalloc(&grad, sizeof(double) * MLP_NPARAM));
+  HCK(cudaMalloc(&lpart, sizeof(double) * nblocks));
+  HCK(cudaMalloc(&lacc, sizeof(double)));
+  HCK(cudaMemcpy(W, weights, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice));
+  HCK(cudaMemcpy(X, xf.data(), sizeof(float) * 6 * n, cudaMemcpyHostToDevice));
+  HCK(cudaMemcpy(Y, yf.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+  HCK(cudaMemset(lacc, 0, sizeof(double)));
+  int st = mlp_gradient(0, W, X, Y, nullptr, 0, n, part, lpart, grad, lacc);
+  double loss = 0.0;
+  if (!st) {
+    HCK(cudaMemcpy(grad_out, grad, sizeof(double) * MLP_NPARAM, cudaMemcpyDeviceToHost));
+    HCK(cudaMemcpy(&loss, lacc, sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  cudaFree(W); cudaFree(X); cudaFree(Y); cudaFree(part); cudaFree(grad); cudaFree(lpart); cudaFree(lacc);
+  if (loss_out) *loss_out = loss / n;
+  return st;
+}
+
+int hydro_exact_solve(const double* WL, const double* WR, long n, double gamma, int guess, const float* weights,
+                      int precision, double* pstar, double* ustar, int* iters) {
+  if (!WL || !WR || n < 1 || !pstar || !ustar || !iters || !(gamma > 1.0))
+    return berr("hydro_exact_solve: bad argument");
+  if (precision != 32 && precision != 64) return berr("hydro_exact_solve: precision must be 32 or 64");
+  if (guess == HYDRO_GUESS_MLP && !weights) return berr("hydro_exact_solve: MLP guess needs weights");
+  double *dl = nullptr, *dr = nullptr, *dp = nullptr, *du = nullptr;
+  int* di = nullptr;
+  float* dw = nullptr;
+  HCK(cudaMalloc(&dl, sizeof(double) * 3 * n));
+  HCK(cudaMalloc(&dr, sizeof(double) * 3 * n));
+  HCK(cudaMalloc(&dp, sizeof(double) * n));
+  HCK(cudaMalloc(&du, sizeof(double) * n));
+  HCK(cudaMalloc(&di, sizeof(int) * n));
+  HCK(cudaMemcpy(dl, WL, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+  HCK(cudaMemcpy(dr, WR, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+  if (guess == HYDRO_GUESS_MLP) {
+    HCK(cudaMalloc(&dw, sizeof(float) * MLP_NPARAM));
+    HCK(cudaMemcpy(dw, weights, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice));
+  }
+  const unsigned blocks = (unsigned)((n + 127) / 128);
+  if (precision == 64)
+    exact_list_kernel<double><<<blocks, 128>>>(dl, dr, n, make_gas<double>(gamma), dw, dp, du, di);
+  else
+    exact_list_kernel<float><<<blocks, 128>>>(dl, dr, n, make_gas<float>(gamma), dw, dp, du, di);
+  HCK(cudaGetLastError());
+  HCK(cudaMemcpy(pstar, dp, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  HCK(cudaMemcpy(ustar, du, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  HCK(cudaMemcpy(iters, di, sizeof(int) * n, cudaMemcpyDeviceToHost));
+  cudaFree(dl); cudaFree(dr); cudaFree(dp); cudaFree(du); cudaFree(di); cudaFree(dw);
+  return HYDRO_OK;
+}
+
+}  // extern "C"

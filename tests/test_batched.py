@@ -1,0 +1,116 @@
+"""Batched tubes (config 4 form) on the GPU vs the FP64 oracle.
+
+FP64: relative L1 <= 1e-11 after 20 steps (per-step 1e-12 bar, accumulated).
+FP32: per-step relative L1 <= 2e-5 with both sides restarted from the
+oracle's state each step.  The MLP guess must not change the answer (Newton
+is polished to roundoff).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_04428_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def small_tubes(ntubes=12, seed=21, lo=256, hi=1100):
+    return wl.tubes(ntubes, seed=seed, lo=lo, hi=hi)
+
+
+def rel_l1(A, B):
+    A = A.astype(np.float64)
+    B = B.astype(np.float64)
+    scale = np.abs(A[0]).sum() + np.abs(A[2]).sum()
+    return np.array([np.abs(B[v] - A[v]).sum() / max(np.abs(A[v]).sum(), 1e-12 * scale) for v in range(3)])
+
+
+def test_fp64_matches_oracle(hydro_lib):
+    w = small_tubes()
+    ref, st = O.batch_run(w["lengths"], w["U"], w["gamma"], O.EXACT, O.MINMOD, 0.8, 20)
+    b = hydro_lib.Batch(w["lengths"], w["gamma"], precision=64)
+    b.set_state(w["U"])
+    b.run(20, 0.8)
+    err = rel_l1(ref, b.get_state())
+    assert np.all(err <= 1e-11), err
+    s = b.stats()
+    assert s["steps"] == 20
+    assert s["faces"] == st["faces"]
+    # Newton iterations agree with the oracle's to within a few per thousand
+    assert abs(s["newton_iters"] - st["newton_iters"]) <= 0.002 * st["newton_iters"] + 5
+
+
+def test_fp64_mlp_guess_changes_nothing(hydro_lib):
+    """Random (untrained) network weights: a poor guess, same polished answer."""
+    w = small_tubes(6, seed=22)
+    rng = np.random.default_rng(0)
+    weights = (0.1 * rng.standard_normal(O.MLP_NPARAM)).astype(np.float32)
+    ref, _ = O.batch_run(w["lengths"], w["U"], w["gamma"], O.EXACT, O.MINMOD, 0.8, 15)
+    b = hydro_lib.Batch(w["lengths"], w["gamma"], precision=64)
+    b.mlp_set(weights, True)
+    b.set_state(w["U"])
+    b.run(15, 0.8)
+    assert np.all(rel_l1(ref, b.get_state()) <= 1e-11)
+    assert b.stats()["mlp_faces"] > 0
+
+
+def test_fp32_per_step(hydro_lib):
+    w = small_tubes(8, seed=23)
+    U = w["U"].astype(np.float32)
+    b = hydro_lib.Batch(w["lengths"], w["gamma"], precision=32)
+    for _ in range(5):
+        b.set_state(U)
+        ref, _ = O.batch_run(w["lengths"], U.astype(np.float64), w["gamma"], O.EXACT, O.MINMOD, 0.8, 1)
+        b.run(1, 0.8)
+        G = b.get_state()
+        assert np.all(rel_l1(ref, G) <= 2e-5), rel_l1(ref, G)
+        U = ref.astype(np.float32)
+
+
+def test_ragged_and_minimum_tubes(hydro_lib):
+    lengths = np.array([2, 3, 511, 512, 513, 1024, 7, 130], dtype=np.int32)
+    WL, WR = wl.tube_states(len(lengths), 24)
+    total = int(lengths.sum())
+    U = np.empty((3, total))
+    off = 0
+    for bi, nb in enumerate(lengths):
+        x = (np.arange(nb) + 0.5) / nb
+        left = x < 0.5
+        W = np.where(left[None, :], WL[bi][:, None], WR[bi][:, None])
+        U[:, off:off + nb] = wl.conserved(5 / 3, W[0], [W[1]], W[2])
+        off += nb
+    ref, _ = O.batch_run(lengths, U, 5 / 3, O.EXACT, O.VANLEER, 0.6, 10)
+    b = hydro_lib.Batch(lengths, 5 / 3, limiter=hydro_lib.HYDRO_VANLEER, precision=64)
+    b.set_state(U)
+    b.run(10, 0.6)
+    assert np.all(rel_l1(ref, b.get_state()) <= 1e-11)
+
+
+def test_full_size_sampled(hydro_lib):
+    """All 4096 tubes (~1.73e7 cells) in the bench's launch configuration;
+    8 tubes recomputed by the oracle."""
+    w = wl.tubes()
+    b = hydro_lib.Batch(w["lengths"], w["gamma"], precision=64)
+    b.set_state(w["U"])
+    b.run(5, 0.8)
+    G = b.get_state()
+    off = np.concatenate([[0], np.cumsum(w["lengths"])])
+    for t in (0, 1, 517, 1234, 2047, 3000, 4094, 4095):
+        sl = slice(off[t], off[t + 1])
+        ref, _ = O.batch_run(w["lengths"][t:t + 1], w["U"][:, sl], w["gamma"], O.EXACT, O.MINMOD, 0.8, 5)
+        assert np.all(rel_l1(ref, G[:, sl]) <= 1e-11), t
+
+
+def test_rejects_bad_input(hydro_lib):
+    H = hydro_lib
+    with pytest.raises(H.HydroError):
+        H.Batch([1, 5], 1.4)
+    with pytest.raises(H.HydroError) as e:
+        H.hydro_batch_create(np.array([8]), H.hydro_eos(1.4, 0), H.HYDRO_HLLC, H.HYDRO_MINMOD, 64, None)
+    assert e.value.status == H.HYDRO_ERR_UNSUPPORTED
+    b = H.Batch([8, 9], 1.4)
+    U = np.ones((3, 17))
+    U[2] = -1.0
+    with pytest.raises(H.HydroError) as e:
+        b.set_state(U)
+    assert e.value.status == H.HYDRO_ERR_NEGATIVE_STATE

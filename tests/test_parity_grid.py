@@ -1,0 +1,278 @@
+"""GPU grid path vs the FP64 oracle, element by element, one step at a time.
+
+Bar: FP64 relative L1 per conserved component <= 1e-12 per step; FP32
+relative L1 <= 2e-5 per step (the oracle is given the FP32-rounded input, so
+this measures the step's FP32 arithmetic; eps_32 = 6e-8 times the O(100)
+rounding steps on the path of one value).  Sizes span several tiles with
+ragged tails along every axis and several z-chunks in 3D.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_04428_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 2e-5}
+
+
+def rel_l1(A, B, dim):
+    """Relative L1 error per conserved component (B against the reference A)."""
+    A = A.astype(np.float64)
+    B = B.astype(np.float64)
+    nv = A.shape[0]
+    scale = np.abs(A[0]).sum() + np.abs(A[1 + dim]).sum()
+    out = []
+    for v in range(nv):
+        den = np.abs(A[v]).sum()
+        if den < 1e-12 * scale:
+            den = scale
+        out.append(np.abs(B[v] - A[v]).sum() / den)
+    return np.array(out)
+
+
+def step_compare(hydro_lib, case, precision, steps=1, tol=None, dt=None):
+    H = hydro_lib
+    if precision == 32:
+        case = dict(case)
+        case["U"] = case["U"].astype(np.float32).astype(np.float64)
+    s = O.solver_from_case(case)
+    g = H.Grid.from_case(case, precision)
+    tol = TOL[precision] if tol is None else tol
+    worst = 0.0
+    for _ in range(steps):
+        d = dt if dt is not None else s.cfl_dt(case["cfl"])
+        s.step(d)
+        g.step(d)
+        A = s.get_state()
+        B = g.get_state()
+        err = rel_l1(A, B, case["dim"])
+        worst = max(worst, err.max())
+        assert np.all(err <= tol), (case["name"], err)
+        if precision == 32:  # restart both from the oracle's state each step
+            g.set_state(A.astype(np.float32))
+            s.set_state(A.astype(np.float32).astype(np.float64))
+    g.close()
+    return worst
+
+
+BCS = [(O.PERIODIC, O.PERIODIC), (O.TRANSMISSIVE, O.REFLECTIVE), (O.REFLECTIVE, O.TRANSMISSIVE)]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("riemann", [O.HLL, O.HLLC, O.EXACT])
+@pytest.mark.parametrize("limiter", [O.FIRST_ORDER, O.MINMOD, O.VANLEER, O.VANALBADA])
+def test_1d_matrix(hydro_lib, precision, riemann, limiter):
+    for bi, bc in enumerate(BCS):
+        ns = (bi + limiter) % 4
+        case = wl.smooth_random(1, [600], ns, seed=3 + bi, bc=[bc], riemann=riemann, limiter=limiter)
+        step_compare(hydro_lib, case, precision, steps=2)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("riemann", [O.HLL, O.HLLC, O.EXACT])
+def test_2d_matrix(hydro_lib, precision, riemann):
+    for limiter in (O.MINMOD, O.VANLEER, O.VANALBADA):
+        for ns in (0, 1, 3):
+            bc = [BCS[(limiter + ns) % 3], BCS[(limiter + 2 * ns + 1) % 3]]
+            case = wl.smooth_random(2, [70, 45], ns, seed=10 * limiter + ns, bc=bc, riemann=riemann,
+                                    limiter=limiter)
+            step_compare(hydro_lib, case, precision, steps=2)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("riemann", [O.HLL, O.HLLC, O.EXACT])
+@pytest.mark.parametrize("ns", [0, 1, 2, 3])
+def test_3d_matrix(hydro_lib, precision, riemann, ns):
+    bc = [BCS[ns % 3], BCS[(ns + 1) % 3], BCS[(ns + 2) % 3]]
+    case = wl.smooth_random(3, [37, 23, 40], ns, seed=100 + ns, bc=bc, riemann=riemann,
+                            limiter=[O.MINMOD, O.VANLEER, O.VANALBADA, O.MINMOD][ns])
+    step_compare(hydro_lib, case, precision, steps=2)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("riemann", [O.HLLC, O.EXACT, O.HLL])
+def test_spherical(hydro_lib, precision, dim, riemann):
+    case = wl.sphere_state(37, 21, 19, dim=dim, riemann=riemann, n_scalars=dim - 1)
+    step_compare(hydro_lib, case, precision, steps=2)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("gravity", [O.GRAV_POINT, O.GRAV_POINT_MONOPOLE])
+def test_spherical_gravity(hydro_lib, precision, gravity):
+    case = wl.sphere_state(40, 12, 10, dim=3, rotating=True, r_range=(1.0, 20.0), n_scalars=1,
+                           bc=[(O.REFLECTIVE, O.TRANSMISSIVE), (O.REFLECTIVE, O.REFLECTIVE),
+                               (O.PERIODIC, O.PERIODIC)])
+    case["sources"] = dict(gravity=gravity, G=0.01, Mc=2.0)
+    step_compare(hydro_lib, case, precision, steps=3)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_uniform_gravity_and_heating(hydro_lib, precision):
+    case = wl.rt2d(40, 96, riemann=O.HLLC)
+    step_compare(hydro_lib, case, precision, steps=3)
+    case = wl.smooth_random(2, [33, 20], 1, seed=5)
+    case["sources"] = dict(gravity=O.GRAV_UNIFORM, g0=(0.3, -0.2, 0.0), heating=O.HEAT_CONST,
+                           heat_params=(0.05,))
+    step_compare(hydro_lib, case, precision, steps=2)
+
+
+def test_ni56_heating(hydro_lib):
+    n = 300
+    case = wl.smooth_random(1, [n], 2, seed=8)
+    case["U"] = case["U"] * np.array([1e-9, 1e-9 * 1e8, 1e-3, 1e-9, 1e-9])[:, None, None, None]
+    case["sources"] = dict(heating=O.HEAT_NI56, heat_params=(1,))
+    s = O.solver_from_case(case)
+    s.set_time(86400.0 * 5)
+    g = hydro_lib.Grid.from_case(case, 64)
+    g.set_time(86400.0 * 5)
+    s.step(30.0)
+    g.step(30.0)
+    assert np.all(rel_l1(s.get_state(), g.get_state(), 1) <= 1e-12)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_minimum_sizes(hydro_lib, precision):
+    """n = 2 along an axis (the smallest allowed) and thin slabs."""
+    for n, dim in (([2], 1), ([2, 2], 2), ([2, 3, 2], 3), ([65, 2], 2), ([2, 2, 33], 3)):
+        case = wl.smooth_random(dim, n, 1, seed=sum(n),
+                                bc=[BCS[d % 3] for d in range(dim)])
+        step_compare(hydro_lib, case, precision, steps=2)
+
+
+def test_device_dt_run_matches_oracle_sod(hydro_lib):
+    """hydro_run (device CFL time step, graph replay) to t=0.2 on the Sod tube."""
+    case = wl.sod(1000)
+    s = O.solver_from_case(case)
+    t, k = 0.0, 0
+    while t < 0.2 * (1 - 1e-14):
+        dt = min(s.cfl_dt(0.8), 0.2 - t)
+        s.step(dt)
+        t += dt
+        k += 1
+    g = hydro_lib.Grid.from_case(case, 64)
+    t_gpu = g.run(k + 5, 0.8, t_end=0.2)
+    assert abs(t_gpu - 0.2) < 1e-14
+    assert g.stats()["steps"] == k
+    assert np.all(rel_l1(s.get_state(), g.get_state(), 1) <= 1e-10)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_totals_and_cfl(hydro_lib, precision):
+    case = wl.sphere_state(30, 10, 12, n_scalars=2)
+    s = O.solver_from_case(case)
+    g = hydro_lib.Grid.from_case(case, precision)
+    tol = 1e-14 if precision == 64 else 1e-6
+    assert np.all(np.abs(g.totals() - s.totals()) <= tol * np.abs(s.totals()).max())
+    assert abs(g.cfl_dt(0.4) - s.cfl_dt(0.4)) <= tol * 10 * s.cfl_dt(0.4)
+
+
+def test_invalid_states_are_rejected(hydro_lib):
+    H = hydro_lib
+    case = wl.smooth_random(2, [20, 12], 0, seed=1)
+    g = H.Grid.from_case(case, 64)
+    before = g.get_state()
+    bad = case["U"].copy()
+    bad[3, 0, 4, 5] = 0.0  # energy below kinetic: negative pressure
+    with pytest.raises(H.HydroError) as e:
+        g.set_state(bad)
+    assert e.value.status == H.HYDRO_ERR_NEGATIVE_STATE
+    bad = case["U"].copy()
+    bad[0, 0, 2, 2] = np.nan
+    with pytest.raises(H.HydroError) as e:
+        g.set_state(bad)
+    assert e.value.status == H.HYDRO_ERR_NONFINITE
+    assert np.array_equal(g.get_state(), before)
+
+
+def test_failed_step_rolls_back(hydro_lib):
+    H = hydro_lib
+    case = wl.sod(200)
+    g = H.Grid.from_case(case, 64)
+    g.step(g.cfl_dt(0.5))
+    before = g.get_state()
+    with pytest.raises(H.HydroError) as e:
+        g.step(50.0)  # far beyond the CFL limit: the update goes non-physical
+    assert e.value.status in (H.HYDRO_ERR_NEGATIVE_STATE, H.HYDRO_ERR_NONFINITE)
+    assert np.array_equal(g.get_state(), before)
+    assert g.stats()["steps"] == 1
+    g.step(g.cfl_dt(0.5))  # the handle keeps working
+    assert g.stats()["steps"] == 2
+
+
+def test_bad_arguments(hydro_lib):
+    H = hydro_lib
+    with pytest.raises(H.HydroError):
+        H.Grid(1, [1], [np.array([0.0, 1.0])], [(0, 0)], 0, 1.4, 0, 1, 1)  # n < 2
+    with pytest.raises(H.HydroError):
+        H.Grid(1, [4], [np.array([0.0, 1.0, 0.5, 2.0, 3.0])], [(1, 1)], 0, 1.4, 0, 1, 1)  # faces
+    with pytest.raises(H.HydroError):
+        H.Grid(1, [4], [np.linspace(0, 1, 5)], [(1, 1)], 0, 1.4, 4, 1, 1)  # too many scalars
+    g = H.Grid(1, [4], [np.linspace(0, 1, 5)], [(1, 1)], 0, 1.4, 0, 1, 1)
+    with pytest.raises(H.HydroError):
+        g.step(-1.0)
+    with pytest.raises(H.HydroError):
+        g.set_sources(gravity=H.HYDRO_GRAV_POINT, G=1.0, Mc=1.0)  # needs spherical
+
+
+# ---- full-size configurations, in the launch configuration of the bench ----
+
+def test_rt2d_full_size(hydro_lib):
+    """512 x 1536 Rayleigh-Taylor: one FP64 and one FP32 step against the oracle."""
+    case = wl.rt2d()
+    for precision in (64, 32):
+        step_compare(hydro_lib, case, precision, steps=1)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_sedov_full_size_window(hydro_lib, precision):
+    """256^3 Sedov, one step with hydro_run (autotuned, graph): a 36^3 window
+    around the blast is recomputed by the oracle; its interior (3 cells in,
+    beyond the one-step stencil reach) must match."""
+    case = wl.sedov3d(256)
+    U0 = case["U"].astype(np.float32 if precision == 32 else np.float64)
+    g = hydro_lib.Grid.from_case(dict(case, U=U0), precision)
+    g.run(1, case["cfl"])
+    dt = g.stats()["last_dt"]
+    B = g.get_state()
+    lo, hi = 110, 146
+    f = case["faces"][0][lo:hi + 1]
+    win = O.Solver(3, [hi - lo] * 3, [f, f, f], [(O.TRANSMISSIVE, O.TRANSMISSIVE)] * 3, O.CARTESIAN,
+                   1.4, 0, case["riemann"], case["limiter"])
+    win.set_state(U0[:, lo:hi, lo:hi, lo:hi].astype(np.float64))
+    win.step(dt)
+    A = win.get_state()[:, 3:-3, 3:-3, 3:-3]
+    Bw = B[:, lo + 3:hi - 3, lo + 3:hi - 3, lo + 3:hi - 3]
+    assert np.all(rel_l1(A, Bw, 3) <= TOL[precision])
+    # far field untouched in one step, and the blast is octant-symmetric
+    assert np.array_equal(B[:, :100, :100, :100], U0[:, :100, :100, :100])
+    assert np.abs(B[0] - B[0][::-1, ::-1, ::-1]).max() <= (1e-12 if precision == 64 else 1e-5)
+
+
+def test_wedge_full_size_window(hydro_lib):
+    """1024x128x128 spherical wedge (FP32 bulk), one step without gravity:
+    windows at the inner and outer radius recomputed by the oracle."""
+    case = wl.wedge()
+    case["sources"] = None
+    U0 = case["U"].astype(np.float32)
+    g = hydro_lib.Grid.from_case(dict(case, U=U0), 32)
+    g.run(1, case["cfl"])
+    dt = g.stats()["last_dt"]
+    B = g.get_state()
+    rf, tf, pf = case["faces"]
+    for r0, r1 in ((0, 30), (990, 1024)):
+        j0, j1, k0, k1 = 0, 24, 100, 128
+        bc = [(O.REFLECTIVE if r0 == 0 else O.TRANSMISSIVE, O.TRANSMISSIVE if r1 == 1024 else O.TRANSMISSIVE),
+              (O.REFLECTIVE, O.TRANSMISSIVE), (O.TRANSMISSIVE, O.REFLECTIVE)]
+        win = O.Solver(3, [r1 - r0, j1 - j0, k1 - k0], [rf[r0:r1 + 1], tf[j0:j1 + 1], pf[k0:k1 + 1]], bc,
+                       O.SPHERICAL, case["gamma"], 3, case["riemann"], case["limiter"])
+        win.set_state(U0[:, k0:k1, j0:j1, r0:r1].astype(np.float64))
+        win.step(dt)
+        A = win.get_state()
+        # keep cells 3 away from every window edge that is not a true boundary
+        ri = slice(0 if r0 == 0 else 3, (r1 - r0) if r1 == 1024 else (r1 - r0 - 3))
+        sl = (slice(None), slice(3, k1 - k0), slice(0, j1 - j0 - 3), ri)
+        Bw = B[:, k0:k1, j0:j1, r0:r1][sl]
+        assert np.all(rel_l1(A[sl], Bw, 3) <= TOL[32])
