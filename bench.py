@@ -1,0 +1,357 @@
+"""Benchmark of the batched exact-Riemann workload (4096 tubes, 256-8192 cells each).
+
+One step = one MUSCL-Hancock time step of every tube (primitive recovery,
+limited reconstruction, Hancock predictor, exact Riemann solve with the
+learned or Toro guess, conservative update, per-tube CFL speed), i.e. one
+persistent launch of the batched kernel replayed from a CUDA graph.
+
+Headline (`value`): FP32 bulk + MLP star-pressure guess + batched/graph, in
+cell-updates/s over all ranks, inputs resident in HBM.  Beside it: the plain
+FP64 + Toro-guess form of the same kernel (`fp64_plain`), the end-to-end rate
+through the C ABI with host buffers (`e2e`), the HBM roofline of the kernel,
+and the FP64 CPU oracle on a bounded sample (`cpu_baseline`).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank advances its own 4096 tubes (weak scaling, no data
+exchange); timing is the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CFL = 0.8
+NTUBES = 4096
+METRIC = "cell-updates/s"
+WORKLOAD = "batched exact-Riemann: 4096 1D shock tubes, 256-8192 cells (1.73e7 cells), gamma=5/3, minmod"
+KERNEL_SOURCES = ["paper_2503_04428_gb300/csrc/batched.cuh", "paper_2503_04428_gb300/csrc/physics.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "batched_fp32_mlp_4096tubes.traffic.json")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    d = json.load(open(TRAFFIC_FILE))
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return float(d["dram_bytes_per_launch"])
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                smax = float(f[2].split()[0])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        loaded = [s for s in sm if smax and s > 0.5 * smax] or sm
+        return {"sm_mhz": float(np.median(loaded)) if loaded else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def train_mlp(H, torch, gamma, seed):
+    """Harvest hard faces from an FP64 run, label them with the FP64 exact solver
+    and train the guess network with the library's own kernels (untimed)."""
+    from paper_2503_04428_gb300 import workloads as wl
+    t0 = time.time()
+    w = wl.tubes(512, seed=seed)
+    b = H.Batch(w["lengths"], gamma, precision=64)
+    b.set_state(w["U"])
+    b.harvest_begin(600000, 0.5, 4)
+    b.run(40, CFL)
+    faces = b.harvest_get(600000)
+    WL, WR = wl.tube_states(NTUBES, seed)
+    faces = np.concatenate([np.concatenate([WL, WR], axis=1), faces])
+    ps, _, _ = H.hydro_exact_solve(faces[:, :3], faces[:, 3:], gamma, precision=64)
+    keep = ps > 0
+    loss = b.mlp_train(faces[keep], np.log(ps[keep]), epochs=60, batch=1024, lr=3e-3, seed=4)
+    wts = b.mlp_get()
+    b.close()
+    return wts, {"faces": int(keep.sum()), "loss": loss, "train_s": round(time.time() - t0, 2)}
+
+
+def timed_steps(torch, stream, fn, steps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0
+
+
+def cpu_baseline(steps_sample=4, tubes_sample=192):
+    """The FP64 oracle (as it stands, all host cores) on a bounded sample of the workload."""
+    import oracle as O
+    from paper_2503_04428_gb300 import workloads as wl
+    w = wl.tubes(NTUBES, seed=2)
+    ln = w["lengths"][:tubes_sample]
+    U = w["U"][:, :int(ln.sum())]
+    cores = os.cpu_count() or 1
+    t0 = time.time()
+    O.batch_run(ln, U, w["gamma"], O.EXACT, O.MINMOD, CFL, steps_sample, nthreads=cores)
+    dt = time.time() - t0
+    cells = int(ln.sum()) * steps_sample
+    return {"value": cells / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": "%d of 4096 tubes (%d cells) x %d steps, FP64 Toro guess, OpenMP over tubes"
+                      % (tubes_sample, int(ln.sum()), steps_sample)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2503_04428_gb300 import workloads as wl
+    w = wl.tubes(NTUBES, seed=2)
+    ntub = 96
+    ln = w["lengths"][:ntub]
+    U = w["U"][:, :int(ln.sum())].copy()
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        U, _ = O.batch_run(ln, U, w["gamma"], O.EXACT, O.MINMOD, CFL, 1, nthreads=cores)
+    t0 = time.time()
+    for _ in range(args.steps):
+        U, _ = O.batch_run(ln, U, w["gamma"], O.EXACT, O.MINMOD, CFL, 1, nthreads=cores)
+    dt = time.time() - t0
+    cells = int(ln.sum())
+    value = cells * args.steps / dt
+    sample = "%d of 4096 tubes (%d cells) per step, FP64 Toro guess, OpenMP over tubes" % (ntub, cells)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle on a bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tubes", type=int, default=NTUBES, help="tubes per GPU (profiling a smaller case)")
+    ap.add_argument("--skip-fp64", action="store_true", help="do not time the plain FP64 form")
+    ap.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer path")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2503_04428_gb300 import hydro as H
+    from paper_2503_04428_gb300 import workloads as wl
+
+    seed = 2 + 1000 * rank
+    w = wl.tubes(args.tubes, seed=seed)
+    total = int(w["lengths"].sum())
+    gamma = w["gamma"]
+    stream = torch.cuda.current_stream()
+    weights, train_info = train_mlp(H, torch, gamma, seed)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # --- headline: FP32 + MLP guess, batched persistent launch replayed as a graph
+    U32 = torch.from_numpy(w["U"].astype(np.float32)).cuda()
+    b32 = H.Batch(w["lengths"], gamma, precision=32, stream=stream.cuda_stream)
+    b32.mlp_set(weights, True)
+    b32.set_state(U32)
+    b32.run(args.warmup, CFL)  # includes the autotuner on first use
+    b32.set_state(U32)
+    s0 = b32.stats()
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    t32 = timed_steps(torch, stream, lambda k: b32.run(k, CFL), args.steps)
+    clk = clocks.stop()
+    barrier()
+    s1 = b32.stats()
+    if ws > 1:
+        tt = torch.tensor([t32], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t32 = float(tt.item())
+    faces = s1["faces"] - s0["faces"]
+    it32 = (s1["newton_iters"] - s0["newton_iters"]) / max(faces, 1)
+    mlp_frac = (s1["mlp_faces"] - s0["mlp_faces"]) / max(faces, 1)
+    value = ws * total * args.steps / t32
+    ms = 1000.0 * t32 / args.steps
+    out32 = b32.get_state().astype(np.float64)
+
+    value64 = t64 = it64 = rho_rel = None
+    k64 = 0
+    if not args.skip_fp64:
+        value64, t64, k64, it64, rho_rel = time_fp64(H, torch, stream, w, args, ws, total, out32)
+    e2e = None
+    if not args.skip_e2e:
+        e2e = time_e2e(H, torch, b32, w, args, ws, total, barrier)
+    return report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it32, mlp_frac,
+                  value64, t64, k64, it64, rho_rel)
+
+
+def time_fp64(H, torch, stream, w, args, ws, total, out32):
+    """The plain FP64 form of the same kernel (Toro guess), and the difference
+    of its density field from the headline form's after the same steps."""
+    gamma = w["gamma"]
+    U64 = torch.from_numpy(w["U"]).cuda()
+    b64 = H.Batch(w["lengths"], gamma, precision=64, stream=stream.cuda_stream)
+    b64.set_state(U64)
+    b64.run(max(2, args.warmup // 2), CFL)
+    b64.set_state(U64)
+    k64 = max(5, args.steps // 2)
+    r0 = b64.stats()
+    t64 = timed_steps(torch, stream, lambda k: b64.run(k, CFL), k64)
+    r1 = b64.stats()
+    it64 = (r1["newton_iters"] - r0["newton_iters"]) / max(r1["faces"] - r0["faces"], 1)
+    value64 = ws * total * k64 / t64
+    # same number of steps from the same start for an accuracy comparison
+    b64.set_state(U64)
+    b64.run(args.steps, CFL)
+    out64 = b64.get_state()
+    rho_rel = float(np.abs(out32[0] - out64[0]).sum() / np.abs(out64[0]).sum())
+    b64.close()
+    return value64, t64, k64, it64, rho_rel
+
+
+def time_e2e(H, torch, b32, w, args, ws, total, barrier):
+    """Same metric through the C ABI with pinned host buffers: each step copies
+    the state in, advances one step and copies it out."""
+    host_in = torch.from_numpy(w["U"].astype(np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    ke = max(3, args.steps // 5)
+    b32.set_state(host_in)
+    b32.run(1, CFL)
+    b32.get_state(host_out)
+    barrier()
+    te0 = time.perf_counter()
+    for _ in range(ke):
+        b32.set_state(host_in)
+        b32.run(1, CFL)
+        b32.get_state(host_out)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te0
+    nbytes = 3 * total * 4
+    return {"value": ws * total * ke / te, "unit": METRIC, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes}
+
+
+def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it32, mlp_frac,
+           value64, t64, k64, it64, rho_rel):
+    peak, peak_kind = load_peaks()
+    alg_bytes = 2 * 3 * 4 * total  # read U^n and write U^{n+1}, FP32
+    achieved = alg_bytes / (t32 / args.steps) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": profiled_traffic(), "peak_kind": peak_kind, "kernel": "batched_kernel<float>",
+            "algorithmic_bytes_per_launch": alg_bytes}
+    fp64 = None
+    if value64 is not None:
+        ach64 = 2 * 3 * 8 * total / (t64 / k64) / 1e9
+        fp64 = {"value": value64, "unit": METRIC, "ms_per_step": 1000.0 * t64 / k64, "hbm_frac": ach64 / peak,
+                "newton_iters_per_face": it64, "speedup_of_headline": value / value64}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    if rank == 0:
+        st = b32.stats()
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.tubes == NTUBES else "%d-tube subset of: %s" % (args.tubes, WORKLOAD),
+                       "tubes_per_gpu": args.tubes, "cells_per_gpu": total,
+                       "form": "FP32 bulk + MLP p* guess (two-shock faces) + persistent batched kernel + CUDA graph",
+                       "cfl": CFL, "l2": "state 208 MB per buffer > 129 MB L2 (no flush needed)",
+                       "launch": {"chunk": st["tile_x"], "ctas": st["zchunk"]}},
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "fp64_plain": fp64,
+            "newton_iters_per_face": {"fp32_mlp": it32, "fp64_toro": it64},
+            "mlp": dict(train_info, guessed_face_fraction=mlp_frac),
+            "accuracy": {"rho_rel_l1_fp32mlp_vs_fp64": rho_rel},
+        }))
+    b32.close()
+
+
+if __name__ == "__main__":
+    main()
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch.distributed
+        torch.distributed.destroy_process_group()

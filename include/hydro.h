@@ -149,24 +149,32 @@ int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int
 int hydro_batch_run(hydro_t h, int nsteps, double cfl);
 
 /* Record (with probability keep_prob, counter-based per face and step) the
- * left/right primitive states (rho,u,P)x2 of faces whose Toro guess is not
- * the PVRS one, during later hydro_batch_run calls; capacity faces at most. */
+ * left/right primitive states (rho,u,P)x2 of faces where Toro's rule picks
+ * the two-shock estimate, during later hydro_batch_run calls; capacity faces
+ * at most. */
 int hydro_harvest_begin(hydro_t h, long capacity, double keep_prob, unsigned long long seed);
 /* Copy up to cap harvested faces (6 doubles each) to host memory; *n = count. */
 int hydro_harvest_get(hydro_t h, double* faces6, long cap, long* n);
 
-/* MLP initial guess for the exact solver (6->64->64->1, SiLU, FP32 weights,
- * output ln(p_star/p_ref) with p_ref = sqrt(P_L P_R)).  It is consulted only
- * on faces whose Toro guess is not PVRS; Newton still runs to 1e-10 relative
- * and polishes once.  weights: HYDRO_MLP_NPARAM floats (host). */
+/* MLP initial guess for the exact solver (6->64->64->1, SiLU, FP32 weights).
+ * Inputs: ln(rho_L/rho_ref), ln(rho_R/rho_ref), ln(P_L/P_ref), ln(P_R/P_ref),
+ * u_L/c_ref, u_R/c_ref with rho_ref, P_ref the geometric means of the two
+ * sides and c_ref = sqrt(gamma P_ref/rho_ref).  Output y: the guess is
+ * P_ref exp(y), i.e. the network predicts ln(p_star/P_ref).  It replaces
+ * Toro's adaptive guess only on faces where that rule picks the two-shock
+ * (TSRS) estimate (PVRS serves nearby states; the two-rarefaction estimate
+ * is exact when both waves are rarefactions).  Newton still runs to 1e-10
+ * relative and polishes once.  weights: HYDRO_MLP_NPARAM floats (host). */
 int hydro_mlp_set(hydro_t h, const float* weights, int enable);
 int hydro_mlp_get(hydro_t h, float* weights_out);
 
 /* Train the handle's MLP on the GPU (own forward, backward and Adam
  * kernels): faces6 holds n samples (rho_L,u_L,P_L,rho_R,u_R,P_R), log_pstar
- * their ln(p_star); MSE on ln(p_star/p_ref); minibatches of `batch`, Adam
- * (beta 0.9/0.999) with learning rate lr, shuffled by `seed`.  Host arrays.
- * *loss_out (may be NULL) receives the last epoch's mean loss. */
+ * their ln(p_star); only samples on which the network would be used (Toro's
+ * rule picks the two-shock estimate) are trained on; MSE on
+ * ln(p_star/P_ref); minibatches of `batch`, Adam (beta 0.9/0.999) with a
+ * learning rate decaying from lr to 0 on a cosine, shuffled by `seed`.  Host
+ * arrays.  *loss_out (may be NULL) receives the last epoch's mean loss. */
 int hydro_mlp_train(hydro_t h, const double* faces6, const double* log_pstar, long n, int epochs,
                     int batch, float lr, unsigned long long seed, double* loss_out);
 

@@ -77,6 +77,7 @@ int  orc_exact_star(double gamma, const double* WL, const double* WR, int guess,
                     const float* mlp_weights, double* pstar, double* ustar, int* iters);
 int  orc_exact_sample(double gamma, const double* WL, const double* WR, double xi, double* W);
 double orc_guess_toro(double gamma, const double* WL, const double* WR, int* kind);
+/* x6: network inputs; *pref: sqrt(P_L P_R) (the target is ln(p_star/pref)) */
 int  orc_mlp_features(double gamma, const double* WL, const double* WR, double* x6, double* pref);
 int  orc_mlp_forward(const float* w, const double* x6, long n, double* y);
 double orc_mlp_loss_grad(const float* w, const double* x6, const double* t, long n, double* grad);

@@ -612,10 +612,33 @@ int hydro_mlp_train(hydro_t h, const double* faces6, const double* log_pstar, lo
     set_error("hydro_mlp_train: device allocation failed");
     return HYDRO_ERR_OOM;
   }
+  unsigned char* use_d = nullptr;
+  if (cudaMalloc(&use_d, n)) {
+    cleanup();
+    set_error("hydro_mlp_train: device allocation failed");
+    return HYDRO_ERR_OOM;
+  }
   cudaMemcpyAsync(f6, faces6, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(lp, log_pstar, sizeof(double) * n, cudaMemcpyHostToDevice, s);
-  mlp_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f6, lp, n, h->gamma, X, Y);
-  std::vector<int> perm(n);
+  mlp_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f6, lp, n, make_gas<double>(h->gamma), X, Y,
+                                                                  use_d);
+  // train on the faces where the network is used (two-shock Toro estimate)
+  std::vector<unsigned char> use(n);
+  cudaMemcpyAsync(use.data(), use_d, n, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  cudaFree(use_d);
+  std::vector<int> rows;
+  for (long i = 0; i < n; ++i)
+    if (use[i]) rows.push_back((int)i);
+  if (rows.empty()) {
+    cleanup();
+    return berr("hydro_mlp_train: no sample uses the network (no two-shock Toro estimate)");
+  }
+  const long m_use = (long)rows.size();
+  const long long bsz_use = std::min<long long>(bsz, m_use);
+  const long long steps_per_epoch = m_use / bsz_use;
+  const long long total_steps = steps_per_epoch * (long long)epochs;
+  std::vector<int> perm(m_use);
   unsigned long long state = seed ^ 0xD1B54A32D192ED03ull;
   auto next = [&]() {
     state += 0x9E3779B97F4A7C15ull;
@@ -627,20 +650,22 @@ int hydro_mlp_train(hydro_t h, const double* faces6, const double* log_pstar, lo
   int step = 0;
   double loss = 0.0;
   for (int ep = 0; ep < epochs && st == 0; ++ep) {
-    for (long i = 0; i < n; ++i) perm[i] = (int)i;
-    for (long i = n - 1; i > 0; --i) std::swap(perm[i], perm[next() % (unsigned long long)(i + 1)]);
-    cudaMemcpyAsync(idx, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
+    for (long i = 0; i < m_use; ++i) perm[i] = rows[i];
+    for (long i = m_use - 1; i > 0; --i) std::swap(perm[i], perm[next() % (unsigned long long)(i + 1)]);
+    cudaMemcpyAsync(idx, perm.data(), sizeof(int) * m_use, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(lacc, 0, sizeof(double), s);
-    for (long long first = 0; first + bsz <= n; first += bsz) {
-      if ((st = mlp_gradient(s, bs->w, X, Y, idx, first, bsz, part, lpart, grad, lacc))) break;
+    for (long long first = 0; first + bsz_use <= m_use; first += bsz_use) {
+      if ((st = mlp_gradient(s, bs->w, X, Y, idx, first, bsz_use, part, lpart, grad, lacc))) break;
+      // cosine decay of the learning rate over the whole run
+      const double lr_t = 0.5 * (double)lr * (1.0 + std::cos(3.14159265358979323846 * step / (double)total_steps));
       ++step;
-      adam_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(bs->w, bs->m, bs->v, grad, step, (double)lr, 0.9,
+      adam_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(bs->w, bs->m, bs->v, grad, step, lr_t, 0.9,
                                                            0.999, 1e-8);
       if (cudaGetLastError() != cudaSuccess) { st = HYDRO_ERR_CUDA; break; }
     }
     cudaMemcpyAsync(&loss, lacc, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
-    loss /= (double)((n / bsz) * bsz);
+    loss /= (double)(steps_per_epoch * bsz_use);
   }
   cudaError_t e = cudaStreamSynchronize(s);
   cleanup();

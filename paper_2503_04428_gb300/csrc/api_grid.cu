@@ -109,6 +109,8 @@ enum {
   G_IDXC0 = 0, G_IDXC1, G_IDXC2, G_HW0, G_HW1, G_HW2, G_IW0, G_IW1, G_IW2, G_IR, G_IS,
   G_AF, G_INVA, G_GA, G_QR, G_GR, G_GPT, G_BF, G_INVB, G_ZC, G_GT, G_QT, G_INVC, G_COUNT
 };
+static_assert(G_COUNT <= (int)(sizeof(((hydro_ctx*)nullptr)->geo) / sizeof(void*)),
+              "hydro_ctx::geo too small");
 
 template <typename T>
 static int build_geometry(hydro_ctx* h) {

@@ -7,10 +7,12 @@
 // the cells plus two ghosts per side in shared memory and runs the same
 // MUSCL-Hancock steps as the grid sweep (Sect. 3.2, Eq. 17-19) with the exact
 // Riemann solver (App. C.1):
-//   F1  predicted face states, Toro's guess; faces whose guess is not PVRS
-//       are queued for the MLP (and optionally harvested as training data);
+//   F1  predicted face states, Toro's guess; faces where Toro's rule picks
+//       the two-shock estimate are queued for the MLP (and optionally
+//       harvested as training data);
 //   F2  the queued faces are evaluated by the 6-64-64-1 MLP, one per thread,
-//       so that the network runs on full warps;
+//       so that the network runs on full warps; it predicts
+//       ln(p_star/p_ref), p_ref = sqrt(P_L P_R);
 //   F3  Newton from the guess to 1e-10 (FP64) and one polishing step, sample
 //       at x/t = 0, Godunov flux;
 //   U   conservative update and the tube's next signal speed.
@@ -143,6 +145,8 @@ __global__ void __launch_bounds__(CH)
 
     // F1: predicted face states and the guess of faces s0 .. s0+L
     for (int f = tid; f <= L; f += CH) {
+      // faces shared with the next chunk are solved twice; count them once
+      const bool owned = f < L || s0 + L == nb;
       T Wf[2][3];
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(CH)
         if (!(Wf[side][0] > T(0)) || !(Wf[side][2] > T(0))) {
 #pragma unroll
           for (int v = 0; v < 3; ++v) Wf[side][v] = sm.W[v][q];
-          ++n_fb;
+          if (owned) ++n_fb;
         }
       }
 #pragma unroll
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(CH)
       const T cL = dsqrt(gas.g * Wf[0][2] / Wf[0][0]), cR = dsqrt(gas.g * Wf[1][2] / Wf[1][0]);
       int kind;
       sm.pg[f] = toro_guess<T>(Wf[0][0], Wf[0][1], Wf[0][2], cL, Wf[1][0], Wf[1][1], Wf[1][2], cR, gas, kind);
-      if (kind != 0) {
+      if (kind == 2) {
         if (a.mlp_on) sm.queue[atomicAdd(&sm.qn, 1)] = f;
         if (a.harvest) {
           const unsigned long long id = (unsigned long long)(base + b + s0 + f);
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(CH)
                      (float)sm.WLR[3][f], (float)sm.WLR[4][f], (float)sm.WLR[5][f], x, pref);
         const float y = mlp_forward(sm.w, x);
         sm.pg[f] = (T)((double)pref * exp((double)y));
-        ++n_mlp;
+        if (f < L || s0 + L == nb) ++n_mlp;
       }
       __syncthreads();
     }
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(CH)
       }
       int its = 0, kind = 0;
       const int st = riemann_exact<T, 1, 0, 0>(WL, WR, F, gas, sm.pg[f], its, kind);
-      n_iters += its;
+      if (f < L || s0 + L == nb) n_iters += its;
       if (st != ST_OK && err == 0) err = st;
 #pragma unroll
       for (int v = 0; v < 3; ++v) sm.F[v][f] = F[v];
@@ -349,7 +353,7 @@ __global__ void exact_list_kernel(const double* WL, const double* WR, long long 
     const T cL = dsqrt(gas.g * pL / rL), cR = dsqrt(gas.g * pR / rR);
     int kind;
     toro_guess<T>(rL, uL, pL, cL, rR, uR, pR, cR, gas, kind);
-    if (kind != 0) {
+    if (kind == 2) {
       float x[6], pref;
       mlp_features((float)gas.g, (float)rL, (float)uL, (float)pL, (float)rR, (float)uR, (float)pR, x, pref);
       guess = (T)((double)pref * exp((double)mlp_forward(mlp_w, x)));

@@ -1,7 +1,9 @@
 // mlp.cuh -- training of the star-pressure guess network on the GPU.
 //
 // Network: x (6) -> SiLU(W1 x + b1) (64) -> SiLU(W2 h1 + b2) (64) -> w3.h2 + b3,
-// FP32 weights, loss = mean (y - t)^2 with t = ln(p_star / p_ref).
+// FP32 weights, loss = mean (y - t)^2 with t = ln(p_star / p_ref),
+// p_ref = sqrt(P_L P_R).  Only faces where Toro's rule picks the two-shock
+// estimate are trained on (the only faces where the network is used).
 // One CTA handles 64 samples: the three layers and their reverse-mode
 // derivatives are small dense products done in shared memory; each CTA
 // writes its partial gradient, and a second kernel sums the partials in a
@@ -30,9 +32,11 @@ __device__ __forceinline__ float dsilu_f(float z) {
   return s * (1.0f + z * (1.0f - s));
 }
 
-// Features and targets from face states (double) -- once per training set.
+// Features, targets and the "network is used here" flag (Toro's rule picks
+// the two-shock estimate) from face states (double) -- once per training set.
 __global__ void mlp_features_kernel(const double* faces6, const double* log_pstar, long long n,
-                                    double gamma, float* X, float* Y) {
+                                    Gas<double> gas, float* X, float* Y, unsigned char* use) {
+  const double gamma = gas.g;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double* f = faces6 + 6 * i;
@@ -46,6 +50,12 @@ __global__ void mlp_features_kernel(const double* faces6, const double* log_psta
   X[6 * i + 4] = (float)(f[1] * icref);
   X[6 * i + 5] = (float)(f[4] * icref);
   if (Y) Y[i] = (float)(log_pstar[i] - log(pref));
+  if (use) {
+    const double cL = sqrt(gamma * f[2] / f[0]), cR = sqrt(gamma * f[5] / f[3]);
+    int kind;
+    toro_guess<double>(f[0], f[1], f[2], cL, f[3], f[4], f[5], cR, gas, kind);
+    use[i] = kind == 2;
+  }
 }
 
 // Forward + backward of 64 samples per CTA.  Samples are X[idx[first + s]]

@@ -59,7 +59,7 @@ struct hydro_ctx {
   void* buf[2] = {nullptr, nullptr};
   hydro::Ctrl* ctrl = nullptr;       // device control block
   hydro::Ctrl* ctrl_host = nullptr;  // pinned mirror
-  void* geo[20] = {nullptr};         // device geometry arrays (precision T)
+  void* geo[32] = {nullptr};         // device geometry arrays (precision T)
   double* dvol[3] = {nullptr, nullptr, nullptr};  // FP64 volume factors a, b, c
   double* rc_d = nullptr;            // FP64 radial centres
   double omega = 4.0 * 3.14159265358979323846;

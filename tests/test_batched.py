@@ -18,11 +18,13 @@ def small_tubes(ntubes=12, seed=21, lo=256, hi=1100):
     return wl.tubes(ntubes, seed=seed, lo=lo, hi=hi)
 
 
-def rel_l1(A, B):
+def rel_l1(A, B, gamma=5.0 / 3.0):
+    """Per-component relative L1; momentum measured against at least sum(rho c)."""
     A = A.astype(np.float64)
     B = B.astype(np.float64)
-    scale = np.abs(A[0]).sum() + np.abs(A[2]).sum()
-    return np.array([np.abs(B[v] - A[v]).sum() / max(np.abs(A[v]).sum(), 1e-12 * scale) for v in range(3)])
+    p = np.maximum((gamma - 1) * (A[2] - 0.5 * A[1] ** 2 / A[0]), 0.0)
+    den = [np.abs(A[0]).sum(), max(np.abs(A[1]).sum(), np.sqrt(gamma * p * A[0]).sum()), np.abs(A[2]).sum()]
+    return np.array([np.abs(B[v] - A[v]).sum() / den[v] for v in range(3)])
 
 
 def test_fp64_matches_oracle(hydro_lib):

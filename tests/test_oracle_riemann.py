@@ -107,7 +107,7 @@ def test_exact_newton_polish_independent_of_guess():
     w = np.zeros(O.MLP_NPARAM, dtype=np.float32)
     for gamma, WL, WR in _random_problems(30, 9):
         ps0, us0, _ = O.exact_star(gamma, WL, WR)
-        for b3 in (-3.0, 0.0, 2.0):  # MLP guess p_ref * e^b3, used on non-PVRS faces
+        for b3 in (-3.0, 0.0, 2.0):  # MLP guess sqrt(pL pR) e^b3, used on two-shock faces
             w[-1] = b3
             ps1, us1, _ = O.exact_star(gamma, WL, WR, O.GUESS_MLP, w)
             assert abs(ps1 - ps0) <= 1e-13 * ps0

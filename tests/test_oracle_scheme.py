@@ -297,3 +297,31 @@ def test_spherical_closed_wedge_conserves_mass_and_energy():
     T1 = s.totals()
     for v in (0, 4, 5):  # mass, energy, scalar
         assert abs(T1[v] - T0[v]) < 1e-13 * abs(T0[v])
+
+
+def test_point_gravity_closed_form():
+    """Static uniform gas on a spherical wedge with a point mass: after one step
+    the flux differences and the pressure source cancel, so m_r = -dt rho G Mc/r_i^2
+    and the energy is unchanged (u = 0 at t^n)."""
+    case = wl.sphere_state(12, 5, 4, uniform=True, dim=3, r_range=(2.0, 5.0))
+    s = O.solver_from_case(case)
+    s.set_sources(O.GRAV_POINT, G=0.3, Mc=7.0)
+    dt = 1e-3
+    s.step(dt)
+    rf = case["faces"][0]
+    rc = 0.5 * (rf[1:] + rf[:-1])
+    U = s.get_state()
+    expect = -dt * 1.0 * 0.3 * 7.0 / rc ** 2
+    assert np.abs(U[1] - expect[None, None, :]).max() < 1e-13
+    assert np.abs(U[4] - case["U"][4]).max() < 1e-13
+
+
+def test_totals_of_uniform_state_equal_wedge_volume():
+    """sum U dV of a uniform state = value x exact volume of the wedge."""
+    r0, r1, t0, t1, p0, p1 = 1.0, 3.0, 0.6, 2.4, 0.0, 2 * math.pi
+    case = wl.sphere_state(9, 7, 5, uniform=True, dim=3, r_range=(r0, r1), th_range=(t0, t1), ph_range=(p0, p1))
+    s = O.solver_from_case(case)
+    vol = (r1 ** 3 - r0 ** 3) / 3 * (math.cos(t0) - math.cos(t1)) * (p1 - p0)
+    T = s.totals()
+    assert abs(T[0] - vol) < 1e-13 * vol
+    assert abs(T[4] - vol / (5 / 3 - 1)) < 1e-13 * vol / (5 / 3 - 1)
