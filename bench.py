@@ -112,6 +112,26 @@ def dist_info():
     return ws, rank, local
 
 
+def rank_seed(rank):
+    """Each rank advances its own 4096 tubes (weak scaling): a seed per rank."""
+    return 2 + 1000 * rank
+
+
+def job_rate(elapsed_local, cells_local, steps, dist=None, device=None):
+    """Whole-job rate: cells of all ranks x steps / the slowest rank's time.
+
+    With a process group the elapsed time is max-reduced and the cells are
+    sum-reduced (timing only: no data-path collective)."""
+    if dist is None:
+        return cells_local * steps / elapsed_local, elapsed_local
+    import torch
+    t = torch.tensor([elapsed_local], dtype=torch.float64, device=device)
+    c = torch.tensor([float(cells_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(c.item()) * steps / float(t.item()), float(t.item())
+
+
 def train_mlp(H, torch, gamma, seed):
     """Harvest hard faces from an FP64 run, label them with the FP64 exact solver
     and train the guess network with the library's own kernels (untimed)."""
@@ -214,7 +234,7 @@ def main():
     from paper_2503_04428_gb300 import hydro as H
     from paper_2503_04428_gb300 import workloads as wl
 
-    seed = 2 + 1000 * rank
+    seed = rank_seed(rank)
     w = wl.tubes(args.tubes, seed=seed)
     total = int(w["lengths"].sum())
     gamma = w["gamma"]
@@ -241,14 +261,10 @@ def main():
     clk = clocks.stop()
     barrier()
     s1 = b32.stats()
-    if ws > 1:
-        tt = torch.tensor([t32], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t32 = float(tt.item())
+    value, t32 = job_rate(t32, total, args.steps, torch.distributed if ws > 1 else None, "cuda")
     faces = s1["faces"] - s0["faces"]
     it32 = (s1["newton_iters"] - s0["newton_iters"]) / max(faces, 1)
     mlp_frac = (s1["mlp_faces"] - s0["mlp_faces"]) / max(faces, 1)
-    value = ws * total * args.steps / t32
     ms = 1000.0 * t32 / args.steps
     out32 = b32.get_state().astype(np.float64)
 

@@ -15,7 +15,10 @@
 
 namespace hydro {
 
-static const int BATCH_CH[] = {128, 256, 512};
+// Autotuner candidates: warps per CTA, cells per work item (whole 30-cell
+// segments) and persistent CTAs per SM (up to the occupancy limit).
+static const int BATCH_NW[] = {4, 8};
+static const int BATCH_ITEM[] = {30, 60, 120, 240, 480};
 
 struct BatchState {
   int ntubes = 0;
@@ -28,8 +31,8 @@ struct BatchState {
   double* t_tube = nullptr;
   BatchCtrl* bctrl = nullptr;
   BatchCtrl* bctrl_host = nullptr;
-  // work items of the chosen chunk size
-  int ch = 256, grid = 0;
+  // launch shape: warps per CTA, cells per item, CTAs
+  int nw = 8, item_len = 120, grid = 0;
   int* item_tube = nullptr;
   int* item_start = nullptr;
   int nitems = 0;
@@ -57,56 +60,27 @@ static int berr(const std::string& m) {
   return HYDRO_ERR_ARG;
 }
 
-template <typename T>
-static size_t batch_smem(int ch) {
-  switch (ch) {
-    case 128: return sizeof(BatchSmem<T, 128>);
-    case 256: return sizeof(BatchSmem<T, 256>);
-    default: return sizeof(BatchSmem<T, 512>);
-  }
-}
-
-template <typename T, int CH>
-static int launch_batch_ch(hydro_ctx* h, const BatchArgs<T>& a, int grid) {
-  static bool attr = false;
-  const size_t sm = sizeof(BatchSmem<T, CH>);
-  if (!attr) {
-    HCK(cudaFuncSetAttribute(batched_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
-  batched_kernel<T, CH><<<grid, CH, sm, h->stream>>>(a);
+template <typename T, int NW>
+static int launch_batch_nw(hydro_ctx* h, const BatchArgs<T>& a, int grid) {
+  batched_kernel<T, NW><<<grid, NW * 32, 0, h->stream>>>(a);
   HCK(cudaGetLastError());
   return HYDRO_OK;
 }
 
-template <typename T, int CH>
-static int occupancy(int* blocks) {
-  static bool attr = false;
-  const size_t sm = sizeof(BatchSmem<T, CH>);
-  if (!attr) {
-    HCK(cudaFuncSetAttribute(batched_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
-  HCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batched_kernel<T, CH>, CH, sm));
+template <typename T>
+static int occupancy_nw(int nw, int* blocks) {
+  if (nw == 4) HCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batched_kernel<T, 4>, 128, 0));
+  else HCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batched_kernel<T, 8>, 256, 0));
   return HYDRO_OK;
 }
 
-template <typename T>
-static int occupancy_ch(int ch, int* blocks) {
-  switch (ch) {
-    case 128: return occupancy<T, 128>(blocks);
-    case 256: return occupancy<T, 256>(blocks);
-    default: return occupancy<T, 512>(blocks);
-  }
-}
-
-// Work items (tube, first cell) for chunk size ch.
-static int make_items(hydro_ctx* h, int ch) {
+// Work items (tube, first cell) of item_len cells.
+static int make_items(hydro_ctx* h, int item_len) {
   BatchState* bs = h->bs;
   std::vector<int> tube, start;
   for (int b = 0; b < bs->ntubes; ++b) {
     const int nb = (int)(bs->off[b + 1] - bs->off[b]);
-    for (int s = 0; s < nb; s += ch) {
+    for (int s = 0; s < nb; s += item_len) {
       tube.push_back(b);
       start.push_back(s);
     }
@@ -120,7 +94,7 @@ static int make_items(hydro_ctx* h, int ch) {
   HCK(cudaMemcpy(bs->item_tube, tube.data(), sizeof(int) * tube.size(), cudaMemcpyHostToDevice));
   HCK(cudaMemcpy(bs->item_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
   bs->nitems = (int)tube.size();
-  bs->ch = ch;
+  bs->item_len = item_len;
   return HYDRO_OK;
 }
 
@@ -136,6 +110,7 @@ static BatchArgs<T> batch_args(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const 
   a.off = bs->off_d;
   a.item_tube = bs->item_tube;
   a.item_start = bs->item_start;
+  a.item_len = bs->item_len;
   a.nitems = bs->nitems;
   a.ntubes = bs->ntubes;
   a.smax_cur = smax_cur;
@@ -159,11 +134,8 @@ template <typename T>
 static int launch_batch_t(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const double* smax_cur,
                           unsigned long long* smax_next, double* t_tube) {
   BatchArgs<T> a = batch_args<T>(h, cfl, ctrl, smax_cur, smax_next, t_tube);
-  switch (h->bs->ch) {
-    case 128: return launch_batch_ch<T, 128>(h, a, h->bs->grid);
-    case 256: return launch_batch_ch<T, 256>(h, a, h->bs->grid);
-    default: return launch_batch_ch<T, 512>(h, a, h->bs->grid);
-  }
+  if (h->bs->nw == 4) return launch_batch_nw<T, 4>(h, a, h->bs->grid);
+  return launch_batch_nw<T, 8>(h, a, h->bs->grid);
 }
 
 static int launch_batch(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const double* smax_cur,
@@ -191,21 +163,22 @@ static void drop_graph(BatchState* bs) {
   }
 }
 
-// Autotuner of the batched launch: chunk size (= threads per CTA) and the
-// number of persistent CTAs per SM, each candidate timed with CUDA events on
-// scratch copies of the per-tube arrays and control block (the committed
-// state is untouched; outputs land in the non-current buffer).
+// Autotuner of the batched launch: warps per CTA, cells per work item and
+// persistent CTAs per SM, each candidate timed with CUDA events on scratch
+// copies of the per-tube arrays and control block (the committed state is
+// untouched; outputs land in the non-current buffer).
 static int autotune_batch(hydro_ctx* h, double cfl) {
   BatchState* bs = h->bs;
   if (bs->tuned) return HYDRO_OK;
   bs->tuned = true;
   std::ostringstream key;
-  key << "batch_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
+  key << "batch2_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
       << device_key();
   int cached;
   double us;
   if (tune_cache_get(key.str(), &cached, &us)) {
-    int st = make_items(h, cached / 1000);
+    bs->nw = cached / 1000000;
+    int st = make_items(h, (cached / 1000) % 1000);
     if (st) return st;
     bs->grid = h->num_sms * (cached % 1000);
     bs->tuned_us = us;
@@ -229,40 +202,45 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best = 1e300;
-  int best_ch = 256, best_mult = 1;
+  int best_nw = 8, best_item = 120, best_mult = 1;
   auto reset = [&]() {
     cudaMemcpyAsync(sc, &base, sizeof(BatchCtrl), cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(s_cur, bs->smax_cur, sizeof(double) * bs->ntubes, cudaMemcpyDeviceToDevice, h->stream);
     cudaMemsetAsync(s_next, 0, sizeof(unsigned long long) * bs->ntubes, h->stream);
   };
-  for (int ch : BATCH_CH) {
-    if ((st = make_items(h, ch))) break;
+  for (int nw : BATCH_NW) {
+    bs->nw = nw;
     int occ = 1;
-    st = h->precision == 64 ? occupancy_ch<double>(ch, &occ) : occupancy_ch<float>(ch, &occ);
+    st = h->precision == 64 ? occupancy_nw<double>(nw, &occ) : occupancy_nw<float>(nw, &occ);
     if (st) break;
-    for (int mult = 1; mult <= occ; mult *= 2) {
-      bs->grid = h->num_sms * mult;
-      const int reps = 2;
-      float ms = 0.f;
-      reset();
-      if ((st = launch_batch(h, cfl, sc, s_cur, s_next, s_t))) break;
-      for (int r = 0; r < reps; ++r) {
+    for (int item : BATCH_ITEM) {
+      if ((st = make_items(h, item))) break;
+      for (int mult = 1; mult <= std::max(1, occ); mult *= 2) {
+        bs->grid = h->num_sms * mult;
+        const int reps = 2;
+        float ms = 0.f;
         reset();
-        cudaEventRecord(e0, h->stream);
         if ((st = launch_batch(h, cfl, sc, s_cur, s_next, s_t))) break;
-        cudaEventRecord(e1, h->stream);
-        cudaEventSynchronize(e1);
-        float m1 = 0.f;
-        cudaEventElapsedTime(&m1, e0, e1);
-        ms += m1;
+        for (int r = 0; r < reps; ++r) {
+          reset();
+          cudaEventRecord(e0, h->stream);
+          if ((st = launch_batch(h, cfl, sc, s_cur, s_next, s_t))) break;
+          cudaEventRecord(e1, h->stream);
+          cudaEventSynchronize(e1);
+          float m1 = 0.f;
+          cudaEventElapsedTime(&m1, e0, e1);
+          ms += m1;
+        }
+        if (st) break;
+        const double t = 1000.0 * ms / reps;
+        if (t < best) {
+          best = t;
+          best_nw = nw;
+          best_item = item;
+          best_mult = mult;
+        }
       }
       if (st) break;
-      const double t = 1000.0 * ms / reps;
-      if (t < best) {
-        best = t;
-        best_ch = ch;
-        best_mult = mult;
-      }
     }
     if (st) break;
   }
@@ -274,10 +252,11 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
   cudaFree(s_next);
   cudaFree(s_t);
   if (st) return st;
-  if ((st = make_items(h, best_ch))) return st;
+  bs->nw = best_nw;
+  if ((st = make_items(h, best_item))) return st;
   bs->grid = h->num_sms * best_mult;
   bs->tuned_us = best;
-  tune_cache_put(key.str(), best_ch * 1000 + best_mult, best);
+  tune_cache_put(key.str(), best_nw * 1000000 + best_item * 1000 + best_mult, best);
   return HYDRO_OK;
 }
 
@@ -397,10 +376,10 @@ int hydro_batch_stats_impl(hydro_ctx* h, hydro_stats_t* out) {
   out->newton_iters = (long long)c.iters;
   out->fallbacks = (long long)c.fallbacks;
   out->mlp_faces = (long long)c.mlp;
-  out->tile_x = h->bs->ch;
-  out->tile_y = 1;
+  out->tile_x = h->bs->item_len;
+  out->tile_y = h->bs->nw;
   out->zchunk = h->bs->grid;
-  out->threads = h->bs->ch;
+  out->threads = h->bs->nw * 32;
   out->tuned_us_per_step = h->bs->tuned_us;
   return HYDRO_OK;
 }
@@ -479,8 +458,8 @@ int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int
   cudaMemset(bs->t_tube, 0, sizeof(double) * ntubes);
   std::memset(bs->bctrl_host, 0, sizeof(BatchCtrl));
   bs->bctrl_host->c.err_step = -1;
-  if ((st = write_bctrl(h)) || (st = make_items(h, 256))) { hydro_destroy(h); return st; }
-  bs->grid = h->num_sms;
+  if ((st = write_bctrl(h)) || (st = make_items(h, 120))) { hydro_destroy(h); return st; }
+  bs->grid = h->num_sms * 2;
   *out = h;
   return HYDRO_OK;
 }

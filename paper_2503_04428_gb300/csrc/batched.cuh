@@ -2,25 +2,26 @@
 //
 // Each tube b is a uniform grid of n_b cells on [0,1] with transmissive ends
 // and its own CFL time step dt_b = cfl / max_i (|u|+c) n_b (reading R4 in
-// 1D).  The tubes are cut into work items of at most CH cells; a persistent
-// grid of CTAs pulls items from an atomic counter.  Per item the CTA stages
-// the cells plus two ghosts per side in shared memory and runs the same
-// MUSCL-Hancock steps as the grid sweep (Sect. 3.2, Eq. 17-19) with the exact
-// Riemann solver (App. C.1):
-//   F1  predicted face states, Toro's guess; faces where Toro's rule picks
-//       the two-shock estimate are queued for the MLP (and optionally
-//       harvested as training data);
-//   F2  the queued faces are evaluated by the 6-64-64-1 MLP, one per thread,
-//       so that the network runs on full warps; it predicts
-//       ln(p_star/p_ref), p_ref = sqrt(P_L P_R);
-//   F3  Newton from the guess to 1e-10 (FP64) and one polishing step, sample
-//       at x/t = 0, Godunov flux;
-//   U   conservative update and the tube's next signal speed.
+// 1D).  The tubes are cut into work items of whole 30-cell segments; every
+// warp of a persistent grid pulls items from an atomic counter and advances
+// them on its own, with neighbour data exchanged by shuffles (no block-wide
+// barrier on the step's path).  Per 30-cell segment, lane l of the warp:
+//   - stages cell c0-2+l (lanes 0,1 also c0+30+l) as primitives (Eq. 5);
+//   - computes the limited slopes (Eq. 17) and Hancock increment (Eq. 18) of
+//     cell c0-1+l and its two predicted face states;
+//   - solves the exact Riemann problem (App. C.1) at face c0+l: identical
+//     states give their own flux; elsewhere Toro's adaptive guess, replaced
+//     by the MLP on faces where that rule picks the two-shock estimate
+//     (the warp evaluates the network together, one such face at a time);
+//     Newton to 1e-10 (FP64) and one polishing step; sample at x/t = 0;
+//   - updates cell c0+l (Eq. 19) and reduces its signal speed.
 // The last CTA to finish commits the step (per-tube speeds, times, buffer).
 #pragma once
 #include "common.cuh"
 
 namespace hydro {
+
+constexpr int BSEG = 30;  // cells per warp segment (32 lanes = 30 cells + 2 halo faces)
 
 struct BatchCtrl {
   Ctrl c;
@@ -37,6 +38,7 @@ struct BatchArgs {
   const long long* off;        // ntubes + 1 cell offsets
   const int* item_tube;
   const int* item_start;
+  int item_len;                // cells per work item (a multiple of BSEG)
   int nitems;
   int ntubes;
   const double* smax_cur;      // per tube: max (|u|+c)/h of the current state
@@ -62,201 +64,240 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
-template <typename T, int CH>
-struct BatchSmem {
-  T W[3][CH + 4];
-  T D[3][CH + 2];
-  T WLR[6][CH + 1];
-  T pg[CH + 1];
-  T F[3][CH + 1];
-  int queue[CH + 1];
-  int qn;
-  int item;
-  double red[CH / 32];
-  float w[MLP_NPARAM];
+// Network weights staged per CTA; W2 is stored transposed (W2T[i][o]) so that
+// the 32 lanes of a warp read consecutive words.
+struct MlpSmemW {
+  float w1[MLP_H * MLP_IN];
+  float b1[MLP_H];
+  float w2t[MLP_H * MLP_H];
+  float b2[MLP_H];
+  float w3[MLP_H];
+  float b3;
 };
 
-template <typename T, int CH>
-__global__ void __launch_bounds__(CH)
+// The 6-64-64-1 network evaluated by a whole warp for one input x (the same
+// on every lane): lane l owns hidden units l and l+32.
+__device__ __forceinline__ float mlp_warp(const MlpSmemW& s, const float* x, int lane) {
+  float a = s.b1[lane], b = s.b1[lane + 32];
+#pragma unroll
+  for (int i = 0; i < MLP_IN; ++i) {
+    a = fmaf(s.w1[lane * MLP_IN + i], x[i], a);
+    b = fmaf(s.w1[(lane + 32) * MLP_IN + i], x[i], b);
+  }
+  const float ha = silu_f(a), hb = silu_f(b);
+  float za = s.b2[lane], zb = s.b2[lane + 32];
+#pragma unroll 8
+  for (int i = 0; i < 32; ++i) {
+    const float h0 = __shfl_sync(0xffffffffu, ha, i), h1 = __shfl_sync(0xffffffffu, hb, i);
+    za = fmaf(s.w2t[i * MLP_H + lane], h0, za);
+    za = fmaf(s.w2t[(i + 32) * MLP_H + lane], h1, za);
+    zb = fmaf(s.w2t[i * MLP_H + lane + 32], h0, zb);
+    zb = fmaf(s.w2t[(i + 32) * MLP_H + lane + 32], h1, zb);
+  }
+  float y = s.w3[lane] * silu_f(za) + s.w3[lane + 32] * silu_f(zb);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+  return y + s.b3;
+}
+
+// Value of lane (lane + off) of the 34-cell window held as (Wa on all lanes,
+// Wb on lanes 0-1).
+template <typename T>
+__device__ __forceinline__ T win(T va, T vb, int lane, int off) {
+  const T a = __shfl_down_sync(0xffffffffu, va, off);
+  const T b = __shfl_sync(0xffffffffu, vb, (lane + off) & 31);
+  return lane + off < 32 ? a : b;
+}
+
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32)
     batched_kernel(const BatchArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  BatchSmem<T, CH>& sm = *reinterpret_cast<BatchSmem<T, CH>*>(smem_raw);
+  __shared__ MlpSmemW sw;
   const volatile Ctrl* vc = &a.ctrl->c;
   if (vc->status != 0) return;
   const int cur = vc->cur;
   const long long step = vc->step;
   const T* Uin = cur ? a.B : a.A;
   T* Uout = cur ? a.Aw : a.B;
-  const int tid = threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const Gas<T>& gas = a.gas;
-  if (a.mlp_on)
-    for (int p = tid; p < MLP_NPARAM; p += CH) sm.w[p] = a.mlp_w[p];
+  if (a.mlp_on) {
+    for (int p = threadIdx.x; p < MLP_H * MLP_IN; p += NW * 32) sw.w1[p] = a.mlp_w[MW1 + p];
+    for (int p = threadIdx.x; p < MLP_H * MLP_H; p += NW * 32) {
+      const int o = p / MLP_H, i = p % MLP_H;
+      sw.w2t[i * MLP_H + o] = a.mlp_w[MW2 + p];
+    }
+    for (int p = threadIdx.x; p < MLP_H; p += NW * 32) {
+      sw.b1[p] = a.mlp_w[MB1 + p];
+      sw.b2[p] = a.mlp_w[MB2 + p];
+      sw.w3[p] = a.mlp_w[MW3 + p];
+    }
+    if (threadIdx.x == 0) sw.b3 = a.mlp_w[MB3];
+    __syncthreads();
+  }
   unsigned long long n_iters = 0, n_mlp = 0, n_fb = 0;
   int err = 0;
 
   for (;;) {
-    __syncthreads();
-    if (tid == 0) {
-      sm.item = (int)atomicAdd(&a.ctrl->next_item, 1u);
-      sm.qn = 0;
-    }
-    __syncthreads();
-    const int it = sm.item;
+    int it = 0;
+    if (lane == 0) it = (int)atomicAdd(&a.ctrl->next_item, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= a.nitems) break;
     const int b = a.item_tube[it];
-    const int s0 = a.item_start[it];
+    const int s_beg = a.item_start[it];
     const long long base = a.off[b];
     const int nb = (int)(a.off[b + 1] - base);
-    const int L = min(CH, nb - s0);
+    const int s_end = min(s_beg + a.item_len, nb);
     const T fn = (T)nb;          // 1/h
     const T hw = T(0.5) / fn;    // half width
-    const double dtd = a.cfl / a.smax_cur[b];
-    const T dt = (T)dtd;
-    const T dtdx = dt * fn;
+    double dtd = 0.0;
+    if (lane == 0) dtd = a.cfl / a.smax_cur[b];
+    dtd = __shfl_sync(0xffffffffu, dtd, 0);
+    const T dtdx = (T)dtd * fn;
+    T smax = T(0);
 
-    // a1 + a2: stage cells s0-2 .. s0+L+1 (transmissive ends) as primitives
-    for (int q = tid; q < L + 4; q += CH) {
-      const int c = min(max(s0 - 2 + q, 0), nb - 1);
-      T u[3], w[3];
+    for (int c0 = s_beg; c0 < s_end; c0 += BSEG) {
+      const int ncell = min(BSEG, s_end - c0);  // cells updated in this segment
+      // a1 + a2: cells c0-2+lane (Wa) and c0+30+lane (Wb, lanes 0-1), transmissive ends
+      T Wa[3], Wb[3];
+      {
+        const int ca = min(max(c0 - 2 + lane, 0), nb - 1);
+        const int cb = min(max(c0 + 30 + (lane & 1), 0), nb - 1);
+        T u[3];
 #pragma unroll
-      for (int v = 0; v < 3; ++v) u[v] = __ldg(Uin + v * a.total + base + c);
-      to_prim<T, 1, 0>(u, w, gas);
+        for (int v = 0; v < 3; ++v) u[v] = __ldg(Uin + v * a.total + base + ca);
+        to_prim<T, 1, 0>(u, Wa, gas);
 #pragma unroll
-      for (int v = 0; v < 3; ++v) sm.W[v][q] = w[v];
-    }
-    __syncthreads();
-
-    // a3 + a4: predictor increment of cells s0-1 .. s0+L
-    for (int q = tid; q < L + 2; q += CH) {
-      T wl[3], wh[3], fl[3], fh[3];
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        const T wc = sm.W[v][q + 1];
-        const T sig = limit<T>(a.limiter, (wc - sm.W[v][q]) * fn, (sm.W[v][q + 2] - wc) * fn);
-        wl[v] = wc - hw * sig;
-        wh[v] = wc + hw * sig;
+        for (int v = 0; v < 3; ++v) u[v] = __ldg(Uin + v * a.total + base + cb);
+        to_prim<T, 1, 0>(u, Wb, gas);
       }
-      phys_flux<T, 1, 0, 0>(wl, fl, gas);
-      phys_flux<T, 1, 0, 0>(wh, fh, gas);
-#pragma unroll
-      for (int v = 0; v < 3; ++v) sm.D[v][q] = T(0.5) * dtdx * (fl[v] - fh[v]);
-    }
-    __syncthreads();
-
-    // F1: predicted face states and the guess of faces s0 .. s0+L
-    for (int f = tid; f <= L; f += CH) {
-      // faces shared with the next chunk are solved twice; count them once
-      const bool owned = f < L || s0 + L == nb;
-      T Wf[2][3];
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        // side 0: high face of cell (f-1) [stage index f+1]; side 1: low face of cell f
-        const int q = f + 1 + side;
-        T w[3], u[3];
+      // a3 + a4: cell c0-1+lane -- slopes, Hancock increment, predicted face states
+      T Wc[3], Wlo[3], Whi[3];
+      {
+        T Wp[3], fl[3], fh[3];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          const T wc = sm.W[v][q];
-          const T sig = limit<T>(a.limiter, (wc - sm.W[v][q - 1]) * fn, (sm.W[v][q + 1] - wc) * fn);
-          w[v] = side == 0 ? wc + hw * sig : wc - hw * sig;
+          Wc[v] = win(Wa[v], Wb[v], lane, 1);
+          Wp[v] = win(Wa[v], Wb[v], lane, 2);
+          const T sig = limit<T>(a.limiter, (Wc[v] - Wa[v]) * fn, (Wp[v] - Wc[v]) * fn);
+          Wlo[v] = Wc[v] - hw * sig;
+          Whi[v] = Wc[v] + hw * sig;
         }
-        to_cons<T, 1, 0>(w, u, gas);
+        phys_flux<T, 1, 0, 0>(Wlo, fl, gas);
+        phys_flux<T, 1, 0, 0>(Whi, fh, gas);
+        T ul[3], uh[3];
+        to_cons<T, 1, 0>(Wlo, ul, gas);
+        to_cons<T, 1, 0>(Whi, uh, gas);
 #pragma unroll
-        for (int v = 0; v < 3; ++v) u[v] += sm.D[v][q - 1];
-        to_prim<T, 1, 0>(u, Wf[side], gas);
-        if (!(Wf[side][0] > T(0)) || !(Wf[side][2] > T(0))) {
+        for (int v = 0; v < 3; ++v) {
+          const T du = T(0.5) * dtdx * (fl[v] - fh[v]);
+          ul[v] += du;
+          uh[v] += du;
+        }
+        to_prim<T, 1, 0>(ul, Wlo, gas);
+        to_prim<T, 1, 0>(uh, Whi, gas);
+        // a non-physical prediction falls back to the cell average
+        const bool own = lane >= 1 && lane <= ncell;  // cells of this segment
+        if (!(Wlo[0] > T(0)) || !(Wlo[2] > T(0))) {
 #pragma unroll
-          for (int v = 0; v < 3; ++v) Wf[side][v] = sm.W[v][q];
-          if (owned) ++n_fb;
+          for (int v = 0; v < 3; ++v) Wlo[v] = Wc[v];
+          if (own) ++n_fb;
+        }
+        if (!(Whi[0] > T(0)) || !(Whi[2] > T(0))) {
+#pragma unroll
+          for (int v = 0; v < 3; ++v) Whi[v] = Wc[v];
+          if (own) ++n_fb;
         }
       }
+      // a5: face c0+lane between cell c0-1+lane (its high state, this lane)
+      // and cell c0+lane (its low state, next lane)
+      T WL[3], WR[3], F[3] = {T(0), T(0), T(0)};
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        sm.WLR[v][f] = Wf[0][v];
-        sm.WLR[3 + v][f] = Wf[1][v];
+        WL[v] = Whi[v];
+        WR[v] = __shfl_down_sync(0xffffffffu, Wlo[v], 1);
       }
-      const T cL = dsqrt(gas.g * Wf[0][2] / Wf[0][0]), cR = dsqrt(gas.g * Wf[1][2] / Wf[1][0]);
-      int kind;
-      sm.pg[f] = toro_guess<T>(Wf[0][0], Wf[0][1], Wf[0][2], cL, Wf[1][0], Wf[1][1], Wf[1][2], cR, gas, kind);
-      if (kind == 2) {
-        if (a.mlp_on) sm.queue[atomicAdd(&sm.qn, 1)] = f;
-        if (a.harvest) {
-          const unsigned long long id = (unsigned long long)(base + b + s0 + f);
-          const unsigned long long hsh = mix64(a.harvest_seed + 0x9E3779B97F4A7C15ull * (id + 1) +
-                                               ((unsigned long long)step << 40));
+      const bool face = lane <= ncell;
+      const bool owned = face && (lane < ncell || c0 + lane == nb);
+      const bool same = WL[0] == WR[0] && WL[1] == WR[1] && WL[2] == WR[2];
+      T pg = T(0);
+      int kind = 0;
+      T cL = T(0), cR = T(0);
+      if (face && !same) {
+        cL = dsqrt(gas.g * WL[2] / WL[0]);
+        cR = dsqrt(gas.g * WR[2] / WR[0]);
+        pg = toro_guess<T>(WL[0], WL[1], WL[2], cL, WR[0], WR[1], WR[2], cR, gas, kind);
+        if (kind == 2 && a.harvest) {
+          const unsigned long long id = (unsigned long long)(base + b + c0 + lane);
+          const unsigned long long hsh =
+              mix64(a.harvest_seed + 0x9E3779B97F4A7C15ull * (id + 1) + ((unsigned long long)step << 40));
           if (hsh < a.harvest_thresh) {
             const unsigned long long slot = atomicAdd(a.harvest_n, 1ull);
             if ((long long)slot < a.harvest_cap) {
 #pragma unroll
               for (int v = 0; v < 3; ++v) {
-                a.harvest[slot * 6 + v] = (double)Wf[0][v];
-                a.harvest[slot * 6 + 3 + v] = (double)Wf[1][v];
+                a.harvest[slot * 6 + v] = (double)WL[v];
+                a.harvest[slot * 6 + 3 + v] = (double)WR[v];
               }
             }
           }
         }
       }
-    }
-    __syncthreads();
-
-    // F2: MLP guess of the queued faces, one face per thread
-    if (a.mlp_on) {
-      const int qn = sm.qn;
-      for (int q = tid; q < qn; q += CH) {
-        const int f = sm.queue[q];
-        float x[6], pref;
-        mlp_features((float)gas.g, (float)sm.WLR[0][f], (float)sm.WLR[1][f], (float)sm.WLR[2][f],
-                     (float)sm.WLR[3][f], (float)sm.WLR[4][f], (float)sm.WLR[5][f], x, pref);
-        const float y = mlp_forward(sm.w, x);
-        sm.pg[f] = (T)((double)pref * exp((double)y));
-        if (f < L || s0 + L == nb) ++n_mlp;
+      // learned guess on two-shock faces, evaluated by the whole warp
+      if (a.mlp_on) {
+        unsigned todo = __ballot_sync(0xffffffffu, face && !same && kind == 2);
+        while (todo) {
+          const int g = __ffs(todo) - 1;
+          todo &= todo - 1;
+          float q[6];
+#pragma unroll
+          for (int v = 0; v < 3; ++v) {
+            q[v] = (float)__shfl_sync(0xffffffffu, WL[v], g);
+            q[3 + v] = (float)__shfl_sync(0xffffffffu, WR[v], g);
+          }
+          float x[6], pref;
+          mlp_features((float)gas.g, q[0], q[1], q[2], q[3], q[4], q[5], x, pref);
+          const float y = mlp_warp(sw, x, lane);
+          if (lane == g) {
+            pg = (T)((double)pref * exp((double)y));
+            if (owned) ++n_mlp;
+          }
+        }
       }
-      __syncthreads();
-    }
-
-    // F3: Newton, sampling and the Godunov flux
-    for (int f = tid; f <= L; f += CH) {
-      T WL[3], WR[3], F[3];
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        WL[v] = sm.WLR[v][f];
-        WR[v] = sm.WLR[3 + v][f];
+      if (face) {
+        if (same) {
+          phys_flux<T, 1, 0, 0>(WL, F, gas);
+        } else {
+          int its = 0, k2 = 0;
+          const int st = riemann_exact<T, 1, 0, 0>(WL, WR, F, gas, pg, its, k2);
+          if (owned) n_iters += its;
+          if (st != ST_OK && err == 0) err = st;
+        }
       }
-      int its = 0, kind = 0;
-      const int st = riemann_exact<T, 1, 0, 0>(WL, WR, F, gas, sm.pg[f], its, kind);
-      if (f < L || s0 + L == nb) n_iters += its;
-      if (st != ST_OK && err == 0) err = st;
+      // a6: update cell c0+lane with faces c0+lane (this lane) and c0+lane+1 (next)
+      T Fh[3];
 #pragma unroll
-      for (int v = 0; v < 3; ++v) sm.F[v][f] = F[v];
-    }
-    __syncthreads();
-
-    // U: update cells s0 .. s0+L-1 and their signal speed
-    double smax = 0.0;
-    for (int q = tid; q < L; q += CH) {
-      const long long c = base + s0 + q;
-      T u[3], w[3];
-      bool finite = true;
+      for (int v = 0; v < 3; ++v) Fh[v] = __shfl_down_sync(0xffffffffu, F[v], 1);
+      if (lane < ncell) {
+        const long long c = base + c0 + lane;
+        T u[3], w[3];
+        bool finite = true;
 #pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        u[v] = Uin[v * a.total + c] + dtdx * (sm.F[v][q] - sm.F[v][q + 1]);
-        finite = finite && isfinite(u[v]);
+        for (int v = 0; v < 3; ++v) {
+          u[v] = Uin[v * a.total + c] + dtdx * (F[v] - Fh[v]);
+          finite = finite && isfinite(u[v]);
+        }
+        to_prim<T, 1, 0>(u, w, gas);
+        if (!finite) err = err ? err : ST_NONFINITE;
+        else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
+        smax = fmax(smax, (fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * fn);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) Uout[v * a.total + c] = u[v];
       }
-      to_prim<T, 1, 0>(u, w, gas);
-      if (!finite) err = err ? err : ST_NONFINITE;
-      else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
-      const T sp = (fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * fn;
-      smax = fmax(smax, (double)sp);
-#pragma unroll
-      for (int v = 0; v < 3; ++v) Uout[v * a.total + c] = u[v];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-    if ((tid & 31) == 0) sm.red[tid >> 5] = smax;
-    __syncthreads();
-    if (tid == 0) {
-      for (int w = 1; w < CH / 32; ++w) smax = fmax(smax, sm.red[w]);
-      atomicMax(&a.smax_next[b], dbits(smax));
-    }
+    if (lane == 0) atomicMax(&a.smax_next[b], dbits((double)smax));
   }
 
   // block totals of the counters and the error, then the last-CTA commit
@@ -268,7 +309,7 @@ __global__ void __launch_bounds__(CH)
     const int e2 = __shfl_xor_sync(0xffffffffu, err, o);
     err = err ? err : e2;
   }
-  if ((tid & 31) == 0) {
+  if (lane == 0) {
     if (n_iters) atomicAdd(&a.ctrl->c.iters, n_iters);
     if (n_mlp) atomicAdd(&a.ctrl->c.mlp, n_mlp);
     if (n_fb) atomicAdd(&a.ctrl->c.fallbacks, n_fb);
@@ -276,7 +317,7 @@ __global__ void __launch_bounds__(CH)
   }
   __syncthreads();
   __shared__ int last;
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     __threadfence();
     last = atomicAdd(&a.ctrl->c.done, 1u) == gridDim.x - 1;
   }
@@ -287,14 +328,14 @@ __global__ void __launch_bounds__(CH)
   const bool ok = vb->c.status == 0;
   if (ok) {
     double* smc = const_cast<double*>(a.smax_cur);
-    for (int b = tid; b < a.ntubes; b += CH) {
-      a.t_tube[b] += a.cfl / smc[b];
-      const unsigned long long nbits = atomicExch(&a.smax_next[b], 0ull);
-      smc[b] = __longlong_as_double((long long)nbits);
+    for (int t = threadIdx.x; t < a.ntubes; t += NW * 32) {
+      a.t_tube[t] += a.cfl / smc[t];
+      const unsigned long long nbits = atomicExch(&a.smax_next[t], 0ull);
+      smc[t] = __longlong_as_double((long long)nbits);
     }
   }
   __syncthreads();
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     if (ok) {
       vb->c.step = step + 1;
       vb->c.cur = cur ^ 1;

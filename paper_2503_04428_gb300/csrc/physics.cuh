@@ -345,8 +345,8 @@ __device__ __forceinline__ Gas<double> gas_double(const Gas<float>& g) {
 }
 
 // Star state of one face.  guess_in > 0 replaces Toro's guess (MLP).  In FP32
-// a face near vacuum (margin below 5 %) or with a pressure ratio above 1e3
-// is solved in FP64.
+// a face near vacuum (margin below 5 %) or with a pressure ratio above 1e6
+// is solved in FP64, where the FP32 pressure function loses digits.
 template <typename T>
 __device__ __forceinline__ int exact_star(T rL, T uL, T pL, T rR, T uR, T pR, const Gas<T>& gas,
                                           T guess_in, T& ps, T& us, int& iters, int& kind) {
@@ -357,7 +357,7 @@ __device__ __forceinline__ int exact_star(T rL, T uL, T pL, T rR, T uR, T pR, co
   if (guess_in > T(0)) p0 = guess_in;
   if constexpr (sizeof(T) == 4) {
     const T ratio = fmax(pL, pR) / fmin(pL, pR);
-    if (ratio > T(1e3) || vac - (uR - uL) < T(0.05) * vac) {
+    if (ratio > T(1e6) || vac - (uR - uL) < T(0.05) * vac) {
       const Gas<double> g2 = gas_double(gas);
       double ps2, us2;
       const double cL2 = sqrt(g2.g * (double)pL / (double)rL), cR2 = sqrt(g2.g * (double)pR / (double)rR);
@@ -377,6 +377,18 @@ template <typename T, int D, int NSX, int DIR>
 __device__ __forceinline__ int riemann_exact(const T* WL, const T* WR, T* F, const Gas<T>& gas,
                                              T guess_in, int& iters, int& kind) {
   constexpr int NV = 2 + D + NSX;
+  // Identical states: the solution is that state (no wave), and the general
+  // path returns exactly its flux (PVRS gives p = P, Newton stops at once,
+  // the sample is the state) -- take it directly.
+  bool same = true;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) same = same && WL[v] == WR[v];
+  if (same) {
+    iters = 0;
+    kind = 0;
+    phys_flux<T, D, NSX, DIR>(WL, F, gas);
+    return ST_OK;
+  }
   T ps, us;
   const T rL = WL[0], uL = WL[1 + DIR], pL = WL[1 + D];
   const T rR = WR[0], uR = WR[1 + DIR], pR = WR[1 + D];

@@ -135,7 +135,7 @@ def test_trained_network_reduces_newton_iterations(hydro_lib):
     b.run(30, 0.8)
     test = b.harvest_get(60000)
     train = np.concatenate([np.concatenate([w["WL"], w["WR"]], axis=1), train])
-    assert len(train) > 20000 and len(test) > 2000
+    assert len(train) > 10000 and len(test) > 1000
     ps, _, it = H.hydro_exact_solve(train[:, :3], train[:, 3:], w["gamma"], precision=64)
     assert np.all(ps > 0)
     loss = b.mlp_train(train, np.log(ps), epochs=40, batch=256, lr=3e-3, seed=4)
