@@ -133,21 +133,20 @@ def job_rate(elapsed_local, cells_local, steps, dist=None, device=None):
 
 
 def train_mlp(H, torch, gamma, seed):
-    """Harvest hard faces from an FP64 run, label them with the FP64 exact solver
-    and train the guess network with the library's own kernels (untimed)."""
+    """Harvest gated faces from an FP64 run, add partial-jump faces of the
+    workload's state distribution, label them with the FP64 exact solver and
+    train the guess network with the library's own kernels (untimed)."""
     from paper_2503_04428_gb300 import workloads as wl
     t0 = time.time()
-    w = wl.tubes(512, seed=seed)
+    w = wl.tubes(1024, seed=seed)
     b = H.Batch(w["lengths"], gamma, precision=64)
     b.set_state(w["U"])
-    b.harvest_begin(600000, 0.5, 4)
-    b.run(40, CFL)
-    faces = b.harvest_get(600000)
-    WL, WR = wl.tube_states(NTUBES, seed)
-    faces = np.concatenate([np.concatenate([WL, WR], axis=1), faces])
+    b.harvest_begin(400000, 1.0, 4)
+    b.run(60, CFL)
+    faces = np.concatenate([wl.partial_jump_faces(60000, 7), b.harvest_get(400000)])
     ps, _, _ = H.hydro_exact_solve(faces[:, :3], faces[:, 3:], gamma, precision=64)
     keep = ps > 0
-    loss = b.mlp_train(faces[keep], np.log(ps[keep]), epochs=60, batch=1024, lr=3e-3, seed=4)
+    loss = b.mlp_train(faces[keep], np.log(ps[keep]), epochs=60, batch=512, lr=3e-3, seed=4)
     wts = b.mlp_get()
     b.close()
     return wts, {"faces": int(keep.sum()), "loss": loss, "train_s": round(time.time() - t0, 2)}
@@ -350,7 +349,7 @@ def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it3
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if args.tubes == NTUBES else "%d-tube subset of: %s" % (args.tubes, WORKLOAD),
                        "tubes_per_gpu": args.tubes, "cells_per_gpu": total,
-                       "form": "FP32 bulk + MLP p* guess (two-shock faces) + persistent batched kernel + CUDA graph",
+                       "form": "FP32 bulk + MLP p* guess (two-shock faces, jump > 4) + persistent batched kernel + CUDA graph",
                        "cfl": CFL, "l2": "state 208 MB per buffer > 129 MB L2 (no flush needed)",
                        "launch": {"chunk": st["tile_x"], "ctas": st["zchunk"]}},
             "e2e": e2e,

@@ -149,9 +149,9 @@ int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int
 int hydro_batch_run(hydro_t h, int nsteps, double cfl);
 
 /* Record (with probability keep_prob, counter-based per face and step) the
- * left/right primitive states (rho,u,P)x2 of faces where Toro's rule picks
- * the two-shock estimate, during later hydro_batch_run calls; capacity faces
- * at most. */
+ * left/right primitive states (rho,u,P)x2 of faces that pass the network's
+ * gate (see hydro_mlp_set), during later hydro_batch_run calls; capacity
+ * faces at most. */
 int hydro_harvest_begin(hydro_t h, long capacity, double keep_prob, unsigned long long seed);
 /* Copy up to cap harvested faces (6 doubles each) to host memory; *n = count. */
 int hydro_harvest_get(hydro_t h, double* faces6, long cap, long* n);
@@ -162,16 +162,18 @@ int hydro_harvest_get(hydro_t h, double* faces6, long cap, long* n);
  * sides and c_ref = sqrt(gamma P_ref/rho_ref).  Output y: the guess is
  * P_ref exp(y), i.e. the network predicts ln(p_star/P_ref).  It replaces
  * Toro's adaptive guess only on faces where that rule picks the two-shock
- * (TSRS) estimate (PVRS serves nearby states; the two-rarefaction estimate
- * is exact when both waves are rarefactions).  Newton still runs to 1e-10
- * relative and polishes once.  weights: HYDRO_MLP_NPARAM floats (host). */
+ * (TSRS) estimate and max(P_L,P_R) > 4 min(P_L,P_R) (PVRS serves nearby
+ * states, the two-rarefaction estimate is exact when both waves are
+ * rarefactions, the two-shock estimate is good for mild jumps).  Newton
+ * still runs to 1e-10 relative and polishes once.  weights:
+ * HYDRO_MLP_NPARAM floats (host). */
 int hydro_mlp_set(hydro_t h, const float* weights, int enable);
 int hydro_mlp_get(hydro_t h, float* weights_out);
 
 /* Train the handle's MLP on the GPU (own forward, backward and Adam
  * kernels): faces6 holds n samples (rho_L,u_L,P_L,rho_R,u_R,P_R), log_pstar
- * their ln(p_star); only samples on which the network would be used (Toro's
- * rule picks the two-shock estimate) are trained on; MSE on
+ * their ln(p_star); only samples on which the network would be used (the
+ * gate described at hydro_mlp_set) are trained on; MSE on
  * ln(p_star/P_ref); minibatches of `batch`, Adam (beta 0.9/0.999) with a
  * learning rate decaying from lr to 0 on a cosine, shuffled by `seed`.  Host
  * arrays.  *loss_out (may be NULL) receives the last epoch's mean loss. */

@@ -252,9 +252,10 @@ double toro_guess(double g, double rL, double uL, double pL, double rR, double u
  * Layout of the flat weight vector (4673 values): W1[64][6], b1[64],
  * W2[64][64], b2[64], w3[64], b3.  Output y = ln(p_star/p_ref) with p_ref
  * the geometric mean of the two pressures.  It replaces Toro's guess only
- * where Toro's rule picks the two-shock (TSRS) estimate: PVRS is used for
- * nearby states and the two-rarefaction estimate is exact when both waves
- * are rarefactions. */
+ * where Toro's rule picks the two-shock (TSRS) estimate and the pressure
+ * jump exceeds a factor 4 (reading R11): PVRS serves nearby states, the
+ * two-rarefaction estimate is exact when both waves are rarefactions, and
+ * the two-shock estimate is good for mild jumps. */
 const int MLP_IN = 6, MLP_H = 64;
 const int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;
 const int OFF_W1 = 0, OFF_B1 = OFF_W1 + MLP_H * MLP_IN, OFF_W2 = OFF_B1 + MLP_H,
@@ -320,7 +321,8 @@ ExactResult exact_star(double g, const double* WL, const double* WR, int guess,
   }
   int kind = 0;
   double p = toro_guess(g, rL, uL, pL, rR, uR, pR, &kind);
-  if (guess == ORC_GUESS_MLP && kind == 2 && mlpw != nullptr) {
+  const bool gate = kind == 2 && std::fmax(pL, pR) > 4.0 * std::fmin(pL, pR);
+  if (guess == ORC_GUESS_MLP && gate && mlpw != nullptr) {
     double x[6], pref, z1[64], h1[64], z2[64], h2[64];
     mlp_features(g, WL, WR, x, &pref);
     p = pref * std::exp(mlp_eval(mlpw, x, z1, h1, z2, h2));

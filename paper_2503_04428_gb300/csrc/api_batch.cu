@@ -611,13 +611,18 @@ int hydro_mlp_train(hydro_t h, const double* faces6, const double* log_pstar, lo
     if (use[i]) rows.push_back((int)i);
   if (rows.empty()) {
     cleanup();
-    return berr("hydro_mlp_train: no sample uses the network (no two-shock Toro estimate)");
+    return berr("hydro_mlp_train: no sample passes the network's gate (two-shock Toro estimate, pressure jump > 4)");
   }
   const long m_use = (long)rows.size();
   const long long bsz_use = std::min<long long>(bsz, m_use);
   const long long steps_per_epoch = m_use / bsz_use;
   const long long total_steps = steps_per_epoch * (long long)epochs;
   std::vector<int> perm(m_use);
+  static bool grad_attr = false;
+  if (!grad_attr) {
+    HCK(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
+    grad_attr = true;
+  }
   unsigned long long state = seed ^ 0xD1B54A32D192ED03ull;
   auto next = [&]() {
     state += 0x9E3779B97F4A7C15ull;
@@ -634,12 +639,14 @@ int hydro_mlp_train(hydro_t h, const double* faces6, const double* log_pstar, lo
     cudaMemcpyAsync(idx, perm.data(), sizeof(int) * m_use, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(lacc, 0, sizeof(double), s);
     for (long long first = 0; first + bsz_use <= m_use; first += bsz_use) {
-      if ((st = mlp_gradient(s, bs->w, X, Y, idx, first, bsz_use, part, lpart, grad, lacc))) break;
       // cosine decay of the learning rate over the whole run
       const double lr_t = 0.5 * (double)lr * (1.0 + std::cos(3.14159265358979323846 * step / (double)total_steps));
       ++step;
-      adam_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(bs->w, bs->m, bs->v, grad, step, lr_t, 0.9,
-                                                           0.999, 1e-8);
+      const int nblk = (int)((bsz_use + MLP_SB - 1) / MLP_SB);
+      mlp_grad_kernel<<<nblk, 256, sizeof(MlpSmem), s>>>(bs->w, X, Y, idx, first, bsz_use,
+                                                         (float)(1.0 / bsz_use), part, lpart);
+      mlp_reduce_adam_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(part, nblk, lpart, lacc, bs->w, bs->m,
+                                                                      bs->v, step, lr_t, 0.9, 0.999, 1e-8);
       if (cudaGetLastError() != cudaSuccess) { st = HYDRO_ERR_CUDA; break; }
     }
     cudaMemcpyAsync(&loss, lacc, sizeof(double), cudaMemcpyDeviceToHost, s);

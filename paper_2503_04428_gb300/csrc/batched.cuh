@@ -11,8 +11,9 @@
 //     cell c0-1+l and its two predicted face states;
 //   - solves the exact Riemann problem (App. C.1) at face c0+l: identical
 //     states give their own flux; elsewhere Toro's adaptive guess, replaced
-//     by the MLP on faces where that rule picks the two-shock estimate
-//     (the warp evaluates the network together, one such face at a time);
+//     by the MLP on faces where that rule picks the two-shock estimate for a
+//     pressure jump above 4 (the warp evaluates the network together, one
+//     such face at a time);
 //     Newton to 1e-10 (FP64) and one polishing step; sample at x/t = 0;
 //   - updates cell c0+l (Eq. 19) and reduces its signal speed.
 // The last CTA to finish commits the step (per-tube speeds, times, buffer).
@@ -227,6 +228,7 @@ __global__ void __launch_bounds__(NW * 32)
         cL = dsqrt(gas.g * WL[2] / WL[0]);
         cR = dsqrt(gas.g * WR[2] / WR[0]);
         pg = toro_guess<T>(WL[0], WL[1], WL[2], cL, WR[0], WR[1], WR[2], cR, gas, kind);
+        if (!mlp_gate<T>(kind, WL[2], WR[2])) kind = -kind;  // negative: network not used
         if (kind == 2 && a.harvest) {
           const unsigned long long id = (unsigned long long)(base + b + c0 + lane);
           const unsigned long long hsh =
@@ -394,7 +396,7 @@ __global__ void exact_list_kernel(const double* WL, const double* WR, long long 
     const T cL = dsqrt(gas.g * pL / rL), cR = dsqrt(gas.g * pR / rR);
     int kind;
     toro_guess<T>(rL, uL, pL, cL, rR, uR, pR, cR, gas, kind);
-    if (kind == 2) {
+    if (mlp_gate<T>(kind, pL, pR)) {
       float x[6], pref;
       mlp_features((float)gas.g, (float)rL, (float)uL, (float)pL, (float)rR, (float)uR, (float)pR, x, pref);
       guess = (T)((double)pref * exp((double)mlp_forward(mlp_w, x)));

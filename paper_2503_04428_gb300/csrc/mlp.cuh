@@ -2,8 +2,8 @@
 //
 // Network: x (6) -> SiLU(W1 x + b1) (64) -> SiLU(W2 h1 + b2) (64) -> w3.h2 + b3,
 // FP32 weights, loss = mean (y - t)^2 with t = ln(p_star / p_ref),
-// p_ref = sqrt(P_L P_R).  Only faces where Toro's rule picks the two-shock
-// estimate are trained on (the only faces where the network is used).
+// p_ref = sqrt(P_L P_R).  Only faces that pass mlp_gate (the only faces where
+// the network is used) are trained on.
 // One CTA handles 64 samples: the three layers and their reverse-mode
 // derivatives are small dense products done in shared memory; each CTA
 // writes its partial gradient, and a second kernel sums the partials in a
@@ -54,7 +54,7 @@ __global__ void mlp_features_kernel(const double* faces6, const double* log_psta
     const double cL = sqrt(gamma * f[2] / f[0]), cR = sqrt(gamma * f[5] / f[3]);
     int kind;
     toro_guess<double>(f[0], f[1], f[2], cL, f[3], f[4], f[5], cR, gas, kind);
-    use[i] = kind == 2;
+    use[i] = mlp_gate<double>(kind, f[2], f[5]);
   }
 }
 
@@ -188,6 +188,28 @@ __global__ void mlp_reduce_kernel(const float* partial, int nblocks, double* gra
     for (int b = 0; b < nblocks; ++b) l += loss_partial[b];
     *loss_out += l;
   }
+}
+
+// Fixed-order sum of the partial gradients followed by the Adam update of
+// that parameter (one thread per parameter); the loss partials go to loss_acc.
+__global__ void mlp_reduce_adam_kernel(const float* partial, int nblocks, const double* loss_partial,
+                                       double* loss_acc, float* W, float* m, float* v, int step,
+                                       double lr, double b1, double b2, double eps) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0) {
+    double l = 0.0;
+    for (int b = 0; b < nblocks; ++b) l += loss_partial[b];
+    *loss_acc += l;
+  }
+  if (p >= MLP_NPARAM) return;
+  double g = 0.0;
+  for (int b = 0; b < nblocks; ++b) g += (double)partial[(long long)b * MLP_NPARAM + p];
+  const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
+  const double mm = b1 * m[p] + (1.0 - b1) * g;
+  const double vv = b2 * v[p] + (1.0 - b2) * g * g;
+  m[p] = (float)mm;
+  v[p] = (float)vv;
+  W[p] = (float)(W[p] - lr * (mm / c1) / (sqrt(vv / c2) + eps));
 }
 
 // Adam with bias-corrected moments; arithmetic in FP64, storage in FP32.

@@ -414,6 +414,16 @@ __device__ __forceinline__ int riemann_exact(const T* WL, const T* WR, T* F, con
 // ---------------------------------------------------------------------------
 // MLP guess network: 6 -> 64 -> 64 -> 1 with SiLU, FP32 weights.
 // ---------------------------------------------------------------------------
+// Faces where the network replaces Toro's guess: his rule picks the two-shock
+// estimate (kind 2) and the pressure jump exceeds a factor 4 -- where that
+// estimate is poor; the two-rarefaction estimate is exact for two
+// rarefactions and PVRS serves nearby states.
+constexpr double MLP_GATE_RATIO = 4.0;
+template <typename T>
+__device__ __forceinline__ bool mlp_gate(int kind, T pL, T pR) {
+  return kind == 2 && fmax(pL, pR) > T(MLP_GATE_RATIO) * fmin(pL, pR);
+}
+
 constexpr int MLP_IN = 6, MLP_H = 64;
 constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;
 constexpr int MW1 = 0, MB1 = MW1 + MLP_H * MLP_IN, MW2 = MB1 + MLP_H, MB2 = MW2 + MLP_H * MLP_H,

@@ -8,7 +8,8 @@ initial-condition definition of Sect. 2.1/2.3 applied once to the input).
 
 Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable
 pseudorandom number generators", OOPSLA 2014), a counter-based generator:
-value k of stream `seed` is mix(seed * 2^32 + k ...), see `splitmix64`.
+output k of stream `seed` is the SplitMix64 finaliser of seed + k * 0x9E3779B97F4A7C15
+(see `splitmix64`).
 
 A case is a dict with keys: name, dim, n (3 ints), faces (list of arrays),
 bc (list of (lo, hi)), coords, gamma, n_scalars, riemann, limiter, cfl,
@@ -168,6 +169,17 @@ def tubes(ntubes=4096, seed=2, lo=256, hi=8192, gamma=5.0 / 3.0):
         off += nb
     return dict(name="tubes%d" % ntubes, lengths=lengths, U=U, gamma=gamma, WL=WL, WR=WR,
                 riemann=EXACT, limiter=MINMOD, cfl=0.8)
+
+
+def partial_jump_faces(n, seed):
+    """Riemann problems from the tube-state distribution with partial jumps:
+    (W_L, W_L + t (W_R - W_L)) for t uniform in [0, 1), plus the full jumps.
+    Used (with harvested faces) as training inputs of the star-pressure guess."""
+    WL, WR = tube_states(n, seed)
+    t = uniform01(seed + 0x2545F491, n)[:, None]
+    full = np.concatenate([WL, WR], axis=1)
+    part = np.concatenate([WL, WL + t * (WR - WL)], axis=1)
+    return np.concatenate([full, part])
 
 
 def wedge(nr=1024, nth=128, nph=128, seed=3, riemann=HLLC, limiter=MINMOD):

@@ -107,7 +107,8 @@ def test_gpu_adam_step_matches_oracle(hydro_lib):
     w1 = b.mlp_get()
     X = np.array([O.mlp_features(5 / 3, WL[i], WR[i])[0] for i in range(256)])
     pref = np.array([O.mlp_features(5 / 3, WL[i], WR[i])[1] for i in range(256)])
-    tsrs = np.array([O.guess_toro(5 / 3, WL[i], WR[i])[1] == 2 for i in range(256)])
+    tsrs = np.array([O.guess_toro(5 / 3, WL[i], WR[i])[1] == 2 and
+                     max(WL[i, 2], WR[i, 2]) > 4 * min(WL[i, 2], WR[i, 2]) for i in range(256)])
     X32 = X.astype(np.float32).astype(np.float64)[tsrs]
     T32 = (lp - np.log(pref)).astype(np.float32).astype(np.float64)[tsrs]
     _, g = O.mlp_loss_grad(w0, X32, T32)
@@ -120,28 +121,32 @@ def test_gpu_adam_step_matches_oracle(hydro_lib):
 
 @pytest.mark.gpu
 def test_trained_network_reduces_newton_iterations(hydro_lib):
-    """Train on faces harvested from an FP64 run (seed 4 sampling), evaluate on a
-    held-out harvest (seed 5): fewer iterations than Toro's guess on the faces
-    that use the network (two-shock estimate), identical p* after polishing."""
+    """Train on the initial faces, partial-jump faces of the same state
+    distribution and faces harvested from an FP64 run (seed 4 sampling);
+    evaluate on a held-out harvest (seed 5): on the faces where the network is
+    used (two-shock Toro estimate, pressure jump > 4) Newton needs fewer
+    iterations than from Toro's guess, with identical p* after polishing."""
     H = hydro_lib
-    w = wl.tubes(256, seed=2)
+    w = wl.tubes(1024, seed=2)
     b = H.Batch(w["lengths"], w["gamma"], precision=64)
     b.set_state(w["U"])
-    b.harvest_begin(400000, 0.5, 4)
-    b.run(30, 0.8)
-    train = b.harvest_get(400000)
-    b.set_state(w["U"])
-    b.harvest_begin(60000, 0.5, 5)
-    b.run(30, 0.8)
-    test = b.harvest_get(60000)
-    train = np.concatenate([np.concatenate([w["WL"], w["WR"]], axis=1), train])
-    assert len(train) > 10000 and len(test) > 1000
-    ps, _, it = H.hydro_exact_solve(train[:, :3], train[:, 3:], w["gamma"], precision=64)
+    b.harvest_begin(400000, 1.0, 4)
+    b.run(60, 0.8)
+    harv = b.harvest_get(400000)
+    tw = wl.tubes(512, seed=12)
+    b2 = H.Batch(tw["lengths"], tw["gamma"], precision=64)
+    b2.set_state(tw["U"])
+    b2.harvest_begin(100000, 1.0, 5)
+    b2.run(45, 0.8)
+    test = b2.harvest_get(100000)
+    train = np.concatenate([wl.partial_jump_faces(60000, 7), harv])
+    assert len(harv) > 2000 and len(test) > 500
+    ps, _, _ = H.hydro_exact_solve(train[:, :3], train[:, 3:], w["gamma"], precision=64)
     assert np.all(ps > 0)
-    loss = b.mlp_train(train, np.log(ps), epochs=40, batch=256, lr=3e-3, seed=4)
-    assert loss < 1e-3
+    loss = b.mlp_train(train, np.log(ps), epochs=60, batch=256, lr=3e-3, seed=4)
+    assert loss < 1e-4
     wts = b.mlp_get()
     p_t, _, it_t = H.hydro_exact_solve(test[:, :3], test[:, 3:], w["gamma"], precision=64)
     p_m, _, it_m = H.hydro_exact_solve(test[:, :3], test[:, 3:], w["gamma"], H.HYDRO_GUESS_MLP, wts, 64)
     assert np.all(np.abs(p_m - p_t) <= 1e-13 * p_t)
-    assert it_m.mean() < it_t.mean(), (it_m.mean(), it_t.mean())
+    assert it_m.mean() < 0.95 * it_t.mean(), (it_m.mean(), it_t.mean())
