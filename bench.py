@@ -220,7 +220,16 @@ def main():
     ap.add_argument("--tubes", type=int, default=NTUBES, help="tubes per GPU (profiling a smaller case)")
     ap.add_argument("--skip-fp64", action="store_true", help="do not time the plain FP64 form")
     ap.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer path")
+    ap.add_argument("--skip-grids", action="store_true", help="do not time the 3D grid sweeps")
+    ap.add_argument("--grid-only", choices=["sedov3d_fp32", "sedov3d_fp64", "wedge_fp32"],
+                    help="time one grid sweep only (profiling)")
+    ap.add_argument("--grid-n", type=int, default=0, help="cells per axis for --grid-only sedov3d")
     args = ap.parse_args()
+    if args.grid_only:
+        import torch
+        from paper_2503_04428_gb300 import hydro as H
+        print(json.dumps(time_grids(H, torch, torch.cuda.current_stream(), args, only=args.grid_only)))
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -274,8 +283,72 @@ def main():
     e2e = None
     if not args.skip_e2e:
         e2e = time_e2e(H, torch, b32, w, args, ws, total, barrier)
+    dense = None
+    if not args.skip_fp64:
+        dense = time_dense(H, torch, stream, args, ws, weights)
+    grids = None
+    if not args.skip_grids:
+        grids = time_grids(H, torch, stream, args)
     return report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it32, mlp_frac,
-                  value64, t64, k64, it64, rho_rel)
+                  value64, t64, k64, it64, rho_rel, dense, grids)
+
+
+def time_grids(H, torch, stream, args, only=None):
+    """The fused grid sweep on the 3D configurations: Sedov 256^3 (HLL, NV=5) in
+    FP32 and FP64 and the spherical wedge 1024x128x128 (HLLC, NV=8, point +
+    monopole gravity) in FP32; device-side CFL steps replayed as a graph."""
+    from paper_2503_04428_gb300 import workloads as wl
+    peak, _ = load_peaks()
+    out = {}
+    runs = (("sedov3d_fp32", lambda: wl.sedov3d(args.grid_n or 256), 32, 20),
+            ("sedov3d_fp64", lambda: wl.sedov3d(args.grid_n or 256), 64, 5),
+            ("wedge_fp32", wl.wedge, 32, 10))
+    for name, make, prec, k in runs:
+        if only and name != only:
+            continue
+        if only:
+            k = args.steps
+        case = make()
+        name = "%s_%s" % (case["name"], name.split("_")[-1])
+        dt = np.float32 if prec == 32 else np.float64
+        g = H.Grid.from_case(dict(case, U=case["U"].astype(dt)), prec, stream=stream.cuda_stream)
+        g.run(2, case["cfl"])  # autotuner on first use
+        t = timed_steps(torch, stream, lambda n: g.run(n, case["cfl"]), k)
+        cells = int(np.prod(case["n"]))
+        nv = case["U"].shape[0]
+        bytes_cell = 2 * nv * (4 if prec == 32 else 8)
+        st = g.stats()
+        g.close()
+        gbs = bytes_cell * cells * k / t / 1e9
+        out[name] = {"value": cells * k / t, "unit": METRIC, "ms_per_step": 1000.0 * t / k, "steps": k,
+                     "hbm_gbs": gbs, "hbm_frac": gbs / peak, "tile": [st["tile_x"], st["tile_y"]],
+                     "zchunk": st["zchunk"], "gpu_launches_per_step": 3 if name.startswith("wedge") else 1}
+        del case
+    return out
+
+
+def time_dense(H, torch, stream, args, ws, weights):
+    """The headline form on a dense state: every cell's density and pressure
+    perturbed by 1 %, so that no face has two identical states and every face
+    runs the Newton iteration."""
+    from paper_2503_04428_gb300 import workloads as wl
+    w = wl.tubes(args.tubes, seed=rank_seed(dist_info()[1]), perturb=0.01)
+    total = int(w["lengths"].sum())
+    U = torch.from_numpy(w["U"].astype(np.float32)).cuda()
+    b = H.Batch(w["lengths"], w["gamma"], precision=32, stream=stream.cuda_stream)
+    b.mlp_set(weights, True)
+    b.set_state(U)
+    b.run(2, CFL)
+    b.set_state(U)
+    k = max(5, args.steps // 2)
+    s0 = b.stats()
+    t = timed_steps(torch, stream, lambda n: b.run(n, CFL), k)
+    s1 = b.stats()
+    rate, t = job_rate(t, total, k, torch.distributed if ws > 1 else None, "cuda")
+    it = (s1["newton_iters"] - s0["newton_iters"]) / max(s1["faces"] - s0["faces"], 1)
+    b.close()
+    return {"value": rate, "unit": METRIC, "ms_per_step": 1000.0 * t / k, "newton_iters_per_face": it,
+            "state": "every cell's rho and P x (1 + 0.01 U(-1,1))"}
 
 
 def time_fp64(H, torch, stream, w, args, ws, total, out32):
@@ -325,7 +398,7 @@ def time_e2e(H, torch, b32, w, args, ws, total, barrier):
 
 
 def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it32, mlp_frac,
-           value64, t64, k64, it64, rho_rel):
+           value64, t64, k64, it64, rho_rel, dense=None, grids=None):
     peak, peak_kind = load_peaks()
     alg_bytes = 2 * 3 * 4 * total  # read U^n and write U^{n+1}, FP32
     achieved = alg_bytes / (t32 / args.steps) / 1e9
@@ -358,6 +431,8 @@ def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it3
             "roofline": roof,
             "cpu_baseline": cpu,
             "fp64_plain": fp64,
+            "dense_state": dense,
+            "grid_sweep": grids,
             "newton_iters_per_face": {"fp32_mlp": it32, "fp64_toro": it64},
             "mlp": dict(train_info, guessed_face_fraction=mlp_frac),
             "accuracy": {"rho_rel_l1_fp32mlp_vs_fp64": rho_rel},

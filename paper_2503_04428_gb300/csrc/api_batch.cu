@@ -172,7 +172,7 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
   if (bs->tuned) return HYDRO_OK;
   bs->tuned = true;
   std::ostringstream key;
-  key << "batch2_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
+  key << "batch3_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
       << device_key();
   int cached;
   double us;
@@ -215,7 +215,7 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
     if (st) break;
     for (int item : BATCH_ITEM) {
       if ((st = make_items(h, item))) break;
-      for (int mult = 1; mult <= std::max(1, occ); mult *= 2) {
+      for (int mult = 1; mult <= std::max(1, occ); ++mult) {
         bs->grid = h->num_sms * mult;
         const int reps = 2;
         float ms = 0.f;

@@ -110,8 +110,10 @@ __device__ __forceinline__ T win(T va, T vb, int lane, int off) {
   return lane + off < 32 ? a : b;
 }
 
+// Two register budgets for the autotuner: 8-warp CTAs with 2 resident per SM
+// (128 registers, no spills) and 4-warp CTAs with 6 per SM (about 80).
 template <typename T, int NW>
-__global__ void __launch_bounds__(NW * 32)
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 6)
     batched_kernel(const BatchArgs<T> a) {
   __shared__ MlpSmemW sw;
   const volatile Ctrl* vc = &a.ctrl->c;
@@ -157,21 +159,29 @@ __global__ void __launch_bounds__(NW * 32)
     const T dtdx = (T)dtd * fn;
     T smax = T(0);
 
+    // conserved window of the first segment: cells c0-2+lane (Ua, all lanes)
+    // and c0+30+lane (Ub, lanes 0-1); the next segment's window is fetched
+    // while the current one is computed
+    T Ua[3], Ub[3];
+    auto fetch = [&](int c0, T* ua, T* ub) {
+      const int ca = min(max(c0 - 2 + lane, 0), nb - 1);
+      const int cb = min(max(c0 + 30 + (lane & 1), 0), nb - 1);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        ua[v] = __ldg(Uin + v * a.total + base + ca);
+        ub[v] = __ldg(Uin + v * a.total + base + cb);
+      }
+    };
+    fetch(s_beg, Ua, Ub);
     for (int c0 = s_beg; c0 < s_end; c0 += BSEG) {
       const int ncell = min(BSEG, s_end - c0);  // cells updated in this segment
-      // a1 + a2: cells c0-2+lane (Wa) and c0+30+lane (Wb, lanes 0-1), transmissive ends
+      T Un_[3], Unb[3];
+      const bool more = c0 + BSEG < s_end;
+      if (more) fetch(c0 + BSEG, Un_, Unb);
+      // a1 + a2: primitives of the window (transmissive ends by clamping)
       T Wa[3], Wb[3];
-      {
-        const int ca = min(max(c0 - 2 + lane, 0), nb - 1);
-        const int cb = min(max(c0 + 30 + (lane & 1), 0), nb - 1);
-        T u[3];
-#pragma unroll
-        for (int v = 0; v < 3; ++v) u[v] = __ldg(Uin + v * a.total + base + ca);
-        to_prim<T, 1, 0>(u, Wa, gas);
-#pragma unroll
-        for (int v = 0; v < 3; ++v) u[v] = __ldg(Uin + v * a.total + base + cb);
-        to_prim<T, 1, 0>(u, Wb, gas);
-      }
+      to_prim<T, 1, 0>(Ua, Wa, gas);
+      to_prim<T, 1, 0>(Ub, Wb, gas);
       // a3 + a4: cell c0-1+lane -- slopes, Hancock increment, predicted face states
       T Wc[3], Wlo[3], Whi[3];
       {
@@ -280,13 +290,16 @@ __global__ void __launch_bounds__(NW * 32)
       T Fh[3];
 #pragma unroll
       for (int v = 0; v < 3; ++v) Fh[v] = __shfl_down_sync(0xffffffffu, F[v], 1);
+      T Uo[3];  // conserved state of cell c0+lane, from the window (lane+2)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) Uo[v] = win(Ua[v], Ub[v], lane, 2);
       if (lane < ncell) {
         const long long c = base + c0 + lane;
         T u[3], w[3];
         bool finite = true;
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          u[v] = Uin[v * a.total + c] + dtdx * (F[v] - Fh[v]);
+          u[v] = Uo[v] + dtdx * (F[v] - Fh[v]);
           finite = finite && isfinite(u[v]);
         }
         to_prim<T, 1, 0>(u, w, gas);
@@ -295,6 +308,13 @@ __global__ void __launch_bounds__(NW * 32)
         smax = fmax(smax, (fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * fn);
 #pragma unroll
         for (int v = 0; v < 3; ++v) Uout[v * a.total + c] = u[v];
+      }
+      if (more) {
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          Ua[v] = Un_[v];
+          Ub[v] = Unb[v];
+        }
       }
     }
 #pragma unroll

@@ -151,11 +151,17 @@ def tube_lengths(ntubes=4096, seed=2, lo=256, hi=8192):
     return (lo + np.floor(r * (hi - lo + 1))).astype(np.int32)
 
 
-def tubes(ntubes=4096, seed=2, lo=256, hi=8192, gamma=5.0 / 3.0):
-    """Batched exact-Riemann workload: ragged SoA (3, total cells), interface at x=0.5 of [0,1]."""
+def tubes(ntubes=4096, seed=2, lo=256, hi=8192, gamma=5.0 / 3.0, perturb=0.0):
+    """Batched exact-Riemann workload: ragged SoA (3, total cells), interface at x=0.5 of [0,1].
+
+    perturb > 0 multiplies density and pressure of every cell by
+    1 + perturb U(-1,1) (a dense state in which no two neighbours are equal)."""
     lengths = tube_lengths(ntubes, seed, lo, hi)
     WL, WR = tube_states(ntubes, seed)
     total = int(lengths.sum())
+    noise = None
+    if perturb > 0:
+        noise = 1.0 + perturb * (2.0 * uniform01(seed + 0x68E31DA4, 2 * total).reshape(2, total) - 1.0)
     U = np.empty((3, total))
     off = 0
     for b in range(ntubes):
@@ -165,6 +171,9 @@ def tubes(ntubes=4096, seed=2, lo=256, hi=8192, gamma=5.0 / 3.0):
         rho = np.where(left, WL[b, 0], WR[b, 0])
         u = np.where(left, WL[b, 1], WR[b, 1])
         p = np.where(left, WL[b, 2], WR[b, 2])
+        if noise is not None:
+            rho = rho * noise[0, off:off + nb]
+            p = p * noise[1, off:off + nb]
         U[:, off:off + nb] = conserved(gamma, rho, [u], p)
         off += nb
     return dict(name="tubes%d" % ntubes, lengths=lengths, U=U, gamma=gamma, WL=WL, WR=WR,
