@@ -185,6 +185,25 @@ int hydro_mlp_train(hydro_t h, const double* faces6, const double* log_pstar, lo
 int hydro_mlp_loss_grad(const float* weights, const double* x6, const double* target, long n,
                         double* grad_out, double* loss_out);
 
+/* The same gradient as hydro_mlp_loss_grad, without allocating device memory.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * allocate while they call in -- code running inside CUDA stream capture,
+ * or a host framework that owns all device memory through its own pool.
+ * Every pointer is a device address in the current context: weights
+ * (HYDRO_MLP_NPARAM floats), x6 (n x 6 floats, the network inputs), target
+ * (n floats), grad_out (HYDRO_MLP_NPARAM doubles), loss_out (1 double); work
+ * is queued on `stream` (a cudaStream_t, NULL = legacy default) and the call
+ * returns without synchronising.  The per-CTA partial gradients live in a
+ * static device array of 4.79 MB that every GPU loading the library holds
+ * until the process exits; hence 1 <= n <= HYDRO_NOALLOC_MAX_SAMPLES, larger n
+ * is rejected with HYDRO_ERR_ARG.  The array is shared by all calls: nothing
+ * in it has to start at zero, but calls that overlap on the GPU race on it.
+ * The first call on a device looks the array's address up (no allocation);
+ * make that first call before any stream capture. */
+#define HYDRO_NOALLOC_MAX_SAMPLES 16384
+int hydro_mlp_loss_grad_device(const float* weights, const float* x6, const float* target, long n,
+                               double* grad_out, double* loss_out, void* stream);
+
 /* Exact Riemann star states on the GPU for n independent faces (host arrays
  * WL, WR of n x (rho,u,P)): p_star, u_star and Newton iterations per face.
  * precision 64 or 32; guess HYDRO_GUESS_TORO or HYDRO_GUESS_MLP (weights

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -727,3 +728,98 @@ int hydro_exact_solve(const double* WL, const double* WR, long n, double gamma, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Gradient of the guess network without device allocation.
+//
+// hydro_mlp_loss_grad_device is for callers that cannot allocate device
+// memory while they call in: code running inside CUDA stream capture, memory
+// managed entirely by a host framework's own pool, or a process that must not
+// grow its device footprint.  Its per-CTA partial gradients live in the
+// file-scope array below instead of in cudaMalloc'd scratch.
+// ---------------------------------------------------------------------------
+namespace hydro {
+
+constexpr long NOALLOC_MAX_SAMPLES = 16384;                    // n limit of one call
+constexpr int NOALLOC_MAX_BLOCKS = (int)(NOALLOC_MAX_SAMPLES / MLP_SB);  // 256 CTAs
+constexpr size_t NOALLOC_GRAD_BYTES = (size_t)NOALLOC_MAX_BLOCKS * MLP_NPARAM * sizeof(float);
+constexpr size_t NOALLOC_BYTES = NOALLOC_GRAD_BYTES + (size_t)NOALLOC_MAX_BLOCKS * sizeof(double);
+
+// 4.79 MB, held by every GPU that loads the library until the process exits.
+// Every call reuses it: each CTA first writes all of its partial values and
+// the reduction reads only the partials of the current call, so nothing has
+// to be cleared between calls; calls that overlap on the GPU race on it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of the array, looked up once per device (the host-side
+// symbol is only a stand-in and must not be passed to a kernel).
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64] = {nullptr};
+
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  HCK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("hydro_mlp_loss_grad_device: device index out of range");
+    return HYDRO_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return HYDRO_OK;
+}
+
+// grad[p] = sum of the partials of parameter p (fixed order, FP64);
+// loss = sum of the loss partials / n.
+__global__ void noalloc_reduce_kernel(const float* partial, const double* loss_partial, int nblocks, long n,
+                                      double* grad, double* loss) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < MLP_NPARAM) {
+    double a = 0.0;
+    for (int b = 0; b < nblocks; ++b) a += (double)partial[(long long)b * MLP_NPARAM + p];
+    grad[p] = a;
+  }
+  if (p == 0) {
+    double l = 0.0;
+    for (int b = 0; b < nblocks; ++b) l += loss_partial[b];
+    *loss = l / (double)n;
+  }
+}
+
+}  // namespace hydro
+
+extern "C" int hydro_mlp_loss_grad_device(const float* weights, const float* x6, const float* target, long n,
+                                          double* grad_out, double* loss_out, void* stream) {
+  if (!weights || !x6 || !target || !grad_out || !loss_out)
+    return berr("hydro_mlp_loss_grad_device: null pointer");
+  if (n < 1 || n > hydro::NOALLOC_MAX_SAMPLES) {
+    std::ostringstream m;
+    m << "hydro_mlp_loss_grad_device: n = " << n << " outside [1, " << hydro::NOALLOC_MAX_SAMPLES
+      << "] (the size of its static scratch)";
+    return berr(m.str());
+  }
+  void* scratch = nullptr;
+  int st = hydro::noalloc_scratch(&scratch);
+  if (st) return st;
+  static bool attr = false;
+  if (!attr) {
+    HCK(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
+    attr = true;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  float* partial = (float*)scratch;
+  double* loss_partial = (double*)((unsigned char*)scratch + hydro::NOALLOC_GRAD_BYTES);
+  const int nblocks = (int)((n + MLP_SB - 1) / MLP_SB);
+  mlp_grad_kernel<<<nblocks, 256, sizeof(MlpSmem), s>>>(weights, x6, target, nullptr, 0, n, (float)(1.0 / n),
+                                                        partial, loss_partial);
+  HCK(cudaGetLastError());
+  hydro::noalloc_reduce_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(partial, loss_partial, nblocks, n,
+                                                                       grad_out, loss_out);
+  HCK(cudaGetLastError());
+  return HYDRO_OK;
+}

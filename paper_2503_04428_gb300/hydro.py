@@ -28,6 +28,7 @@ HYDRO_HOST, HYDRO_DEVICE = 0, 1
 HYDRO_GUESS_TORO, HYDRO_GUESS_MLP = 0, 1
 HYDRO_MAX_SCALARS = 3
 HYDRO_MLP_NPARAM = 4673
+HYDRO_NOALLOC_MAX_SAMPLES = 16384
 
 
 class hydro_grid(C.Structure):
@@ -80,6 +81,7 @@ _SIGS = {
     "hydro_mlp_train": [_VP, _D, _D, C.c_long, C.c_int, C.c_int, C.c_float, C.c_ulonglong, _D],
     "hydro_mlp_loss_grad": [_F, _D, _D, C.c_long, _D, _D],
     "hydro_exact_solve": [_D, _D, C.c_long, C.c_double, C.c_int, _F, C.c_int, _D, _D, _I],
+    "hydro_mlp_loss_grad_device": [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP],
     "hydro_destroy": [_VP],
     "hydro_last_error": [],
 }
@@ -239,6 +241,12 @@ def hydro_mlp_loss_grad(weights, x6, target):
     _call("hydro_mlp_loss_grad", w.ctypes.data_as(_F), x.ctypes.data_as(_D), t.ctypes.data_as(_D),
           len(t), g.ctypes.data_as(_D), C.byref(loss))
     return loss.value, g
+
+
+def hydro_mlp_loss_grad_device(weights, x6, target, n, grad_out, loss_out, stream=None):
+    """Allocation-free gradient: every argument is a device address (int), e.g.
+    a CUDA tensor's data_ptr(); queued on `stream`, not synchronised."""
+    _call("hydro_mlp_loss_grad_device", weights, x6, target, n, grad_out, loss_out, stream)
 
 
 def hydro_exact_solve(WL, WR, gamma, guess=HYDRO_GUESS_TORO, weights=None, precision=64):
