@@ -16,10 +16,10 @@
 
 namespace hydro {
 
-// Autotuner candidates: warps per CTA, cells per work item (whole 30-cell
+// Autotuner candidates: warps per CTA, cells per work item (whole 28-cell
 // segments) and persistent CTAs per SM (up to the occupancy limit).
 static const int BATCH_NW[] = {4, 8};
-static const int BATCH_ITEM[] = {30, 60, 120, 240, 480};
+static const int BATCH_ITEM[] = {28, 56, 112, 224, 448, 896};
 
 struct BatchState {
   int ntubes = 0;
@@ -33,7 +33,7 @@ struct BatchState {
   BatchCtrl* bctrl = nullptr;
   BatchCtrl* bctrl_host = nullptr;
   // launch shape: warps per CTA, cells per item, CTAs
-  int nw = 8, item_len = 120, grid = 0;
+  int nw = 8, item_len = 112, grid = 0;
   int* item_tube = nullptr;
   int* item_start = nullptr;
   int nitems = 0;
@@ -173,7 +173,7 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
   if (bs->tuned) return HYDRO_OK;
   bs->tuned = true;
   std::ostringstream key;
-  key << "batch3_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
+  key << "batch4_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
       << device_key();
   int cached;
   double us;
@@ -459,7 +459,7 @@ int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int
   cudaMemset(bs->t_tube, 0, sizeof(double) * ntubes);
   std::memset(bs->bctrl_host, 0, sizeof(BatchCtrl));
   bs->bctrl_host->c.err_step = -1;
-  if ((st = write_bctrl(h)) || (st = make_items(h, 120))) { hydro_destroy(h); return st; }
+  if ((st = write_bctrl(h)) || (st = make_items(h, 112))) { hydro_destroy(h); return st; }
   bs->grid = h->num_sms * 2;
   *out = h;
   return HYDRO_OK;

@@ -324,7 +324,7 @@ static int launch_step_t(hydro_ctx* h, double dt_host, double cfl, double t_end,
                                                       h->shell_kchunk, h->dvol[1], h->dvol[2],
                                                       h->shell_partial);
     HCK(cudaGetLastError());
-    monopole_kernel<T><<<1, 256, 0, h->stream>>>(ctrl, h->shell_partial, h->shell_nchunks, h->n[0],
+    monopole_kernel<T><<<1, MONO_THREADS, 0, h->stream>>>(ctrl, h->shell_partial, h->shell_nchunks, h->n[0],
                                                  h->dvol[0], h->rc_d, h->G, h->Mc,
                                                  4.0 * PI / h->omega, h->shell, (T*)h->gmono);
     HCK(cudaGetLastError());
@@ -332,11 +332,10 @@ static int launch_step_t(hydro_ctx* h, double dt_host, double cfl, double t_end,
   SweepArgs<T> a = sweep_args<T>(h, dt_host, cfl, t_end, ctrl);
   cudaError_t e;
   switch (h->dim) {
-    case 1: e = sweep_dispatch<T, 1>(a, h->nsx, h->riemann, h->stream, &h->tile_x, &h->tile_y); break;
-    case 2: e = sweep_dispatch<T, 2>(a, h->nsx, h->riemann, h->stream, &h->tile_x, &h->tile_y); break;
-    default: e = sweep_dispatch<T, 3>(a, h->nsx, h->riemann, h->stream, &h->tile_x, &h->tile_y); break;
+    case 1: e = sweep_dispatch<T, 1>(a, h->nsx, h->riemann, h->stream, &h->tile_x, &h->tile_y, &h->threads); break;
+    case 2: e = sweep_dispatch<T, 2>(a, h->nsx, h->riemann, h->stream, &h->tile_x, &h->tile_y, &h->threads); break;
+    default: e = sweep_dispatch<T, 3>(a, h->nsx, h->riemann, h->stream, &h->tile_x, &h->tile_y, &h->threads); break;
   }
-  h->threads = h->tile_x * h->tile_y;
   if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
   return HYDRO_OK;
 }

@@ -131,28 +131,44 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Monopole pass 2 (one block): shell masses and the enclosed-mass
-// acceleration, in a fixed order.
+// Monopole pass 2 (one block of MONO_THREADS): shell masses, their prefix
+// sums by a block-wide Hillis-Steele scan (fixed order, so deterministic) and
+// the enclosed-mass acceleration of every radial cell.
+constexpr int MONO_THREADS = 1024;
+
 template <typename T>
-__global__ void monopole_kernel(const Ctrl* ctrl, const double* partial, int nchunks, int n0,
-                                const double* __restrict__ da, const double* __restrict__ rc,
-                                double G, double Mc, double four_pi_over_omega, double* shell,
-                                T* gmono) {
+__global__ void __launch_bounds__(MONO_THREADS)
+    monopole_kernel(const Ctrl* ctrl, const double* partial, int nchunks, int n0,
+                    const double* __restrict__ da, const double* __restrict__ rc, double G,
+                    double Mc, double four_pi_over_omega, double* shell, T* gmono) {
   if (((volatile const Ctrl*)ctrl)->status != 0) return;
-  for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < nchunks; ++q) s += partial[(long long)q * n0 + i];
-    shell[i] = s * da[i];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double below = 0.0;
-    for (int i = 0; i < n0; ++i) {
-      const double M = Mc + four_pi_over_omega * (below + 0.5 * shell[i]);
-      below += shell[i];
+  __shared__ double sh[MONO_THREADS];
+  const int tid = threadIdx.x;
+  double carry = 0.0;  // mass of all shells of the previous chunks
+  for (int base = 0; base < n0; base += MONO_THREADS) {
+    const int i = base + tid;
+    double m = 0.0;
+    if (i < n0) {
+      double s = 0.0;
+      for (int q = 0; q < nchunks; ++q) s += partial[(long long)q * n0 + i];
+      m = s * da[i];
+    }
+    sh[tid] = m;
+    __syncthreads();
+    for (int off = 1; off < MONO_THREADS; off <<= 1) {
+      const double v = tid >= off ? sh[tid - off] : 0.0;
+      __syncthreads();
+      sh[tid] += v;
+      __syncthreads();
+    }
+    const double below = carry + (tid > 0 ? sh[tid - 1] : 0.0);
+    if (i < n0) {
+      const double M = Mc + four_pi_over_omega * (below + 0.5 * m);
       gmono[i] = (T)(-G * M / (rc[i] * rc[i]));
       shell[i] = M;
     }
+    carry += sh[MONO_THREADS - 1];
+    __syncthreads();
   }
 }
 

@@ -2,11 +2,11 @@
 //
 // Each tube b is a uniform grid of n_b cells on [0,1] with transmissive ends
 // and its own CFL time step dt_b = cfl / max_i (|u|+c) n_b (reading R4 in
-// 1D).  The tubes are cut into work items of whole 30-cell segments; every
+// 1D).  The tubes are cut into work items of whole 28-cell segments; every
 // warp of a persistent grid pulls items from an atomic counter and advances
 // them on its own, with neighbour data exchanged by shuffles (no block-wide
-// barrier on the step's path).  Per 30-cell segment, lane l of the warp:
-//   - stages cell c0-2+l (lanes 0,1 also c0+30+l) as primitives (Eq. 5);
+// barrier on the step's path).  Per 28-cell segment, lane l of the warp:
+//   - stages cell c0-2+l as primitives (Eq. 5);
 //   - computes the limited slopes (Eq. 17) and Hancock increment (Eq. 18) of
 //     cell c0-1+l and its two predicted face states;
 //   - solves the exact Riemann problem (App. C.1) at face c0+l: identical
@@ -16,13 +16,15 @@
 //     such face at a time);
 //     Newton to 1e-10 (FP64) and one polishing step; sample at x/t = 0;
 //   - updates cell c0+l (Eq. 19) and reduces its signal speed.
+// A segment whose whole window is one uniform state takes a short path that
+// returns exactly what the full path returns there (U + 0).
 // The last CTA to finish commits the step (per-tube speeds, times, buffer).
 #pragma once
 #include "common.cuh"
 
 namespace hydro {
 
-constexpr int BSEG = 30;  // cells per warp segment (32 lanes = 30 cells + 2 halo faces)
+constexpr int BSEG = 28;  // cells per warp segment (32 lanes = 28 cells + 2 halo cells each side)
 
 struct BatchCtrl {
   Ctrl c;
@@ -101,19 +103,16 @@ __device__ __forceinline__ float mlp_warp(const MlpSmemW& s, const float* x, int
   return y + s.b3;
 }
 
-// Value of lane (lane + off) of the 34-cell window held as (Wa on all lanes,
-// Wb on lanes 0-1).
+// Value of lane (lane + off) of the 32-cell window (lanes beyond 31 are never used).
 template <typename T>
-__device__ __forceinline__ T win(T va, T vb, int lane, int off) {
-  const T a = __shfl_down_sync(0xffffffffu, va, off);
-  const T b = __shfl_sync(0xffffffffu, vb, (lane + off) & 31);
-  return lane + off < 32 ? a : b;
+__device__ __forceinline__ T win(T va, int off) {
+  return __shfl_down_sync(0xffffffffu, va, off);
 }
 
 // Two register budgets for the autotuner: 8-warp CTAs with 2 resident per SM
-// (128 registers, no spills) and 4-warp CTAs with 6 per SM (about 80).
+// (128 registers) and 4-warp CTAs with 5 per SM (about 100).
 template <typename T, int NW>
-__global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 6)
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     batched_kernel(const BatchArgs<T> a) {
   __shared__ MlpSmemW sw;
   const volatile Ctrl* vc = &a.ctrl->c;
@@ -159,37 +158,64 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 6)
     const T dtdx = (T)dtd * fn;
     T smax = T(0);
 
-    // conserved window of the first segment: cells c0-2+lane (Ua, all lanes)
-    // and c0+30+lane (Ub, lanes 0-1); the next segment's window is fetched
-    // while the current one is computed
-    T Ua[3], Ub[3];
-    auto fetch = [&](int c0, T* ua, T* ub) {
+    // conserved window of the first segment: cells c0-2+lane; the next
+    // segment's window is fetched while the current one is computed
+    T Ua[3];
+    auto fetch = [&](int c0, T* ua) {
       const int ca = min(max(c0 - 2 + lane, 0), nb - 1);
-      const int cb = min(max(c0 + 30 + (lane & 1), 0), nb - 1);
 #pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        ua[v] = __ldg(Uin + v * a.total + base + ca);
-        ub[v] = __ldg(Uin + v * a.total + base + cb);
-      }
+      for (int v = 0; v < 3; ++v) ua[v] = __ldg(Uin + v * a.total + base + ca);
     };
-    fetch(s_beg, Ua, Ub);
+    fetch(s_beg, Ua);
     for (int c0 = s_beg; c0 < s_end; c0 += BSEG) {
       const int ncell = min(BSEG, s_end - c0);  // cells updated in this segment
-      T Un_[3], Unb[3];
+      T Un_[3];
       const bool more = c0 + BSEG < s_end;
-      if (more) fetch(c0 + BSEG, Un_, Unb);
+      if (more) fetch(c0 + BSEG, Un_);
+      // A window holding one state everywhere (clamped tube ends included)
+      // has zero slopes, a +0 Hancock increment, identical face states and
+      // equal fluxes, so the full path below returns U + 0 for every cell:
+      // produce exactly that without the face work.
+      // (the shuffles run on every lane before the comparison: a shuffle
+      // inside a short-circuit condition would leave lanes out of it)
+      const T r0 = __shfl_sync(0xffffffffu, Ua[0], 0);
+      const T r1 = __shfl_sync(0xffffffffu, Ua[1], 0);
+      const T r2 = __shfl_sync(0xffffffffu, Ua[2], 0);
+      const bool uniform = __all_sync(0xffffffffu, (Ua[0] == r0) & (Ua[1] == r1) & (Ua[2] == r2));
+      if (uniform) {
+        if (lane < ncell) {
+          const long long c = base + c0 + lane;
+          T u[3], w[3];
+          bool finite = true;
+#pragma unroll
+          for (int v = 0; v < 3; ++v) {
+            u[v] = Ua[v] + T(0);
+            finite = finite && isfinite(u[v]);
+          }
+          to_prim<T, 1, 0>(u, w, gas);
+          if (!finite) err = err ? err : ST_NONFINITE;
+          else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
+          smax = fmax(smax, (fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * fn);
+#pragma unroll
+          for (int v = 0; v < 3; ++v) Uout[v * a.total + c] = u[v];
+        }
+        if (more) {
+#pragma unroll
+          for (int v = 0; v < 3; ++v) Ua[v] = Un_[v];
+        }
+        continue;
+      }
       // a1 + a2: primitives of the window (transmissive ends by clamping)
-      T Wa[3], Wb[3];
+      T Wa[3];
       to_prim<T, 1, 0>(Ua, Wa, gas);
-      to_prim<T, 1, 0>(Ub, Wb, gas);
       // a3 + a4: cell c0-1+lane -- slopes, Hancock increment, predicted face states
       T Wc[3], Wlo[3], Whi[3];
       {
         T Wp[3], fl[3], fh[3];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          Wc[v] = win(Wa[v], Wb[v], lane, 1);
-          Wp[v] = win(Wa[v], Wb[v], lane, 2);
+          Wc[v] = win(Wa[v], 1);
+          Wp[v] = win(Wa[v], 2);
           const T sig = limit<T>(a.limiter, (Wc[v] - Wa[v]) * fn, (Wp[v] - Wc[v]) * fn);
           Wlo[v] = Wc[v] - hw * sig;
           Whi[v] = Wc[v] + hw * sig;
@@ -292,7 +318,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 6)
       for (int v = 0; v < 3; ++v) Fh[v] = __shfl_down_sync(0xffffffffu, F[v], 1);
       T Uo[3];  // conserved state of cell c0+lane, from the window (lane+2)
 #pragma unroll
-      for (int v = 0; v < 3; ++v) Uo[v] = win(Ua[v], Ub[v], lane, 2);
+      for (int v = 0; v < 3; ++v) Uo[v] = win(Ua[v], 2);
       if (lane < ncell) {
         const long long c = base + c0 + lane;
         T u[3], w[3];
@@ -311,10 +337,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 6)
       }
       if (more) {
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          Ua[v] = Un_[v];
-          Ub[v] = Unb[v];
-        }
+        for (int v = 0; v < 3; ++v) Ua[v] = Un_[v];
       }
     }
 #pragma unroll

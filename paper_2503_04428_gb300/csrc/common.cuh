@@ -85,7 +85,8 @@ struct SweepArgs {
 };
 
 template <typename T, int DIM>
-cudaError_t sweep_dispatch(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s, int* tx, int* ty);
+cudaError_t sweep_dispatch(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s, int* tx, int* ty,
+                           int* nt);
 
 // Bits of a non-negative double, for an ordered atomicMax.
 __device__ __forceinline__ unsigned long long dbits(double x) {

@@ -22,6 +22,9 @@
 
 namespace hydro {
 
+// Tile shape per (precision, dimension, scalar slots); NT (threads per CTA)
+// is chosen so that the heavy phases (predictor over the tile plus halo,
+// faces) take few, nearly full rounds of the CTA's threads.
 template <typename T, int DIM, int NSX>
 struct TileCfg;
 // float
@@ -31,9 +34,9 @@ template <> struct TileCfg<float, 1, 3> { static constexpr int TX = 256, TY = 1;
 template <> struct TileCfg<float, 2, 0> { static constexpr int TX = 32, TY = 16; };
 template <> struct TileCfg<float, 2, 1> { static constexpr int TX = 32, TY = 16; };
 template <> struct TileCfg<float, 2, 3> { static constexpr int TX = 32, TY = 8; };
-template <> struct TileCfg<float, 3, 0> { static constexpr int TX = 32, TY = 16; };
-template <> struct TileCfg<float, 3, 1> { static constexpr int TX = 32, TY = 8; };
-template <> struct TileCfg<float, 3, 3> { static constexpr int TX = 16, TY = 16; };
+template <> struct TileCfg<float, 3, 0> { static constexpr int TX = 32, TY = 16, NT = 640; };
+template <> struct TileCfg<float, 3, 1> { static constexpr int TX = 32, TY = 8, NT = 384; };
+template <> struct TileCfg<float, 3, 3> { static constexpr int TX = 16, TY = 16, NT = 416; };
 // double
 template <> struct TileCfg<double, 1, 0> { static constexpr int TX = 256, TY = 1; };
 template <> struct TileCfg<double, 1, 1> { static constexpr int TX = 256, TY = 1; };
@@ -41,9 +44,14 @@ template <> struct TileCfg<double, 1, 3> { static constexpr int TX = 256, TY = 1
 template <> struct TileCfg<double, 2, 0> { static constexpr int TX = 32, TY = 8; };
 template <> struct TileCfg<double, 2, 1> { static constexpr int TX = 32, TY = 8; };
 template <> struct TileCfg<double, 2, 3> { static constexpr int TX = 32, TY = 8; };
-template <> struct TileCfg<double, 3, 0> { static constexpr int TX = 16, TY = 16; };
-template <> struct TileCfg<double, 3, 1> { static constexpr int TX = 16, TY = 16; };
-template <> struct TileCfg<double, 3, 3> { static constexpr int TX = 16, TY = 8; };
+template <> struct TileCfg<double, 3, 0> { static constexpr int TX = 16, TY = 16, NT = 416; };
+template <> struct TileCfg<double, 3, 1> { static constexpr int TX = 16, TY = 16, NT = 416; };
+template <> struct TileCfg<double, 3, 3> { static constexpr int TX = 16, TY = 8, NT = 224; };
+
+template <typename C, typename = void>
+struct TileThreads { static constexpr int value = C::TX * C::TY; };
+template <typename C>
+struct TileThreads<C, decltype((void)C::NT)> { static constexpr int value = C::NT; };
 
 template <typename T, int DIM, int NSX>
 struct SweepShape {
@@ -56,7 +64,7 @@ struct SweepShape {
   static constexpr int PX = TX + 2, PY = TY + 2 * QY;    // predictor plane extents
   static constexpr int WP = DIM == 3 ? 5 : 1;            // primitive planes in flight
   static constexpr int DP = DIM == 3 ? 3 : 1;            // predictor planes in flight
-  static constexpr int NT = TX * TY;                     // threads per CTA
+  static constexpr int NT = TileThreads<TileCfg<T, DIM, NSX>>::value;  // threads per CTA
   static constexpr int WPL = EX * EY, DPL = PX * PY;
   static constexpr int NFX = (TX + 1) * TY;
   static constexpr int NFY = DIM >= 2 ? TX * (TY + 1) : 0;
@@ -295,13 +303,24 @@ struct Sweep {
     }
   }
 
-  // a5 for the x and y faces of plane gz (and in 3D its top z face).
+  // a5 for the x and y faces of plane gz and, in 3D, its top z face, in one
+  // loop over all of them.
   __device__ void faces_plane(int gz) {
     const int n0 = a.n[0], n1 = a.n[1];
     const int slot = wslot(gz), ds = dslot(gz);
-    for (int idx = threadIdx.x; idx < S::NFX + S::NFY; idx += NT) {
+    T* Fzo = Fz + ((gz + 1) & 1) * NV * S::NFZ;
+    for (int idx = threadIdx.x; idx < S::NFX + S::NFY + S::NFZ; idx += NT) {
       T WL[NV], WR[NV], F[NV];
-      if (idx < S::NFX) {
+      if (DIM == 3 && idx >= S::NFX + S::NFY) {
+        const int k = idx - S::NFX - S::NFY;
+        const int fi = k % TX, fj = k / TX;
+        if (x0 + fi >= n0 || y0 + fj >= n1) continue;
+        face_state<2, 1>(slot, fj + HY, fi + 2, gz, ds, fj + QY, fi + 1, gz, WL);
+        face_state<2, 0>(wslot(gz + 1), fj + HY, fi + 2, gz + 1, dslot(gz + 1), fj + QY, fi + 1, gz + 1, WR);
+        riemann<2>(WL, WR, F);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fzo[v * S::NFZ + k] = F[v];
+      } else if (idx < S::NFX) {
         const int fi = idx % (TX + 1), fj = idx / (TX + 1);
         if (x0 + fi > n0 || (DIM >= 2 && y0 + fj >= n1)) continue;
         const int gi = x0 + fi, gj = y0 + fj;
@@ -323,7 +342,6 @@ struct Sweep {
         for (int v = 0; v < NV; ++v) Fy[v * S::NFY + k] = F[v];
       }
     }
-    if constexpr (DIM == 3) zfaces(gz);
   }
 
   // a6-a9: update plane gz.
@@ -587,23 +605,33 @@ cudaError_t launch_sweep(const SweepArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Launch one instantiation and report its tile shape and threads per CTA.
+template <typename T, int DIM, int NSX, int RS>
+cudaError_t launch_sweep_shape(const SweepArgs<T>& a, cudaStream_t s, int* tx, int* ty, int* nt) {
+  using S = SweepShape<T, DIM, NSX>;
+  *tx = S::TX;
+  *ty = S::TY;
+  *nt = S::NT;
+  return launch_sweep<T, DIM, NSX, RS>(a, s);
+}
+
 // Instantiate the dispatcher of one (precision, dimension) pair.
-#define HYDRO_SWEEP_DISPATCH(T, DIM)                                                            \
-  template <>                                                                                   \
-  cudaError_t sweep_dispatch<T, DIM>(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s,    \
-                                     int* tx, int* ty) {                                        \
-    switch (nsx * 4 + rs) {                                                                     \
-      case 0: *tx = TileCfg<T, DIM, 0>::TX; *ty = TileCfg<T, DIM, 0>::TY; return launch_sweep<T, DIM, 0, RS_HLL>(a, s);   \
-      case 1: *tx = TileCfg<T, DIM, 0>::TX; *ty = TileCfg<T, DIM, 0>::TY; return launch_sweep<T, DIM, 0, RS_HLLC>(a, s);  \
-      case 2: *tx = TileCfg<T, DIM, 0>::TX; *ty = TileCfg<T, DIM, 0>::TY; return launch_sweep<T, DIM, 0, RS_EXACT>(a, s); \
-      case 4: *tx = TileCfg<T, DIM, 1>::TX; *ty = TileCfg<T, DIM, 1>::TY; return launch_sweep<T, DIM, 1, RS_HLL>(a, s);   \
-      case 5: *tx = TileCfg<T, DIM, 1>::TX; *ty = TileCfg<T, DIM, 1>::TY; return launch_sweep<T, DIM, 1, RS_HLLC>(a, s);  \
-      case 6: *tx = TileCfg<T, DIM, 1>::TX; *ty = TileCfg<T, DIM, 1>::TY; return launch_sweep<T, DIM, 1, RS_EXACT>(a, s); \
-      case 12: *tx = TileCfg<T, DIM, 3>::TX; *ty = TileCfg<T, DIM, 3>::TY; return launch_sweep<T, DIM, 3, RS_HLL>(a, s);  \
-      case 13: *tx = TileCfg<T, DIM, 3>::TX; *ty = TileCfg<T, DIM, 3>::TY; return launch_sweep<T, DIM, 3, RS_HLLC>(a, s); \
-      case 14: *tx = TileCfg<T, DIM, 3>::TX; *ty = TileCfg<T, DIM, 3>::TY; return launch_sweep<T, DIM, 3, RS_EXACT>(a, s);\
-      default: return cudaErrorInvalidValue;                                                    \
-    }                                                                                           \
+#define HYDRO_SWEEP_DISPATCH(T, DIM)                                                          \
+  template <>                                                                                 \
+  cudaError_t sweep_dispatch<T, DIM>(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s,  \
+                                     int* tx, int* ty, int* nt) {                             \
+    switch (nsx * 4 + rs) {                                                                   \
+      case 0: return launch_sweep_shape<T, DIM, 0, RS_HLL>(a, s, tx, ty, nt);                 \
+      case 1: return launch_sweep_shape<T, DIM, 0, RS_HLLC>(a, s, tx, ty, nt);                \
+      case 2: return launch_sweep_shape<T, DIM, 0, RS_EXACT>(a, s, tx, ty, nt);               \
+      case 4: return launch_sweep_shape<T, DIM, 1, RS_HLL>(a, s, tx, ty, nt);                 \
+      case 5: return launch_sweep_shape<T, DIM, 1, RS_HLLC>(a, s, tx, ty, nt);                \
+      case 6: return launch_sweep_shape<T, DIM, 1, RS_EXACT>(a, s, tx, ty, nt);               \
+      case 12: return launch_sweep_shape<T, DIM, 3, RS_HLL>(a, s, tx, ty, nt);                \
+      case 13: return launch_sweep_shape<T, DIM, 3, RS_HLLC>(a, s, tx, ty, nt);               \
+      case 14: return launch_sweep_shape<T, DIM, 3, RS_EXACT>(a, s, tx, ty, nt);              \
+      default: return cudaErrorInvalidValue;                                                  \
+    }                                                                                         \
   }
 
 }  // namespace hydro

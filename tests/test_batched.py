@@ -117,3 +117,23 @@ def test_rejects_bad_input(hydro_lib):
     with pytest.raises(H.HydroError) as e:
         b.set_state(U)
     assert e.value.status == H.HYDRO_ERR_NEGATIVE_STATE
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_uniform_tubes_are_unchanged(hydro_lib, precision):
+    """Tubes holding one state everywhere: every face is trivial and every step
+    returns the state bit for bit (the uniform-window path and the full path
+    both give U + 0)."""
+    lengths = np.array([100, 57, 3000, 28, 29, 56], dtype=np.int32)
+    total = int(lengths.sum())
+    rho = np.repeat(np.array([1.0, 0.5, 2.0, 1e-3, 3.0, 0.7]), lengths)
+    u = np.repeat(np.array([0.3, -1.0, 0.0, 2.0, -0.5, 0.1]), lengths)
+    p = np.repeat(np.array([1.0, 0.2, 5.0, 1e-4, 0.9, 1.1]), lengths)
+    U = wl.conserved(5 / 3, rho, [u], p)
+    dt = np.float64 if precision == 64 else np.float32
+    U0 = U.astype(dt)
+    b = hydro_lib.Batch(lengths, 5 / 3, precision=precision)
+    b.set_state(U0)
+    b.run(3, 0.8)
+    assert np.array_equal(b.get_state(), U0)
+    assert b.stats()["newton_iters"] == 0

@@ -294,3 +294,29 @@ def test_wedge_full_size_window(hydro_lib):
         sl = (slice(None), slice(3, k1 - k0), slice(0, j1 - j0 - 3), ri)
         Bw = B[:, k0:k1, j0:j1, r0:r1][sl]
         assert np.all(rel_l1(A[sl], Bw, 3, case["gamma"]) <= TOL[32])
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_runs_are_deterministic(hydro_lib, precision):
+    """Two identical runs give bitwise identical states (the only atomics are
+    the order-independent speed maximum and counters)."""
+    case = wl.smooth_random(3, [37, 23, 40], 1, seed=5, riemann=O.HLLC)
+    outs = []
+    for _ in range(2):
+        g = hydro_lib.Grid.from_case(case, precision)
+        g.run(5, 0.4)
+        outs.append(g.get_state())
+        g.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_fp32_periodic_conservation(hydro_lib):
+    """FP32 bulk with FP64/Kahan totals: mass, momentum and energy of a periodic
+    KH box stay constant to FP32 rounding of the state over 50 steps."""
+    case = wl.kh2d(128, 256)
+    g = hydro_lib.Grid.from_case(dict(case, U=case["U"].astype(np.float32)), 32)
+    T0 = g.totals()
+    g.run(50, 0.4)
+    T1 = g.totals()
+    scale = np.abs(T0).max()
+    assert np.all(np.abs(T1 - T0) <= 2e-6 * scale), (T1 - T0) / scale

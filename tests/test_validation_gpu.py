@@ -1,0 +1,108 @@
+"""Physics validation runs of the paper on the GPU path (next rows f1, f2).
+
+- Sect. 4.3: off-centre Sedov blast on a spherical wedge (gamma = 5/3): the
+  shock stays a sphere about r0 whose radius follows Eq. 25 with xi0 = 1.15.
+- App. C.4: 1D spherical Sedov (gamma = 1.4): shock radius from Eq. 25 with
+  the oracle's xi0(1.4), and the FP64 GPU run equals the oracle's run.
+- App. C.1: Sod at t = 0.2 against the exact solution (the paper's Fig. tube).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_04428_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _offcentre_sedov(n=64):
+    """Spherical wedge r in [0.1,1.3], theta, phi in [pi/4, 3pi/4]; rho0=1, P0=0.01;
+    E1 = 1 in the cell containing (0.7, pi/2, pi/2); transmissive everywhere."""
+    g = 5.0 / 3.0
+    rf = np.linspace(0.1, 1.3, n + 1)
+    af = np.linspace(math.pi / 4, 3 * math.pi / 4, n + 1)
+    rc, ac = 0.5 * (rf[1:] + rf[:-1]), 0.5 * (af[1:] + af[:-1])
+    shape = (n, n, n)
+    rho = np.ones(shape)
+    p = np.full(shape, 0.01)
+    zero = np.zeros(shape)
+    U = wl.conserved(g, rho, [zero, zero, zero], p)
+    i0 = int(np.searchsorted(rf, 0.7) - 1)
+    j0 = int(np.searchsorted(af, math.pi / 2) - 1)
+    dV = (rf[i0 + 1] ** 3 - rf[i0] ** 3) / 3 * (math.cos(af[j0]) - math.cos(af[j0 + 1])) * (af[j0 + 1] - af[j0])
+    U[4, j0, j0, i0] += 1.0 / dV
+    tb = (wl.TRANSMISSIVE, wl.TRANSMISSIVE)
+    case = dict(dim=3, n=[n, n, n], faces=[rf, af, af], bc=[tb, tb, tb], coords=wl.SPHERICAL, gamma=g,
+                n_scalars=0, riemann=wl.HLLC, limiter=wl.MINMOD, sources=None, U=U)
+    centre = np.array([rc[i0] * math.sin(ac[j0]) * math.cos(ac[j0]),
+                       rc[i0] * math.sin(ac[j0]) * math.sin(ac[j0]), rc[i0] * math.cos(ac[j0])])
+    return case, rc, ac, centre
+
+
+def test_offcentre_spherical_sedov_radius(hydro_lib):
+    n = 64
+    case, rc, ac, centre = _offcentre_sedov(n)
+    g = hydro_lib.Grid.from_case(case, 64)
+    t_end = 0.08
+    t = 0.0
+    for _ in range(40):
+        t = g.run(1000, 0.4, t_end=t_end)
+        if t >= t_end:
+            break
+    assert abs(t - t_end) < 1e-12
+    rho = g.get_state()[0]  # (phi, theta, r)
+    R, TH, PH = np.meshgrid(rc, ac, ac, indexing="ij")
+    X = np.stack([R * np.sin(TH) * np.cos(PH), R * np.sin(TH) * np.sin(PH), R * np.cos(TH)], -1)
+    d = np.linalg.norm(X - centre, axis=-1).transpose(2, 1, 0)  # to (phi, theta, r)
+    d_exact = 1.15 * (1.0 * t_end ** 2 / 1.0) ** 0.2
+    # shock position: radius of maximum density along radial rays through the blast
+    bins = np.linspace(0, 0.7, 141)
+    prof = np.array([rho[(d >= a) & (d < b)].mean() if np.any((d >= a) & (d < b)) else 0
+                     for a, b in zip(bins[:-1], bins[1:])])
+    d_shock = 0.5 * (bins[np.argmax(prof)] + bins[np.argmax(prof) + 1])
+    dr = 1.2 / n
+    assert abs(d_shock - d_exact) < 3 * dr, (d_shock, d_exact)
+    # sphericity: the density peak radius seen along the three axes through the blast
+    peaks = []
+    for axis in range(3):
+        sel = np.ones_like(d, dtype=bool)
+        for other in range(3):
+            if other != axis:
+                sel &= np.abs(np.moveaxis(X, -1, 0)[other].transpose(2, 1, 0) - centre[other]) < 1.5 * dr
+        peaks.append(d[sel][np.argmax(rho[sel])])
+    assert max(peaks) - min(peaks) < 4 * dr, peaks
+
+
+def test_spherical_sedov_1d_matches_oracle_and_theory(hydro_lib):
+    case = wl.sedov1d_spherical(400)
+    s = O.solver_from_case(case)
+    t, k = 0.0, 0
+    t_end = 0.7
+    while t < t_end * (1 - 1e-14):
+        dt = min(s.cfl_dt(0.4), t_end - t)
+        s.step(dt)
+        t += dt
+        k += 1
+    g = hydro_lib.Grid.from_case(case, 64)
+    tg = g.run(k + 10, 0.4, t_end=t_end)
+    assert abs(tg - t_end) < 1e-12
+    A, B = s.get_state()[0, 0, 0], g.get_state()[0, 0, 0]
+    assert np.abs(A - B).sum() / np.abs(A).sum() < 1e-9
+    rf = case["faces"][0]
+    rc = 0.5 * (rf[1:] + rf[:-1])
+    r_exact = O.sedov_xi0(1.4) * t_end ** 0.4
+    assert abs(rc[np.argmax(B)] - r_exact) < 3 * (rf[1] - rf[0])
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_sod_matches_exact_solution(hydro_lib, precision):
+    case = wl.sod(1000)
+    dt = np.float64 if precision == 64 else np.float32
+    g = hydro_lib.Grid.from_case(dict(case, U=case["U"].astype(dt)), precision)
+    assert abs(g.run(3000, 0.8, t_end=0.2) - 0.2) < 1e-12
+    rho = g.get_state()[0, 0, 0].astype(np.float64)
+    x = 0.5 * (case["faces"][0][1:] + case["faces"][0][:-1])
+    ex = np.array([O.exact_sample(1.4, [1, 0, 1], [0.125, 0, 0.1], (xx - 0.5) / 0.2)[0] for xx in x])
+    assert np.mean(np.abs(rho - ex)) < 3e-3
