@@ -61,17 +61,35 @@ static int berr(const std::string& m) {
   return HYDRO_ERR_ARG;
 }
 
+// Allow the ring's dynamic shared memory (once per instantiation).
+template <typename T, int NW>
+static int batch_attr() {
+  static bool done = false;
+  if (!done) {
+    HCK(cudaFuncSetAttribute(batched_kernel<T, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batched_smem_bytes<T, NW>()));
+    done = true;
+  }
+  return HYDRO_OK;
+}
+
 template <typename T, int NW>
 static int launch_batch_nw(hydro_ctx* h, const BatchArgs<T>& a, int grid) {
-  batched_kernel<T, NW><<<grid, NW * 32, 0, h->stream>>>(a);
+  int st = batch_attr<T, NW>();
+  if (st) return st;
+  batched_kernel<T, NW><<<grid, NW * 32, batched_smem_bytes<T, NW>(), h->stream>>>(a);
   HCK(cudaGetLastError());
   return HYDRO_OK;
 }
 
 template <typename T>
 static int occupancy_nw(int nw, int* blocks) {
-  if (nw == 4) HCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batched_kernel<T, 4>, 128, 0));
-  else HCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batched_kernel<T, 8>, 256, 0));
+  int st = nw == 4 ? batch_attr<T, 4>() : batch_attr<T, 8>();
+  if (st) return st;
+  if (nw == 4)
+    HCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batched_kernel<T, 4>, 128, batched_smem_bytes<T, 4>()));
+  else
+    HCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batched_kernel<T, 8>, 256, batched_smem_bytes<T, 8>()));
   return HYDRO_OK;
 }
 

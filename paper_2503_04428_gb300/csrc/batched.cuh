@@ -17,7 +17,9 @@
 //     Newton to 1e-10 (FP64) and one polishing step; sample at x/t = 0;
 //   - updates cell c0+l (Eq. 19) and reduces its signal speed.
 // A segment whose whole window is one uniform state takes a short path that
-// returns exactly what the full path returns there (U + 0).
+// returns exactly what the full path returns there (U + 0).  Segment windows
+// are streamed into a per-warp shared-memory ring by cp.async, several
+// segments ahead, so that enough loads are in flight to cover HBM latency.
 // The last CTA to finish commits the step (per-tube speeds, times, buffer).
 #pragma once
 #include "common.cuh"
@@ -25,6 +27,31 @@
 namespace hydro {
 
 constexpr int BSEG = 28;  // cells per warp segment (32 lanes = 28 cells + 2 halo cells each side)
+constexpr int BDEPTH = 8;  // segment windows per warp in the shared-memory ring (BDEPTH-1 in flight)
+
+// Dynamic shared memory of batched_kernel<T, NW>: one ring of BDEPTH windows
+// (3 variables x 32 cells) per warp.
+template <typename T, int NW>
+constexpr size_t batched_smem_bytes() {
+  return (size_t)NW * BDEPTH * 3 * 32 * sizeof(T);
+}
+
+// Asynchronous 4- or 8-byte global -> shared copy (cp.async, completion
+// tracked per thread by commit/wait groups).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(T) == 4) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 struct BatchCtrl {
   Ctrl c;
@@ -115,6 +142,7 @@ template <typename T, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     batched_kernel(const BatchArgs<T> a) {
   __shared__ MlpSmemW sw;
+  extern __shared__ __align__(16) unsigned char ring_raw[];
   const volatile Ctrl* vc = &a.ctrl->c;
   if (vc->status != 0) return;
   const int cur = vc->cur;
@@ -122,6 +150,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
   const T* Uin = cur ? a.B : a.A;
   T* Uout = cur ? a.Aw : a.B;
   const int lane = threadIdx.x & 31;
+  T* ring = reinterpret_cast<T*>(ring_raw) + (threadIdx.x >> 5) * (BDEPTH * 96);
   const Gas<T>& gas = a.gas;
   if (a.mlp_on) {
     for (int p = threadIdx.x; p < MLP_H * MLP_IN; p += NW * 32) sw.w1[p] = a.mlp_w[MW1 + p];
@@ -158,20 +187,30 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     const T dtdx = (T)dtd * fn;
     T smax = T(0);
 
-    // conserved window of the first segment: cells c0-2+lane; the next
-    // segment's window is fetched while the current one is computed
-    T Ua[3];
-    auto fetch = [&](int c0, T* ua) {
-      const int ca = min(max(c0 - 2 + lane, 0), nb - 1);
+    // The conserved window of segment s (cells c0-2+lane, clamped to the
+    // tube: transmissive ends) streams through this warp's ring by cp.async,
+    // BDEPTH-1 segments ahead of the one being computed.  Lane l copies and
+    // later reads only its own ring entries, so its own wait suffices.
+    const int nseg = (s_end - s_beg + BSEG - 1) / BSEG;
+    auto issue = [&](int sg) {
+      if (sg < nseg) {
+        const int ca = min(max(s_beg + sg * BSEG - 2 + lane, 0), nb - 1);
+        T* dst = ring + (sg % BDEPTH) * 96 + lane;
 #pragma unroll
-      for (int v = 0; v < 3; ++v) ua[v] = __ldg(Uin + v * a.total + base + ca);
+        for (int v = 0; v < 3; ++v) cp_async_elem(dst + 32 * v, Uin + v * a.total + base + ca);
+      }
+      cp_async_commit();  // (an empty group when sg is past the item)
     };
-    fetch(s_beg, Ua);
-    for (int c0 = s_beg; c0 < s_end; c0 += BSEG) {
+#pragma unroll
+    for (int sg = 0; sg < BDEPTH - 1; ++sg) issue(sg);
+    for (int sg = 0; sg < nseg; ++sg) {
+      const int c0 = s_beg + sg * BSEG;
+      issue(sg + BDEPTH - 1);      // into the ring slot read one segment ago
+      cp_async_wait<BDEPTH - 1>();  // segment sg has landed
+      T Ua[3];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) Ua[v] = ring[(sg % BDEPTH) * 96 + 32 * v + lane];
       const int ncell = min(BSEG, s_end - c0);  // cells updated in this segment
-      T Un_[3];
-      const bool more = c0 + BSEG < s_end;
-      if (more) fetch(c0 + BSEG, Un_);
       // A window holding one state everywhere (clamped tube ends included)
       // has zero slopes, a +0 Hancock increment, identical face states and
       // equal fluxes, so the full path below returns U + 0 for every cell:
@@ -198,10 +237,6 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
           smax = fmax(smax, (fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * fn);
 #pragma unroll
           for (int v = 0; v < 3; ++v) Uout[v * a.total + c] = u[v];
-        }
-        if (more) {
-#pragma unroll
-          for (int v = 0; v < 3; ++v) Ua[v] = Un_[v];
         }
         continue;
       }
@@ -334,10 +369,6 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
         smax = fmax(smax, (fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * fn);
 #pragma unroll
         for (int v = 0; v < 3; ++v) Uout[v * a.total + c] = u[v];
-      }
-      if (more) {
-#pragma unroll
-        for (int v = 0; v < 3; ++v) Ua[v] = Un_[v];
       }
     }
 #pragma unroll

@@ -3,75 +3,77 @@
 // One kernel launch is one full time step (HERACLES++ Sect. 3.2):
 //   a1 ghost cells, synthesised at load time from the boundary kinds;
 //   a2 primitive recovery (Eq. 5) of every staged cell;
-//   a3/a4 limited slopes (Eq. 17) and the unsplit Hancock predictor (Eq. 18),
-//         whose increment dU is kept in shared memory;
-//   a5 one Riemann solve per face (HLL, HLLC or exact);
+//   a3/a4 limited slopes (Eq. 17) and the unsplit Hancock predictor (Eq. 18);
+//         every predicted face state is formed once, by the cell it belongs
+//         to, and parked in a shared-memory slot of its face;
+//   a5 one Riemann solve per face (HLL, HLLC or exact), whose flux is written
+//      over the face's left state;
 //   a6 conservative update with dS/dV and the spherical sources (Eq. 13-16);
 //   a7/a8 gravity (Eq. 2-4) and heating (Sect. 2.4) from the t^n state;
 //   a9 the signal speed of the new state (max over cells) for the next CFL
 //      time step, committed by the last CTA through the control block.
 //
 // Tiling: a CTA owns TX x TY cells of the (axis0, axis1) plane and, in 3D,
-// marches along axis 2 over `zchunk` planes with rolling shared-memory
-// windows: 5 planes of primitives (halo 2), 3 planes of predictor increments
-// (halo 1) and the fluxes of the current plane's x/y faces plus two z-face
-// planes.  Each value is read from HBM once per CTA (halo re-reads hit L2)
-// and written once.
+// marches along axis 2 over `zchunk` planes.  Shared memory holds a ring of
+// three primitive planes (halo 2 on axes 0/1), the left/right states of the
+// current plane's x and y faces, and the z-face states (lower side: two
+// planes, upper side: one).  Thread t < TX*TY owns tile cell t for the whole
+// march and keeps the partial update of its cell in the plane below in
+// registers until that plane's upper z flux is known.  Each state value is
+// read from HBM once per CTA (halo re-reads hit L2) and written once.
 #pragma once
 #include "common.cuh"
 
 namespace hydro {
 
-// Tile shape per (precision, dimension, scalar slots); NT (threads per CTA)
-// is chosen so that the heavy phases (predictor over the tile plus halo,
-// faces) take few, nearly full rounds of the CTA's threads.
+// Tile shape per (precision, dimension, scalar slots) and the CTAs per SM
+// the register budget is sized for (MB; the exact solver, whose Newton
+// iteration needs more registers, always gets one CTA's budget).  The CTA has one thread per
+// predictor cell (the tile plus a one-cell halo without corners), rounded up
+// to whole warps.
 template <typename T, int DIM, int NSX>
 struct TileCfg;
 // float
-template <> struct TileCfg<float, 1, 0> { static constexpr int TX = 256, TY = 1; };
-template <> struct TileCfg<float, 1, 1> { static constexpr int TX = 256, TY = 1; };
-template <> struct TileCfg<float, 1, 3> { static constexpr int TX = 256, TY = 1; };
-template <> struct TileCfg<float, 2, 0> { static constexpr int TX = 32, TY = 16; };
-template <> struct TileCfg<float, 2, 1> { static constexpr int TX = 32, TY = 16; };
-template <> struct TileCfg<float, 2, 3> { static constexpr int TX = 32, TY = 8; };
-template <> struct TileCfg<float, 3, 0> { static constexpr int TX = 32, TY = 16, NT = 640; };
-template <> struct TileCfg<float, 3, 1> { static constexpr int TX = 32, TY = 8, NT = 384; };
-template <> struct TileCfg<float, 3, 3> { static constexpr int TX = 16, TY = 16, NT = 416; };
+template <> struct TileCfg<float, 1, 0> { static constexpr int TX = 254, TY = 1, MB = 1; };
+template <> struct TileCfg<float, 1, 1> { static constexpr int TX = 254, TY = 1, MB = 1; };
+template <> struct TileCfg<float, 1, 3> { static constexpr int TX = 254, TY = 1, MB = 1; };
+template <> struct TileCfg<float, 2, 0> { static constexpr int TX = 32, TY = 16, MB = 1; };
+template <> struct TileCfg<float, 2, 1> { static constexpr int TX = 32, TY = 16, MB = 1; };
+template <> struct TileCfg<float, 2, 3> { static constexpr int TX = 32, TY = 8, MB = 1; };
+template <> struct TileCfg<float, 3, 0> { static constexpr int TX = 16, TY = 16, MB = 2; };
+template <> struct TileCfg<float, 3, 1> { static constexpr int TX = 16, TY = 16, MB = 2; };
+template <> struct TileCfg<float, 3, 3> { static constexpr int TX = 16, TY = 16, MB = 2; };
 // double
-template <> struct TileCfg<double, 1, 0> { static constexpr int TX = 256, TY = 1; };
-template <> struct TileCfg<double, 1, 1> { static constexpr int TX = 256, TY = 1; };
-template <> struct TileCfg<double, 1, 3> { static constexpr int TX = 256, TY = 1; };
-template <> struct TileCfg<double, 2, 0> { static constexpr int TX = 32, TY = 8; };
-template <> struct TileCfg<double, 2, 1> { static constexpr int TX = 32, TY = 8; };
-template <> struct TileCfg<double, 2, 3> { static constexpr int TX = 32, TY = 8; };
-template <> struct TileCfg<double, 3, 0> { static constexpr int TX = 16, TY = 16, NT = 416; };
-template <> struct TileCfg<double, 3, 1> { static constexpr int TX = 16, TY = 16, NT = 416; };
-template <> struct TileCfg<double, 3, 3> { static constexpr int TX = 16, TY = 8, NT = 224; };
-
-template <typename C, typename = void>
-struct TileThreads { static constexpr int value = C::TX * C::TY; };
-template <typename C>
-struct TileThreads<C, decltype((void)C::NT)> { static constexpr int value = C::NT; };
+template <> struct TileCfg<double, 1, 0> { static constexpr int TX = 254, TY = 1, MB = 1; };
+template <> struct TileCfg<double, 1, 1> { static constexpr int TX = 254, TY = 1, MB = 1; };
+template <> struct TileCfg<double, 1, 3> { static constexpr int TX = 254, TY = 1, MB = 1; };
+template <> struct TileCfg<double, 2, 0> { static constexpr int TX = 32, TY = 8, MB = 1; };
+template <> struct TileCfg<double, 2, 1> { static constexpr int TX = 32, TY = 8, MB = 1; };
+template <> struct TileCfg<double, 2, 3> { static constexpr int TX = 32, TY = 8, MB = 1; };
+template <> struct TileCfg<double, 3, 0> { static constexpr int TX = 16, TY = 16, MB = 1; };
+template <> struct TileCfg<double, 3, 1> { static constexpr int TX = 16, TY = 16, MB = 1; };
+template <> struct TileCfg<double, 3, 3> { static constexpr int TX = 16, TY = 8, MB = 1; };
 
 template <typename T, int DIM, int NSX>
 struct SweepShape {
   static constexpr int NV = 2 + DIM + NSX;
   static constexpr int TX = TileCfg<T, DIM, NSX>::TX;
   static constexpr int TY = TileCfg<T, DIM, NSX>::TY;
-  static constexpr int HY = DIM >= 2 ? 2 : 0;            // primitive halo along axis 1
-  static constexpr int EX = TX + 4, EY = TY + 2 * HY;    // primitive plane extents
-  static constexpr int QY = DIM >= 2 ? 1 : 0;            // predictor halo along axis 1
-  static constexpr int PX = TX + 2, PY = TY + 2 * QY;    // predictor plane extents
-  static constexpr int WP = DIM == 3 ? 5 : 1;            // primitive planes in flight
-  static constexpr int DP = DIM == 3 ? 3 : 1;            // predictor planes in flight
-  static constexpr int NT = TileThreads<TileCfg<T, DIM, NSX>>::value;  // threads per CTA
-  static constexpr int WPL = EX * EY, DPL = PX * PY;
+  static constexpr int HY = DIM >= 2 ? 2 : 0;              // primitive halo along axis 1
+  static constexpr int EX = TX + 4, EY = TY + 2 * HY;      // primitive plane extents
+  static constexpr int QY = DIM >= 2 ? 1 : 0;              // predictor halo along axis 1
+  static constexpr int WP = DIM == 3 ? 3 : 1;              // primitive planes in flight
+  static constexpr int NI = TX * TY;                        // tile cells, one owner thread each
+  static constexpr int NH = 2 * TY + (DIM >= 2 ? 2 * TX : 0);  // halo predictor cells
+  static constexpr int NP = NI + NH;                        // predictor cells
+  static constexpr int NT = (NP + 31) / 32 * 32;            // threads per CTA
+  static constexpr int MB = TileCfg<T, DIM, NSX>::MB;       // resident CTAs per SM (register budget)
+  static constexpr int WPL = EX * EY;
   static constexpr int NFX = (TX + 1) * TY;
   static constexpr int NFY = DIM >= 2 ? TX * (TY + 1) : 0;
   static constexpr int NFZ = DIM == 3 ? TX * TY : 0;
-  static constexpr size_t smem_elems =
-      (size_t)WP * NV * WPL + (size_t)DP * NV * DPL + (size_t)NV * NFX + (size_t)NV * NFY +
-      (size_t)2 * NV * NFZ;
+  static constexpr size_t smem_elems = (size_t)WP * NV * WPL + (size_t)2 * NV * NFX +
+                                       (size_t)2 * NV * NFY + (size_t)3 * NV * NFZ;
   static constexpr size_t smem_bytes = smem_elems * sizeof(T);
 };
 
@@ -94,19 +96,25 @@ __device__ __forceinline__ int map_axis(int g, int n, int lo, int hi, bool& flip
   return g;
 }
 
+// Which face states a predictor pass writes.
+enum { PRED_ALL = 0, PRED_ZHI = 1, PRED_ZLO = 2 };
+
 template <typename T, int DIM, int NSX, int RS>
 struct Sweep {
   using S = SweepShape<T, DIM, NSX>;
-  static constexpr int NV = S::NV, TX = S::TX, TY = S::TY, EX = S::EX, EY = S::EY, PX = S::PX,
-                       PY = S::PY, HY = S::HY, QY = S::QY, NT = S::NT;
+  static constexpr int NV = S::NV, TX = S::TX, TY = S::TY, EX = S::EX, EY = S::EY, HY = S::HY,
+                       QY = S::QY, NT = S::NT, NI = S::NI, NP = S::NP, NFX = S::NFX,
+                       NFY = S::NFY, NFZ = S::NFZ;
 
   const SweepArgs<T>& a;
-  T* Ws;
-  T* Ds;
-  T* Fx;
-  T* Fy;
-  T* Fz;
-  int x0, y0;
+  T* Ws;  // primitive planes [slot][v][ey][ex]
+  T* XL;  // x faces [v][row*(TX+1)+f]: left state, then the flux
+  T* XR;  // x faces: right state
+  T* YL;  // y faces [v][fy*TX+col]: left (lower) state, then the flux
+  T* YR;
+  T* ZL;  // [2][v][j*TX+i]: state below the z face above plane (slot = plane & 1)
+  T* ZR;  // [v][j*TX+i]: state above the z face below the current plane, then the flux
+  int x0, y0, z1, n2;
   T dt, half_dt;
   const T* Uin;
   T* Uout;
@@ -114,23 +122,26 @@ struct Sweep {
   int err = 0;
   double smax = 0.0;
   T hfac = T(0);
+  // owner registers: partial update of the owned cell, its predictor
+  // increment (1D/2D) and the spherical partial sums of Eq. 13-16
+  T acc[NV];
+  T dUo[NV];
+  T fzb3 = T(0), tth = T(0), x2 = T(0), s3 = T(0);
 
   __device__ Sweep(const SweepArgs<T>& args, T* smem) : a(args) {
     Ws = smem;
-    Ds = Ws + S::WP * NV * S::WPL;
-    Fx = Ds + S::DP * NV * S::DPL;
-    Fy = Fx + NV * S::NFX;
-    Fz = Fy + NV * S::NFY;
+    XL = Ws + S::WP * NV * S::WPL;
+    XR = XL + NV * NFX;
+    YL = XR + NV * NFX;
+    YR = YL + NV * NFY;
+    ZL = YR + NV * NFY;
+    ZR = ZL + 2 * NV * NFZ;
   }
 
   __device__ __forceinline__ T& W(int slot, int v, int ey, int ex) {
     return Ws[((slot * NV + v) * EY + ey) * EX + ex];
   }
-  __device__ __forceinline__ T& Dq(int slot, int v, int py, int px) {
-    return Ds[((slot * NV + v) * PY + py) * PX + px];
-  }
-  static __device__ __forceinline__ int wslot(int gz) { return DIM == 3 ? (gz + 10) % 5 : 0; }
-  static __device__ __forceinline__ int dslot(int gz) { return DIM == 3 ? (gz + 6) % 3 : 0; }
+  static __device__ __forceinline__ int wslot(int gz) { return DIM == 3 ? (gz + 6) % 3 : 0; }
 
   // a1 + a2: stage plane gz (axis-2 index, may be a ghost) as primitives.
   __device__ void load_plane(int gz) {
@@ -185,96 +196,164 @@ struct Sweep {
     }
   }
 
-  // Neighbour fetch of the primitive plane data.
-  template <int DIR>
-  __device__ __forceinline__ void neighbours(int slot, int ey, int ex, int gz, T* Wm, T* Wc,
-                                             T* Wp) {
+  // Predictor cell of item t: (px, py) in the (TX+2) x (TY+2QY) region around
+  // the tile.  Items 0..NI-1 are the tile cells in owner order, then the
+  // axis-0 halo columns, then the axis-1 halo rows (corners are never needed).
+  static __device__ __forceinline__ void item_cell(int t, int& px, int& py) {
+    if (t < NI) {
+      px = 1 + t % TX;
+      py = QY + t / TX;
+      return;
+    }
+    int h = t - NI;
+    if (h < 2 * TY) {
+      px = h < TY ? 0 : TX + 1;
+      py = QY + (h < TY ? h : h - TY);
+      return;
+    }
+    h -= 2 * TY;
+    px = 1 + (h < TX ? h : h - TX);
+    py = h < TX ? 0 : TY + 1;
+  }
+
+  // Turn the limited state parked at p (stride `st`) into the predicted face
+  // state: W -> U, + dU, U -> W; a non-physical result falls back to Wc.
+  __device__ __forceinline__ void finish_state(T* p, int st, const T* Wc, const T* dU, bool owned) {
+    T w[NV], u[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = p[v * st];
+    to_cons<T, DIM, NSX>(w, u, a.gas);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] += dU[v];
+    to_prim<T, DIM, NSX>(u, w, a.gas);
+    if (!(w[0] > T(0)) || !(w[1 + DIM] > T(0))) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w[v] = Wc[v];
+      if (owned) ++n_fallback;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) p[v * st] = w[v];
+  }
+
+  // a3 + a4 for plane gz: the predictor increment dU = dt/2 sum_d
+  // (F_d(W_lo) - F_d(W_hi))/h_d of every needed cell, and its predicted face
+  // states.  PRED_ALL: tile plus halo, every face state of the plane;
+  // PRED_ZHI / PRED_ZLO: tile cells only, the upper / lower z state.
+  template <int MODE>
+  __device__ void predictor(int gz) {
+    const int t = threadIdx.x;
+    if (t >= (MODE == PRED_ALL ? NP : NI)) return;
+    const int n0 = a.n[0], n1 = a.n[1];
+    int px, py;
+    item_cell(t, px, py);
+    const int gi = x0 - 1 + px;
+    const int gj = DIM >= 2 ? y0 - 1 + py : 0;
+    if (gi > n0 || (DIM >= 2 && gj > n1)) return;
+    const int slot = wslot(gz);
+    const int ex = px + 1, ey = py + (HY - QY);
+    const bool trow = DIM < 2 || (py >= 1 && py <= TY);  // a tile row
+    const bool tcol = px >= 1 && px <= TX;               // a tile column
+    const bool rreal = DIM < 2 || gj < n1;               // a domain row
+    const bool creal = gi < n0;                          // a domain column
+    const int row = py - QY, col = px - 1;
+    // face-state slots written by this cell
+    const bool xlo = MODE == PRED_ALL && px >= 1 && trow && rreal;
+    const bool xhi = MODE == PRED_ALL && px <= TX && trow && rreal && creal;
+    const bool ylo = DIM >= 2 && MODE == PRED_ALL && py >= 1 && tcol && creal;
+    const bool yhi = DIM >= 2 && MODE == PRED_ALL && py <= TY && tcol && creal && rreal;
+    const bool zin = DIM == 3 && tcol && trow && creal && rreal;
+    const bool zlo = zin && MODE != PRED_ZHI;
+    const bool zhi = zin && MODE != PRED_ZLO;
+    const int ixlo = row * (TX + 1) + px - 1, ixhi = ixlo + 1;
+    const int iylo = (py - 1) * TX + col, iyhi = iylo + TX;
+    const int iz = row * TX + col;
+    T* zhp = ZL + (gz & 1) * NV * NFZ;
+
+    T Wc[NV], dU[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       Wc[v] = W(slot, v, ey, ex);
-      if (DIR == 0) {
+      dU[v] = T(0);
+    }
+    {
+      T Wm[NV], Wp[NV], Wl[NV], Wh[NV], Fl[NV], Fh[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
         Wm[v] = W(slot, v, ey, ex - 1);
         Wp[v] = W(slot, v, ey, ex + 1);
-      } else if (DIR == 1) {
+      }
+      faces_of<0>(Wm, Wc, Wp, gi, Wl, Wh);
+      phys_flux<T, DIM, NSX, 0>(Wl, Fl, a.gas);
+      phys_flux<T, DIM, NSX, 0>(Wh, Fh, a.gas);
+      const T ih = inv_h(0, gi, gj, gz);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        dU[v] += (Fl[v] - Fh[v]) * ih;
+        if (xlo) XR[v * NFX + ixlo] = Wl[v];
+        if (xhi) XL[v * NFX + ixhi] = Wh[v];
+      }
+    }
+    if constexpr (DIM >= 2) {
+      T Wm[NV], Wp[NV], Wl[NV], Wh[NV], Fl[NV], Fh[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
         Wm[v] = W(slot, v, ey - 1, ex);
         Wp[v] = W(slot, v, ey + 1, ex);
-      } else {
+      }
+      faces_of<1>(Wm, Wc, Wp, gj, Wl, Wh);
+      phys_flux<T, DIM, NSX, 1>(Wl, Fl, a.gas);
+      phys_flux<T, DIM, NSX, 1>(Wh, Fh, a.gas);
+      const T ih = inv_h(1, gi, gj, gz);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        dU[v] += (Fl[v] - Fh[v]) * ih;
+        if (ylo) YR[v * NFY + iylo] = Wl[v];
+        if (yhi) YL[v * NFY + iyhi] = Wh[v];
+      }
+    }
+    if constexpr (DIM == 3) {
+      T Wm[NV], Wp[NV], Wl[NV], Wh[NV], Fl[NV], Fh[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
         Wm[v] = W(wslot(gz - 1), v, ey, ex);
         Wp[v] = W(wslot(gz + 1), v, ey, ex);
       }
+      faces_of<2>(Wm, Wc, Wp, gz, Wl, Wh);
+      phys_flux<T, DIM, NSX, 2>(Wl, Fl, a.gas);
+      phys_flux<T, DIM, NSX, 2>(Wh, Fh, a.gas);
+      const T ih = inv_h(2, gi, gj, gz);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        dU[v] += (Fl[v] - Fh[v]) * ih;
+        if (zlo) ZR[v * NFZ + iz] = Wl[v];
+        if (zhi) zhp[v * NFZ + iz] = Wh[v];
+      }
     }
-  }
-
-  // a3 + a4: predictor increment dU = dt/2 sum_d (F_d(W_lo) - F_d(W_hi))/h_d
-  // for plane gz over the tile plus a one-cell halo.
-  __device__ void predictor_plane(int gz) {
-    const int n0 = a.n[0], n1 = a.n[1];
-    const int slot = wslot(gz), ds = dslot(gz);
-    for (int idx = threadIdx.x; idx < S::DPL; idx += NT) {
-      const int px = idx % PX, py = idx / PX;
-      const int gi = x0 - 1 + px;
-      const int gj = DIM >= 2 ? y0 - 1 + py : 0;
-      if (gi > n0 || (DIM >= 2 && gj > n1)) continue;
-      const int ex = px + 1, ey = py + (DIM >= 2 ? 1 : 0);
-      T acc[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] = T(0);
-      {
-        T Wm[NV], Wc[NV], Wp[NV], Wl[NV], Wh[NV], Fl[NV], Fh[NV];
-        neighbours<0>(slot, ey, ex, gz, Wm, Wc, Wp);
-        faces_of<0>(Wm, Wc, Wp, gi, Wl, Wh);
-        phys_flux<T, DIM, NSX, 0>(Wl, Fl, a.gas);
-        phys_flux<T, DIM, NSX, 0>(Wh, Fh, a.gas);
-        const T ih = inv_h(0, gi, gj, gz);
+    for (int v = 0; v < NV; ++v) dU[v] = half_dt * dU[v];
+    if constexpr (DIM < 3) {
+      if (t < NI) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] += (Fl[v] - Fh[v]) * ih;
+        for (int v = 0; v < NV; ++v) dUo[v] = dU[v];
       }
-      if constexpr (DIM >= 2) {
-        T Wm[NV], Wc[NV], Wp[NV], Wl[NV], Wh[NV], Fl[NV], Fh[NV];
-        neighbours<1>(slot, ey, ex, gz, Wm, Wc, Wp);
-        faces_of<1>(Wm, Wc, Wp, gj, Wl, Wh);
-        phys_flux<T, DIM, NSX, 1>(Wl, Fl, a.gas);
-        phys_flux<T, DIM, NSX, 1>(Wh, Fh, a.gas);
-        const T ih = inv_h(1, gi, gj, gz);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] += (Fl[v] - Fh[v]) * ih;
-      }
-      if constexpr (DIM == 3) {
-        T Wm[NV], Wc[NV], Wp[NV], Wl[NV], Wh[NV], Fl[NV], Fh[NV];
-        neighbours<2>(slot, ey, ex, gz, Wm, Wc, Wp);
-        faces_of<2>(Wm, Wc, Wp, gz, Wl, Wh);
-        phys_flux<T, DIM, NSX, 2>(Wl, Fl, a.gas);
-        phys_flux<T, DIM, NSX, 2>(Wh, Fh, a.gas);
-        const T ih = inv_h(2, gi, gj, gz);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] += (Fl[v] - Fh[v]) * ih;
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) Dq(ds, v, py, px) = half_dt * acc[v];
     }
-  }
-
-  // Predicted face state (primitive) on side HI (1) or LO (0) of a cell.
-  // A non-physical prediction falls back to the cell average.
-  template <int DIR, int HI>
-  __device__ __forceinline__ void face_state(int slot, int ey, int ex, int gz, int ds, int py,
-                                             int px, int g, T* Wf) {
-    T Wm[NV], Wc[NV], Wp[NV], Wl[NV], Wh[NV], U[NV];
-    neighbours<DIR>(slot, ey, ex, gz, Wm, Wc, Wp);
-    faces_of<DIR>(Wm, Wc, Wp, g, Wl, Wh);
-    to_cons<T, DIM, NSX>(HI ? Wh : Wl, U, a.gas);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) U[v] += Dq(ds, v, py, px);
-    to_prim<T, DIM, NSX>(U, Wf, a.gas);
-    if (!(Wf[0] > T(0)) || !(Wf[1 + DIM] > T(0))) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) Wf[v] = Wc[v];
-      ++n_fallback;
+    // A face is counted (fallbacks, Newton iterations) by the one CTA that
+    // owns it: its tile's faces except the upper edge, unless that is the
+    // domain's last face.
+    if (xlo) finish_state(XR + ixlo, NFX, Wc, dU, px - 1 < TX || gi == n0);
+    if (xhi) finish_state(XL + ixhi, NFX, Wc, dU, px < TX || gi + 1 == n0);
+    if constexpr (DIM >= 2) {
+      if (ylo) finish_state(YR + iylo, NFY, Wc, dU, py - 1 < TY || gj == n1);
+      if (yhi) finish_state(YL + iyhi, NFY, Wc, dU, py < TY || gj + 1 == n1);
+    }
+    if constexpr (DIM == 3) {
+      if (zlo) finish_state(ZR + iz, NFZ, Wc, dU, gz < z1 || gz == n2);
+      if (zhi) finish_state(zhp + iz, NFZ, Wc, dU, gz + 1 < z1 || gz + 1 == n2);
     }
   }
 
   template <int DIR>
-  __device__ __forceinline__ void riemann(const T* WL, const T* WR, T* F) {
+  __device__ __forceinline__ void riemann(const T* WL, const T* WR, T* F, bool owned) {
     if constexpr (RS == RS_HLL) {
       riemann_hll<T, DIM, NSX, DIR>(WL, WR, F, a.gas);
     } else if constexpr (RS == RS_HLLC) {
@@ -282,176 +361,192 @@ struct Sweep {
     } else {
       int it = 0, kind = 0;
       const int st = riemann_exact<T, DIM, NSX, DIR>(WL, WR, F, a.gas, T(0), it, kind);
-      n_iters += it;
+      if (owned) n_iters += it;
       if (st != ST_OK && err == 0) err = st;
     }
   }
 
-  // The face between axis-2 planes zl and zl+1 (3D only), into Fz[(zl+1)&1].
-  __device__ void zfaces(int zl) {
+  // a5: one Riemann solve per face, the flux written over the left state.
+  // XY: the x and y faces of the current plane; Z: the z face below plane gz.
+  template <bool XY, bool Z>
+  __device__ void faces(int gz) {
     const int n0 = a.n[0], n1 = a.n[1];
-    T* Fzo = Fz + ((zl + 1) & 1) * NV * S::NFZ;
-    for (int idx = threadIdx.x; idx < S::NFZ; idx += NT) {
-      const int fi = idx % TX, fj = idx / TX;
-      if (x0 + fi >= n0 || y0 + fj >= n1) continue;
+    constexpr int NXY = XY ? NFX + NFY : 0;
+    constexpr int NALL = NXY + (Z ? NFZ : 0);
+    const T* zlp = ZL + ((gz - 1) & 1) * NV * NFZ;
+    for (int idx = threadIdx.x; idx < NALL; idx += NT) {
       T WL[NV], WR[NV], F[NV];
-      face_state<2, 1>(wslot(zl), fj + HY, fi + 2, zl, dslot(zl), fj + QY, fi + 1, zl, WL);
-      face_state<2, 0>(wslot(zl + 1), fj + HY, fi + 2, zl + 1, dslot(zl + 1), fj + QY, fi + 1, zl + 1, WR);
-      riemann<2>(WL, WR, F);
+      if (XY && idx < NFX) {
+        const int f = idx % (TX + 1), row = idx / (TX + 1);
+        if (x0 + f > n0 || (DIM >= 2 && y0 + row >= n1)) continue;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Fzo[v * S::NFZ + idx] = F[v];
-    }
-  }
-
-  // a5 for the x and y faces of plane gz and, in 3D, its top z face, in one
-  // loop over all of them.
-  __device__ void faces_plane(int gz) {
-    const int n0 = a.n[0], n1 = a.n[1];
-    const int slot = wslot(gz), ds = dslot(gz);
-    T* Fzo = Fz + ((gz + 1) & 1) * NV * S::NFZ;
-    for (int idx = threadIdx.x; idx < S::NFX + S::NFY + S::NFZ; idx += NT) {
-      T WL[NV], WR[NV], F[NV];
-      if (DIM == 3 && idx >= S::NFX + S::NFY) {
-        const int k = idx - S::NFX - S::NFY;
-        const int fi = k % TX, fj = k / TX;
-        if (x0 + fi >= n0 || y0 + fj >= n1) continue;
-        face_state<2, 1>(slot, fj + HY, fi + 2, gz, ds, fj + QY, fi + 1, gz, WL);
-        face_state<2, 0>(wslot(gz + 1), fj + HY, fi + 2, gz + 1, dslot(gz + 1), fj + QY, fi + 1, gz + 1, WR);
-        riemann<2>(WL, WR, F);
+        for (int v = 0; v < NV; ++v) {
+          WL[v] = XL[v * NFX + idx];
+          WR[v] = XR[v * NFX + idx];
+        }
+        riemann<0>(WL, WR, F, f < TX || x0 + f == n0);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Fzo[v * S::NFZ + k] = F[v];
-      } else if (idx < S::NFX) {
-        const int fi = idx % (TX + 1), fj = idx / (TX + 1);
-        if (x0 + fi > n0 || (DIM >= 2 && y0 + fj >= n1)) continue;
-        const int gi = x0 + fi, gj = y0 + fj;
-        face_state<0, 1>(slot, fj + HY, fi + 1, gz, ds, fj + QY, fi, gi - 1, WL);
-        face_state<0, 0>(slot, fj + HY, fi + 2, gz, ds, fj + QY, fi + 1, gi, WR);
-        (void)gj;
-        riemann<0>(WL, WR, F);
+        for (int v = 0; v < NV; ++v) XL[v * NFX + idx] = F[v];
+      } else if (XY && DIM >= 2 && idx < NXY) {
+        const int k = idx - NFX;
+        const int col = k % TX, fy = k / TX;
+        if (x0 + col >= n0 || y0 + fy > n1) continue;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Fx[v * S::NFX + idx] = F[v];
-      } else if constexpr (DIM >= 2) {
-        const int k = idx - S::NFX;
-        const int fi = k % TX, fj = k / TX;
-        if (x0 + fi >= n0 || y0 + fj > n1) continue;
-        const int gj = y0 + fj;
-        face_state<1, 1>(slot, fj - 1 + HY, fi + 2, gz, ds, fj - 1 + QY, fi + 1, gj - 1, WL);
-        face_state<1, 0>(slot, fj + HY, fi + 2, gz, ds, fj + QY, fi + 1, gj, WR);
-        riemann<1>(WL, WR, F);
+        for (int v = 0; v < NV; ++v) {
+          WL[v] = YL[v * NFY + k];
+          WR[v] = YR[v * NFY + k];
+        }
+        riemann<(DIM >= 2 ? 1 : 0)>(WL, WR, F, fy < TY || y0 + fy == n1);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Fy[v * S::NFY + k] = F[v];
+        for (int v = 0; v < NV; ++v) YL[v * NFY + k] = F[v];
+      } else if (DIM == 3 && Z) {
+        const int k = idx - NXY;
+        const int i = k % TX, j = k / TX;
+        if (x0 + i >= n0 || y0 + j >= n1) continue;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          WL[v] = zlp[v * NFZ + k];
+          WR[v] = ZR[v * NFZ + k];
+        }
+        riemann<(DIM == 3 ? 2 : 0)>(WL, WR, F, gz < z1 || gz == n2);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ZR[v * NFZ + k] = F[v];
       }
     }
   }
 
-  // a6-a9: update plane gz.
-  __device__ void update_plane(int gz) {
+  // a6 flux differences of the owned cell (i, j) from the x and y faces of
+  // the current plane, plus (3D) the lower z face of plane gz; also the
+  // spherical partial sums that use these fluxes.
+  __device__ __forceinline__ void open_cell(int gz, int i, int j, int gi, int gj) {
+    const int fx = j * (TX + 1) + i;
+    const T Afl = a.geo.Af[gi], Afh = a.geo.Af[gi + 1], ia = a.geo.inva[gi];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = (XL[v * NFX + fx] * Afl - XL[v * NFX + fx + 1] * Afh) * ia;
+    if constexpr (DIM >= 2) {
+      const T Bfl = a.geo.Bf[gj], Bfh = a.geo.Bf[gj + 1];
+      const T cy = a.geo.ga[gi] * a.geo.invb[gj];
+      const int fy = j * TX + i;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += (YL[v * NFY + fy] * Bfl - YL[v * NFY + fy + TX] * Bfh) * cy;
+      if (a.spherical) {
+        tth = T(0.5) * (YL[2 * NFY + fy] + YL[2 * NFY + fy + TX]);
+        x2 = XL[2 * NFX + fx + 1] * Afh + XL[2 * NFX + fx] * Afl;
+        if constexpr (DIM == 3) {
+          const T frl = XL[3 * NFX + fx], frh = XL[3 * NFX + fx + 1];
+          const T ftl = YL[3 * NFY + fy], fth = YL[3 * NFY + fy + TX];
+          s3 = -a.geo.qr[gi] * (frh * Afh + frl * Afl) - a.geo.ga[gi] * a.geo.qt[gj] * (fth * Bfh + ftl * Bfl);
+        }
+      }
+    }
+    if constexpr (DIM == 3) {
+      const int iz = j * TX + i;
+      const T cz = a.geo.ga[gi] * a.geo.zc[gj] * a.geo.invc[gz];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += ZR[v * NFZ + iz] * cz;
+      fzb3 = ZR[3 * NFZ + iz];
+    }
+  }
+
+  // a6-a9: the new state of the owned cell (i, j) of plane gz from acc, the
+  // sources, the validity checks and the signal speed.  fzt3 = the axis-2
+  // momentum flux of the upper z face (3D).
+  __device__ void close_cell(int gz, int i, int j, int gi, int gj, T fzt3) {
     const int n0 = a.n[0], n1 = a.n[1];
     const int nvact = 2 + DIM + a.ns;
-    const T* Fzb = Fz + (gz & 1) * NV * S::NFZ;
-    const T* Fzt = Fz + ((gz + 1) & 1) * NV * S::NFZ;
-    for (int idx = threadIdx.x; idx < TX * TY; idx += NT) {
-      const int i = idx % TX, j = idx / TX;
-      const int gi = x0 + i, gj = y0 + j;
-      if (gi >= n0 || gj >= n1) continue;
-      const long long c = ((long long)gz * n1 + gj) * n0 + gi;
-      T Uo[NV], Un[NV], acc[NV];
+    const long long c = ((long long)gz * n1 + gj) * n0 + gi;
+    T Uo[NV], Un[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Uo[v] = v < nvact ? Uin[(long long)v * a.ncell + c] : T(0);
-      const int fx = j * (TX + 1) + i;
-      const T Afl = a.geo.Af[gi], Afh = a.geo.Af[gi + 1], ia = a.geo.inva[gi];
+    for (int v = 0; v < NV; ++v) Uo[v] = v < nvact ? Uin[(long long)v * a.ncell + c] : T(0);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] = (Fx[v * S::NFX + fx] * Afl - Fx[v * S::NFX + fx + 1] * Afh) * ia;
-      T cy = T(0), Bfl = T(1), Bfh = T(1);
-      if constexpr (DIM >= 2) {
-        Bfl = a.geo.Bf[gj];
-        Bfh = a.geo.Bf[gj + 1];
-        cy = a.geo.ga[gi] * a.geo.invb[gj];
-        const int fy = j * TX + i;
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-          acc[v] += (Fy[v * S::NFY + fy] * Bfl - Fy[v * S::NFY + fy + TX] * Bfh) * cy;
-      }
-      if constexpr (DIM == 3) {
-        const T cz = a.geo.ga[gi] * a.geo.zc[gj] * a.geo.invc[gz];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] += (Fzb[v * S::NFZ + idx] - Fzt[v * S::NFZ + idx]) * cz;
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) Un[v] = Uo[v] + dt * acc[v];
+    for (int v = 0; v < NV; ++v) Un[v] = Uo[v] + dt * acc[v];
 
-      if (a.spherical) {
-        // Geometric momentum sources, Eq. 13-16 (face-flux forms).  An absent
-        // axis uses the pressure of the half-step cell state U + dU (or of U
-        // if that state is not physical).
-        T P = T(0);
-        if constexpr (DIM < 3) {
-          T Uh[NV], Wh[NV], Wo[NV];
+    if (a.spherical) {
+      // Geometric momentum sources, Eq. 13-16 (face-flux forms).  An absent
+      // axis uses the pressure of the half-step cell state U + dU (or of U
+      // if that state is not physical).
+      T P = T(0);
+      if constexpr (DIM < 3) {
+        T Uh[NV], Wh[NV], Wo[NV];
 #pragma unroll
-          for (int v = 0; v < NV; ++v) Uh[v] = Uo[v] + Dq(dslot(gz), v, j + QY, i + 1);
-          to_prim<T, DIM, NSX>(Uh, Wh, a.gas);
-          to_prim<T, DIM, NSX>(Uo, Wo, a.gas);
-          P = (Wh[0] > T(0) && Wh[1 + DIM] > T(0)) ? Wh[1 + DIM] : Wo[1 + DIM];
-        }
-        T Tth = P, Tph = P;
-        if constexpr (DIM >= 2) Tth = T(0.5) * (Fy[2 * S::NFY + j * TX + i] + Fy[2 * S::NFY + j * TX + i + TX]);
-        if constexpr (DIM == 3) Tph = T(0.5) * (Fzb[3 * S::NFZ + idx] + Fzt[3 * S::NFZ + idx]);
-        Un[1] += dt * T(0.5) * (Tth + Tph) * a.geo.gr[gi];
-        if constexpr (DIM >= 2) {
-          const T frl = Fx[2 * S::NFX + fx], frh = Fx[2 * S::NFX + fx + 1];
-          Un[2] += dt * (-a.geo.qr[gi] * (frh * Afh + frl * Afl) + Tph * a.geo.ga[gi] * a.geo.gt[gj]);
-        }
-        if constexpr (DIM == 3) {
-          const T frl = Fx[3 * S::NFX + fx], frh = Fx[3 * S::NFX + fx + 1];
-          const T ftl = Fy[3 * S::NFY + j * TX + i], fth = Fy[3 * S::NFY + j * TX + i + TX];
-          Un[3] += dt * (-a.geo.qr[gi] * (frh * Afh + frl * Afl) -
-                         a.geo.ga[gi] * a.geo.qt[gj] * (fth * Bfh + ftl * Bfl));
-        }
+        for (int v = 0; v < NV; ++v) Uh[v] = Uo[v] + dUo[v];
+        to_prim<T, DIM, NSX>(Uh, Wh, a.gas);
+        to_prim<T, DIM, NSX>(Uo, Wo, a.gas);
+        P = (Wh[0] > T(0) && Wh[1 + DIM] > T(0)) ? Wh[1 + DIM] : Wo[1 + DIM];
       }
-      if (a.gravity != GRAV_NONE) {
-        T g[3] = {T(0), T(0), T(0)};
-        if (a.gravity == GRAV_UNIFORM) {
+      T Tth = P, Tph = P;
+      if constexpr (DIM >= 2) Tth = tth;
+      if constexpr (DIM == 3) Tph = T(0.5) * (fzb3 + fzt3);
+      Un[1] += dt * T(0.5) * (Tth + Tph) * a.geo.gr[gi];
+      if constexpr (DIM >= 2) Un[2] += dt * (-a.geo.qr[gi] * x2 + Tph * a.geo.ga[gi] * a.geo.gt[gj]);
+      if constexpr (DIM == 3) Un[3] += dt * s3;
+    }
+    if (a.gravity != GRAV_NONE) {
+      T g[3] = {T(0), T(0), T(0)};
+      if (a.gravity == GRAV_UNIFORM) {
 #pragma unroll
-          for (int d = 0; d < DIM; ++d) g[d] = a.g0[d];
-        } else if (a.gravity == GRAV_POINT) {
-          g[0] = a.geo.gpt[gi];
-        } else {
-          g[0] = a.gmono[gi];
-        }
-        T work = T(0);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          Un[1 + d] += dt * Uo[0] * g[d];
-          work += Uo[1 + d] * g[d];
-        }
-        Un[1 + DIM] += dt * work;
+        for (int d = 0; d < DIM; ++d) g[d] = a.g0[d];
+      } else if (a.gravity == GRAV_POINT) {
+        g[0] = a.geo.gpt[gi];
+      } else {
+        g[0] = a.gmono[gi];
       }
-      if (a.heating == HEAT_CONST) {
-        Un[1 + DIM] += dt * a.heat_q;
-      } else if (a.heating == HEAT_NI56) {
-        T rf = T(0);
+      T work = T(0);
 #pragma unroll
-        for (int s = 0; s < NSX; ++s)
-          if (s == a.ni_index) rf = Uo[2 + DIM + s];
-        Un[1 + DIM] += dt * hfac * rf;
+      for (int d = 0; d < DIM; ++d) {
+        Un[1 + d] += dt * Uo[0] * g[d];
+        work += Uo[1 + d] * g[d];
       }
+      Un[1 + DIM] += dt * work;
+    }
+    if (a.heating == HEAT_CONST) {
+      Un[1 + DIM] += dt * a.heat_q;
+    } else if (a.heating == HEAT_NI56) {
+      T rf = T(0);
+#pragma unroll
+      for (int s = 0; s < NSX; ++s)
+        if (s == a.ni_index) rf = Uo[2 + DIM + s];
+      Un[1 + DIM] += dt * hfac * rf;
+    }
 
-      // validity and the signal speed of the new state
-      T Wn[NV];
-      to_prim<T, DIM, NSX>(Un, Wn, a.gas);
-      bool finite = true;
+    // validity and the signal speed of the new state
+    T Wn[NV];
+    to_prim<T, DIM, NSX>(Un, Wn, a.gas);
+    bool finite = true;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) finite = finite && isfinite(Un[v]);
-      if (!finite) err = err ? err : ST_NONFINITE;
-      else if (!(Wn[0] > T(0)) || !(Wn[1 + DIM] > T(0))) err = err ? err : ST_NEG;
-      const T cs = dsqrt(a.gas.g * Wn[1 + DIM] / Wn[0]);
-      T sp = T(0);
+    for (int v = 0; v < NV; ++v) finite = finite && isfinite(Un[v]);
+    if (!finite) err = err ? err : ST_NONFINITE;
+    else if (!(Wn[0] > T(0)) || !(Wn[1 + DIM] > T(0))) err = err ? err : ST_NEG;
+    const T cs = dsqrt(a.gas.g * Wn[1 + DIM] / Wn[0]);
+    T sp = T(0);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) sp += (fabs(Wn[1 + d]) + cs) * inv_h(d, gi, gj, gz);
-      smax = fmax(smax, (double)sp);
+    for (int d = 0; d < DIM; ++d) sp += (fabs(Wn[1 + d]) + cs) * inv_h(d, gi, gj, gz);
+    smax = fmax(smax, (double)sp);
 #pragma unroll
-      for (int v = 0; v < NV; ++v)
-        if (v < nvact) Uout[(long long)v * a.ncell + c] = Un[v];
+    for (int v = 0; v < NV; ++v)
+      if (v < nvact) Uout[(long long)v * a.ncell + c] = Un[v];
+  }
+
+  // The owner's work after the face solves of plane gz: in 3D, close the
+  // cell of plane gz-1 with the flux of the z face between them and open
+  // the cell of plane gz; in 1D/2D both in one go.
+  __device__ void owner_step(int gz, bool close_prev, bool open_cur) {
+    const int t = threadIdx.x;
+    if (t >= NI) return;
+    const int i = t % TX, j = t / TX;
+    const int gi = x0 + i, gj = y0 + j;
+    if (gi >= a.n[0] || (DIM >= 2 && gj >= a.n[1])) return;
+    if constexpr (DIM == 3) {
+      if (close_prev) {
+        const T cz = a.geo.ga[gi] * a.geo.zc[gj] * a.geo.invc[gz - 1];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] -= ZR[v * NFZ + t] * cz;
+        close_cell(gz - 1, i, j, gi, gj, ZR[3 * NFZ + t]);
+      }
+      if (open_cur) open_cell(gz, i, j, gi, gj);
+    } else {
+      open_cell(0, i, j, gi, gj);
+      close_cell(0, i, j, gi, gj, T(0));
     }
   }
 };
@@ -537,7 +632,7 @@ __device__ __forceinline__ bool step_begin(const Ctrl* ctrl, double dt_host, dou
 }
 
 template <typename T, int DIM, int NSX, int RS>
-__global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT, 1)
+__global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT, RS == RS_EXACT ? 1 : SweepShape<T, DIM, NSX>::MB)
     sweep_kernel(const SweepArgs<T> args) {
   using S = SweepShape<T, DIM, NSX>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -549,6 +644,7 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT, 1)
   Sweep<T, DIM, NSX, RS> sw(args, reinterpret_cast<T*>(smem_raw));
   sw.x0 = blockIdx.x * S::TX;
   sw.y0 = blockIdx.y * S::TY;
+  sw.n2 = DIM == 3 ? args.n[2] : 1;
   sw.dt = (T)dtd;
   sw.half_dt = T(0.5) * sw.dt;
   sw.Uin = cur ? args.B : args.A;
@@ -560,29 +656,34 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT, 1)
   if constexpr (DIM == 3) {
     const int z0 = blockIdx.z * args.zchunk;
     const int z1 = min(z0 + args.zchunk, args.n[2]);
-    for (int q = z0 - 2; q <= z0 + 1; ++q) sw.load_plane(q);
+    sw.z1 = z1;
+    for (int q = z0 - 2; q <= z0; ++q) sw.load_plane(q);
     __syncthreads();
-    sw.predictor_plane(z0 - 1);
-    sw.predictor_plane(z0);
+    sw.template predictor<PRED_ZHI>(z0 - 1);
     __syncthreads();
-    sw.zfaces(z0 - 1);
-    for (int z = z0; z < z1; ++z) {
-      sw.load_plane(z + 2);
+    // Plane k: its face states, then its x/y faces and the z face below it;
+    // the owners close plane k-1 and open plane k.  k = z1 only supplies the
+    // z face above the chunk's last plane.
+    for (int k = z0; k <= z1; ++k) {
+      sw.load_plane(k + 1);
       __syncthreads();
-      sw.predictor_plane(z + 1);
+      if (k < z1) sw.template predictor<PRED_ALL>(k);
+      else sw.template predictor<PRED_ZLO>(k);
       __syncthreads();
-      sw.faces_plane(z);
+      if (k < z1) sw.template faces<true, true>(k);
+      else sw.template faces<false, true>(k);
       __syncthreads();
-      sw.update_plane(z);
+      sw.owner_step(k, k > z0, k < z1);
     }
   } else {
+    sw.z1 = 1;
     sw.load_plane(0);
     __syncthreads();
-    sw.predictor_plane(0);
+    sw.template predictor<PRED_ALL>(0);
     __syncthreads();
-    sw.faces_plane(0);
+    sw.template faces<true, false>(0);
     __syncthreads();
-    sw.update_plane(0);
+    sw.owner_step(0, false, true);
   }
   __syncthreads();
   finish_step<S::NT>(args.ctrl, sw.smax, sw.err, sw.n_fallback, sw.n_iters, 0ull, step, dtd);
