@@ -35,6 +35,8 @@ METRIC = "cell-updates/s"
 WORKLOAD = "batched exact-Riemann: 4096 1D shock tubes, 256-8192 cells (1.73e7 cells), gamma=5/3, minmod"
 KERNEL_SOURCES = ["paper_2503_04428_gb300/csrc/batched.cuh", "paper_2503_04428_gb300/csrc/physics.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "batched_fp32_mlp_4096tubes.traffic.json")
+SWEEP_SOURCES = ["paper_2503_04428_gb300/csrc/sweep.cuh", "paper_2503_04428_gb300/csrc/physics.cuh"]
+SWEEP_FLOPS_FILE = os.path.join(ROOT, "profiles", "sweep_sedov3d_fp64.flops.json")
 
 
 def load_peaks():
@@ -45,11 +47,28 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_hash():
+def kernel_hash(sources=KERNEL_SOURCES):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def sweep_fp64_flops_per_cell():
+    """FP64 flops per cell-update of the FP64 Sedov sweep (DFMA = 2, DADD and
+    DMUL = 1) from the committed ncu counts, if they match this kernel."""
+    if not os.path.exists(SWEEP_FLOPS_FILE):
+        return None
+    d = json.load(open(SWEEP_FLOPS_FILE))
+    if d.get("kernel_hash") != kernel_hash(SWEEP_SOURCES):
+        return None
+    return float(d["fp64_flops_per_cell"])
+
+
+def alu_peaks(H):
+    """Dense FMA peaks of this GPU, measured now by the library's FMA-chain kernel."""
+    return {"fp64_tflops": H.hydro_fma_rate(64), "fp32_tflops": H.hydro_fma_rate(32),
+            "source": "hydro_fma_rate: 8 independent FMA chains per thread, 8 CTAs of 256 per SM"}
 
 
 def profiled_traffic():
@@ -230,7 +249,8 @@ def main():
     if args.grid_only:
         import torch
         from paper_2503_04428_gb300 import hydro as H
-        print(json.dumps(time_grids(H, torch, torch.cuda.current_stream(), args, only=args.grid_only)))
+        print(json.dumps(time_grids(H, torch, torch.cuda.current_stream(), args, only=args.grid_only,
+                                    alu=alu_peaks(H))))
         return
     if args.impl == "reference":
         run_reference(args)
@@ -294,14 +314,15 @@ def main():
     dense = None
     if not args.skip_fp64:
         dense = time_dense(H, torch, stream, args, ws, weights)
+    alu = alu_peaks(H)
     grids = None
     if not args.skip_grids:
-        grids = time_grids(H, torch, stream, args)
+        grids = time_grids(H, torch, stream, args, alu=alu)
     return report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it32, mlp_frac,
-                  value64, t64, k64, it64, rho_rel, dense, grids)
+                  value64, t64, k64, it64, rho_rel, dense, grids, alu)
 
 
-def time_grids(H, torch, stream, args, only=None):
+def time_grids(H, torch, stream, args, only=None, alu=None):
     """The fused grid sweep on the 3D configurations: Sedov 256^3 (HLL, NV=5) in
     FP32 and FP64 and the spherical wedge 1024x128x128 (HLLC, NV=8, point +
     monopole gravity) in FP32; device-side CFL steps replayed as a graph."""
@@ -330,7 +351,14 @@ def time_grids(H, torch, stream, args, only=None):
         gbs = bytes_cell * cells * k / t / 1e9
         out[name] = {"value": cells * k / t, "unit": METRIC, "ms_per_step": 1000.0 * t / k, "steps": k,
                      "hbm_gbs": gbs, "hbm_frac": gbs / peak, "tile": [st["tile_x"], st["tile_y"]],
-                     "zchunk": st["zchunk"], "gpu_launches_per_step": 3 if name.startswith("wedge") else 1}
+                     "threads": st["threads"], "zchunk": st["zchunk"],
+                     "gpu_launches_per_step": 3 if name.startswith("wedge") else 1}
+        fpc = sweep_fp64_flops_per_cell() if (prec == 64 and name.startswith("sedov")) else None
+        if fpc is not None and alu is not None:
+            ach = fpc * cells * k / t / 1e12
+            out[name]["roofline"] = {"bound": "fp64", "achieved": ach, "peak": alu["fp64_tflops"],
+                                     "unit": "TFLOP/s", "frac": ach / alu["fp64_tflops"],
+                                     "flops_per_cell": fpc, "peak_kind": "measured (hydro_fma_rate)"}
         del case
     return out
 
@@ -406,7 +434,7 @@ def time_e2e(H, torch, b32, w, args, ws, total, barrier):
 
 
 def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it32, mlp_frac,
-           value64, t64, k64, it64, rho_rel, dense=None, grids=None):
+           value64, t64, k64, it64, rho_rel, dense=None, grids=None, alu=None):
     peak, peak_kind = load_peaks()
     nsteps = args.steps * args.repeats
     alg_bytes = 2 * 3 * 4 * total  # read U^n and write U^{n+1}, FP32
@@ -418,6 +446,7 @@ def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it3
     if value64 is not None:
         ach64 = 2 * 3 * 8 * total / (t64 / k64) / 1e9
         fp64 = {"value": value64, "unit": METRIC, "ms_per_step": 1000.0 * t64 / k64, "hbm_frac": ach64 / peak,
+                "fp64_peak_tflops": alu["fp64_tflops"] if alu else None,
                 "newton_iters_per_face": it64, "speedup_of_headline": value / value64}
 
     cpu = None
@@ -444,6 +473,7 @@ def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it3
             "fp64_plain": fp64,
             "dense_state": dense,
             "grid_sweep": grids,
+            "alu_peaks": alu,
             "newton_iters_per_face": {"fp32_mlp": it32, "fp64_toro": it64},
             "mlp": dict(train_info, guessed_face_fraction=mlp_frac),
             "accuracy": {"rho_rel_l1_fp32mlp_vs_fp64": rho_rel},

@@ -212,6 +212,14 @@ int hydro_exact_solve(const double* WL, const double* WR, long n, double gamma, 
                       const float* weights, int precision, double* pstar, double* ustar,
                       int* iters);
 
+/* Measured arithmetic peak of the current GPU: dense fused multiply-adds in
+ * FP64 (precision 64) or FP32 (32), in TFLOP/s (2 flops per FMA), the best
+ * of four ~20 ms launches of eight independent FMA chains per thread.  The
+ * paper has no counterpart: the FP64 forms of the step are bound by this
+ * rate rather than by HBM on this hardware, and their roofline needs it
+ * measured on the machine at hand.  Synchronous; allocates a few bytes. */
+int hydro_fma_rate(int precision, double* tflops_out);
+
 const char* hydro_last_error(void);
 void hydro_destroy(hydro_t h);
 

@@ -27,7 +27,7 @@
 namespace hydro {
 
 constexpr int BSEG = 28;  // cells per warp segment (32 lanes = 28 cells + 2 halo cells each side)
-constexpr int BDEPTH = 8;  // segment windows per warp in the shared-memory ring (BDEPTH-1 in flight)
+constexpr int BDEPTH = 4;  // segment windows per warp in the shared-memory ring (BDEPTH-1 in flight)
 
 // Dynamic shared memory of batched_kernel<T, NW>: one ring of BDEPTH windows
 // (3 variables x 32 cells) per warp.
@@ -168,6 +168,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
   }
   unsigned long long n_iters = 0, n_mlp = 0, n_fb = 0;
   int err = 0;
+  // the last uniform window's state and its |u| + c (warp-uniform values)
+  bool have_u = false;
+  T ur[3] = {T(0), T(0), T(0)}, u_spd = T(0);
 
   for (;;) {
     int it = 0;
@@ -222,21 +225,27 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
       const T r2 = __shfl_sync(0xffffffffu, Ua[2], 0);
       const bool uniform = __all_sync(0xffffffffu, (Ua[0] == r0) & (Ua[1] == r1) & (Ua[2] == r2));
       if (uniform) {
-        if (lane < ncell) {
-          const long long c = base + c0 + lane;
-          T u[3], w[3];
-          bool finite = true;
-#pragma unroll
-          for (int v = 0; v < 3; ++v) {
-            u[v] = Ua[v] + T(0);
-            finite = finite && isfinite(u[v]);
-          }
+        // One state (r0, r1, r2) on every lane: its validity and |u| + c are
+        // those of the last uniform window whenever the state repeats, as it
+        // does along the undisturbed stretches of a tube.
+        if (!(have_u && r0 == ur[0] && r1 == ur[1] && r2 == ur[2])) {
+          have_u = true;
+          ur[0] = r0;
+          ur[1] = r1;
+          ur[2] = r2;
+          T u[3] = {r0 + T(0), r1 + T(0), r2 + T(0)}, w[3];
+          const bool finite = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
           to_prim<T, 1, 0>(u, w, gas);
           if (!finite) err = err ? err : ST_NONFINITE;
           else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
-          smax = fmax(smax, (fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * fn);
-#pragma unroll
-          for (int v = 0; v < 3; ++v) Uout[v * a.total + c] = u[v];
+          u_spd = fabs(w[1]) + dsqrt(gas.g * w[2] / w[0]);
+        }
+        smax = fmax(smax, u_spd * fn);
+        if (lane < ncell) {
+          const long long c = base + c0 + lane;
+          Uout[c] = r0 + T(0);
+          Uout[a.total + c] = r1 + T(0);
+          Uout[2 * a.total + c] = r2 + T(0);
         }
         continue;
       }

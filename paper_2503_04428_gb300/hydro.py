@@ -83,6 +83,7 @@ _SIGS = {
     "hydro_exact_solve": [_D, _D, C.c_long, C.c_double, C.c_int, _F, C.c_int, _D, _D, _I],
     "hydro_mlp_loss_grad_device": [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP],
     "hydro_destroy": [_VP],
+    "hydro_fma_rate": [C.c_int, C.POINTER(C.c_double)],
     "hydro_last_error": [],
 }
 
@@ -260,6 +261,13 @@ def hydro_exact_solve(WL, WR, gamma, guess=HYDRO_GUESS_TORO, weights=None, preci
           None if w is None else w.ctypes.data_as(_F), precision, ps.ctypes.data_as(_D),
           us.ctypes.data_as(_D), it.ctypes.data_as(_I))
     return ps, us, it
+
+
+def hydro_fma_rate(precision=64):
+    """Measured dense FMA peak of the current GPU in TFLOP/s (FP64 or FP32)."""
+    out = C.c_double()
+    _call("hydro_fma_rate", int(precision), C.byref(out))
+    return out.value
 
 
 def hydro_destroy(h):
