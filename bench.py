@@ -182,8 +182,10 @@ def timed_steps(torch, stream, fn, steps):
     return e0.elapsed_time(e1) / 1000.0
 
 
-def cpu_baseline(steps_sample=4, tubes_sample=192):
-    """The FP64 oracle (as it stands, all host cores) on a bounded sample of the workload."""
+def cpu_baseline(steps_sample=4, tubes_sample=NTUBES):
+    """The FP64 oracle (as it stands, all host cores) on a bounded sample of the
+    workload: every tube for 4 steps (~20 s of CPU time on 16 cores), and on
+    one core over the first 256 tubes."""
     import oracle as O
     from paper_2503_04428_gb300 import workloads as wl
     w = wl.tubes(NTUBES, seed=2)
@@ -194,9 +196,17 @@ def cpu_baseline(steps_sample=4, tubes_sample=192):
     O.batch_run(ln, U, w["gamma"], O.EXACT, O.MINMOD, CFL, steps_sample, nthreads=cores)
     dt = time.time() - t0
     cells = int(ln.sum()) * steps_sample
+    # the same oracle on one core, over the first quarter of the sample
+    ln1 = ln[:256]
+    t0 = time.time()
+    O.batch_run(ln1, U[:, :int(ln1.sum())], w["gamma"], O.EXACT, O.MINMOD, CFL, steps_sample, nthreads=1)
+    v1 = int(ln1.sum()) * steps_sample / (time.time() - t0)
     return {"value": cells / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": "%d of 4096 tubes (%d cells) x %d steps, FP64 Toro guess, OpenMP over tubes"
-                      % (tubes_sample, int(ln.sum()), steps_sample)}
+            "sample": "%d of 4096 tubes (%d cells) x %d steps from the initial state, FP64 Toro guess, "
+                      "OpenMP over tubes"
+                      % (tubes_sample, int(ln.sum()), steps_sample),
+            "single_core": {"value": v1, "sample": "%d tubes (%d cells) x %d steps"
+                                                   % (len(ln1), int(ln1.sum()), steps_sample)}}
 
 
 def run_reference(args):
@@ -206,7 +216,7 @@ def run_reference(args):
     import oracle as O
     from paper_2503_04428_gb300 import workloads as wl
     w = wl.tubes(NTUBES, seed=2)
-    ntub = 96
+    ntub = 1024  # a quarter of the tubes per step: ~0.1 s of 16 host cores
     ln = w["lengths"][:ntub]
     U = w["U"][:, :int(ln.sum())].copy()
     cores = os.cpu_count() or 1
@@ -223,7 +233,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle on a bounded sample)"},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tubes_per_gpu": NTUBES, "cells_per_gpu": int(w["lengths"].sum()),
+                   "form": "FP64 CPU oracle (the reference arm), Toro guess", "sample": sample},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -303,11 +315,23 @@ def main():
     mlp_frac = mlp_acc / max(face_acc, 1)
     ms = 1000.0 * t32 / nsteps
     out32 = b32.get_state().astype(np.float64)
+    times32 = b32.times()
 
     value64 = t64 = it64 = rho_rel = None
     k64 = 0
+    accuracy = {"rho_rel_l1_fp32mlp_vs_fp64": None}
     if not args.skip_fp64:
-        value64, t64, k64, it64, rho_rel = time_fp64(H, torch, stream, w, args, ws, total, out32)
+        value64, t64, k64, it64, rho_rel, out64, times64 = time_fp64(H, torch, stream, w, args, ws, total,
+                                                                       out32)
+        # equal stated accuracy: both forms' per-tube L1(rho) error against the
+        # exact solution at the final time, averaged over tubes
+        e32 = exact_l1_rho(H, w, out32[0], times32)
+        e64 = exact_l1_rho(H, w, out64[0], times64)
+        accuracy = {"rho_rel_l1_fp32mlp_vs_fp64": rho_rel,
+                    "l1_rho_vs_exact": {"fp32_mlp": e32, "fp64_toro": e64,
+                                        "relative_difference": abs(e32 - e64) / e64,
+                                        "steps": args.steps,
+                                        "definition": "mean over tubes of sum_i |rho_i - rho_exact(x_i, t_b)| / n_b"}}
     e2e = None
     if not args.skip_e2e:
         e2e = time_e2e(H, torch, b32, w, args, ws, total, barrier)
@@ -319,7 +343,7 @@ def main():
     if not args.skip_grids:
         grids = time_grids(H, torch, stream, args, alu=alu)
     return report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it32, mlp_frac,
-                  value64, t64, k64, it64, rho_rel, dense, grids, alu)
+                  value64, t64, k64, it64, accuracy, dense, grids, alu)
 
 
 def time_grids(H, torch, stream, args, only=None, alu=None):
@@ -387,6 +411,21 @@ def time_dense(H, torch, stream, args, ws, weights):
             "state": "every cell's rho and P x (1 + 0.01 U(-1,1))"}
 
 
+def exact_l1_rho(H, w, rho, times):
+    """Mean over tubes of the L1 density error against the exact Riemann
+    solution at each tube's own time (sum_i |rho_i - rho_exact(x_i)| / n_b),
+    the exact solution sampled by the library (hydro_exact_sample, FP64)."""
+    lengths = np.asarray(w["lengths"], dtype=np.int64)
+    face_of = np.repeat(np.arange(len(lengths), dtype=np.int64), lengths)
+    start = np.repeat(np.cumsum(lengths) - lengths, lengths)
+    i = np.arange(int(lengths.sum()), dtype=np.int64) - start
+    nb = lengths[face_of].astype(np.float64)
+    xi = ((i + 0.5) / nb - 0.5) / np.asarray(times)[face_of]
+    ex = H.hydro_exact_sample(w["WL"], w["WR"], w["gamma"], face_of, xi)[:, 0]
+    err = np.abs(np.asarray(rho, dtype=np.float64) - ex) / nb
+    return float(np.bincount(face_of, weights=err).mean())
+
+
 def time_fp64(H, torch, stream, w, args, ws, total, out32):
     """The plain FP64 form of the same kernel (Toro guess), and the difference
     of its density field from the headline form's after the same steps."""
@@ -401,14 +440,15 @@ def time_fp64(H, torch, stream, w, args, ws, total, out32):
     t64 = timed_steps(torch, stream, lambda k: b64.run(k, CFL), k64)
     r1 = b64.stats()
     it64 = (r1["newton_iters"] - r0["newton_iters"]) / max(r1["faces"] - r0["faces"], 1)
-    value64 = ws * total * k64 / t64
+    value64, t64 = job_rate(t64, total, k64, torch.distributed if ws > 1 else None, "cuda")
     # same number of steps from the same start for an accuracy comparison
     b64.set_state(U64)
     b64.run(args.steps, CFL)
     out64 = b64.get_state()
+    times64 = b64.times()
     rho_rel = float(np.abs(out32[0] - out64[0]).sum() / np.abs(out64[0]).sum())
     b64.close()
-    return value64, t64, k64, it64, rho_rel
+    return value64, t64, k64, it64, rho_rel, out64, times64
 
 
 def time_e2e(H, torch, b32, w, args, ws, total, barrier):
@@ -434,7 +474,7 @@ def time_e2e(H, torch, b32, w, args, ws, total, barrier):
 
 
 def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it32, mlp_frac,
-           value64, t64, k64, it64, rho_rel, dense=None, grids=None, alu=None):
+           value64, t64, k64, it64, accuracy, dense=None, grids=None, alu=None):
     peak, peak_kind = load_peaks()
     nsteps = args.steps * args.repeats
     alg_bytes = 2 * 3 * 4 * total  # read U^n and write U^{n+1}, FP32
@@ -476,7 +516,7 @@ def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it3
             "alu_peaks": alu,
             "newton_iters_per_face": {"fp32_mlp": it32, "fp64_toro": it64},
             "mlp": dict(train_info, guessed_face_fraction=mlp_frac),
-            "accuracy": {"rho_rel_l1_fp32mlp_vs_fp64": rho_rel},
+            "accuracy": accuracy,
         }))
     b32.close()
 

@@ -220,6 +220,20 @@ int hydro_exact_solve(const double* WL, const double* WR, long n, double gamma, 
  * measured on the machine at hand.  Synchronous; allocates a few bytes. */
 int hydro_fma_rate(int precision, double* tflops_out);
 
+/* Sample the exact Riemann solution (Toro ch. 4; the reference solution of
+ * the paper's shock-tube tests, App. C.1) in FP64 on the GPU: WL, WR hold nf
+ * faces as (rho,u,P); point k belongs to face face_of[k] (0 <= face_of[k] <
+ * nf) and sits at the similarity coordinate xi[k] = (x - x_face)/t; W_out
+ * (npts x 3) receives (rho,u,P) there.  Star states come from the Toro guess
+ * and the Newton rule of hydro_exact_solve; a face without one (vacuum)
+ * fails with HYDRO_ERR_NEWTON.  Host arrays. */
+int hydro_exact_sample(const double* WL, const double* WR, long nf, double gamma,
+                       const long long* face_of, const double* xi, long npts, double* W_out);
+
+/* Simulation time of every tube of a batch (ntubes doubles, host): the sum of
+ * its own CFL steps dt_b = cfl / max_i (|u|+c)_i n_b since hydro_set_state. */
+int hydro_batch_times(hydro_t h, double* t_out);
+
 const char* hydro_last_error(void);
 void hydro_destroy(hydro_t h);
 

@@ -745,6 +745,63 @@ int hydro_exact_solve(const double* WL, const double* WR, long n, double gamma, 
   return HYDRO_OK;
 }
 
+int hydro_exact_sample(const double* WL, const double* WR, long nf, double gamma, const long long* face_of,
+                       const double* xi, long npts, double* W_out) {
+  if (!WL || !WR || nf < 1 || npts < 0 || (npts > 0 && (!face_of || !xi || !W_out)) || !(gamma > 1.0))
+    return berr("hydro_exact_sample: bad argument");
+  for (long k = 0; k < npts; ++k)
+    if (face_of[k] < 0 || face_of[k] >= nf || !std::isfinite(xi[k]))
+      return berr("hydro_exact_sample: face index out of range or non-finite x/t");
+  if (npts == 0) return HYDRO_OK;
+  double *dl = nullptr, *dr = nullptr, *dp = nullptr, *du = nullptr, *dxi = nullptr, *dw = nullptr;
+  long long* df = nullptr;
+  int* di = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(dl); cudaFree(dr); cudaFree(dp); cudaFree(du); cudaFree(dxi); cudaFree(dw);
+    cudaFree(df); cudaFree(di);
+  };
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r) { if (e == cudaSuccess) e = r; return e == cudaSuccess; };
+  ok(cudaMalloc(&dl, sizeof(double) * 3 * nf)) && ok(cudaMalloc(&dr, sizeof(double) * 3 * nf)) &&
+      ok(cudaMalloc(&dp, sizeof(double) * nf)) && ok(cudaMalloc(&du, sizeof(double) * nf)) &&
+      ok(cudaMalloc(&di, sizeof(int) * nf)) && ok(cudaMalloc(&df, sizeof(long long) * npts)) &&
+      ok(cudaMalloc(&dxi, sizeof(double) * npts)) && ok(cudaMalloc(&dw, sizeof(double) * 3 * npts)) &&
+      ok(cudaMemcpy(dl, WL, sizeof(double) * 3 * nf, cudaMemcpyHostToDevice)) &&
+      ok(cudaMemcpy(dr, WR, sizeof(double) * 3 * nf, cudaMemcpyHostToDevice)) &&
+      ok(cudaMemcpy(df, face_of, sizeof(long long) * npts, cudaMemcpyHostToDevice)) &&
+      ok(cudaMemcpy(dxi, xi, sizeof(double) * npts, cudaMemcpyHostToDevice));
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "hydro_exact_sample");
+  }
+  const Gas<double> gas = make_gas<double>(gamma);
+  exact_list_kernel<double><<<(unsigned)((nf + 127) / 128), 128>>>(dl, dr, nf, gas, nullptr, dp, du, di);
+  std::vector<double> ps(nf);
+  ok(cudaGetLastError()) && ok(cudaMemcpy(ps.data(), dp, sizeof(double) * nf, cudaMemcpyDeviceToHost));
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "hydro_exact_sample");
+  }
+  for (long f = 0; f < nf; ++f)
+    if (!(ps[f] > 0.0)) {
+      cleanup();
+      set_error("hydro_exact_sample: no star state (vacuum or Newton failure) at face " + std::to_string(f));
+      return HYDRO_ERR_NEWTON;
+    }
+  exact_sample_kernel<<<(unsigned)((npts + 255) / 256), 256>>>(dl, dr, dp, du, df, dxi, npts, gas, dw);
+  ok(cudaGetLastError()) && ok(cudaMemcpy(W_out, dw, sizeof(double) * 3 * npts, cudaMemcpyDeviceToHost));
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_exact_sample");
+  return HYDRO_OK;
+}
+
+int hydro_batch_times(hydro_t h, double* t_out) {
+  if (!h || !h->batched || !t_out) return berr("hydro_batch_times: bad argument");
+  HCK(cudaMemcpyAsync(t_out, h->bs->t_tube, sizeof(double) * h->bs->ntubes, cudaMemcpyDeviceToHost, h->stream));
+  HCK(cudaStreamSynchronize(h->stream));
+  return HYDRO_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -12,6 +12,7 @@
 #include <sstream>
 #include <string>
 #include <vector>
+#include <algorithm>
 
 #include "aux_kernels.cuh"
 #include "common.cuh"
@@ -444,11 +445,30 @@ static int autotune_grid(hydro_ctx* h, double cfl) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cands[] = {4, 8, 16, 32, 64};
+  // Powers of two, then (once the first launch has set the tile shape)
+  // chunk lengths that make the CTA count just fill whole waves of the SMs.
+  std::vector<int> cands = {4, 8, 16, 32, 64};
   double best = 1e300;
   int best_z = h->zchunk;
   double dt = base.smax_cur > 0.0 ? cfl / base.smax_cur : 1e-12;
-  for (int zc : cands) {
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  bool waves_added = false;
+  for (size_t ci = 0; ci < cands.size(); ++ci) {
+    if (!waves_added && h->tile_x > 0 && h->tile_y > 0 && nsm > 0) {
+      waves_added = true;
+      const long long plane = (long long)((h->n[0] + h->tile_x - 1) / h->tile_x) *
+                              ((h->n[1] + h->tile_y - 1) / h->tile_y);
+      for (int w = 1; w <= 16; ++w) {
+        const long long nch = (long long)w * nsm / plane;
+        if (nch < 1) continue;
+        const int z = (int)((h->n[2] + nch - 1) / nch);
+        if (z >= 2 && z <= h->n[2] && std::find(cands.begin(), cands.end(), z) == cands.end())
+          cands.push_back(z);
+      }
+    }
+    const int zc = cands[ci];
     if (zc > h->n[2]) continue;
     h->zchunk = zc;
     const int reps = 3;

@@ -493,4 +493,22 @@ __global__ void exact_list_kernel(const double* WL, const double* WR, long long 
   iters[i] = st == ST_OK ? its : -st;
 }
 
+// The exact solution of face face_of[k] at x/t = xi[k], in FP64, from the
+// star states of exact_list_kernel: W_out[3k..3k+2] = (rho, u, P).
+__global__ void exact_sample_kernel(const double* WL, const double* WR, const double* pstar,
+                                    const double* ustar, const long long* face_of, const double* xi,
+                                    long long npts, Gas<double> gas, double* W_out) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= npts) return;
+  const long long f = face_of[k];
+  const double rL = WL[3 * f], uL = WL[3 * f + 1], pL = WL[3 * f + 2];
+  const double rR = WR[3 * f], uR = WR[3 * f + 1], pR = WR[3 * f + 2];
+  const double cL = sqrt(gas.g * pL / rL), cR = sqrt(gas.g * pR / rR);
+  double rho, u, p;
+  sample_xi<double>(xi[k], rL, uL, pL, cL, rR, uR, pR, cR, pstar[f], ustar[f], gas, rho, u, p);
+  W_out[3 * k] = rho;
+  W_out[3 * k + 1] = u;
+  W_out[3 * k + 2] = p;
+}
+
 }  // namespace hydro

@@ -270,15 +270,16 @@ __device__ __forceinline__ int newton_star(T p, T rL, T uL, T pL, T cL, T rR, T 
   return ST_OK;
 }
 
-// Sample the exact solution at x/t = 0 given the star state; returns the
-// (rho, u, P) there and whether it lies left of the contact (ties left).
+// Sample the exact solution at x/t = S given the star state (Toro ch. 4.5);
+// returns the (rho, u, P) there and whether it lies left of the contact
+// (ties left).
 template <typename T>
-__device__ __forceinline__ bool sample0(T rL, T uL, T pL, T cL, T rR, T uR, T pR, T cR, T ps, T us,
-                                        const Gas<T>& gas, T& rho, T& u, T& p) {
-  if (T(0) <= us) {
+__device__ __forceinline__ bool sample_xi(T S, T rL, T uL, T pL, T cL, T rR, T uR, T pR, T cR, T ps,
+                                          T us, const Gas<T>& gas, T& rho, T& u, T& p) {
+  if (S <= us) {
     if (ps > pL) {
       const T SL = uL - cL * dsqrt(gas.zp * ps / pL + gas.z);
-      if (T(0) <= SL) { rho = rL; u = uL; p = pL; }
+      if (S <= SL) { rho = rL; u = uL; p = pL; }
       else {
         const T q = ps / pL;
         rho = rL * (q + gas.Bq) / (gas.Bq * q + T(1));
@@ -288,13 +289,14 @@ __device__ __forceinline__ bool sample0(T rL, T uL, T pL, T cL, T rR, T uR, T pR
       const T SHL = uL - cL;
       const T cs = cL * dpow(ps / pL, gas.z);
       const T STL = us - cs;
-      if (T(0) <= SHL) { rho = rL; u = uL; p = pL; }
-      else if (T(0) >= STL) {
+      if (S <= SHL) { rho = rL; u = uL; p = pL; }
+      else if (S >= STL) {
         rho = rL * dpow(ps / pL, gas.ig);
         u = us; p = ps;
       } else {
-        const T c = gas.A2 * (cL + T(0.5) * gas.gm1 * uL);
-        u = c;
+        // inside the left fan: c = 2/(g+1) (cL + (g-1)/2 (uL - S)), u = c + S
+        const T c = gas.A2 * (cL + T(0.5) * gas.gm1 * (uL - S));
+        u = c + S;
         rho = rL * dpow(c / cL, gas.two_gm1);
         p = pL * dpow(c / cL, gas.pow_c);
       }
@@ -303,7 +305,7 @@ __device__ __forceinline__ bool sample0(T rL, T uL, T pL, T cL, T rR, T uR, T pR
   }
   if (ps > pR) {
     const T SR = uR + cR * dsqrt(gas.zp * ps / pR + gas.z);
-    if (T(0) >= SR) { rho = rR; u = uR; p = pR; }
+    if (S >= SR) { rho = rR; u = uR; p = pR; }
     else {
       const T q = ps / pR;
       rho = rR * (q + gas.Bq) / (gas.Bq * q + T(1));
@@ -313,18 +315,26 @@ __device__ __forceinline__ bool sample0(T rL, T uL, T pL, T cL, T rR, T uR, T pR
     const T SHR = uR + cR;
     const T cs = cR * dpow(ps / pR, gas.z);
     const T STR = us + cs;
-    if (T(0) >= SHR) { rho = rR; u = uR; p = pR; }
-    else if (T(0) <= STR) {
+    if (S >= SHR) { rho = rR; u = uR; p = pR; }
+    else if (S <= STR) {
       rho = rR * dpow(ps / pR, gas.ig);
       u = us; p = ps;
     } else {
-      const T c = gas.A2 * (cR - T(0.5) * gas.gm1 * uR);
-      u = -c;
+      // inside the right fan: c = 2/(g+1) (cR - (g-1)/2 (uR - S)), u = S - c
+      const T c = gas.A2 * (cR - T(0.5) * gas.gm1 * (uR - S));
+      u = S - c;
       rho = rR * dpow(c / cR, gas.two_gm1);
       p = pR * dpow(c / cR, gas.pow_c);
     }
   }
   return false;
+}
+
+// The same at x/t = 0, the value the Godunov flux needs.
+template <typename T>
+__device__ __forceinline__ bool sample0(T rL, T uL, T pL, T cL, T rR, T uR, T pR, T cR, T ps, T us,
+                                        const Gas<T>& gas, T& rho, T& u, T& p) {
+  return sample_xi<T>(T(0), rL, uL, pL, cL, rR, uR, pR, cR, ps, us, gas, rho, u, p);
 }
 
 // Newton tolerance per precision: 1e-10 in FP64; in FP32 the relative

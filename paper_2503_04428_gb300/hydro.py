@@ -84,6 +84,8 @@ _SIGS = {
     "hydro_mlp_loss_grad_device": [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP],
     "hydro_destroy": [_VP],
     "hydro_fma_rate": [C.c_int, C.POINTER(C.c_double)],
+    "hydro_exact_sample": [_D, _D, C.c_long, C.c_double, C.POINTER(C.c_longlong), _D, C.c_long, _D],
+    "hydro_batch_times": [_VP, _D],
     "hydro_last_error": [],
 }
 
@@ -263,6 +265,27 @@ def hydro_exact_solve(WL, WR, gamma, guess=HYDRO_GUESS_TORO, weights=None, preci
     return ps, us, it
 
 
+def hydro_exact_sample(WL, WR, gamma, face_of, xi):
+    """Exact Riemann solution (rho, u, P) of face face_of[k] at x/t = xi[k] (FP64, GPU)."""
+    WL = np.ascontiguousarray(WL, dtype=np.float64).reshape(-1, 3)
+    WR = np.ascontiguousarray(WR, dtype=np.float64).reshape(-1, 3)
+    face_of = np.ascontiguousarray(face_of, dtype=np.int64).ravel()
+    xi = np.ascontiguousarray(xi, dtype=np.float64).ravel()
+    if len(face_of) != len(xi):
+        raise ValueError("face_of and xi differ in length")
+    W = np.empty((len(xi), 3))
+    _call("hydro_exact_sample", WL.ctypes.data_as(_D), WR.ctypes.data_as(_D), len(WL), gamma,
+          face_of.ctypes.data_as(C.POINTER(C.c_longlong)), xi.ctypes.data_as(_D), len(xi),
+          W.ctypes.data_as(_D))
+    return W
+
+
+def hydro_batch_times(h, ntubes):
+    t = np.empty(ntubes)
+    _call("hydro_batch_times", h, t.ctypes.data_as(_D))
+    return t
+
+
 def hydro_fma_rate(precision=64):
     """Measured dense FMA peak of the current GPU in TFLOP/s (FP64 or FP32)."""
     out = C.c_double()
@@ -398,6 +421,10 @@ class Batch:
 
     def stats(self):
         return hydro_stats(self.h)
+
+    def times(self):
+        """Simulation time of every tube (each advances at its own CFL step)."""
+        return hydro_batch_times(self.h, len(self.lengths))
 
     def mlp_set(self, weights, enable=True):
         hydro_mlp_set(self.h, weights, enable)

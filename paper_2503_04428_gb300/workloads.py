@@ -113,6 +113,36 @@ def rt2d(nx=512, ny=1536, seed=1, riemann=HLLC, limiter=MINMOD):
                  CARTESIAN, 1.4, 1, riemann, limiter, 0.4, U, sources=src)
 
 
+def rt2d_single_mode(nx=256, nz=512, riemann=HLLC, limiter=MINMOD):
+    """Single-mode 2D Rayleigh-Taylor of App. C.2: x in [-0.5,0.5], z in [-1,1],
+    g_z = -0.5, gamma = 1.4, rho = 2 above the interface z = h(x) = h0 cos(kappa x)
+    (h0 = 0.01, kappa = 4 pi) and 1 below, smoothed into a tanh of width 0.005;
+    hydrostatic P(z) = P0 + int_{-1}^z rho g dz with P0 = 10/7 + 1/4 (integrated
+    exactly for the tanh profile); one scalar = 0 below and 1 above (same
+    profile).  Periodic x, reflective z (the paper states no boundary kinds).
+    Linear theory: amplitude h0 cosh(sqrt(A g kappa) t), Atwood number A = 1/3."""
+    xf = np.linspace(-0.5, 0.5, nx + 1)
+    zf = np.linspace(-1.0, 1.0, nz + 1)
+    x, z = np.meshgrid(_centres(xf), _centres(zf), indexing="xy")
+    g, h0, kappa, w = -0.5, 0.01, 4.0 * math.pi, 0.005
+    h = h0 * np.cos(kappa * x)
+    s = (z - h) / w
+    rho = 1.5 + 0.5 * np.tanh(s)
+
+    def lncosh(a):
+        a = np.abs(a)
+        return a + np.log1p(np.exp(-2.0 * a)) - math.log(2.0)
+
+    # int_{-1}^{z} rho dz = 1.5 (z + 1) + 0.5 w [ln cosh s - ln cosh s(-1)]
+    integral = 1.5 * (z + 1.0) + 0.5 * w * (lncosh(s) - lncosh((-1.0 - h) / w))
+    p = 10.0 / 7.0 + 0.25 + g * integral
+    f = 0.5 + 0.5 * np.tanh(s)
+    U = conserved(1.4, rho, [np.zeros_like(x), np.zeros_like(x)], p, [f])
+    src = dict(gravity=GRAV_UNIFORM, g0=(0.0, g, 0.0))
+    return _case("rt2d_mode_%dx%d" % (nx, nz), 2, [xf, zf], [(PERIODIC, PERIODIC), (REFLECTIVE, REFLECTIVE)],
+                 CARTESIAN, 1.4, 1, riemann, limiter, 0.4, U, sources=src)
+
+
 def sedov3d(n=256, riemann=HLL, limiter=MINMOD):
     """3D Sedov blast on [-1,1]^3: rho=1, p=1e-5, E=1 over the central 2^3 cells (Sect. 4.3 style)."""
     f = np.linspace(-1.0, 1.0, n + 1)
