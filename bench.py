@@ -254,7 +254,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true", help="do not time the plain FP64 form")
     ap.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer path")
     ap.add_argument("--skip-grids", action="store_true", help="do not time the 3D grid sweeps")
-    ap.add_argument("--grid-only", choices=["sedov3d_fp32", "sedov3d_fp64", "wedge_fp32"],
+    ap.add_argument("--grid-only", choices=["sedov3d_fp32", "sedov3d_fp64", "wedge_fp32", "wedge_fp32_rad"],
                     help="time one grid sweep only (profiling)")
     ap.add_argument("--grid-n", type=int, default=0, help="cells per axis for --grid-only sedov3d")
     args = ap.parse_args()
@@ -355,14 +355,17 @@ def time_grids(H, torch, stream, args, only=None, alu=None):
     out = {}
     runs = (("sedov3d_fp32", lambda: wl.sedov3d(args.grid_n or 256), 32, 20),
             ("sedov3d_fp64", lambda: wl.sedov3d(args.grid_n or 256), 64, 5),
-            ("wedge_fp32", wl.wedge, 32, 10))
+            ("wedge_fp32", wl.wedge, 32, 10),
+            # the same wedge read through the gas + radiation EoS (Eq. 6-7) with
+            # R = 1 and a = 2.5e8 in code units: P_rad/P_gas ~ 1 at r = 1, ~1e-3 at r = 1000
+            ("wedge_fp32_rad", lambda: dict(wl.wedge(), eos_rad=(1.0, 2.5e8)), 32, 10))
     for name, make, prec, k in runs:
         if only and name != only:
             continue
         if only:
             k = args.steps
         case = make()
-        name = "%s_%s" % (case["name"], name.split("_")[-1])
+        name = "%s_%s" % (case["name"], name.split("_", 1)[1])
         dt = np.float32 if prec == 32 else np.float64
         g = H.Grid.from_case(dict(case, U=case["U"].astype(dt)), prec, stream=stream.cuda_stream)
         g.run(2, case["cfl"])  # autotuner on first use
@@ -376,7 +379,8 @@ def time_grids(H, torch, stream, args, only=None, alu=None):
         out[name] = {"value": cells * k / t, "unit": METRIC, "ms_per_step": 1000.0 * t / k, "steps": k,
                      "hbm_gbs": gbs, "hbm_frac": gbs / peak, "tile": [st["tile_x"], st["tile_y"]],
                      "threads": st["threads"], "zchunk": st["zchunk"],
-                     "gpu_launches_per_step": 3 if name.startswith("wedge") else 1}
+                     "gpu_launches_per_step": 3 if name.startswith("wedge") else 1,
+                     "eos": "gas + radiation (Eq. 6-7)" if case.get("eos_rad") else "ideal gas (Eq. 5)"}
         fpc = sweep_fp64_flops_per_cell() if (prec == 64 and name.startswith("sedov")) else None
         if fpc is not None and alu is not None:
             ach = fpc * cells * k / t / 1e12
@@ -452,25 +456,34 @@ def time_fp64(H, torch, stream, w, args, ws, total, out32):
 
 
 def time_e2e(H, torch, b32, w, args, ws, total, barrier):
-    """Same metric through the C ABI with pinned host buffers: each step copies
-    the state in, advances one step and copies it out."""
+    """Same metric through the C ABI with pinned host buffers: every step
+    copies the state in from host memory, advances one step and copies it
+    out (hydro_batch_run_host: the copies of one group of tubes overlap the
+    steps of the others).  Also the unpipelined sequence set_state + run +
+    get_state for reference."""
     host_in = torch.from_numpy(w["U"].astype(np.float32)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     ke = max(3, args.steps // 5)
-    b32.set_state(host_in)
-    b32.run(1, CFL)
-    b32.get_state(host_out)
+    b32.run_host(host_in, host_out, 1, CFL)
     barrier()
     te0 = time.perf_counter()
+    for _ in range(ke):
+        b32.run_host(host_in, host_out, 1, CFL)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te0
+    rate, te = job_rate(te, total, ke, torch.distributed if ws > 1 else None, "cuda")
+    barrier()
+    ts0 = time.perf_counter()
     for _ in range(ke):
         b32.set_state(host_in)
         b32.run(1, CFL)
         b32.get_state(host_out)
     torch.cuda.synchronize()
-    te = time.perf_counter() - te0
+    ts = time.perf_counter() - ts0
     nbytes = 3 * total * 4
-    return {"value": ws * total * ke / te, "unit": METRIC, "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes}
+    return {"value": rate, "unit": METRIC, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "api": "hydro_batch_run_host (8 groups of tubes, pinned buffers)",
+            "unpipelined_value": ws * total * ke / ts}
 
 
 def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it32, mlp_frac,

@@ -103,6 +103,20 @@ typedef struct {
 int hydro_create(const hydro_grid* grid, int coords, const hydro_eos* eos, int riemann,
                  int limiter, int precision, void* stream, hydro_t* out);
 
+/* Equation of state: switch a grid handle from the ideal gas (Eq. 5) to an
+ * ideal gas in equilibrium with radiation (Sect. 2.3, Eq. 6-7):
+ *   e = rho R_gas T/(gamma-1) + a_rad T^4,   P = rho R_gas T + a_rad T^4/3,
+ *   c^2 = (gamma/(gamma-1) + 20 alpha + 16 alpha^2)/(1/(gamma-1) + 12 alpha)
+ *         * P_gas/rho,   alpha = P_rad/P_gas,
+ * with R_gas = k_b/(mu m_u) the specific gas constant and a_rad the radiation
+ * constant, both in the caller's units (R_gas > 0, a_rad >= 0; a_rad = 0 is
+ * the ideal gas computed the same way).  The temperature of every EoS call is
+ * found by Newton's method from the upper bound min(gas-only, radiation-only
+ * temperature), to a relative step of 1e-13 (FP64) or 1e-6 (FP32) plus one
+ * more step.  HLL and HLLC only: with the exact solver the call fails with
+ * HYDRO_ERR_UNSUPPORTED.  Call before hydro_set_state. */
+int hydro_set_eos_radiation(hydro_t h, double R_gas, double a_rad);
+
 /* Source terms.  gravity (Eq. 2-4): UNIFORM uses g0 (components along the
  * grid axes); POINT uses -G Mc / r^2 e_r; POINT_MONOPOLE adds the enclosed
  * mass M(r) of the current state (spherically symmetric approximation,
@@ -147,6 +161,19 @@ int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int
  * CUDA graph); the first call runs the launch-shape autotuner on a scratch
  * copy of the state. */
 int hydro_batch_run(hydro_t h, int nsteps, double cfl);
+
+/* Advance a batch whose state lives in host memory: U_in (3 x total cells,
+ * the layout of hydro_batch_set_state) is copied in, every tube advances
+ * nsteps of its own CFL steps, and the result is copied to U_out.  The tubes
+ * are cut into nparts groups of about equal cell counts (0 = 8) whose input
+ * copy, steps and output copy are ordered by events on three streams, so that
+ * the copies of one group overlap the computation of the others; the overlap
+ * needs U_in and U_out in pinned (page-locked) host memory.  The result equals
+ * hydro_batch_set_state + hydro_batch_run + hydro_batch_get_state bit for bit
+ * and the handle holds it afterwards.  An invalid input state or a failed
+ * step returns its status, and U_out is then unspecified.  The paper has no
+ * counterpart: this serves callers whose tubes live in host memory. */
+int hydro_batch_run_host(hydro_t h, const void* U_in, void* U_out, int nsteps, double cfl, int nparts);
 
 /* Record (with probability keep_prob, counter-based per face and step) the
  * left/right primitive states (rho,u,P)x2 of faces that pass the network's

@@ -72,6 +72,10 @@ def lib():
         L.orc_sedov_xi0.restype = C.c_double
         L.orc_heating_rate.argtypes = [C.c_int, _D, C.c_double, C.c_double]
         L.orc_heating_rate.restype = C.c_double
+        L.orc_set_eos_radiation.argtypes = [C.c_void_p, C.c_double, C.c_double]
+        L.orc_set_dual_energy.argtypes = [C.c_void_p, C.c_double]
+        L.orc_eos_rad.argtypes = [C.c_double] * 5 + [_D, _D, _D]
+        L.orc_eos_rad_eint.argtypes = [C.c_double] * 5 + [_D, _D]
         _lib = L
     return _lib
 
@@ -123,6 +127,14 @@ class Solver:
         hp[:len(heat_params)] = heat_params
         _check(lib().orc_set_sources(self._h, gravity, _dp(g), G, Mc, heating, _dp(hp)), "set_sources")
 
+    def set_eos_radiation(self, R, a):
+        """Gas + radiation EoS (Sect. 2.3 Eq. 6-7), HLL/HLLC only."""
+        _check(lib().orc_set_eos_radiation(self._h, R, a), "set_eos_radiation")
+
+    def set_dual_energy(self, eps):
+        """Dual-energy correction of Sect. 2.5 (eps = 0: off)."""
+        _check(lib().orc_set_dual_energy(self._h, eps), "set_dual_energy")
+
     def set_guess(self, guess, weights=None):
         w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
         self._w = w
@@ -169,6 +181,10 @@ def solver_from_case(case):
     """Build an oracle solver from a workload case (see the package's workloads module)."""
     s = Solver(case["dim"], case["n"], case["faces"], case["bc"], case["coords"], case["gamma"],
                case["n_scalars"], case["riemann"], case["limiter"])
+    if case.get("eos_rad"):
+        s.set_eos_radiation(*case["eos_rad"])
+    if case.get("dual_energy"):
+        s.set_dual_energy(case["dual_energy"])
     src = case.get("sources")
     if src:
         s.set_sources(**src)
@@ -188,6 +204,20 @@ def batch_run(lengths, U, gamma, riemann, limiter, cfl, nsteps, guess=GUESS_TORO
                                st.ctypes.data_as(_LL)), "batch_run")
     return U, dict(faces=int(st[0]), newton_iters=int(st[1]), fallbacks=int(st[2]),
                    mlp_faces=int(st[3]))
+
+
+def eos_rad(gamma, R, a, rho, e):
+    """Gas + radiation EoS from (rho, e): (T, P, c)."""
+    T, P, c = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().orc_eos_rad(gamma, R, a, rho, e, C.byref(T), C.byref(P), C.byref(c)), "eos_rad")
+    return T.value, P.value, c.value
+
+
+def eos_rad_eint(gamma, R, a, rho, P):
+    """Gas + radiation EoS from (rho, P): (T, e)."""
+    T, e = C.c_double(), C.c_double()
+    _check(lib().orc_eos_rad_eint(gamma, R, a, rho, P, C.byref(T), C.byref(e)), "eos_rad_eint")
+    return T.value, e.value
 
 
 def limiter(kind, dm, dp):

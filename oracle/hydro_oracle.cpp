@@ -39,6 +39,17 @@
  *   R9  monopole mass M_i = Mc + (4 pi/Omega)(sum_{i'<i} m_i' + m_i/2).
  *   R10 exact solver: Newton from a guess until 2|dp|/(p_k+p_{k-1}) < 1e-10,
  *       then one more Newton step; sampled at x/t = 0, ties go to the left.
+ *   R13 gas + radiation EoS (Eq. 6): the gas part is rho R T with R = k_b/(mu
+ *       m_u) (Eq. 6 prints k_b/mu without the atomic mass unit).
+ *   R14 its temperature: Newton on the monotone, convex e(T) or P(T) from the
+ *       upper bound min(gas-only, radiation-only temperature), until the
+ *       relative step is below 1e-13, then one more step.
+ *   R15 dual energy (Sect. 2.5): div(u e) and P div(u) use the face fluxes
+ *       u_f e_f = F_rho (e/rho)_upwind and u_f = F_rho/rho_upwind (upwind by
+ *       the sign of F_rho) with the dS/dV of the update; P is the cell's t^n
+ *       pressure; alpha comes from the t^n state; heating enters delta2;
+ *       where alpha = 1 the total energy is left as the update gives it;
+ *       otherwise E = e_new + rho|u|^2/2 of the new state.
  */
 #include "hydro_oracle.h"
 
@@ -58,6 +69,12 @@ const int NG = 2;  // ghost layers per side
 
 /* ------------------------------------------------------------------ */
 /* Ideal-gas EoS, Sect. 2.3 Eq. 5:  P = (gamma-1) e,  c = sqrt(gamma P/rho)   */
+/* Gas + radiation EoS, Sect. 2.3 Eq. 6-7 (kind 1):                           */
+/*   e = rho R T/(gamma-1) + a T^4,  P = rho R T + a T^4/3,                    */
+/*   c^2 = (gamma/(gamma-1) + 20 alpha + 16 alpha^2)/(1/(gamma-1) + 12 alpha)  */
+/*         * P_g/rho,  alpha = P_r/P_g,                                        */
+/* with R = k_b/(mu m_u) the specific gas constant (reading R13: Eq. 6 prints  */
+/* k_b/mu; the atomic mass unit belongs with mu) and a the radiation constant. */
 /* Primitive vector W = (rho, u_1..u_D, P, f_1..f_S); conserved U = (rho,     */
 /* rho u_1..rho u_D, E, rho f_1..rho f_S), E = e + rho|u|^2/2 (Sect. 2.1).      */
 /* ------------------------------------------------------------------ */
@@ -65,8 +82,55 @@ struct Eos {
   double gamma;
   int D;  // number of velocity components (= dim)
   int S;  // passive scalars
+  int kind = 0;              // 0 ideal gas, 1 gas + radiation
+  double R = 0.0, a = 0.0;   // gas + radiation constants
   int nv() const { return 2 + D + S; }
 };
+
+/* Temperature where c1 T + c4 T^4 = y (c1 > 0, c4 >= 0, y > 0): the left side
+ * is increasing and convex in T > 0, so Newton started from the upper bound
+ * min(y/c1, (y/c4)^(1/4)) decreases monotonically to the root (the paper's
+ * "Newton-Raphson approach", Sect. 2.3).  Reading R14: stop once the relative
+ * step is below 1e-13, then take one more step.  y <= 0 returns y/c1 <= 0,
+ * which the callers' positivity checks reject. */
+double rad_temperature(double c1, double c4, double y) {
+  double T = y / c1;
+  if (!(y > 0.0)) return T;
+  if (c4 > 0.0) T = std::fmin(T, std::pow(y / c4, 0.25));
+  bool conv = false;
+  for (int it = 0; it < 200; ++it) {
+    double f = c1 * T + c4 * T * T * T * T - y;
+    double df = c1 + 4.0 * c4 * T * T * T;
+    double Tn = T - f / df;
+    double ch = std::fabs(Tn - T) / Tn;
+    T = Tn;
+    if (conv) break;
+    if (ch < 1e-13) conv = true;
+  }
+  return T;
+}
+
+/* Pressure from the internal energy per volume (Eq. 5 or Eq. 6). */
+double eos_pressure(const Eos& eos, double rho, double e) {
+  if (eos.kind == 0) return (eos.gamma - 1.0) * e;
+  double T = rad_temperature(rho * eos.R / (eos.gamma - 1.0), eos.a, e);
+  return rho * eos.R * T + eos.a * T * T * T * T / 3.0;
+}
+
+/* Internal energy per volume from the pressure. */
+double eos_eint(const Eos& eos, double rho, double p) {
+  if (eos.kind == 0) return p / (eos.gamma - 1.0);
+  double T = rad_temperature(rho * eos.R, eos.a / 3.0, p);
+  return rho * eos.R * T / (eos.gamma - 1.0) + eos.a * T * T * T * T;
+}
+
+double sound_speed(const Eos& eos, double rho, double p) {
+  if (eos.kind == 0) return std::sqrt(eos.gamma * p / rho);
+  double T = rad_temperature(rho * eos.R, eos.a / 3.0, p);
+  double pg = rho * eos.R * T, pr = eos.a * T * T * T * T / 3.0;
+  double al = pr / pg, g = eos.gamma;
+  return std::sqrt((g / (g - 1.0) + 20.0 * al + 16.0 * al * al) / (1.0 / (g - 1.0) + 12.0 * al) * pg / rho);
+}
 
 void cons_to_prim(const Eos& eos, const double* U, double* W) {
   double rho = U[0];
@@ -76,7 +140,8 @@ void cons_to_prim(const Eos& eos, const double* U, double* W) {
     W[1 + d] = U[1 + d] / rho;
     ke += 0.5 * U[1 + d] * W[1 + d];
   }
-  W[1 + eos.D] = (eos.gamma - 1.0) * (U[1 + eos.D] - ke);
+  if (eos.kind == 0) W[1 + eos.D] = (eos.gamma - 1.0) * (U[1 + eos.D] - ke);
+  else W[1 + eos.D] = eos_pressure(eos, rho, U[1 + eos.D] - ke);
   for (int s = 0; s < eos.S; ++s) W[2 + eos.D + s] = U[2 + eos.D + s] / rho;
 }
 
@@ -88,18 +153,17 @@ void prim_to_cons(const Eos& eos, const double* W, double* U) {
     U[1 + d] = rho * W[1 + d];
     ke += 0.5 * rho * W[1 + d] * W[1 + d];
   }
-  U[1 + eos.D] = W[1 + eos.D] / (eos.gamma - 1.0) + ke;
+  if (eos.kind == 0) U[1 + eos.D] = W[1 + eos.D] / (eos.gamma - 1.0) + ke;
+  else U[1 + eos.D] = eos_eint(eos, rho, W[1 + eos.D]) + ke;
   for (int s = 0; s < eos.S; ++s) U[2 + eos.D + s] = rho * W[2 + eos.D + s];
 }
-
-double sound_speed(const Eos& eos, double rho, double p) { return std::sqrt(eos.gamma * p / rho); }
 
 /* Physical flux of Eq. 1 through a face normal to axis d (from the primitives). */
 void phys_flux(const Eos& eos, const double* W, int d, double* F) {
   double rho = W[0], un = W[1 + d], p = W[1 + eos.D];
   double ke = 0.0;
   for (int e = 0; e < eos.D; ++e) ke += 0.5 * rho * W[1 + e] * W[1 + e];
-  double E = p / (eos.gamma - 1.0) + ke;
+  double E = (eos.kind == 0 ? p / (eos.gamma - 1.0) : eos_eint(eos, rho, p)) + ke;
   F[0] = rho * un;
   for (int e = 0; e < eos.D; ++e) F[1 + e] = rho * un * W[1 + e];
   F[1 + d] += p;
@@ -473,6 +537,7 @@ struct Solver {
   int dim, n[3], coords, riemann, lim, bc[3][2];
   Eos eos;
   int gravity = ORC_GRAV_NONE, heating = ORC_HEAT_NONE, guess = ORC_GUESS_TORO;
+  double eps_dual = 0.0;        // dual-energy criterion epsilon (Sect. 2.5); 0 = off
   double g0[3] = {0, 0, 0}, G = 0.0, Mc = 0.0, heat_prm[4] = {0, 0, 0, 0};
   std::vector<float> mlpw;
   double t = 0.0;
@@ -750,9 +815,15 @@ int Solver::step(double dt) {
    * by the extended index of the cell on the LOW side of the face's high
    * neighbour, i.e. face (ie+1/2) is stored at ie. */
   std::vector<double> Fl[3];
+  /* dual energy (Sect. 2.5, reading R15): per face the advected internal
+   * energy u_f e_f = F_rho (e/rho)_upwind and the face velocity
+   * u_f = F_rho / rho_upwind, upwind by the sign of the mass flux */
+  std::vector<double> Q1[3], Q2[3];
   ExactStats est;
   for (int d = 0; d < dim; ++d) {
     Fl[d].assign((size_t)nv * ne, 0.0);
+    Q1[d].assign((size_t)ne, 0.0);
+    Q2[d].assign((size_t)ne, 0.0);
     long stride = d == 0 ? 1 : d == 1 ? m(0) : (long)m(0) * m(1);
     /* for axis d the face index runs 0..n[d]; the other axes over interior cells */
     int fl[3] = {0, 0, 0}, fh[3] = {n[0], n[1], n[2]};
@@ -779,6 +850,12 @@ int Solver::step(double dt) {
           }
           ++st_faces;
           for (int v = 0; v < nv; ++v) Fl[d][(size_t)v * ne + eL] = F[v];
+          if (eps_dual > 0.0) {
+            const double* Wu = F[0] >= 0.0 ? WL : WR;
+            const double eu = eos_eint(eos, Wu[0], Wu[1 + dim]);
+            Q1[d][(size_t)eL] = F[0] * eu / Wu[0];
+            Q2[d][(size_t)eL] = F[0] / Wu[0];
+          }
         }
   }
   st_iters += est.iters;
@@ -803,6 +880,7 @@ int Solver::step(double dt) {
         }
         cons_to_prim(eos, Uc, Wc);
         double Flo[3][16], Fhi[3][16], Slo[3], Shi[3];
+        double A1 = 0.0, A2 = 0.0;  // sums of u_f e_f dS and u_f dS (dual energy)
         for (int d = 0; d < dim; ++d) {
           long stride = d == 0 ? 1 : d == 1 ? m(0) : (long)m(0) * m(1);
           Slo[d] = dS(d, 0, ie, je, ke);
@@ -812,6 +890,10 @@ int Solver::step(double dt) {
             Fhi[d][v] = Fl[d][(size_t)v * ne + e];
             acc[v] += Flo[d][v] * Slo[d];
             acc[v] -= Fhi[d][v] * Shi[d];
+          }
+          if (eps_dual > 0.0) {
+            A1 += Q1[d][(size_t)(e - stride)] * Slo[d] - Q1[d][(size_t)e] * Shi[d];
+            A2 += Q2[d][(size_t)(e - stride)] * Slo[d] - Q2[d][(size_t)e] * Shi[d];
           }
         }
         double Unew[16];
@@ -861,10 +943,32 @@ int Solver::step(double dt) {
           Unew[1 + dim] += dt * work;
         }
 
+        double dheat = 0.0;
         if (heating != ORC_HEAT_NONE) {
           double rfni = 0.0;
           if (heating == ORC_HEAT_NI56) rfni = Uc[2 + dim + (int)heat_prm[0]];
-          Unew[1 + dim] += dt * heating_rate(heating, heat_prm, t, rfni);
+          dheat = dt * heating_rate(heating, heat_prm, t, rfni);
+          Unew[1 + dim] += dheat;
+        }
+
+        /* dual energy (Sect. 2.5): where the internal energy is small against
+         * the kinetic energy, blend the internal-energy change of the total-
+         * energy update (delta1) with that of de/dt + div(u e) + P div(u) = 0
+         * (delta2, plus the heating) by the weight alpha of the t^n state. */
+        if (eps_dual > 0.0) {
+          double ke0 = 0.0, ke1 = 0.0;
+          for (int d = 0; d < dim; ++d) {
+            ke0 += 0.5 * Uc[1 + d] * Uc[1 + d] / Uc[0];
+            ke1 += 0.5 * Unew[1 + d] * Unew[1 + d] / Unew[0];
+          }
+          double e0 = Uc[1 + dim] - ke0;
+          double crit = eps_dual * ke0;
+          double alpha = e0 >= crit ? 1.0 : (e0 > 0.1 * crit ? (e0 / crit) * (e0 / crit) : 0.0);
+          if (alpha < 1.0) {
+            double d1 = (Unew[1 + dim] - ke1) - e0;
+            double d2 = dt / vol * (A1 + Wc[1 + dim] * A2) + dheat;
+            Unew[1 + dim] = e0 + alpha * d1 + (1.0 - alpha) * d2 + ke1;
+          }
         }
 
         for (int v = 0; v < nv; ++v) Un[(size_t)v * nc + iidx(i, j, k)] = Unew[v];
@@ -934,6 +1038,41 @@ int orc_set_sources(orc_t h, int gravity, const double* g0, double G, double Mc,
   s.Mc = Mc;
   s.heating = heating;
   for (int i = 0; i < 4; ++i) s.heat_prm[i] = heat_params ? heat_params[i] : 0.0;
+  return ORC_OK;
+}
+
+int orc_set_dual_energy(orc_t h, double eps) {
+  if (!(eps >= 0.0)) return ORC_ERR_ARG;
+  h->s.eps_dual = eps;
+  return ORC_OK;
+}
+
+int orc_set_eos_radiation(orc_t h, double R, double a) {
+  if (!(R > 0.0) || !(a >= 0.0) || h->s.riemann == ORC_EXACT) return ORC_ERR_ARG;
+  h->s.eos.kind = 1;
+  h->s.eos.R = R;
+  h->s.eos.a = a;
+  return ORC_OK;
+}
+
+int orc_eos_rad(double gamma, double R, double a, double rho, double e, double* T, double* P, double* c) {
+  Eos eos = {gamma, 1, 0};
+  eos.kind = 1;
+  eos.R = R;
+  eos.a = a;
+  *T = rad_temperature(rho * R / (gamma - 1.0), a, e);
+  *P = eos_pressure(eos, rho, e);
+  *c = sound_speed(eos, rho, *P);
+  return ORC_OK;
+}
+
+int orc_eos_rad_eint(double gamma, double R, double a, double rho, double P, double* T, double* e) {
+  Eos eos = {gamma, 1, 0};
+  eos.kind = 1;
+  eos.R = R;
+  eos.a = a;
+  *T = rad_temperature(rho * R, a / 3.0, P);
+  *e = eos_eint(eos, rho, P);
   return ORC_OK;
 }
 

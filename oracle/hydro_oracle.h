@@ -11,7 +11,7 @@
  * Method (HERACLES++, arXiv:2503.04428):
  *   Euler equations with gravity, heating and passive scalars  -- Sect. 2.1, Eq. 1
  *   gravity: uniform / point mass / monopole                    -- Sect. 2.2, Eq. 2-4
- *   ideal-gas EoS                                               -- Sect. 2.3, Eq. 5
+ *   ideal-gas EoS; gas + radiation EoS                          -- Sect. 2.3, Eq. 5-7
  *   heating/cooling, Ni-56 decay chain                          -- Sect. 2.4, Eq. 8-9
  *   mesh, dS and dV per geometry                                -- Sect. 3.1.1
  *   spherical geometric momentum sources                        -- Sect. 3.1.2, Eq. 13-16
@@ -52,6 +52,12 @@ void orc_destroy(orc_t h);
 int  orc_set_sources(orc_t h, int gravity, const double* g0, double G, double Mc,
                      int heating, const double* heat_params);
 int  orc_set_guess(orc_t h, int guess, const float* mlp_weights);
+/* Switch to the gas + radiation EoS of Sect. 2.3 Eq. 6-7 (R = k_b/(mu m_u),
+ * a = radiation constant, both in the caller's units); HLL/HLLC only. */
+int  orc_set_eos_radiation(orc_t h, double R, double a);
+/* Dual-energy internal-energy correction of Sect. 2.5 with criterion eps
+ * (0 = off; the paper typically uses 1e-6). */
+int  orc_set_dual_energy(orc_t h, double eps);
 int  orc_set_state(orc_t h, const double* U);
 int  orc_get_state(orc_t h, double* U);
 int  orc_set_time(orc_t h, double t);
@@ -84,6 +90,10 @@ double orc_mlp_loss_grad(const float* w, const double* x6, const double* t, long
 int  orc_adam_step(float* w, float* m, float* v, const double* grad, int nparam, int step,
                    double lr, double beta1, double beta2, double eps);
 double orc_sedov_xi0(double gamma);
+/* Gas + radiation EoS (Eq. 6-7) at one point: from (rho, e) the temperature,
+ * pressure and sound speed; from (rho, P) the temperature and e. */
+int  orc_eos_rad(double gamma, double R, double a, double rho, double e, double* T, double* P, double* c);
+int  orc_eos_rad_eint(double gamma, double R, double a, double rho, double P, double* T, double* e);
 double orc_heating_rate(int heating, const double* heat_params, double t, double rho_f_ni);
 
 #ifdef __cplusplus

@@ -37,6 +37,13 @@ struct BatchState {
   int* item_tube = nullptr;
   int* item_start = nullptr;
   int nitems = 0;
+  std::vector<int> item_first;  // first item of every tube (+ nitems)
+  // host-resident runs: per-part control blocks, copy streams and events
+  int nparts = 0;
+  BatchCtrl* part_ctrl = nullptr;
+  BatchCtrl* part_ctrl_host = nullptr;
+  cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_done;
   // MLP
   float* w = nullptr;
   float* m = nullptr;
@@ -97,7 +104,9 @@ static int occupancy_nw(int nw, int* blocks) {
 static int make_items(hydro_ctx* h, int item_len) {
   BatchState* bs = h->bs;
   std::vector<int> tube, start;
+  bs->item_first.assign(bs->ntubes + 1, 0);
   for (int b = 0; b < bs->ntubes; ++b) {
+    bs->item_first[b] = (int)tube.size();
     const int nb = (int)(bs->off[b + 1] - bs->off[b]);
     for (int s = 0; s < nb; s += item_len) {
       tube.push_back(b);
@@ -113,6 +122,7 @@ static int make_items(hydro_ctx* h, int item_len) {
   HCK(cudaMemcpy(bs->item_tube, tube.data(), sizeof(int) * tube.size(), cudaMemcpyHostToDevice));
   HCK(cudaMemcpy(bs->item_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
   bs->nitems = (int)tube.size();
+  bs->item_first[bs->ntubes] = bs->nitems;
   bs->item_len = item_len;
   return HYDRO_OK;
 }
@@ -132,6 +142,7 @@ static BatchArgs<T> batch_args(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const 
   a.item_len = bs->item_len;
   a.nitems = bs->nitems;
   a.ntubes = bs->ntubes;
+  a.tube0 = 0;
   a.smax_cur = smax_cur;
   a.smax_next = smax_next;
   a.t_tube = t_tube;
@@ -286,7 +297,7 @@ static int batch_speed(hydro_ctx* h, int slot, int* status) {
   HCK(cudaMalloc(&d_status, sizeof(int)));
   HCK(cudaMemsetAsync(d_status, 0, sizeof(int), h->stream));
   HCK(cudaMemsetAsync(bs->smax_next, 0, sizeof(unsigned long long) * bs->ntubes, h->stream));
-  batch_speed_kernel<T><<<bs->ntubes, 256, 0, h->stream>>>((const T*)h->buf[slot], bs->total, bs->off_d,
+  batch_speed_kernel<T><<<bs->ntubes, 256, 0, h->stream>>>((const T*)h->buf[slot], bs->total, bs->off_d, 0,
                                                             bs->ntubes, make_gas<T>(h->gamma), bs->smax_next,
                                                             d_status);
   HCK(cudaGetLastError());
@@ -406,6 +417,12 @@ int hydro_batch_stats_impl(hydro_ctx* h, hydro_stats_t* out) {
 void hydro_batch_free_impl(hydro_ctx* h) {
   BatchState* bs = h->bs;
   drop_graph(bs);
+  cudaFree(bs->part_ctrl);
+  cudaFreeHost(bs->part_ctrl_host);
+  if (bs->s_h2d) cudaStreamDestroy(bs->s_h2d);
+  if (bs->s_d2h) cudaStreamDestroy(bs->s_d2h);
+  for (cudaEvent_t e : bs->ev_in) cudaEventDestroy(e);
+  for (cudaEvent_t e : bs->ev_done) cudaEventDestroy(e);
   cudaFree(bs->off_d);
   cudaFree(bs->smax_cur);
   cudaFree(bs->smax_next);
@@ -421,6 +438,131 @@ void hydro_batch_free_impl(hydro_ctx* h) {
   cudaFree(bs->harvest_n);
   delete bs;
   h->bs = nullptr;
+}
+
+// Pipelined host-resident run: the tubes are split into parts of about equal
+// cell counts; part p's input copy (stream s_h2d), its steps (the handle's
+// stream) and its output copy (stream s_d2h) are ordered by events, so the
+// copies of one part overlap the computation of others.  Every part has its
+// own control block and work-queue range; the per-cell arithmetic is that of
+// hydro_batch_set_state + hydro_batch_run + hydro_batch_get_state.
+template <typename T>
+static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, double cfl, int nparts) {
+  BatchState* bs = h->bs;
+  const int P = std::max(1, std::min(nparts, bs->ntubes));
+  if (bs->nparts < P) {
+    cudaFree(bs->part_ctrl);
+    cudaFreeHost(bs->part_ctrl_host);
+    bs->part_ctrl = nullptr;
+    bs->part_ctrl_host = nullptr;
+    bs->nparts = 0;
+    HCK(cudaMalloc(&bs->part_ctrl, sizeof(BatchCtrl) * P));
+    HCK(cudaMallocHost(&bs->part_ctrl_host, sizeof(BatchCtrl) * P));
+    bs->nparts = P;
+  }
+  if (!bs->s_h2d) HCK(cudaStreamCreateWithFlags(&bs->s_h2d, cudaStreamNonBlocking));
+  if (!bs->s_d2h) HCK(cudaStreamCreateWithFlags(&bs->s_d2h, cudaStreamNonBlocking));
+  while ((int)bs->ev_in.size() < P) {
+    cudaEvent_t a, b;
+    HCK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    HCK(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    bs->ev_in.push_back(a);
+    bs->ev_done.push_back(b);
+  }
+  int st = read_bctrl(h);
+  if (st) return st;
+  // part boundaries at tubes, about total/P cells each
+  std::vector<int> b0(P + 1, bs->ntubes);
+  b0[0] = 0;
+  for (int p = 1, b = 0; p < P; ++p) {
+    const long long target = bs->total * p / P;
+    while (b < bs->ntubes && bs->off[b] < target) ++b;
+    b0[p] = std::max(b, b0[p - 1] + 1);
+  }
+  for (int p = 1; p <= P; ++p) b0[p] = std::min(std::max(b0[p], b0[p - 1]), bs->ntubes);
+  b0[P] = bs->ntubes;
+  const int slot = 0;  // input lands in buffer 0; the result is in buffer (nsteps & 1)
+  const int out_slot = nsteps & 1;
+  for (int p = 0; p < P; ++p) {
+    BatchCtrl& c = bs->part_ctrl_host[p];
+    std::memset(&c, 0, sizeof(BatchCtrl));
+    c.c.cur = slot;
+    c.c.step = bs->bctrl_host->c.step;
+    c.c.err_step = -1;
+  }
+  HCK(cudaMemcpyAsync(bs->part_ctrl, bs->part_ctrl_host, sizeof(BatchCtrl) * P, cudaMemcpyHostToDevice, h->stream));
+  HCK(cudaStreamSynchronize(h->stream));
+  const Gas<T> gas = make_gas<T>(h->gamma);
+  T* buf_in = (T*)h->buf[slot];
+  T* buf_out = (T*)h->buf[out_slot];
+  for (int p = 0; p < P; ++p) {
+    const int t0 = b0[p], t1 = b0[p + 1];
+    if (t1 <= t0) continue;
+    const long long c0 = bs->off[t0], nc = bs->off[t1] - c0;
+    for (int v = 0; v < 3; ++v)
+      HCK(cudaMemcpyAsync(buf_in + v * bs->total + c0, U_in + v * bs->total + c0, sizeof(T) * nc,
+                          cudaMemcpyHostToDevice, bs->s_h2d));
+    HCK(cudaEventRecord(bs->ev_in[p], bs->s_h2d));
+    HCK(cudaStreamWaitEvent(h->stream, bs->ev_in[p], 0));
+    // the part's per-tube speeds and validity (as hydro_batch_set_state)
+    HCK(cudaMemsetAsync(bs->smax_next + t0, 0, sizeof(unsigned long long) * (t1 - t0), h->stream));
+    HCK(cudaMemsetAsync(bs->t_tube + t0, 0, sizeof(double) * (t1 - t0), h->stream));
+    batch_speed_kernel<T><<<t1 - t0, 256, 0, h->stream>>>(buf_in, bs->total, bs->off_d, t0, t1 - t0, gas,
+                                                         bs->smax_next, &bs->part_ctrl[p].c.status);
+    HCK(cudaGetLastError());
+    HCK(cudaMemcpyAsync(bs->smax_cur + t0, bs->smax_next + t0, sizeof(double) * (t1 - t0),
+                        cudaMemcpyDeviceToDevice, h->stream));
+    HCK(cudaMemsetAsync(bs->smax_next + t0, 0, sizeof(unsigned long long) * (t1 - t0), h->stream));
+    BatchArgs<T> a = batch_args<T>(h, cfl, &bs->part_ctrl[p], bs->smax_cur, bs->smax_next, bs->t_tube);
+    const int i0 = bs->item_first[t0], i1 = bs->item_first[t1];
+    a.item_tube = bs->item_tube + i0;
+    a.item_start = bs->item_start + i0;
+    a.nitems = i1 - i0;
+    a.tube0 = t0;
+    a.ntubes = t1 - t0;
+    for (int k = 0; k < nsteps; ++k) {
+      st = bs->nw == 4 ? launch_batch_nw<T, 4>(h, a, bs->grid) : launch_batch_nw<T, 8>(h, a, bs->grid);
+      if (st) return st;
+    }
+    HCK(cudaEventRecord(bs->ev_done[p], h->stream));
+    HCK(cudaStreamWaitEvent(bs->s_d2h, bs->ev_done[p], 0));
+    for (int v = 0; v < 3; ++v)
+      HCK(cudaMemcpyAsync(U_out + v * bs->total + c0, buf_out + v * bs->total + c0, sizeof(T) * nc,
+                          cudaMemcpyDeviceToHost, bs->s_d2h));
+  }
+  HCK(cudaMemcpyAsync(bs->part_ctrl_host, bs->part_ctrl, sizeof(BatchCtrl) * P, cudaMemcpyDeviceToHost,
+                      h->stream));
+  HCK(cudaStreamSynchronize(h->stream));
+  HCK(cudaStreamSynchronize(bs->s_d2h));
+  int code = 0;
+  long long iters = 0, mlp = 0, fb = 0;
+  for (int p = 0; p < P; ++p) {
+    const Ctrl& c = bs->part_ctrl_host[p].c;
+    if (c.status && !code) code = c.status;
+    iters += (long long)c.iters;
+    mlp += (long long)c.mlp;
+    fb += (long long)c.fallbacks;
+  }
+  // the handle now holds the result, as after set_state + run
+  BatchCtrl& g = *bs->bctrl_host;
+  g.c.status = 0;
+  g.c.done = 0;
+  g.c.err_step = -1;
+  g.next_item = 0;
+  if (!code) {
+    g.c.cur = out_slot;
+    g.c.step += nsteps;
+    g.c.iters += iters;
+    g.c.mlp += mlp;
+    g.c.fallbacks += fb;
+  }
+  if ((st = write_bctrl(h))) return st;
+  if (code) {
+    set_error("hydro_batch_run_host: device status " + std::to_string(code) +
+              " (the state copied in is invalid or a step failed); the output is unspecified");
+    return code;
+  }
+  return HYDRO_OK;
 }
 
 extern "C" {
@@ -481,6 +623,18 @@ int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int
   bs->grid = h->num_sms * 2;
   *out = h;
   return HYDRO_OK;
+}
+
+int hydro_batch_run_host(hydro_t h, const void* U_in, void* U_out, int nsteps, double cfl, int nparts) {
+  if (!h || !h->batched || !U_in || !U_out) return berr("hydro_batch_run_host: bad argument");
+  if (nsteps < 1 || !(cfl > 0.0)) return berr("hydro_batch_run_host: need nsteps >= 1 and cfl > 0");
+  if (nparts < 0) return berr("hydro_batch_run_host: nparts must be >= 0");
+  int st;
+  if ((st = autotune_batch(h, cfl))) return st;
+  if (nparts == 0) nparts = 8;
+  return h->precision == 64
+             ? batch_run_host_t<double>(h, (const double*)U_in, (double*)U_out, nsteps, cfl, nparts)
+             : batch_run_host_t<float>(h, (const float*)U_in, (float*)U_out, nsteps, cfl, nparts);
 }
 
 int hydro_batch_run(hydro_t h, int nsteps, double cfl) {

@@ -275,6 +275,21 @@ Gas<T> make_gas(double gm) {
 template Gas<float> make_gas<float>(double);
 template Gas<double> make_gas<double>(double);
 
+template <typename T>
+GasRad<T> make_gas_rad(double gm, double R, double a) {
+  GasRad<T> g;
+  static_cast<Gas<T>&>(g) = make_gas<T>(gm);
+  g.R = (T)R;
+  g.Rg = (T)(R / (gm - 1.0));
+  g.a = (T)a;
+  g.a3 = (T)(a / 3.0);
+  g.c_g = (T)(gm / (gm - 1.0));
+  g.c_1 = (T)(1.0 / (gm - 1.0));
+  return g;
+}
+template GasRad<float> make_gas_rad<float>(double, double, double);
+template GasRad<double> make_gas_rad<double>(double, double, double);
+
 // Ni-56 decay heating constants of Eq. 8-9 (CGS).
 static const double M_U = 1.66053906660e-24, MEV = 1.602176634e-6, DAY = 86400.0;
 
@@ -307,6 +322,7 @@ static SweepArgs<T> sweep_args(hydro_ctx* h, double dt_host, double cfl, double 
   a.ni_tni = tni;
   a.ni_tco = tco;
   a.gas = make_gas<T>(h->gamma);
+  a.grad = make_gas_rad<T>(h->gamma, h->R_gas, h->a_rad);
   a.dt_host = dt_host;
   a.cfl = cfl;
   a.t_end = t_end;
@@ -332,10 +348,21 @@ static int launch_step_t(hydro_ctx* h, double dt_host, double cfl, double t_end,
   }
   SweepArgs<T> a = sweep_args<T>(h, dt_host, cfl, t_end, ctrl);
   cudaError_t e;
-  switch (h->dim) {
-    case 1: e = sweep_dispatch<T, 1>(a, h->nsx, h->riemann, h->stream, &h->tile_x, &h->tile_y, &h->threads); break;
-    case 2: e = sweep_dispatch<T, 2>(a, h->nsx, h->riemann, h->stream, &h->tile_x, &h->tile_y, &h->threads); break;
-    default: e = sweep_dispatch<T, 3>(a, h->nsx, h->riemann, h->stream, &h->tile_x, &h->tile_y, &h->threads); break;
+  int* tx = &h->tile_x;
+  int* ty = &h->tile_y;
+  int* nt = &h->threads;
+  if (h->eos_rad) {
+    switch (h->dim) {
+      case 1: e = sweep_dispatch_rad<T, 1>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+      case 2: e = sweep_dispatch_rad<T, 2>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+      default: e = sweep_dispatch_rad<T, 3>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+    }
+  } else {
+    switch (h->dim) {
+      case 1: e = sweep_dispatch<T, 1>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+      case 2: e = sweep_dispatch<T, 2>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+      default: e = sweep_dispatch<T, 3>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+    }
   }
   if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
   return HYDRO_OK;
@@ -425,7 +452,8 @@ static int autotune_grid(hydro_ctx* h, double cfl) {
   h->tuned = true;
   if (h->dim < 3) return HYDRO_OK;
   std::ostringstream key;
-  key << "grid_d" << h->dim << "_p" << h->precision << "_r" << h->riemann << "_ns" << h->ns << "_n"
+  key << "grid_d" << h->dim << "_p" << h->precision << "_r" << h->riemann << "_ns" << h->ns
+      << (h->eos_rad ? "_rad" : "") << "_n"
       << h->n[0] << "x" << h->n[1] << "x" << h->n[2] << "_" << device_key();
   int cached;
   double us;
@@ -506,7 +534,8 @@ static int validate_into(hydro_ctx* h, int slot, int* status_out, double* smax_o
   d_smax = (unsigned long long*)(d_status + 2);
   HCK(cudaMemsetAsync(d_status, 0, sizeof(int) + sizeof(unsigned long long) + 8, h->stream));
   const int blocks = (int)std::max<long long>(1, std::min<long long>((h->ncell + 255) / 256, (long long)h->num_sms * 8));
-  Gas<T> gas = make_gas<T>(h->gamma);
+  const Gas<T> gas = make_gas<T>(h->gamma);
+  const GasRad<T> grad = make_gas_rad<T>(h->gamma, h->R_gas, h->a_rad);
   const T* U = (const T*)h->buf[slot];
   const T* w0 = (const T*)h->geo[G_IW0];
   const T* w1 = (const T*)h->geo[G_IW1];
@@ -514,10 +543,20 @@ static int validate_into(hydro_ctx* h, int slot, int* status_out, double* smax_o
   const T* ir = (const T*)h->geo[G_IR];
   const T* is = (const T*)h->geo[G_IS];
   const int sph = h->coords == HYDRO_SPHERICAL;
-  switch (h->dim) {
-    case 1: validate_kernel<T, 1><<<blocks, 256, 0, h->stream>>>(U, h->ncell, h->n[0], h->n[1], h->nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
-    case 2: validate_kernel<T, 2><<<blocks, 256, 0, h->stream>>>(U, h->ncell, h->n[0], h->n[1], h->nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
-    default: validate_kernel<T, 3><<<blocks, 256, 0, h->stream>>>(U, h->ncell, h->n[0], h->n[1], h->nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
+  const long long nc = h->ncell;
+  const int n0 = h->n[0], n1 = h->n[1], nv = h->nv;
+  if (h->eos_rad) {
+    switch (h->dim) {
+      case 1: validate_kernel<T, 1><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, grad, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
+      case 2: validate_kernel<T, 2><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, grad, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
+      default: validate_kernel<T, 3><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, grad, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
+    }
+  } else {
+    switch (h->dim) {
+      case 1: validate_kernel<T, 1><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
+      case 2: validate_kernel<T, 2><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
+      default: validate_kernel<T, 3><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
+    }
   }
   HCK(cudaGetLastError());
   int hs[4];
@@ -624,6 +663,25 @@ int hydro_create(const hydro_grid* grid, int coords, const hydro_eos* eos, int r
     return st;
   }
   *out = h;
+  return HYDRO_OK;
+}
+
+int hydro_set_eos_radiation(hydro_t h, double R_gas, double a_rad) {
+  if (!h || h->batched) return arg_error("hydro_set_eos_radiation: grid handle required");
+  if (!(R_gas > 0.0) || !(a_rad >= 0.0) || !std::isfinite(R_gas) || !std::isfinite(a_rad))
+    return arg_error("hydro_set_eos_radiation: need R_gas > 0 and a_rad >= 0");
+  if (h->riemann == HYDRO_EXACT) {
+    set_error("hydro_set_eos_radiation: the exact Riemann solver assumes the ideal gas; use HLL or HLLC");
+    return HYDRO_ERR_UNSUPPORTED;
+  }
+  h->eos_rad = 1;
+  h->R_gas = R_gas;
+  h->a_rad = a_rad;
+  h->tuned = false;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
   return HYDRO_OK;
 }
 

@@ -1,7 +1,8 @@
 // aux_kernels.cuh -- small kernels around the fused sweep.
 //
 //   validate_kernel  a2 + a9 on a candidate state: rho > 0, P > 0, finite,
-//                    and the CFL signal speed max_cells sum_d (|u_d|+c)/h_d.
+//                    and the CFL signal speed max_cells sum_d (|u_d|+c)/h_d
+//                    (ideal gas, Eq. 5, or gas + radiation, Eq. 6-7).
 //   totals kernels   a10: sum_cells U dV per variable; per-thread compensated
 //                    (Kahan) partials in the state precision, FP64 block
 //                    trees in a fixed order, so the result is deterministic.
@@ -13,9 +14,9 @@
 
 namespace hydro {
 
-template <typename T, int DIM>
+template <typename T, int DIM, typename G>
 __global__ void __launch_bounds__(256)
-    validate_kernel(const T* __restrict__ U, long long ncell, int n0, int n1, int nv, Gas<T> gas,
+    validate_kernel(const T* __restrict__ U, long long ncell, int n0, int n1, int nv, G gas,
                     int spherical, const T* __restrict__ w0, const T* __restrict__ w1,
                     const T* __restrict__ w2, const T* __restrict__ ir, const T* __restrict__ is,
                     int* status, unsigned long long* smax_bits) {
@@ -39,9 +40,15 @@ __global__ void __launch_bounds__(256)
     T ke = T(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) ke += u[1 + d] * u[1 + d];
-    const T p = gas.gm1 * (u[1 + DIM] - T(0.5) * ke / rho);
+    T p, c2;
+    if constexpr (G::RAD) {
+      gas.from_e(rho, u[1 + DIM] - T(0.5) * ke / rho, p, c2);
+    } else {
+      p = gas.gm1 * (u[1 + DIM] - T(0.5) * ke / rho);
+      c2 = gas.g * p / rho;
+    }
     if (!(rho > T(0)) || !(p > T(0))) { err = err ? err : ST_NEG; continue; }
-    const T cs = dsqrt(gas.g * p / rho);
+    const T cs = dsqrt(c2);
     T sp = (fabs(u[1] / rho) + cs) * w0[i + 2];
     if (DIM >= 2) {
       const T ih = spherical ? w1[j + 2] * ir[i + 2] : w1[j + 2];

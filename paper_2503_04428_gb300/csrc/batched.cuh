@@ -70,7 +70,8 @@ struct BatchArgs {
   const int* item_start;
   int item_len;                // cells per work item (a multiple of BSEG)
   int nitems;
-  int ntubes;
+  int ntubes;                  // tubes committed by this launch: tube0 .. tube0+ntubes-1
+  int tube0;
   const double* smax_cur;      // per tube: max (|u|+c)/h of the current state
   unsigned long long* smax_next;
   double* t_tube;
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
   const bool ok = vb->c.status == 0;
   if (ok) {
     double* smc = const_cast<double*>(a.smax_cur);
-    for (int t = threadIdx.x; t < a.ntubes; t += NW * 32) {
+    for (int t = a.tube0 + threadIdx.x; t < a.tube0 + a.ntubes; t += NW * 32) {
       a.t_tube[t] += a.cfl / smc[t];
       const unsigned long long nbits = atomicExch(&a.smax_next[t], 0ull);
       smc[t] = __longlong_as_double((long long)nbits);
@@ -433,10 +434,10 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
 
 // Signal speed of the current state per tube (after set_state).
 template <typename T>
-__global__ void batch_speed_kernel(const T* U, long long total, const long long* off, int ntubes,
-                                   Gas<T> gas, unsigned long long* smax_bits, int* status) {
-  const int b = blockIdx.x;
-  if (b >= ntubes) return;
+__global__ void batch_speed_kernel(const T* U, long long total, const long long* off, int tube0,
+                                   int ntubes, Gas<T> gas, unsigned long long* smax_bits, int* status) {
+  if ((int)blockIdx.x >= ntubes) return;
+  const int b = tube0 + blockIdx.x;
   const long long base = off[b];
   const int nb = (int)(off[b + 1] - base);
   double smax = 0.0;

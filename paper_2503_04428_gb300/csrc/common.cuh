@@ -76,6 +76,7 @@ struct SweepArgs {
   T heat_q;               // CONST: volumetric rate
   double ni_lambda, ni_a, ni_qco, ni_tni, ni_tco;  // Eq. 8 constants (CGS)
   Gas<T> gas;
+  GasRad<T> grad;         // gas + radiation constants (kernels instantiated for Eq. 6-7)
   double dt_host;         // > 0: use this dt; otherwise CFL on the device
   double cfl;
   double t_end;           // > 0: clip dt so t does not pass t_end
@@ -87,6 +88,10 @@ struct SweepArgs {
 template <typename T, int DIM>
 cudaError_t sweep_dispatch(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s, int* tx, int* ty,
                            int* nt);
+// The same for the gas + radiation EoS (HLL and HLLC only).
+template <typename T, int DIM>
+cudaError_t sweep_dispatch_rad(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s, int* tx, int* ty,
+                               int* nt);
 
 // Bits of a non-negative double, for an ordered atomicMax.
 __device__ __forceinline__ unsigned long long dbits(double x) {

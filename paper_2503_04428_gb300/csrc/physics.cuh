@@ -21,8 +21,10 @@ enum { RS_HLL = 0, RS_HLLC = 1, RS_EXACT = 2 };
 enum { ST_OK = 0, ST_NEG = -3, ST_NONFINITE = -4, ST_NEWTON = -5, ST_VACUUM = -8 };
 
 // Gas constants precomputed on the host (double) and passed by value.
+// Gas<T> is the ideal gas of Eq. 5.
 template <typename T>
 struct Gas {
+  static constexpr bool RAD = false;
   T g;        // gamma
   T gm1;      // gamma - 1
   T igm1;     // 1/(gamma - 1)
@@ -34,6 +36,65 @@ struct Gas {
   T two_gm1;  // 2/(gamma - 1)
   T ig;       // 1/gamma
   T pow_c;    // 2 gamma/(gamma - 1)
+};
+
+template <typename T> __device__ __forceinline__ T temp_tol();
+template <> __device__ __forceinline__ double temp_tol<double>() { return 1e-13; }
+template <> __device__ __forceinline__ float temp_tol<float>() { return 1e-6f; }
+
+// Ideal gas in equilibrium with radiation, Eq. 6-7: e = rho R T/(gamma-1) +
+// a T^4, P = rho R T + a T^4/3 with R = k_b/(mu m_u), and the sound speed of
+// Eq. 7.  The temperature comes from a Newton iteration (Sect. 2.3).
+template <typename T>
+struct GasRad : Gas<T> {
+  static constexpr bool RAD = true;
+  T R;    // specific gas constant k_b/(mu m_u)
+  T Rg;   // R/(gamma - 1)
+  T a;    // radiation constant
+  T a3;   // a/3
+  T c_g;  // gamma/(gamma - 1), numerator constant of Eq. 7
+  T c_1;  // 1/(gamma - 1), denominator constant of Eq. 7
+
+  // The temperature where c1 t + c4 t^4 = y (c1 > 0, c4 >= 0).  The left side
+  // is increasing and convex in t > 0, so Newton from the upper bound
+  // min(y/c1, (y/c4)^(1/4)) descends monotonically to the root; it stops when
+  // the relative step is below temp_tol and takes one more step.  y <= 0
+  // gives y/c1 <= 0, which the positivity checks reject.
+  __device__ __forceinline__ T temperature(T c1, T c4, T y) const {
+    T t = y / c1;
+    if (!(y > T(0))) return t;
+    if (c4 > T(0)) t = fmin(t, dsqrt_(dsqrt_(y / c4)));
+    bool conv = false;
+    for (int it = 0; it < 60; ++it) {
+      const T t3 = t * t * t;
+      const T tn = t - (c1 * t + c4 * t3 * t - y) / (c1 + T(4) * c4 * t3);
+      const T ch = fabs(tn - t) / tn;
+      t = tn;
+      if (conv) break;
+      if (ch < temp_tol<T>()) conv = true;
+    }
+    return t;
+  }
+  static __device__ __forceinline__ T dsqrt_(T x) { return sqrt(x); }
+  // Eq. 7 from the gas and radiation pressures
+  __device__ __forceinline__ T sound2(T rho, T pg, T pr) const {
+    const T al = pr / pg;
+    return (c_g + T(20) * al + T(16) * al * al) / (c_1 + T(12) * al) * pg / rho;
+  }
+  // P and c^2 from (rho, e)
+  __device__ __forceinline__ void from_e(T rho, T e, T& p, T& c2) const {
+    const T t = temperature(rho * Rg, a, e);
+    const T pg = rho * R * t, pr = a3 * t * t * t * t;
+    p = pg + pr;
+    c2 = sound2(rho, pg, pr);
+  }
+  // e and c^2 from (rho, P)
+  __device__ __forceinline__ void from_p(T rho, T p, T& e, T& c2) const {
+    const T t = temperature(rho * R, a3, p);
+    const T pg = rho * R * t, pr = a3 * t * t * t * t;
+    e = pg * c_1 + T(3) * pr;
+    c2 = sound2(rho, pg, pr);
+  }
 };
 
 template <typename T> __device__ __forceinline__ T dsqrt(T x);
@@ -52,8 +113,8 @@ template <> __device__ __forceinline__ float dlog<float>(float x) { return logf(
 // ---------------------------------------------------------------------------
 // EoS conversions (Eq. 5 with E = e + rho|u|^2/2)
 // ---------------------------------------------------------------------------
-template <typename T, int D, int NSX>
-__device__ __forceinline__ void to_prim(const T* U, T* W, const Gas<T>& gas) {
+template <typename T, int D, int NSX, typename G>
+__device__ __forceinline__ void to_prim(const T* U, T* W, const G& gas) {
   const T rho = U[0];
   const T ir = T(1) / rho;
   T ke = T(0);
@@ -63,13 +124,60 @@ __device__ __forceinline__ void to_prim(const T* U, T* W, const Gas<T>& gas) {
     ke += U[1 + d] * W[1 + d];
   }
   W[0] = rho;
-  W[1 + D] = gas.gm1 * (U[1 + D] - T(0.5) * ke);
+  if constexpr (G::RAD) {
+    T c2;
+    gas.from_e(rho, U[1 + D] - T(0.5) * ke, W[1 + D], c2);
+  } else {
+    W[1 + D] = gas.gm1 * (U[1 + D] - T(0.5) * ke);
+  }
 #pragma unroll
   for (int s = 0; s < NSX; ++s) W[2 + D + s] = U[2 + D + s] * ir;
 }
 
-template <typename T, int D, int NSX>
-__device__ __forceinline__ void to_cons(const T* W, T* U, const Gas<T>& gas) {
+// to_prim for the gas + radiation EoS that also returns c^2 (Eq. 7) from the
+// same temperature solve.
+template <typename T, int D, int NSX, typename G>
+__device__ __forceinline__ void to_prim_c2(const T* U, T* W, T& c2, const G& gas) {
+  const T rho = U[0];
+  const T ir = T(1) / rho;
+  T ke = T(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    W[1 + d] = U[1 + d] * ir;
+    ke += U[1 + d] * W[1 + d];
+  }
+  W[0] = rho;
+  gas.from_e(rho, U[1 + D] - T(0.5) * ke, W[1 + D], c2);
+#pragma unroll
+  for (int s = 0; s < NSX; ++s) W[2 + D + s] = U[2 + D + s] * ir;
+}
+
+// Internal energy per volume of the primitive state (rho, p) (Eq. 5 or 6).
+template <typename T, typename G>
+__device__ __forceinline__ T eint_of(const G& gas, T rho, T p) {
+  if constexpr (G::RAD) {
+    T e, c2;
+    gas.from_p(rho, p, e, c2);
+    return e;
+  } else {
+    return p * gas.igm1;
+  }
+}
+
+// Square of the sound speed at (rho, p): gamma p/rho (Eq. 5) or Eq. 7.
+template <typename T, typename G>
+__device__ __forceinline__ T sound2_of(const G& gas, T rho, T p) {
+  if constexpr (G::RAD) {
+    T e, c2;
+    gas.from_p(rho, p, e, c2);
+    return c2;
+  } else {
+    return gas.g * p / rho;
+  }
+}
+
+template <typename T, int D, int NSX, typename G>
+__device__ __forceinline__ void to_cons(const T* W, T* U, const G& gas) {
   const T rho = W[0];
   T v2 = T(0);
 #pragma unroll
@@ -78,19 +186,22 @@ __device__ __forceinline__ void to_cons(const T* W, T* U, const Gas<T>& gas) {
     v2 += W[1 + d] * W[1 + d];
   }
   U[0] = rho;
-  U[1 + D] = W[1 + D] * gas.igm1 + T(0.5) * rho * v2;
+  if constexpr (G::RAD) U[1 + D] = eint_of(gas, rho, W[1 + D]) + T(0.5) * rho * v2;
+  else U[1 + D] = W[1 + D] * gas.igm1 + T(0.5) * rho * v2;
 #pragma unroll
   for (int s = 0; s < NSX; ++s) U[2 + D + s] = rho * W[2 + D + s];
 }
 
 // Physical flux through a face normal to axis DIR, from primitives.
-template <typename T, int D, int NSX, int DIR>
-__device__ __forceinline__ void phys_flux(const T* W, T* F, const Gas<T>& gas) {
+template <typename T, int D, int NSX, int DIR, typename G>
+__device__ __forceinline__ void phys_flux(const T* W, T* F, const G& gas) {
   const T rho = W[0], un = W[1 + DIR], p = W[1 + D];
   T v2 = T(0);
 #pragma unroll
   for (int d = 0; d < D; ++d) v2 += W[1 + d] * W[1 + d];
-  const T E = p * gas.igm1 + T(0.5) * rho * v2;
+  T E;
+  if constexpr (G::RAD) E = eint_of(gas, rho, p) + T(0.5) * rho * v2;
+  else E = p * gas.igm1 + T(0.5) * rho * v2;
   const T mn = rho * un;
   F[0] = mn;
 #pragma unroll
@@ -117,8 +228,113 @@ __device__ __forceinline__ T limit(int kind, T dm, T dp) {
 // ---------------------------------------------------------------------------
 // HLL with Davis wave-speed bounds.
 // ---------------------------------------------------------------------------
+// Flux through a face normal to DIR and the conserved state of a primitive
+// state whose internal energy per volume e is already known.
 template <typename T, int D, int NSX, int DIR>
-__device__ __forceinline__ void riemann_hll(const T* WL, const T* WR, T* F, const Gas<T>& gas) {
+__device__ __forceinline__ void flux_cons_e(const T* W, T e, T* F, T* U) {
+  const T rho = W[0], un = W[1 + DIR], p = W[1 + D];
+  T v2 = T(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) v2 += W[1 + d] * W[1 + d];
+  const T E = e + T(0.5) * rho * v2;
+  const T mn = rho * un;
+  F[0] = mn;
+  U[0] = rho;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    F[1 + d] = mn * W[1 + d];
+    U[1 + d] = rho * W[1 + d];
+  }
+  F[1 + DIR] += p;
+  F[1 + D] = un * (E + p);
+  U[1 + D] = E;
+#pragma unroll
+  for (int s = 0; s < NSX; ++s) {
+    F[2 + D + s] = mn * W[2 + D + s];
+    U[2 + D + s] = rho * W[2 + D + s];
+  }
+}
+
+// HLL for the gas + radiation EoS: one temperature solve per side gives e
+// and the Eq. 7 sound speed.
+template <typename T, int D, int NSX, int DIR, typename G>
+__device__ __forceinline__ void riemann_hll_rad(const T* WL, const T* WR, T* F, const G& gas) {
+  constexpr int NV = 2 + D + NSX;
+  T eL, c2L, eR, c2R;
+  gas.from_p(WL[0], WL[1 + D], eL, c2L);
+  gas.from_p(WR[0], WR[1 + D], eR, c2R);
+  const T cL = dsqrt(c2L), cR = dsqrt(c2R);
+  const T SL = fmin(WL[1 + DIR] - cL, WR[1 + DIR] - cR);
+  const T SR = fmax(WL[1 + DIR] + cL, WR[1 + DIR] + cR);
+  T FL[NV], FR[NV], UL[NV], UR[NV];
+  flux_cons_e<T, D, NSX, DIR>(WL, eL, FL, UL);
+  flux_cons_e<T, D, NSX, DIR>(WR, eR, FR, UR);
+  if (SL >= T(0)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = FL[v];
+    return;
+  }
+  if (SR <= T(0)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = FR[v];
+    return;
+  }
+  const T inv = T(1) / (SR - SL);
+  const T sLR = SL * SR;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[v] = (SR * FL[v] - SL * FR[v] + sLR * (UR[v] - UL[v])) * inv;
+}
+
+// HLLC for the gas + radiation EoS (the star states need only E, p, rho, u).
+template <typename T, int D, int NSX, int DIR, typename G>
+__device__ __forceinline__ void riemann_hllc_rad(const T* WL, const T* WR, T* F, const G& gas) {
+  constexpr int NV = 2 + D + NSX;
+  const T rL = WL[0], rR = WR[0], uL = WL[1 + DIR], uR = WR[1 + DIR];
+  const T pL = WL[1 + D], pR = WR[1 + D];
+  T eL, c2L, eR, c2R;
+  gas.from_p(rL, pL, eL, c2L);
+  gas.from_p(rR, pR, eR, c2R);
+  const T cL = dsqrt(c2L), cR = dsqrt(c2R);
+  const T SL = fmin(uL - cL, uR - cR);
+  const T SR = fmax(uL + cL, uR + cR);
+  T Fk[NV], Uk[NV];
+  if (SL >= T(0)) {
+    flux_cons_e<T, D, NSX, DIR>(WL, eL, F, Uk);
+    return;
+  }
+  if (SR <= T(0)) {
+    flux_cons_e<T, D, NSX, DIR>(WR, eR, F, Uk);
+    return;
+  }
+  const T aL = rL * (SL - uL), aR = rR * (SR - uR);
+  const T Ss = (pR - pL + uL * aL - uR * aR) / (aL - aR);
+  const bool left = Ss >= T(0);
+  T W[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) W[v] = left ? WL[v] : WR[v];
+  const T S = left ? SL : SR;
+  const T a = left ? aL : aR;
+  const T rho = W[0], un = W[1 + DIR], p = W[1 + D];
+  flux_cons_e<T, D, NSX, DIR>(W, left ? eL : eR, Fk, Uk);
+  const T fac = a / (S - Ss);
+  T Us[NV];
+  Us[0] = fac;
+#pragma unroll
+  for (int d = 0; d < D; ++d) Us[1 + d] = fac * W[1 + d];
+  Us[1 + DIR] = fac * Ss;
+  Us[1 + D] = fac * (Uk[1 + D] / rho + (Ss - un) * (Ss + p / a));
+#pragma unroll
+  for (int s = 0; s < NSX; ++s) Us[2 + D + s] = fac * W[2 + D + s];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[v] = Fk[v] + S * (Us[v] - Uk[v]);
+}
+
+template <typename T, int D, int NSX, int DIR, typename G>
+__device__ __forceinline__ void riemann_hll(const T* WL, const T* WR, T* F, const G& gas) {
+  if constexpr (G::RAD) {
+    riemann_hll_rad<T, D, NSX, DIR>(WL, WR, F, gas);
+    return;
+  }
   constexpr int NV = 2 + D + NSX;
   const T cL = dsqrt(gas.g * WL[1 + D] / WL[0]);
   const T cR = dsqrt(gas.g * WR[1 + D] / WR[0]);
@@ -149,8 +365,12 @@ __device__ __forceinline__ void riemann_hll(const T* WL, const T* WR, T* F, cons
 // velocities and scalars.  Branches: SL>=0 -> F_L; S*>=0 -> F*_L; SR>0 -> F*_R;
 // otherwise F_R.
 // ---------------------------------------------------------------------------
-template <typename T, int D, int NSX, int DIR>
-__device__ __forceinline__ void riemann_hllc(const T* WL, const T* WR, T* F, const Gas<T>& gas) {
+template <typename T, int D, int NSX, int DIR, typename G>
+__device__ __forceinline__ void riemann_hllc(const T* WL, const T* WR, T* F, const G& gas) {
+  if constexpr (G::RAD) {
+    riemann_hllc_rad<T, D, NSX, DIR>(WL, WR, F, gas);
+    return;
+  }
   constexpr int NV = 2 + D + NSX;
   const T rL = WL[0], rR = WR[0], uL = WL[1 + DIR], uR = WR[1 + DIR];
   const T pL = WL[1 + D], pR = WR[1 + D];

@@ -37,6 +37,7 @@ int hydro_batch_stats_impl(hydro_ctx* h, hydro_stats_t* out);
 void hydro_batch_free_impl(hydro_ctx* h);
 namespace hydro {
 template <typename T> Gas<T> make_gas(double gm);
+template <typename T> GasRad<T> make_gas_rad(double gm, double R, double a);
 int tune_cache_get(const std::string& key, int* value, double* us);
 void tune_cache_put(const std::string& key, int value, double us);
 std::string device_key();
@@ -54,6 +55,8 @@ struct hydro_ctx {
   int dim = 1, n[3] = {1, 1, 1}, coords = 0, riemann = 1, limiter = 1, ns = 0, nsx = 0, nv = 3;
   int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   double gamma = 1.4;
+  int eos_rad = 0;                   // 1: gas + radiation EoS (Eq. 6-7)
+  double R_gas = 0.0, a_rad = 0.0;   // its constants
   long long ncell = 0;
   std::vector<double> faces[3];
   void* buf[2] = {nullptr, nullptr};

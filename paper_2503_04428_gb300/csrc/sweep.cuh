@@ -99,7 +99,7 @@ __device__ __forceinline__ int map_axis(int g, int n, int lo, int hi, bool& flip
 // Which face states a predictor pass writes.
 enum { PRED_ALL = 0, PRED_ZHI = 1, PRED_ZLO = 2 };
 
-template <typename T, int DIM, int NSX, int RS>
+template <typename T, int DIM, int NSX, int RS, int EOS>
 struct Sweep {
   using S = SweepShape<T, DIM, NSX>;
   static constexpr int NV = S::NV, TX = S::TX, TY = S::TY, EX = S::EX, EY = S::EY, HY = S::HY,
@@ -138,6 +138,12 @@ struct Sweep {
     ZR = ZL + 2 * NV * NFZ;
   }
 
+  // the EoS of this instantiation: ideal gas (Eq. 5) or gas + radiation (Eq. 6-7)
+  __device__ __forceinline__ const auto& gas() const {
+    if constexpr (EOS == 1) return a.grad;
+    else return a.gas;
+  }
+
   __device__ __forceinline__ T& W(int slot, int v, int ey, int ex) {
     return Ws[((slot * NV + v) * EY + ey) * EX + ex];
   }
@@ -164,7 +170,7 @@ struct Sweep {
       if (fx) u[1] = -u[1];
       if (DIM >= 2 && fy) u[2] = -u[2];
       if (DIM == 3 && fz) u[3] = -u[3];
-      to_prim<T, DIM, NSX>(u, w, a.gas);
+      to_prim<T, DIM, NSX>(u, w, gas());
 #pragma unroll
       for (int v = 0; v < NV; ++v) W(slot, v, ey, ex) = w[v];
     }
@@ -222,10 +228,10 @@ struct Sweep {
     T w[NV], u[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) w[v] = p[v * st];
-    to_cons<T, DIM, NSX>(w, u, a.gas);
+    to_cons<T, DIM, NSX>(w, u, gas());
 #pragma unroll
     for (int v = 0; v < NV; ++v) u[v] += dU[v];
-    to_prim<T, DIM, NSX>(u, w, a.gas);
+    to_prim<T, DIM, NSX>(u, w, gas());
     if (!(w[0] > T(0)) || !(w[1 + DIM] > T(0))) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) w[v] = Wc[v];
@@ -283,8 +289,8 @@ struct Sweep {
         Wp[v] = W(slot, v, ey, ex + 1);
       }
       faces_of<0>(Wm, Wc, Wp, gi, Wl, Wh);
-      phys_flux<T, DIM, NSX, 0>(Wl, Fl, a.gas);
-      phys_flux<T, DIM, NSX, 0>(Wh, Fh, a.gas);
+      phys_flux<T, DIM, NSX, 0>(Wl, Fl, gas());
+      phys_flux<T, DIM, NSX, 0>(Wh, Fh, gas());
       const T ih = inv_h(0, gi, gj, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -301,8 +307,8 @@ struct Sweep {
         Wp[v] = W(slot, v, ey + 1, ex);
       }
       faces_of<1>(Wm, Wc, Wp, gj, Wl, Wh);
-      phys_flux<T, DIM, NSX, 1>(Wl, Fl, a.gas);
-      phys_flux<T, DIM, NSX, 1>(Wh, Fh, a.gas);
+      phys_flux<T, DIM, NSX, 1>(Wl, Fl, gas());
+      phys_flux<T, DIM, NSX, 1>(Wh, Fh, gas());
       const T ih = inv_h(1, gi, gj, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -319,8 +325,8 @@ struct Sweep {
         Wp[v] = W(wslot(gz + 1), v, ey, ex);
       }
       faces_of<2>(Wm, Wc, Wp, gz, Wl, Wh);
-      phys_flux<T, DIM, NSX, 2>(Wl, Fl, a.gas);
-      phys_flux<T, DIM, NSX, 2>(Wh, Fh, a.gas);
+      phys_flux<T, DIM, NSX, 2>(Wl, Fl, gas());
+      phys_flux<T, DIM, NSX, 2>(Wh, Fh, gas());
       const T ih = inv_h(2, gi, gj, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -355,9 +361,9 @@ struct Sweep {
   template <int DIR>
   __device__ __forceinline__ void riemann(const T* WL, const T* WR, T* F, bool owned) {
     if constexpr (RS == RS_HLL) {
-      riemann_hll<T, DIM, NSX, DIR>(WL, WR, F, a.gas);
+      riemann_hll<T, DIM, NSX, DIR>(WL, WR, F, gas());
     } else if constexpr (RS == RS_HLLC) {
-      riemann_hllc<T, DIM, NSX, DIR>(WL, WR, F, a.gas);
+      riemann_hllc<T, DIM, NSX, DIR>(WL, WR, F, gas());
     } else {
       int it = 0, kind = 0;
       const int st = riemann_exact<T, DIM, NSX, DIR>(WL, WR, F, a.gas, T(0), it, kind);
@@ -470,8 +476,8 @@ struct Sweep {
         T Uh[NV], Wh[NV], Wo[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) Uh[v] = Uo[v] + dUo[v];
-        to_prim<T, DIM, NSX>(Uh, Wh, a.gas);
-        to_prim<T, DIM, NSX>(Uo, Wo, a.gas);
+        to_prim<T, DIM, NSX>(Uh, Wh, gas());
+        to_prim<T, DIM, NSX>(Uo, Wo, gas());
         P = (Wh[0] > T(0) && Wh[1 + DIM] > T(0)) ? Wh[1 + DIM] : Wo[1 + DIM];
       }
       T Tth = P, Tph = P;
@@ -510,14 +516,19 @@ struct Sweep {
     }
 
     // validity and the signal speed of the new state
-    T Wn[NV];
-    to_prim<T, DIM, NSX>(Un, Wn, a.gas);
+    T Wn[NV], c2n;
+    if constexpr (EOS == 1) {
+      to_prim_c2<T, DIM, NSX>(Un, Wn, c2n, a.grad);
+    } else {
+      to_prim<T, DIM, NSX>(Un, Wn, a.gas);
+      c2n = a.gas.g * Wn[1 + DIM] / Wn[0];
+    }
     bool finite = true;
 #pragma unroll
     for (int v = 0; v < NV; ++v) finite = finite && isfinite(Un[v]);
     if (!finite) err = err ? err : ST_NONFINITE;
     else if (!(Wn[0] > T(0)) || !(Wn[1 + DIM] > T(0))) err = err ? err : ST_NEG;
-    const T cs = dsqrt(a.gas.g * Wn[1 + DIM] / Wn[0]);
+    const T cs = dsqrt(c2n);
     T sp = T(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) sp += (fabs(Wn[1 + d]) + cs) * inv_h(d, gi, gj, gz);
@@ -631,8 +642,9 @@ __device__ __forceinline__ bool step_begin(const Ctrl* ctrl, double dt_host, dou
   return dt > 0.0;
 }
 
-template <typename T, int DIM, int NSX, int RS>
-__global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT, RS == RS_EXACT ? 1 : SweepShape<T, DIM, NSX>::MB)
+template <typename T, int DIM, int NSX, int RS, int EOS>
+__global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
+                                  (RS == RS_EXACT || EOS == 1) ? 1 : SweepShape<T, DIM, NSX>::MB)
     sweep_kernel(const SweepArgs<T> args) {
   using S = SweepShape<T, DIM, NSX>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -641,7 +653,7 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT, RS == RS_EXACT ? 
   int cur;
   if (!step_begin(args.ctrl, args.dt_host, args.cfl, args.t_end, dtd, t, step, cur)) return;
 
-  Sweep<T, DIM, NSX, RS> sw(args, reinterpret_cast<T*>(smem_raw));
+  Sweep<T, DIM, NSX, RS, EOS> sw(args, reinterpret_cast<T*>(smem_raw));
   sw.x0 = blockIdx.x * S::TX;
   sw.y0 = blockIdx.y * S::TY;
   sw.n2 = DIM == 3 ? args.n[2] : 1;
@@ -689,12 +701,12 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT, RS == RS_EXACT ? 
   finish_step<S::NT>(args.ctrl, sw.smax, sw.err, sw.n_fallback, sw.n_iters, 0ull, step, dtd);
 }
 
-template <typename T, int DIM, int NSX, int RS>
+template <typename T, int DIM, int NSX, int RS, int EOS>
 cudaError_t launch_sweep(const SweepArgs<T>& a, cudaStream_t s) {
   using S = SweepShape<T, DIM, NSX>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, DIM, NSX, RS>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, DIM, NSX, RS, EOS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::smem_bytes);
     if (e != cudaSuccess) return e;
@@ -702,18 +714,18 @@ cudaError_t launch_sweep(const SweepArgs<T>& a, cudaStream_t s) {
   }
   dim3 grid((a.n[0] + S::TX - 1) / S::TX, DIM >= 2 ? (a.n[1] + S::TY - 1) / S::TY : 1,
             DIM == 3 ? (a.n[2] + a.zchunk - 1) / a.zchunk : 1);
-  sweep_kernel<T, DIM, NSX, RS><<<grid, S::NT, S::smem_bytes, s>>>(a);
+  sweep_kernel<T, DIM, NSX, RS, EOS><<<grid, S::NT, S::smem_bytes, s>>>(a);
   return cudaGetLastError();
 }
 
 // Launch one instantiation and report its tile shape and threads per CTA.
-template <typename T, int DIM, int NSX, int RS>
+template <typename T, int DIM, int NSX, int RS, int EOS = 0>
 cudaError_t launch_sweep_shape(const SweepArgs<T>& a, cudaStream_t s, int* tx, int* ty, int* nt) {
   using S = SweepShape<T, DIM, NSX>;
   *tx = S::TX;
   *ty = S::TY;
   *nt = S::NT;
-  return launch_sweep<T, DIM, NSX, RS>(a, s);
+  return launch_sweep<T, DIM, NSX, RS, EOS>(a, s);
 }
 
 // Instantiate the dispatcher of one (precision, dimension) pair.
@@ -731,6 +743,22 @@ cudaError_t launch_sweep_shape(const SweepArgs<T>& a, cudaStream_t s, int* tx, i
       case 12: return launch_sweep_shape<T, DIM, 3, RS_HLL>(a, s, tx, ty, nt);                \
       case 13: return launch_sweep_shape<T, DIM, 3, RS_HLLC>(a, s, tx, ty, nt);               \
       case 14: return launch_sweep_shape<T, DIM, 3, RS_EXACT>(a, s, tx, ty, nt);              \
+      default: return cudaErrorInvalidValue;                                                  \
+    }                                                                                         \
+  }
+
+// The gas + radiation dispatcher of one (precision, dimension) pair.
+#define HYDRO_SWEEP_DISPATCH_RAD(T, DIM)                                                      \
+  template <>                                                                                 \
+  cudaError_t sweep_dispatch_rad<T, DIM>(const SweepArgs<T>& a, int nsx, int rs,              \
+                                         cudaStream_t s, int* tx, int* ty, int* nt) {         \
+    switch (nsx * 4 + rs) {                                                                   \
+      case 0: return launch_sweep_shape<T, DIM, 0, RS_HLL, 1>(a, s, tx, ty, nt);              \
+      case 1: return launch_sweep_shape<T, DIM, 0, RS_HLLC, 1>(a, s, tx, ty, nt);             \
+      case 4: return launch_sweep_shape<T, DIM, 1, RS_HLL, 1>(a, s, tx, ty, nt);              \
+      case 5: return launch_sweep_shape<T, DIM, 1, RS_HLLC, 1>(a, s, tx, ty, nt);             \
+      case 12: return launch_sweep_shape<T, DIM, 3, RS_HLL, 1>(a, s, tx, ty, nt);             \
+      case 13: return launch_sweep_shape<T, DIM, 3, RS_HLLC, 1>(a, s, tx, ty, nt);            \
       default: return cudaErrorInvalidValue;                                                  \
     }                                                                                         \
   }

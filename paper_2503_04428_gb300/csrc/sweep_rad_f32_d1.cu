@@ -1,0 +1,6 @@
+// Fused sweep kernels with the gas + radiation EoS (Eq. 6-7): float state, 1D grids, HLL and HLLC.
+#include "sweep.cuh"
+
+namespace hydro {
+HYDRO_SWEEP_DISPATCH_RAD(float, 1)
+}  // namespace hydro

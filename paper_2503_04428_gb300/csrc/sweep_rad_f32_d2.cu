@@ -1,0 +1,6 @@
+// Fused sweep kernels with the gas + radiation EoS (Eq. 6-7): float state, 2D grids, HLL and HLLC.
+#include "sweep.cuh"
+
+namespace hydro {
+HYDRO_SWEEP_DISPATCH_RAD(float, 2)
+}  // namespace hydro

@@ -1,0 +1,6 @@
+// Fused sweep kernels with the gas + radiation EoS (Eq. 6-7): double state, 1D grids, HLL and HLLC.
+#include "sweep.cuh"
+
+namespace hydro {
+HYDRO_SWEEP_DISPATCH_RAD(double, 1)
+}  // namespace hydro

@@ -84,6 +84,8 @@ _SIGS = {
     "hydro_mlp_loss_grad_device": [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP],
     "hydro_destroy": [_VP],
     "hydro_fma_rate": [C.c_int, C.POINTER(C.c_double)],
+    "hydro_set_eos_radiation": [_VP, C.c_double, C.c_double],
+    "hydro_batch_run_host": [_VP, _VP, _VP, C.c_int, C.c_double, C.c_int],
     "hydro_exact_sample": [_D, _D, C.c_long, C.c_double, C.POINTER(C.c_longlong), _D, C.c_long, _D],
     "hydro_batch_times": [_VP, _D],
     "hydro_last_error": [],
@@ -123,6 +125,21 @@ def _ptr(a):
         where = HYDRO_DEVICE if a.is_cuda else HYDRO_HOST
         return a.data_ptr(), where
     return a.ctypes.data, HYDRO_HOST
+
+
+def _host_address(U, dtype, shape):
+    """Address of a C-contiguous host array (numpy, or a CPU torch tensor) of
+    the given dtype and shape; anything else is rejected."""
+    if hasattr(U, "data_ptr"):
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.float32
+        if U.is_cuda or U.dtype != want or tuple(U.shape) != tuple(shape) or not U.is_contiguous():
+            raise ValueError("need a contiguous CPU tensor of shape %s and dtype %s" % (shape, want))
+        return U.data_ptr()
+    if (not isinstance(U, np.ndarray) or U.dtype != dtype or U.shape != tuple(shape)
+            or not U.flags.c_contiguous):
+        raise ValueError("need a C-contiguous array of shape %s and dtype %s" % (shape, np.dtype(dtype).name))
+    return U.ctypes.data
 
 
 def _stream(stream):
@@ -326,6 +343,8 @@ class Grid:
     def from_case(cls, case, precision=64, stream=None):
         g = cls(case["dim"], case["n"], case["faces"], case["bc"], case["coords"], case["gamma"],
                 case["n_scalars"], case["riemann"], case["limiter"], precision, stream)
+        if case.get("eos_rad"):
+            g.set_eos_radiation(*case["eos_rad"])
         src = case.get("sources")
         if src:
             g.set_sources(**src)
@@ -356,6 +375,10 @@ class Grid:
         a = np.empty(self.shape, dtype=self.dtype)
         hydro_get_state(self.h, a.ctypes.data, HYDRO_HOST)
         return a
+
+    def set_eos_radiation(self, R_gas, a_rad):
+        """Gas + radiation EoS (Sect. 2.3 Eq. 6-7); call before set_state."""
+        _call("hydro_set_eos_radiation", self.h, R_gas, a_rad)
 
     def set_time(self, t):
         hydro_set_time(self.h, t)
@@ -421,6 +444,13 @@ class Batch:
 
     def stats(self):
         return hydro_stats(self.h)
+
+    def run_host(self, U_in, U_out, nsteps, cfl, nparts=0):
+        """Copy the host state U_in in, advance nsteps, copy the result to U_out
+        (host arrays, pinned for overlap), pipelined over groups of tubes."""
+        pin = _host_address(U_in, self.dtype, (3, self.total))
+        pout = _host_address(U_out, self.dtype, (3, self.total))
+        _call("hydro_batch_run_host", self.h, pin, pout, int(nsteps), float(cfl), int(nparts))
 
     def times(self):
         """Simulation time of every tube (each advances at its own CFL step)."""

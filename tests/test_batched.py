@@ -137,3 +137,36 @@ def test_uniform_tubes_are_unchanged(hydro_lib, precision):
     b.run(3, 0.8)
     assert np.array_equal(b.get_state(), U0)
     assert b.stats()["newton_iters"] == 0
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_run_host_equals_set_run_get(hydro_lib, precision):
+    """hydro_batch_run_host (copies pipelined with the steps of other groups
+    of tubes) gives the state, the per-tube times and the handle state of
+    set_state + run + get_state, bit for bit."""
+    import torch
+    w = wl.tubes(40, seed=8, lo=100, hi=2000)
+    dt = np.float32 if precision == 32 else np.float64
+    U = np.ascontiguousarray(w["U"].astype(dt))
+    b = hydro_lib.Batch(w["lengths"], w["gamma"], precision=precision)
+    rng = np.random.default_rng(1)
+    b.mlp_set((0.05 * rng.standard_normal(hydro_lib.HYDRO_MLP_NPARAM)).astype(np.float32), True)
+    b.set_state(U)
+    b.run(3, 0.8)
+    ref, tref = b.get_state(), b.times()
+    out = np.empty_like(U)
+    b.run_host(U, out, 3, 0.8, nparts=5)
+    assert np.array_equal(out, ref)
+    assert np.array_equal(b.times(), tref)
+    assert np.array_equal(b.get_state(), ref)
+    # pinned tensors, more parts than tubes
+    pin_in = torch.from_numpy(U).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    b.run_host(pin_in, pin_out, 3, 0.8, nparts=100)
+    assert np.array_equal(pin_out.numpy(), ref)
+    # an invalid input state is reported
+    bad = U.copy()
+    bad[0, 5] = -1.0
+    with pytest.raises(hydro_lib.HydroError):
+        b.run_host(bad, out, 1, 0.8)
+    b.close()

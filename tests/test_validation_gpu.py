@@ -5,6 +5,8 @@
 - App. C.4: 1D spherical Sedov (gamma = 1.4): shock radius from Eq. 25 with
   the oracle's xi0(1.4), and the FP64 GPU run equals the oracle's run.
 - App. C.1: Sod at t = 0.2 against the exact solution (the paper's Fig. tube).
+- App. C.2: single-mode Rayleigh-Taylor amplitude against linear theory.
+- App. C.4: 2D spherical Sedov restarted from the 1D run at t = 0.3.
 """
 import math
 
@@ -106,3 +108,91 @@ def test_sod_matches_exact_solution(hydro_lib, precision):
     x = 0.5 * (case["faces"][0][1:] + case["faces"][0][:-1])
     ex = np.array([O.exact_sample(1.4, [1, 0, 1], [0.125, 0, 0.1], (xx - 0.5) / 0.2)[0] for xx in x])
     assert np.mean(np.abs(rho - ex)) < 3e-3
+
+
+def _interface_amplitude(case, U):
+    """Half the spread over columns of the height where the scalar crosses 1/2."""
+    zc = 0.5 * (case["faces"][1][1:] + case["faces"][1][:-1])
+    f = U[4, 0] / U[0, 0]  # (nz, nx)
+    zs = []
+    for i in range(f.shape[1]):
+        col = f[:, i]
+        k = np.where((col[:-1] < 0.5) & (col[1:] >= 0.5))[0]
+        k = k[np.argmin(np.abs(zc[k]))]
+        zs.append(zc[k] + (0.5 - col[k]) / (col[k + 1] - col[k]) * (zc[k + 1] - zc[k]))
+    return 0.5 * (max(zs) - min(zs))
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_rayleigh_taylor_single_mode_linear_growth(hydro_lib, precision):
+    """App. C.2: the interface amplitude follows h0 cosh(sqrt(A g kappa) t)
+    (A = 1/3, g = 0.5, kappa = 4 pi) through the linear phase.  At 256x512
+    the oracle gives 0.96-0.99 of the theory up to t = 1.25."""
+    case = wl.rt2d_single_mode(256, 512)
+    dt = np.float64 if precision == 64 else np.float32
+    g = hydro_lib.Grid.from_case(dict(case, U=case["U"].astype(dt)), precision)
+    sigma = math.sqrt(1.0 / 3.0 * 0.5 * 4.0 * math.pi)
+    for t_end in (0.5, 1.0, 1.25):
+        t = 0.0
+        for _ in range(50):
+            t = g.run(1000, case["cfl"], t_end=t_end)
+            if t >= t_end:
+                break
+        assert abs(t - t_end) < 1e-9
+        ratio = _interface_amplitude(case, g.get_state().astype(np.float64)) / (0.01 * math.cosh(sigma * t_end))
+        assert 0.93 < ratio < 1.03, (t_end, ratio)
+    g.close()
+
+
+def _run_to(g, t_end, cfl=0.4):
+    """Device-dt steps (graph replays) until t_end; the time reached."""
+    t = 0.0
+    for _ in range(400):
+        t = g.run(2000, cfl, t_end=t_end)
+        if t >= t_end:
+            break
+    return t
+
+
+def test_spherical_sedov_2d_restart_from_1d(hydro_lib):
+    """App. C.4: the 2D spherical run r in [0.3,1.3], theta in [pi/4,3pi/4]
+    (400 x 400) restarted at t = 0.3 from the 1D run, with the profile copied
+    across all polar angles: at t = 0.7 every polar row holds the same radial
+    profile, and the shock sits where the 1D run and Eq. 25 put it."""
+    one = wl.sedov1d_spherical(400)
+    g1 = hydro_lib.Grid.from_case(one, 64)
+    t = _run_to(g1, 0.3)
+    assert abs(t - 0.3) < 1e-12
+    U1 = g1.get_state()[:, 0, 0]  # (3, 400): rho, rho u_r, E on r in [0,1]
+    n = 400
+    rf = np.linspace(0.3, 1.3, n + 1)
+    tf = np.linspace(math.pi / 4, 3 * math.pi / 4, n + 1)
+    U2 = np.zeros((4, 1, n, n))
+    U2[0], U2[3] = 1.0, 1e-12  # ambient gas beyond r = 1
+    i0 = 120  # 1D cell i0 + i is 2D cell i (both dr = 1/400)
+    m = 400 - i0
+    U2[0, 0, :, :m] = U1[0, i0:]
+    U2[1, 0, :, :m] = U1[1, i0:]
+    U2[3, 0, :, :m] = U1[2, i0:]
+    tb = (wl.TRANSMISSIVE, wl.TRANSMISSIVE)
+    case2 = dict(dim=2, n=[n, n, 1], faces=[rf, tf], bc=[tb, (wl.REFLECTIVE, wl.REFLECTIVE)],
+                 coords=wl.SPHERICAL, gamma=1.4, n_scalars=0, riemann=wl.HLLC, limiter=wl.MINMOD,
+                 sources=None, U=U2)
+    g2 = hydro_lib.Grid.from_case(case2, 64)
+    g2.set_time(0.3)
+    assert abs(_run_to(g2, 0.7) - 0.7) < 1e-12
+    assert abs(_run_to(g1, 0.7) - 0.7) < 1e-12
+    rho2 = g2.get_state()[0, 0]  # (theta, r)
+    rho1 = g1.get_state()[0, 0, 0]
+    # no polar structure appears: every row equals the equator's
+    mid = n // 2
+    assert np.max(np.abs(rho2 - rho2[mid])) <= 1e-8 * np.max(rho2)
+    rc2 = 0.5 * (rf[1:] + rf[:-1])
+    rc1 = (np.arange(400) + 0.5) / 400
+    r_shock2, r_shock1 = rc2[np.argmax(rho2[mid])], rc1[np.argmax(rho1)]
+    r_exact = O.sedov_xi0(1.4) * 0.7 ** 0.4
+    dr = 1.0 / 400
+    assert abs(r_shock2 - r_shock1) <= 3 * dr, (r_shock2, r_shock1)
+    assert abs(r_shock2 - r_exact) <= 4 * dr, (r_shock2, r_exact)
+    g1.close()
+    g2.close()

@@ -41,3 +41,27 @@ def test_small_cases_are_physical():
         p = (case["gamma"] - 1) * (U[1 + dim] - ke)
         assert np.all(rho > 0) and np.all(p > 0), case["name"]
         assert U.shape == (2 + dim + case["n_scalars"], case["n"][2], case["n"][1], case["n"][0])
+
+
+def test_rt_single_mode_input():
+    """App. C.2 initial state: densities 1 and 2, the scalar in [0, 1], P > 0,
+    hydrostatic balance dP/dz = rho g wherever rho is flat, and the interface
+    (scalar 1/2) at h0 cos(kappa x)."""
+    case = wl.rt2d_single_mode(64, 256)
+    U = case["U"][:, 0]  # (nv, nz, nx)
+    rho, p = U[0], 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0])
+    f = U[4] / rho
+    assert rho.min() >= 1.0 - 1e-15 and rho.max() <= 2.0 + 1e-15
+    assert f.min() >= 0.0 and f.max() <= 1.0 and p.min() > 0.0
+    zc = 0.5 * (case["faces"][1][1:] + case["faces"][1][:-1])
+    dz = zc[1] - zc[0]
+    xc = 0.5 * (case["faces"][0][1:] + case["faces"][0][:-1])
+    h = 0.01 * np.cos(4 * np.pi * xc)
+    far = np.abs(zc[:, None] - h[None, :]) > 0.1
+    both = far[1:] & far[:-1]
+    dpdz = np.diff(p, axis=0) / dz
+    assert np.max(np.abs(dpdz - (-0.5) * rho[1:])[both]) < 1e-11
+    # the scalar crosses 1/2 between the two cells around z = h(x)
+    for i in range(0, 64, 8):
+        k = np.searchsorted(zc, h[i])
+        assert f[k - 1, i] < 0.5 + 1e-12 and f[k, i] > 0.5 - 1e-12
