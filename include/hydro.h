@@ -117,6 +117,18 @@ int hydro_create(const hydro_grid* grid, int coords, const hydro_eos* eos, int r
  * HYDRO_ERR_UNSUPPORTED.  Call before hydro_set_state. */
 int hydro_set_eos_radiation(hydro_t h, double R_gas, double a_rad);
 
+/* Internal-energy monitoring in highly supersonic regions (Sect. 2.5): with
+ * eps > 0 every cell whose t^n internal energy e is below eps times its
+ * kinetic energy density e_k takes e_new = e + alpha d1 + (1 - alpha) d2,
+ * where d1 is the change of e implied by the total-energy update, d2 that of
+ * de/dt + div(u e) + P div(u) = 0 integrated with the step's face fluxes
+ * (u_f e_f = F_rho (e/rho)_upwind, u_f = F_rho/rho_upwind, upwind by the sign
+ * of the mass flux; P the cell's t^n pressure; plus the heating), and alpha =
+ * 1 for e >= eps e_k, (e/(eps e_k))^2 down to eps e_k/10, 0 below; the total
+ * energy is then e_new + rho|u|^2/2.  Cells with alpha = 1 are untouched.
+ * eps = 0 (the default) switches the correction off; the paper uses 1e-6. */
+int hydro_set_dual_energy(hydro_t h, double eps);
+
 /* Source terms.  gravity (Eq. 2-4): UNIFORM uses g0 (components along the
  * grid axes); POINT uses -G Mc / r^2 e_r; POINT_MONOPOLE adds the enclosed
  * mass M(r) of the current state (spherically symmetric approximation,

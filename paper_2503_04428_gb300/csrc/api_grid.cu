@@ -323,6 +323,7 @@ static SweepArgs<T> sweep_args(hydro_ctx* h, double dt_host, double cfl, double 
   a.ni_tco = tco;
   a.gas = make_gas<T>(h->gamma);
   a.grad = make_gas_rad<T>(h->gamma, h->R_gas, h->a_rad);
+  a.eps_dual = (T)h->eps_dual;
   a.dt_host = dt_host;
   a.cfl = cfl;
   a.t_end = t_end;
@@ -351,11 +352,18 @@ static int launch_step_t(hydro_ctx* h, double dt_host, double cfl, double t_end,
   int* tx = &h->tile_x;
   int* ty = &h->tile_y;
   int* nt = &h->threads;
+  const int dual = h->eps_dual > 0.0;
   if (h->eos_rad) {
     switch (h->dim) {
-      case 1: e = sweep_dispatch_rad<T, 1>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
-      case 2: e = sweep_dispatch_rad<T, 2>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
-      default: e = sweep_dispatch_rad<T, 3>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+      case 1: e = sweep_dispatch_rad<T, 1>(a, h->nsx, h->riemann, dual, h->stream, tx, ty, nt); break;
+      case 2: e = sweep_dispatch_rad<T, 2>(a, h->nsx, h->riemann, dual, h->stream, tx, ty, nt); break;
+      default: e = sweep_dispatch_rad<T, 3>(a, h->nsx, h->riemann, dual, h->stream, tx, ty, nt); break;
+    }
+  } else if (dual) {
+    switch (h->dim) {
+      case 1: e = sweep_dispatch_dual<T, 1>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+      case 2: e = sweep_dispatch_dual<T, 2>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+      default: e = sweep_dispatch_dual<T, 3>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
     }
   } else {
     switch (h->dim) {
@@ -453,7 +461,7 @@ static int autotune_grid(hydro_ctx* h, double cfl) {
   if (h->dim < 3) return HYDRO_OK;
   std::ostringstream key;
   key << "grid_d" << h->dim << "_p" << h->precision << "_r" << h->riemann << "_ns" << h->ns
-      << (h->eos_rad ? "_rad" : "") << "_n"
+      << (h->eos_rad ? "_rad" : "") << (h->eps_dual > 0.0 ? "_dual" : "") << "_n"
       << h->n[0] << "x" << h->n[1] << "x" << h->n[2] << "_" << device_key();
   int cached;
   double us;
@@ -663,6 +671,18 @@ int hydro_create(const hydro_grid* grid, int coords, const hydro_eos* eos, int r
     return st;
   }
   *out = h;
+  return HYDRO_OK;
+}
+
+int hydro_set_dual_energy(hydro_t h, double eps) {
+  if (!h || h->batched) return arg_error("hydro_set_dual_energy: grid handle required");
+  if (!(eps >= 0.0) || !std::isfinite(eps)) return arg_error("hydro_set_dual_energy: need eps >= 0");
+  if ((eps > 0.0) != (h->eps_dual > 0.0)) h->tuned = false;  // another kernel: tune again
+  h->eps_dual = eps;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
   return HYDRO_OK;
 }
 

@@ -77,6 +77,7 @@ struct SweepArgs {
   double ni_lambda, ni_a, ni_qco, ni_tni, ni_tco;  // Eq. 8 constants (CGS)
   Gas<T> gas;
   GasRad<T> grad;         // gas + radiation constants (kernels instantiated for Eq. 6-7)
+  T eps_dual;             // dual-energy criterion epsilon (Sect. 2.5); 0 = off
   double dt_host;         // > 0: use this dt; otherwise CFL on the device
   double cfl;
   double t_end;           // > 0: clip dt so t does not pass t_end
@@ -88,10 +89,14 @@ struct SweepArgs {
 template <typename T, int DIM>
 cudaError_t sweep_dispatch(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s, int* tx, int* ty,
                            int* nt);
-// The same for the gas + radiation EoS (HLL and HLLC only).
+// The same with the dual-energy correction (Sect. 2.5).
 template <typename T, int DIM>
-cudaError_t sweep_dispatch_rad(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s, int* tx, int* ty,
-                               int* nt);
+cudaError_t sweep_dispatch_dual(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s, int* tx, int* ty,
+                                int* nt);
+// The gas + radiation EoS (HLL and HLLC only), with or without dual energy.
+template <typename T, int DIM>
+cudaError_t sweep_dispatch_rad(const SweepArgs<T>& a, int nsx, int rs, int dual, cudaStream_t s, int* tx,
+                               int* ty, int* nt);
 
 // Bits of a non-negative double, for an ordered atomicMax.
 __device__ __forceinline__ unsigned long long dbits(double x) {

@@ -57,6 +57,7 @@ struct hydro_ctx {
   double gamma = 1.4;
   int eos_rad = 0;                   // 1: gas + radiation EoS (Eq. 6-7)
   double R_gas = 0.0, a_rad = 0.0;   // its constants
+  double eps_dual = 0.0;             // dual-energy criterion (Sect. 2.5); 0 = off
   long long ncell = 0;
   std::vector<double> faces[3];
   void* buf[2] = {nullptr, nullptr};

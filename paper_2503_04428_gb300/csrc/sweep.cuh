@@ -74,7 +74,10 @@ struct SweepShape {
   static constexpr int NFZ = DIM == 3 ? TX * TY : 0;
   static constexpr size_t smem_elems = (size_t)WP * NV * WPL + (size_t)2 * NV * NFX +
                                        (size_t)2 * NV * NFY + (size_t)3 * NV * NFZ;
-  static constexpr size_t smem_bytes = smem_elems * sizeof(T);
+  static constexpr size_t dual_elems = (size_t)2 * (NFX + NFY + NFZ);  // dual-energy face terms
+  static constexpr size_t smem_bytes_for(bool dual) {
+    return (smem_elems + (dual ? dual_elems : 0)) * sizeof(T);
+  }
 };
 
 // Ghost mapping of one axis (periodic wrap, transmissive copy of the edge
@@ -99,8 +102,13 @@ __device__ __forceinline__ int map_axis(int g, int n, int lo, int hi, bool& flip
 // Which face states a predictor pass writes.
 enum { PRED_ALL = 0, PRED_ZHI = 1, PRED_ZLO = 2 };
 
-template <typename T, int DIM, int NSX, int RS, int EOS>
+// MODE bit 0: gas + radiation EoS (Eq. 6-7); bit 1: dual-energy correction
+// (Sect. 2.5).  Each combination is its own instantiation, so the plain step
+// carries none of the optional work.
+template <typename T, int DIM, int NSX, int RS, int MODE>
 struct Sweep {
+  static constexpr int EOS = MODE & 1;
+  static constexpr bool DUAL = (MODE & 2) != 0;
   using S = SweepShape<T, DIM, NSX>;
   static constexpr int NV = S::NV, TX = S::TX, TY = S::TY, EX = S::EX, EY = S::EY, HY = S::HY,
                        QY = S::QY, NT = S::NT, NI = S::NI, NP = S::NP, NFX = S::NFX,
@@ -114,6 +122,9 @@ struct Sweep {
   T* YR;
   T* ZL;  // [2][v][j*TX+i]: state below the z face above plane (slot = plane & 1)
   T* ZR;  // [v][j*TX+i]: state above the z face below the current plane, then the flux
+  T* XQ;  // dual energy (Sect. 2.5): [2][face] u_f e_f and u_f of the x faces
+  T* YQ;  //   ... of the y faces
+  T* ZQ;  //   ... of the z face below the current plane
   int x0, y0, z1, n2;
   T dt, half_dt;
   const T* Uin;
@@ -127,6 +138,7 @@ struct Sweep {
   T acc[NV];
   T dUo[NV];
   T fzb3 = T(0), tth = T(0), x2 = T(0), s3 = T(0);
+  T aq1 = T(0), aq2 = T(0);  // dual energy: divergences of u e and of u (times dt^-1)
 
   __device__ Sweep(const SweepArgs<T>& args, T* smem) : a(args) {
     Ws = smem;
@@ -136,6 +148,20 @@ struct Sweep {
     YR = YL + NV * NFY;
     ZL = YR + NV * NFY;
     ZR = ZL + 2 * NV * NFZ;
+    XQ = ZR + NV * NFZ;  // the dual-energy arrays exist only in DUAL instantiations
+    YQ = XQ + 2 * NFX;
+    ZQ = YQ + 2 * NFY;
+  }
+
+  // Dual energy (Sect. 2.5, reading R15): the advected internal energy
+  // u_f e_f = F_rho (e/rho)_upwind and the face velocity u_f = F_rho/rho_upwind,
+  // upwind by the sign of the mass flux.
+  __device__ __forceinline__ void dual_terms(const T* WL, const T* WR, const T* F, T* q, int st,
+                                             int idx) const {
+    const T* Wu = F[0] >= T(0) ? WL : WR;
+    const T eu = eint_of(gas(), Wu[0], Wu[1 + DIM]);
+    q[idx] = F[0] * eu / Wu[0];
+    q[st + idx] = F[0] / Wu[0];
   }
 
   // the EoS of this instantiation: ideal gas (Eq. 5) or gas + radiation (Eq. 6-7)
@@ -245,10 +271,10 @@ struct Sweep {
   // (F_d(W_lo) - F_d(W_hi))/h_d of every needed cell, and its predicted face
   // states.  PRED_ALL: tile plus halo, every face state of the plane;
   // PRED_ZHI / PRED_ZLO: tile cells only, the upper / lower z state.
-  template <int MODE>
+  template <int PM>
   __device__ void predictor(int gz) {
     const int t = threadIdx.x;
-    if (t >= (MODE == PRED_ALL ? NP : NI)) return;
+    if (t >= (PM == PRED_ALL ? NP : NI)) return;
     const int n0 = a.n[0], n1 = a.n[1];
     int px, py;
     item_cell(t, px, py);
@@ -263,13 +289,13 @@ struct Sweep {
     const bool creal = gi < n0;                          // a domain column
     const int row = py - QY, col = px - 1;
     // face-state slots written by this cell
-    const bool xlo = MODE == PRED_ALL && px >= 1 && trow && rreal;
-    const bool xhi = MODE == PRED_ALL && px <= TX && trow && rreal && creal;
-    const bool ylo = DIM >= 2 && MODE == PRED_ALL && py >= 1 && tcol && creal;
-    const bool yhi = DIM >= 2 && MODE == PRED_ALL && py <= TY && tcol && creal && rreal;
+    const bool xlo = PM == PRED_ALL && px >= 1 && trow && rreal;
+    const bool xhi = PM == PRED_ALL && px <= TX && trow && rreal && creal;
+    const bool ylo = DIM >= 2 && PM == PRED_ALL && py >= 1 && tcol && creal;
+    const bool yhi = DIM >= 2 && PM == PRED_ALL && py <= TY && tcol && creal && rreal;
     const bool zin = DIM == 3 && tcol && trow && creal && rreal;
-    const bool zlo = zin && MODE != PRED_ZHI;
-    const bool zhi = zin && MODE != PRED_ZLO;
+    const bool zlo = zin && PM != PRED_ZHI;
+    const bool zhi = zin && PM != PRED_ZLO;
     const int ixlo = row * (TX + 1) + px - 1, ixhi = ixlo + 1;
     const int iylo = (py - 1) * TX + col, iyhi = iylo + TX;
     const int iz = row * TX + col;
@@ -380,6 +406,7 @@ struct Sweep {
     constexpr int NXY = XY ? NFX + NFY : 0;
     constexpr int NALL = NXY + (Z ? NFZ : 0);
     const T* zlp = ZL + ((gz - 1) & 1) * NV * NFZ;
+    constexpr bool dual = DUAL;
     for (int idx = threadIdx.x; idx < NALL; idx += NT) {
       T WL[NV], WR[NV], F[NV];
       if (XY && idx < NFX) {
@@ -391,6 +418,7 @@ struct Sweep {
           WR[v] = XR[v * NFX + idx];
         }
         riemann<0>(WL, WR, F, f < TX || x0 + f == n0);
+        if constexpr (dual) dual_terms(WL, WR, F, XQ, NFX, idx);
 #pragma unroll
         for (int v = 0; v < NV; ++v) XL[v * NFX + idx] = F[v];
       } else if (XY && DIM >= 2 && idx < NXY) {
@@ -403,6 +431,7 @@ struct Sweep {
           WR[v] = YR[v * NFY + k];
         }
         riemann<(DIM >= 2 ? 1 : 0)>(WL, WR, F, fy < TY || y0 + fy == n1);
+        if constexpr (dual) dual_terms(WL, WR, F, YQ, NFY, k);
 #pragma unroll
         for (int v = 0; v < NV; ++v) YL[v * NFY + k] = F[v];
       } else if (DIM == 3 && Z) {
@@ -415,6 +444,7 @@ struct Sweep {
           WR[v] = ZR[v * NFZ + k];
         }
         riemann<(DIM == 3 ? 2 : 0)>(WL, WR, F, gz < z1 || gz == n2);
+        if constexpr (dual) dual_terms(WL, WR, F, ZQ, NFZ, k);
 #pragma unroll
         for (int v = 0; v < NV; ++v) ZR[v * NFZ + k] = F[v];
       }
@@ -427,14 +457,23 @@ struct Sweep {
   __device__ __forceinline__ void open_cell(int gz, int i, int j, int gi, int gj) {
     const int fx = j * (TX + 1) + i;
     const T Afl = a.geo.Af[gi], Afh = a.geo.Af[gi + 1], ia = a.geo.inva[gi];
+    constexpr bool dual = DUAL;
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = (XL[v * NFX + fx] * Afl - XL[v * NFX + fx + 1] * Afh) * ia;
+    if constexpr (dual) {
+      aq1 = (XQ[fx] * Afl - XQ[fx + 1] * Afh) * ia;
+      aq2 = (XQ[NFX + fx] * Afl - XQ[NFX + fx + 1] * Afh) * ia;
+    }
     if constexpr (DIM >= 2) {
       const T Bfl = a.geo.Bf[gj], Bfh = a.geo.Bf[gj + 1];
       const T cy = a.geo.ga[gi] * a.geo.invb[gj];
       const int fy = j * TX + i;
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += (YL[v * NFY + fy] * Bfl - YL[v * NFY + fy + TX] * Bfh) * cy;
+      if constexpr (dual) {
+        aq1 += (YQ[fy] * Bfl - YQ[fy + TX] * Bfh) * cy;
+        aq2 += (YQ[NFY + fy] * Bfl - YQ[NFY + fy + TX] * Bfh) * cy;
+      }
       if (a.spherical) {
         tth = T(0.5) * (YL[2 * NFY + fy] + YL[2 * NFY + fy + TX]);
         x2 = XL[2 * NFX + fx + 1] * Afh + XL[2 * NFX + fx] * Afl;
@@ -451,6 +490,10 @@ struct Sweep {
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += ZR[v * NFZ + iz] * cz;
       fzb3 = ZR[3 * NFZ + iz];
+      if constexpr (dual) {
+        aq1 += ZQ[iz] * cz;
+        aq2 += ZQ[NFZ + iz] * cz;
+      }
     }
   }
 
@@ -505,14 +548,39 @@ struct Sweep {
       }
       Un[1 + DIM] += dt * work;
     }
+    T dheat = T(0);
     if (a.heating == HEAT_CONST) {
-      Un[1 + DIM] += dt * a.heat_q;
+      dheat = dt * a.heat_q;
+      Un[1 + DIM] += dheat;
     } else if (a.heating == HEAT_NI56) {
       T rf = T(0);
 #pragma unroll
       for (int s = 0; s < NSX; ++s)
         if (s == a.ni_index) rf = Uo[2 + DIM + s];
-      Un[1 + DIM] += dt * hfac * rf;
+      dheat = dt * hfac * rf;
+      Un[1 + DIM] += dheat;
+    }
+
+    // Dual energy (Sect. 2.5): where e is small against the kinetic energy
+    // of the t^n state, blend the internal-energy change of the total-energy
+    // update with that of de/dt + div(u e) + P div(u) = 0 (plus heating).
+    if constexpr (DUAL) {
+      T ke0 = T(0), ke1 = T(0);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        ke0 += T(0.5) * Uo[1 + d] * Uo[1 + d] / Uo[0];
+        ke1 += T(0.5) * Un[1 + d] * Un[1 + d] / Un[0];
+      }
+      const T e0 = Uo[1 + DIM] - ke0;
+      const T crit = a.eps_dual * ke0;
+      const T alpha = e0 >= crit ? T(1) : (e0 > T(0.1) * crit ? (e0 / crit) * (e0 / crit) : T(0));
+      if (alpha < T(1)) {
+        T Wo[NV];
+        to_prim<T, DIM, NSX>(Uo, Wo, gas());
+        const T d1 = (Un[1 + DIM] - ke1) - e0;
+        const T d2 = dt * (aq1 + Wo[1 + DIM] * aq2) + dheat;
+        Un[1 + DIM] = e0 + alpha * d1 + (T(1) - alpha) * d2 + ke1;
+      }
     }
 
     // validity and the signal speed of the new state
@@ -552,6 +620,10 @@ struct Sweep {
         const T cz = a.geo.ga[gi] * a.geo.zc[gj] * a.geo.invc[gz - 1];
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc[v] -= ZR[v * NFZ + t] * cz;
+        if constexpr (DUAL) {
+          aq1 -= ZQ[t] * cz;
+          aq2 -= ZQ[NFZ + t] * cz;
+        }
         close_cell(gz - 1, i, j, gi, gj, ZR[3 * NFZ + t]);
       }
       if (open_cur) open_cell(gz, i, j, gi, gj);
@@ -642,9 +714,9 @@ __device__ __forceinline__ bool step_begin(const Ctrl* ctrl, double dt_host, dou
   return dt > 0.0;
 }
 
-template <typename T, int DIM, int NSX, int RS, int EOS>
+template <typename T, int DIM, int NSX, int RS, int MODE>
 __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
-                                  (RS == RS_EXACT || EOS == 1) ? 1 : SweepShape<T, DIM, NSX>::MB)
+                                  (RS == RS_EXACT || (MODE & 1)) ? 1 : SweepShape<T, DIM, NSX>::MB)
     sweep_kernel(const SweepArgs<T> args) {
   using S = SweepShape<T, DIM, NSX>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -653,7 +725,7 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
   int cur;
   if (!step_begin(args.ctrl, args.dt_host, args.cfl, args.t_end, dtd, t, step, cur)) return;
 
-  Sweep<T, DIM, NSX, RS, EOS> sw(args, reinterpret_cast<T*>(smem_raw));
+  Sweep<T, DIM, NSX, RS, MODE> sw(args, reinterpret_cast<T*>(smem_raw));
   sw.x0 = blockIdx.x * S::TX;
   sw.y0 = blockIdx.y * S::TY;
   sw.n2 = DIM == 3 ? args.n[2] : 1;
@@ -701,64 +773,74 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
   finish_step<S::NT>(args.ctrl, sw.smax, sw.err, sw.n_fallback, sw.n_iters, 0ull, step, dtd);
 }
 
-template <typename T, int DIM, int NSX, int RS, int EOS>
+template <typename T, int DIM, int NSX, int RS, int MODE>
 cudaError_t launch_sweep(const SweepArgs<T>& a, cudaStream_t s) {
   using S = SweepShape<T, DIM, NSX>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, DIM, NSX, RS, EOS>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, DIM, NSX, RS, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::smem_bytes);
+                                         (int)S::smem_bytes_for(MODE & 2));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 grid((a.n[0] + S::TX - 1) / S::TX, DIM >= 2 ? (a.n[1] + S::TY - 1) / S::TY : 1,
             DIM == 3 ? (a.n[2] + a.zchunk - 1) / a.zchunk : 1);
-  sweep_kernel<T, DIM, NSX, RS, EOS><<<grid, S::NT, S::smem_bytes, s>>>(a);
+  sweep_kernel<T, DIM, NSX, RS, MODE><<<grid, S::NT, S::smem_bytes_for(MODE & 2), s>>>(a);
   return cudaGetLastError();
 }
 
 // Launch one instantiation and report its tile shape and threads per CTA.
-template <typename T, int DIM, int NSX, int RS, int EOS = 0>
+template <typename T, int DIM, int NSX, int RS, int MODE = 0>
 cudaError_t launch_sweep_shape(const SweepArgs<T>& a, cudaStream_t s, int* tx, int* ty, int* nt) {
   using S = SweepShape<T, DIM, NSX>;
   *tx = S::TX;
   *ty = S::TY;
   *nt = S::NT;
-  return launch_sweep<T, DIM, NSX, RS, EOS>(a, s);
+  return launch_sweep<T, DIM, NSX, RS, MODE>(a, s);
 }
 
-// Instantiate the dispatcher of one (precision, dimension) pair.
-#define HYDRO_SWEEP_DISPATCH(T, DIM)                                                          \
+// Instantiate the dispatcher of one (precision, dimension) pair and MODE
+// (ideal gas: 0, ideal gas + dual energy: 2).
+#define HYDRO_SWEEP_DISPATCH_MODE(NAME, T, DIM, MODE)                                         \
   template <>                                                                                 \
-  cudaError_t sweep_dispatch<T, DIM>(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s,  \
-                                     int* tx, int* ty, int* nt) {                             \
+  cudaError_t NAME<T, DIM>(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s, int* tx,   \
+                           int* ty, int* nt) {                                                \
     switch (nsx * 4 + rs) {                                                                   \
-      case 0: return launch_sweep_shape<T, DIM, 0, RS_HLL>(a, s, tx, ty, nt);                 \
-      case 1: return launch_sweep_shape<T, DIM, 0, RS_HLLC>(a, s, tx, ty, nt);                \
-      case 2: return launch_sweep_shape<T, DIM, 0, RS_EXACT>(a, s, tx, ty, nt);               \
-      case 4: return launch_sweep_shape<T, DIM, 1, RS_HLL>(a, s, tx, ty, nt);                 \
-      case 5: return launch_sweep_shape<T, DIM, 1, RS_HLLC>(a, s, tx, ty, nt);                \
-      case 6: return launch_sweep_shape<T, DIM, 1, RS_EXACT>(a, s, tx, ty, nt);               \
-      case 12: return launch_sweep_shape<T, DIM, 3, RS_HLL>(a, s, tx, ty, nt);                \
-      case 13: return launch_sweep_shape<T, DIM, 3, RS_HLLC>(a, s, tx, ty, nt);               \
-      case 14: return launch_sweep_shape<T, DIM, 3, RS_EXACT>(a, s, tx, ty, nt);              \
+      case 0: return launch_sweep_shape<T, DIM, 0, RS_HLL, MODE>(a, s, tx, ty, nt);           \
+      case 1: return launch_sweep_shape<T, DIM, 0, RS_HLLC, MODE>(a, s, tx, ty, nt);          \
+      case 2: return launch_sweep_shape<T, DIM, 0, RS_EXACT, MODE>(a, s, tx, ty, nt);         \
+      case 4: return launch_sweep_shape<T, DIM, 1, RS_HLL, MODE>(a, s, tx, ty, nt);           \
+      case 5: return launch_sweep_shape<T, DIM, 1, RS_HLLC, MODE>(a, s, tx, ty, nt);          \
+      case 6: return launch_sweep_shape<T, DIM, 1, RS_EXACT, MODE>(a, s, tx, ty, nt);         \
+      case 12: return launch_sweep_shape<T, DIM, 3, RS_HLL, MODE>(a, s, tx, ty, nt);          \
+      case 13: return launch_sweep_shape<T, DIM, 3, RS_HLLC, MODE>(a, s, tx, ty, nt);         \
+      case 14: return launch_sweep_shape<T, DIM, 3, RS_EXACT, MODE>(a, s, tx, ty, nt);        \
       default: return cudaErrorInvalidValue;                                                  \
     }                                                                                         \
   }
+#define HYDRO_SWEEP_DISPATCH(T, DIM) HYDRO_SWEEP_DISPATCH_MODE(sweep_dispatch, T, DIM, 0)
+#define HYDRO_SWEEP_DISPATCH_DUAL(T, DIM) HYDRO_SWEEP_DISPATCH_MODE(sweep_dispatch_dual, T, DIM, 2)
 
-// The gas + radiation dispatcher of one (precision, dimension) pair.
+// The gas + radiation dispatcher (HLL, HLLC) of one (precision, dimension)
+// pair, without (MODE 1) and with (MODE 3) the dual-energy correction.
 #define HYDRO_SWEEP_DISPATCH_RAD(T, DIM)                                                      \
   template <>                                                                                 \
-  cudaError_t sweep_dispatch_rad<T, DIM>(const SweepArgs<T>& a, int nsx, int rs,              \
+  cudaError_t sweep_dispatch_rad<T, DIM>(const SweepArgs<T>& a, int nsx, int rs, int dual,    \
                                          cudaStream_t s, int* tx, int* ty, int* nt) {         \
-    switch (nsx * 4 + rs) {                                                                   \
+    switch ((nsx * 4 + rs) * 2 + (dual ? 1 : 0)) {                                            \
       case 0: return launch_sweep_shape<T, DIM, 0, RS_HLL, 1>(a, s, tx, ty, nt);              \
-      case 1: return launch_sweep_shape<T, DIM, 0, RS_HLLC, 1>(a, s, tx, ty, nt);             \
-      case 4: return launch_sweep_shape<T, DIM, 1, RS_HLL, 1>(a, s, tx, ty, nt);              \
-      case 5: return launch_sweep_shape<T, DIM, 1, RS_HLLC, 1>(a, s, tx, ty, nt);             \
-      case 12: return launch_sweep_shape<T, DIM, 3, RS_HLL, 1>(a, s, tx, ty, nt);             \
-      case 13: return launch_sweep_shape<T, DIM, 3, RS_HLLC, 1>(a, s, tx, ty, nt);            \
+      case 1: return launch_sweep_shape<T, DIM, 0, RS_HLL, 3>(a, s, tx, ty, nt);              \
+      case 2: return launch_sweep_shape<T, DIM, 0, RS_HLLC, 1>(a, s, tx, ty, nt);             \
+      case 3: return launch_sweep_shape<T, DIM, 0, RS_HLLC, 3>(a, s, tx, ty, nt);             \
+      case 8: return launch_sweep_shape<T, DIM, 1, RS_HLL, 1>(a, s, tx, ty, nt);              \
+      case 9: return launch_sweep_shape<T, DIM, 1, RS_HLL, 3>(a, s, tx, ty, nt);              \
+      case 10: return launch_sweep_shape<T, DIM, 1, RS_HLLC, 1>(a, s, tx, ty, nt);            \
+      case 11: return launch_sweep_shape<T, DIM, 1, RS_HLLC, 3>(a, s, tx, ty, nt);            \
+      case 24: return launch_sweep_shape<T, DIM, 3, RS_HLL, 1>(a, s, tx, ty, nt);             \
+      case 25: return launch_sweep_shape<T, DIM, 3, RS_HLL, 3>(a, s, tx, ty, nt);             \
+      case 26: return launch_sweep_shape<T, DIM, 3, RS_HLLC, 1>(a, s, tx, ty, nt);            \
+      case 27: return launch_sweep_shape<T, DIM, 3, RS_HLLC, 3>(a, s, tx, ty, nt);            \
       default: return cudaErrorInvalidValue;                                                  \
     }                                                                                         \
   }

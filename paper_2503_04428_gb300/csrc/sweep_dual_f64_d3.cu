@@ -1,0 +1,6 @@
+// Fused sweep kernels with the dual-energy correction (Sect. 2.5): double state, 3D grids, ideal gas.
+#include "sweep.cuh"
+
+namespace hydro {
+HYDRO_SWEEP_DISPATCH_DUAL(double, 3)
+}  // namespace hydro

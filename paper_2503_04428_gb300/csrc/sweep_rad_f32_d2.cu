@@ -1,4 +1,4 @@
-// Fused sweep kernels with the gas + radiation EoS (Eq. 6-7): float state, 2D grids, HLL and HLLC.
+// Fused sweep kernels with the gas + radiation EoS (Eq. 6-7): float state, 2D grids, HLL and HLLC, with and without dual energy.
 #include "sweep.cuh"
 
 namespace hydro {

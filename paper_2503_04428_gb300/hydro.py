@@ -85,6 +85,7 @@ _SIGS = {
     "hydro_destroy": [_VP],
     "hydro_fma_rate": [C.c_int, C.POINTER(C.c_double)],
     "hydro_set_eos_radiation": [_VP, C.c_double, C.c_double],
+    "hydro_set_dual_energy": [_VP, C.c_double],
     "hydro_batch_run_host": [_VP, _VP, _VP, C.c_int, C.c_double, C.c_int],
     "hydro_exact_sample": [_D, _D, C.c_long, C.c_double, C.POINTER(C.c_longlong), _D, C.c_long, _D],
     "hydro_batch_times": [_VP, _D],
@@ -345,6 +346,8 @@ class Grid:
                 case["n_scalars"], case["riemann"], case["limiter"], precision, stream)
         if case.get("eos_rad"):
             g.set_eos_radiation(*case["eos_rad"])
+        if case.get("dual_energy"):
+            g.set_dual_energy(case["dual_energy"])
         src = case.get("sources")
         if src:
             g.set_sources(**src)
@@ -375,6 +378,10 @@ class Grid:
         a = np.empty(self.shape, dtype=self.dtype)
         hydro_get_state(self.h, a.ctypes.data, HYDRO_HOST)
         return a
+
+    def set_dual_energy(self, eps):
+        """Internal-energy correction of Sect. 2.5 (eps = 0: off)."""
+        _call("hydro_set_dual_energy", self.h, float(eps))
 
     def set_eos_radiation(self, R_gas, a_rad):
         """Gas + radiation EoS (Sect. 2.3 Eq. 6-7); call before set_state."""
