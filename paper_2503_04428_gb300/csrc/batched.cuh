@@ -107,8 +107,9 @@ struct MlpSmemW {
 };
 
 // The 6-64-64-1 network evaluated by a whole warp for one input x (the same
-// on every lane): lane l owns hidden units l and l+32.
-__device__ __forceinline__ float mlp_warp(const MlpSmemW& s, const float* x, int lane) {
+// on every lane): lane l owns hidden units l and l+32.  Out of line: few
+// faces use it, and its unrolled layers would crowd the instruction cache.
+static __device__ __noinline__ float mlp_warp(const MlpSmemW& s, const float* x, int lane) {
   float a = s.b1[lane], b = s.b1[lane + 32];
 #pragma unroll
   for (int i = 0; i < MLP_IN; ++i) {

@@ -102,7 +102,10 @@ template <> __device__ __forceinline__ double dsqrt<double>(double x) { return s
 template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
 template <typename T> __device__ __forceinline__ T dpow(T x, T y);
 template <> __device__ __forceinline__ double dpow<double>(double x, double y) { return pow(x, y); }
-template <> __device__ __forceinline__ float dpow<float>(float x, float y) { return powf(x, y); }
+// FP32 powers (x > 0) as exp2(y log2 x): a few ulp, against the accurate
+// powf, whose extended-precision logarithm is several times longer and
+// dominated the instruction stream of the FP32 exact solver.
+template <> __device__ __forceinline__ float dpow<float>(float x, float y) { return exp2f(y * log2f(x)); }
 template <typename T> __device__ __forceinline__ T dexp(T x);
 template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
 template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
@@ -577,6 +580,20 @@ __device__ __forceinline__ Gas<double> gas_double(const Gas<float>& g) {
 // Star state of one face.  guess_in > 0 replaces Toro's guess (MLP).  In FP32
 // a face near vacuum (margin below 5 %) or with a pressure ratio above 1e6
 // is solved in FP64, where the FP32 pressure function loses digits.
+// The FP64 Newton solve of an FP32 face near vacuum or with a pressure ratio
+// above 1e6 (reading R12).  Kept out of line: it is rare, and its FP64 code
+// would crowd the instruction cache of the FP32 kernels.
+static __device__ __noinline__ int newton_star_fp64(float p0, float rL, float uL, float pL, float rR, float uR,
+                                             float pR, Gas<float> gas, float& ps, float& us, int& iters) {
+  const Gas<double> g2 = gas_double(gas);
+  double ps2, us2;
+  const double cL2 = sqrt(g2.g * (double)pL / (double)rL), cR2 = sqrt(g2.g * (double)pR / (double)rR);
+  const int st = newton_star<double>((double)p0, rL, uL, pL, cL2, rR, uR, pR, cR2, g2, 1e-10, ps2, us2, iters);
+  ps = (float)ps2;
+  us = (float)us2;
+  return st;
+}
+
 template <typename T>
 __device__ __forceinline__ int exact_star(T rL, T uL, T pL, T rR, T uR, T pR, const Gas<T>& gas,
                                           T guess_in, T& ps, T& us, int& iters, int& kind) {
@@ -587,16 +604,8 @@ __device__ __forceinline__ int exact_star(T rL, T uL, T pL, T rR, T uR, T pR, co
   if (guess_in > T(0)) p0 = guess_in;
   if constexpr (sizeof(T) == 4) {
     const T ratio = fmax(pL, pR) / fmin(pL, pR);
-    if (ratio > T(1e6) || vac - (uR - uL) < T(0.05) * vac) {
-      const Gas<double> g2 = gas_double(gas);
-      double ps2, us2;
-      const double cL2 = sqrt(g2.g * (double)pL / (double)rL), cR2 = sqrt(g2.g * (double)pR / (double)rR);
-      const int st = newton_star<double>((double)p0, rL, uL, pL, cL2, rR, uR, pR, cR2, g2, 1e-10,
-                                         ps2, us2, iters);
-      ps = (T)ps2;
-      us = (T)us2;
-      return st;
-    }
+    if (ratio > T(1e6) || vac - (uR - uL) < T(0.05) * vac)
+      return newton_star_fp64(p0, rL, uL, pL, rR, uR, pR, gas, ps, us, iters);
   }
   return newton_star<T>(p0, rL, uL, pL, cL, rR, uR, pR, cR, gas, newton_tol<T>(), ps, us, iters);
 }
