@@ -37,7 +37,13 @@ struct BatchState {
   int* item_tube = nullptr;
   int* item_start = nullptr;
   int nitems = 0;
-  std::vector<int> item_first;  // first item of every tube (+ nitems)
+  std::vector<int> item_first;  // first item of every tube (+ nitems), tube order
+  std::vector<int> h_tube, h_start;  // the items in tube order (host)
+  // items ordered longest-first within each group of tubes of a host-resident
+  // run (part_items_P = the group count they were built for)
+  int* part_item_tube = nullptr;
+  int* part_item_start = nullptr;
+  int part_items_P = 0;
   // host-resident runs: per-part control blocks, copy streams and events
   int nparts = 0;
   BatchCtrl* part_ctrl = nullptr;
@@ -101,29 +107,78 @@ static int occupancy_nw(int nw, int* blocks) {
 }
 
 // Work items (tube, first cell) of item_len cells.
+// Expected cost order of items [i0, i1) of the tube-ordered list: the waves
+// of every tube start at its interface (x = 1/2) and spread from there, so
+// items near it run the exact solver and the rest mostly take the
+// uniform-window path.  Handing out the expensive items first keeps warps
+// from waiting at the end of the persistent queue (longest processing time
+// first); the order changes no result.
+static void order_items(const BatchState* bs, int item_len, int i0, int i1, std::vector<int>& tube,
+                        std::vector<int>& start) {
+  std::vector<int> ord(i1 - i0);
+  std::vector<double> key(i1 - i0);
+  for (int q = i0; q < i1; ++q) {
+    const int b = bs->h_tube[q];
+    const double nb = (double)(bs->off[b + 1] - bs->off[b]);
+    const double mid = (bs->h_start[q] + 0.5 * std::min((double)item_len, nb - bs->h_start[q])) / nb;
+    key[q - i0] = std::fabs(mid - 0.5);
+    ord[q - i0] = q;
+  }
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return key[x - i0] < key[y - i0]; });
+  for (int q = i0; q < i1; ++q) {
+    tube[q] = bs->h_tube[ord[q - i0]];
+    start[q] = bs->h_start[ord[q - i0]];
+  }
+}
+
+static int upload_items(const std::vector<int>& tube, const std::vector<int>& start, int** d_tube,
+                        int** d_start) {
+  cudaFree(*d_tube);
+  cudaFree(*d_start);
+  *d_tube = nullptr;
+  *d_start = nullptr;
+  HCK(cudaMalloc(d_tube, sizeof(int) * tube.size()));
+  HCK(cudaMalloc(d_start, sizeof(int) * start.size()));
+  HCK(cudaMemcpy(*d_tube, tube.data(), sizeof(int) * tube.size(), cudaMemcpyHostToDevice));
+  HCK(cudaMemcpy(*d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
+  return HYDRO_OK;
+}
+
+// Work items (tube, first cell) of item_len cells, handed out longest first.
 static int make_items(hydro_ctx* h, int item_len) {
   BatchState* bs = h->bs;
-  std::vector<int> tube, start;
+  bs->h_tube.clear();
+  bs->h_start.clear();
   bs->item_first.assign(bs->ntubes + 1, 0);
   for (int b = 0; b < bs->ntubes; ++b) {
-    bs->item_first[b] = (int)tube.size();
+    bs->item_first[b] = (int)bs->h_tube.size();
     const int nb = (int)(bs->off[b + 1] - bs->off[b]);
     for (int s = 0; s < nb; s += item_len) {
-      tube.push_back(b);
-      start.push_back(s);
+      bs->h_tube.push_back(b);
+      bs->h_start.push_back(s);
     }
   }
-  if (bs->item_tube) {
-    cudaFree(bs->item_tube);
-    cudaFree(bs->item_start);
-  }
-  HCK(cudaMalloc(&bs->item_tube, sizeof(int) * tube.size()));
-  HCK(cudaMalloc(&bs->item_start, sizeof(int) * start.size()));
-  HCK(cudaMemcpy(bs->item_tube, tube.data(), sizeof(int) * tube.size(), cudaMemcpyHostToDevice));
-  HCK(cudaMemcpy(bs->item_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
-  bs->nitems = (int)tube.size();
+  bs->nitems = (int)bs->h_tube.size();
   bs->item_first[bs->ntubes] = bs->nitems;
   bs->item_len = item_len;
+  std::vector<int> tube(bs->nitems), start(bs->nitems);
+  order_items(bs, item_len, 0, bs->nitems, tube, start);
+  bs->part_items_P = 0;  // the host-resident order is rebuilt on demand
+  return upload_items(tube, start, &bs->item_tube, &bs->item_start);
+}
+
+// The item order of a host-resident run over the tube groups b0: longest
+// first within each group (a group's items stay a contiguous range).
+static int part_items(hydro_ctx* h, const std::vector<int>& b0) {
+  BatchState* bs = h->bs;
+  const int P = (int)b0.size() - 1;
+  if (bs->part_items_P == P && bs->part_item_tube) return HYDRO_OK;
+  std::vector<int> tube(bs->nitems), start(bs->nitems);
+  for (int p = 0; p < P; ++p)
+    order_items(bs, bs->item_len, bs->item_first[b0[p]], bs->item_first[b0[p + 1]], tube, start);
+  int st = upload_items(tube, start, &bs->part_item_tube, &bs->part_item_start);
+  if (st) return st;
+  bs->part_items_P = P;
   return HYDRO_OK;
 }
 
@@ -419,6 +474,8 @@ void hydro_batch_free_impl(hydro_ctx* h) {
   drop_graph(bs);
   cudaFree(bs->part_ctrl);
   cudaFreeHost(bs->part_ctrl_host);
+  cudaFree(bs->part_item_tube);
+  cudaFree(bs->part_item_start);
   if (bs->s_h2d) cudaStreamDestroy(bs->s_h2d);
   if (bs->s_d2h) cudaStreamDestroy(bs->s_d2h);
   for (cudaEvent_t e : bs->ev_in) cudaEventDestroy(e);
@@ -481,6 +538,7 @@ static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
   }
   for (int p = 1; p <= P; ++p) b0[p] = std::min(std::max(b0[p], b0[p - 1]), bs->ntubes);
   b0[P] = bs->ntubes;
+  if ((st = part_items(h, b0))) return st;
   const int slot = 0;  // input lands in buffer 0; the result is in buffer (nsteps & 1)
   const int out_slot = nsteps & 1;
   for (int p = 0; p < P; ++p) {
@@ -515,8 +573,8 @@ static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
     HCK(cudaMemsetAsync(bs->smax_next + t0, 0, sizeof(unsigned long long) * (t1 - t0), h->stream));
     BatchArgs<T> a = batch_args<T>(h, cfl, &bs->part_ctrl[p], bs->smax_cur, bs->smax_next, bs->t_tube);
     const int i0 = bs->item_first[t0], i1 = bs->item_first[t1];
-    a.item_tube = bs->item_tube + i0;
-    a.item_start = bs->item_start + i0;
+    a.item_tube = bs->part_item_tube + i0;
+    a.item_start = bs->part_item_start + i0;
     a.nitems = i1 - i0;
     a.tube0 = t0;
     a.ntubes = t1 - t0;

@@ -88,6 +88,21 @@ struct GasRad : Gas<T> {
     p = pg + pr;
     c2 = sound2(rho, pg, pr);
   }
+  // P, c^2 and the temperature from (rho, e)
+  __device__ __forceinline__ void from_e_t(T rho, T e, T& p, T& c2, T& t) const {
+    t = temperature(rho * Rg, a, e);
+    const T pg = rho * R * t, pr = a3 * t * t * t * t;
+    p = pg + pr;
+    c2 = sound2(rho, pg, pr);
+  }
+  // the temperature of (rho, P)
+  __device__ __forceinline__ T temp_p(T rho, T p) const { return temperature(rho * R, a3, p); }
+  // e and c^2 of a state whose temperature is known
+  __device__ __forceinline__ void from_t(T rho, T t, T& e, T& c2) const {
+    const T pg = rho * R * t, pr = a3 * t * t * t * t;
+    e = pg * c_1 + T(3) * pr;
+    c2 = sound2(rho, pg, pr);
+  }
   // e and c^2 from (rho, P)
   __device__ __forceinline__ void from_p(T rho, T p, T& e, T& c2) const {
     const T t = temperature(rho * R, a3, p);
@@ -260,12 +275,16 @@ __device__ __forceinline__ void flux_cons_e(const T* W, T e, T* F, T* U) {
 
 // HLL for the gas + radiation EoS: one temperature solve per side gives e
 // and the Eq. 7 sound speed.
+// (TL, TR > 0: the face states' temperatures, known to the caller; no solve)
 template <typename T, int D, int NSX, int DIR, typename G>
-__device__ __forceinline__ void riemann_hll_rad(const T* WL, const T* WR, T* F, const G& gas) {
+__device__ __forceinline__ void riemann_hll_rad(const T* WL, const T* WR, T* F, const G& gas, T TL = T(0),
+                                                T TR = T(0)) {
   constexpr int NV = 2 + D + NSX;
   T eL, c2L, eR, c2R;
-  gas.from_p(WL[0], WL[1 + D], eL, c2L);
-  gas.from_p(WR[0], WR[1 + D], eR, c2R);
+  if (TL > T(0)) gas.from_t(WL[0], TL, eL, c2L);
+  else gas.from_p(WL[0], WL[1 + D], eL, c2L);
+  if (TR > T(0)) gas.from_t(WR[0], TR, eR, c2R);
+  else gas.from_p(WR[0], WR[1 + D], eR, c2R);
   const T cL = dsqrt(c2L), cR = dsqrt(c2R);
   const T SL = fmin(WL[1 + DIR] - cL, WR[1 + DIR] - cR);
   const T SR = fmax(WL[1 + DIR] + cL, WR[1 + DIR] + cR);
@@ -290,13 +309,16 @@ __device__ __forceinline__ void riemann_hll_rad(const T* WL, const T* WR, T* F, 
 
 // HLLC for the gas + radiation EoS (the star states need only E, p, rho, u).
 template <typename T, int D, int NSX, int DIR, typename G>
-__device__ __forceinline__ void riemann_hllc_rad(const T* WL, const T* WR, T* F, const G& gas) {
+__device__ __forceinline__ void riemann_hllc_rad(const T* WL, const T* WR, T* F, const G& gas, T TL = T(0),
+                                                 T TR = T(0)) {
   constexpr int NV = 2 + D + NSX;
   const T rL = WL[0], rR = WR[0], uL = WL[1 + DIR], uR = WR[1 + DIR];
   const T pL = WL[1 + D], pR = WR[1 + D];
   T eL, c2L, eR, c2R;
-  gas.from_p(rL, pL, eL, c2L);
-  gas.from_p(rR, pR, eR, c2R);
+  if (TL > T(0)) gas.from_t(rL, TL, eL, c2L);
+  else gas.from_p(rL, pL, eL, c2L);
+  if (TR > T(0)) gas.from_t(rR, TR, eR, c2R);
+  else gas.from_p(rR, pR, eR, c2R);
   const T cL = dsqrt(c2L), cR = dsqrt(c2R);
   const T SL = fmin(uL - cL, uR - cR);
   const T SR = fmax(uL + cL, uR + cR);

@@ -75,8 +75,9 @@ struct SweepShape {
   static constexpr size_t smem_elems = (size_t)WP * NV * WPL + (size_t)2 * NV * NFX +
                                        (size_t)2 * NV * NFY + (size_t)3 * NV * NFZ;
   static constexpr size_t dual_elems = (size_t)2 * (NFX + NFY + NFZ);  // dual-energy face terms
-  static constexpr size_t smem_bytes_for(bool dual) {
-    return (smem_elems + (dual ? dual_elems : 0)) * sizeof(T);
+  static constexpr size_t rad_elems = (size_t)2 * NFX + 2 * NFY + 3 * NFZ;  // face-state temperatures
+  static constexpr size_t smem_bytes_for(int mode) {
+    return (smem_elems + ((mode & 2) ? dual_elems : 0) + ((mode & 1) ? rad_elems : 0)) * sizeof(T);
   }
 };
 
@@ -125,6 +126,14 @@ struct Sweep {
   T* XQ;  // dual energy (Sect. 2.5): [2][face] u_f e_f and u_f of the x faces
   T* YQ;  //   ... of the y faces
   T* ZQ;  //   ... of the z face below the current plane
+  // radiation EoS: temperatures of the parked face states (same indices as
+  // XL/XR, YL/YR, ZL (two planes), ZR)
+  T* XTL;
+  T* XTR;
+  T* YTL;
+  T* YTR;
+  T* ZTL;
+  T* ZTR;
   int x0, y0, z1, n2;
   T dt, half_dt;
   const T* Uin;
@@ -148,9 +157,17 @@ struct Sweep {
     YR = YL + NV * NFY;
     ZL = YR + NV * NFY;
     ZR = ZL + 2 * NV * NFZ;
-    XQ = ZR + NV * NFZ;  // the dual-energy arrays exist only in DUAL instantiations
+    // the dual-energy and temperature arrays exist only in the instantiations
+    // that use them
+    XQ = ZR + NV * NFZ;
     YQ = XQ + 2 * NFX;
     ZQ = YQ + 2 * NFY;
+    XTL = DUAL ? ZQ + 2 * NFZ : XQ;
+    XTR = XTL + NFX;
+    YTL = XTR + NFX;
+    YTR = YTL + NFY;
+    ZTL = YTR + NFY;
+    ZTR = ZTL + 2 * NFZ;
   }
 
   // Dual energy (Sect. 2.5, reading R15): the advected internal energy
@@ -250,21 +267,67 @@ struct Sweep {
 
   // Turn the limited state parked at p (stride `st`) into the predicted face
   // state: W -> U, + dU, U -> W; a non-physical result falls back to Wc.
-  __device__ __forceinline__ void finish_state(T* p, int st, const T* Wc, const T* dU, bool owned) {
+  // The radiation EoS parks the conserved state (the flux evaluation already
+  // solved for its energy) and records the temperature of the result at tp.
+  __device__ __forceinline__ void finish_state(T* p, int st, const T* Wc, const T* dU, bool owned,
+                                               T* tp = nullptr) {
     T w[NV], u[NV];
+    if constexpr (EOS == 1) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) w[v] = p[v * st];
-    to_cons<T, DIM, NSX>(w, u, gas());
+      for (int v = 0; v < NV; ++v) u[v] = p[v * st] + dU[v];
+      const T rho = u[0], ir = T(1) / rho;
+      T ke = T(0);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) u[v] += dU[v];
-    to_prim<T, DIM, NSX>(u, w, gas());
-    if (!(w[0] > T(0)) || !(w[1 + DIM] > T(0))) {
+      for (int d = 0; d < DIM; ++d) {
+        w[1 + d] = u[1 + d] * ir;
+        ke += u[1 + d] * w[1 + d];
+      }
+      w[0] = rho;
+      T c2, t;
+      a.grad.from_e_t(rho, u[1 + DIM] - T(0.5) * ke, w[1 + DIM], c2, t);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) w[v] = Wc[v];
-      if (owned) ++n_fallback;
+      for (int s = 0; s < NSX; ++s) w[2 + DIM + s] = u[2 + DIM + s] * ir;
+      if (!(w[0] > T(0)) || !(w[1 + DIM] > T(0))) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w[v] = Wc[v];
+        t = a.grad.temp_p(Wc[0], Wc[1 + DIM]);
+        if (owned) ++n_fallback;
+      }
+      *tp = t;
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w[v] = p[v * st];
+      to_cons<T, DIM, NSX>(w, u, gas());
+#pragma unroll
+      for (int v = 0; v < NV; ++v) u[v] += dU[v];
+      to_prim<T, DIM, NSX>(u, w, gas());
+      if (!(w[0] > T(0)) || !(w[1 + DIM] > T(0))) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w[v] = Wc[v];
+        if (owned) ++n_fallback;
+      }
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) p[v * st] = w[v];
+  }
+
+  // Physical fluxes of the two limited states of one direction and what is
+  // parked in their face slots: the primitive states (ideal gas) or, for the
+  // radiation EoS, the conserved states from the same temperature solve.
+  template <int DIR>
+  __device__ __forceinline__ void limited_fluxes(const T* Wl, const T* Wh, T* Fl, T* Fh, T* Pl, T* Ph) const {
+    if constexpr (EOS == 1) {
+      flux_cons_e<T, DIM, NSX, DIR>(Wl, eint_of(a.grad, Wl[0], Wl[1 + DIM]), Fl, Pl);
+      flux_cons_e<T, DIM, NSX, DIR>(Wh, eint_of(a.grad, Wh[0], Wh[1 + DIM]), Fh, Ph);
+    } else {
+      phys_flux<T, DIM, NSX, DIR>(Wl, Fl, a.gas);
+      phys_flux<T, DIM, NSX, DIR>(Wh, Fh, a.gas);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        Pl[v] = Wl[v];
+        Ph[v] = Wh[v];
+      }
+    }
   }
 
   // a3 + a4 for plane gz: the predictor increment dU = dt/2 sum_d
@@ -315,14 +378,14 @@ struct Sweep {
         Wp[v] = W(slot, v, ey, ex + 1);
       }
       faces_of<0>(Wm, Wc, Wp, gi, Wl, Wh);
-      phys_flux<T, DIM, NSX, 0>(Wl, Fl, gas());
-      phys_flux<T, DIM, NSX, 0>(Wh, Fh, gas());
+      T Pl[NV], Ph[NV];
+      limited_fluxes<0>(Wl, Wh, Fl, Fh, Pl, Ph);
       const T ih = inv_h(0, gi, gj, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         dU[v] += (Fl[v] - Fh[v]) * ih;
-        if (xlo) XR[v * NFX + ixlo] = Wl[v];
-        if (xhi) XL[v * NFX + ixhi] = Wh[v];
+        if (xlo) XR[v * NFX + ixlo] = Pl[v];
+        if (xhi) XL[v * NFX + ixhi] = Ph[v];
       }
     }
     if constexpr (DIM >= 2) {
@@ -333,14 +396,14 @@ struct Sweep {
         Wp[v] = W(slot, v, ey + 1, ex);
       }
       faces_of<1>(Wm, Wc, Wp, gj, Wl, Wh);
-      phys_flux<T, DIM, NSX, 1>(Wl, Fl, gas());
-      phys_flux<T, DIM, NSX, 1>(Wh, Fh, gas());
+      T Pl[NV], Ph[NV];
+      limited_fluxes<1>(Wl, Wh, Fl, Fh, Pl, Ph);
       const T ih = inv_h(1, gi, gj, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         dU[v] += (Fl[v] - Fh[v]) * ih;
-        if (ylo) YR[v * NFY + iylo] = Wl[v];
-        if (yhi) YL[v * NFY + iyhi] = Wh[v];
+        if (ylo) YR[v * NFY + iylo] = Pl[v];
+        if (yhi) YL[v * NFY + iyhi] = Ph[v];
       }
     }
     if constexpr (DIM == 3) {
@@ -351,14 +414,14 @@ struct Sweep {
         Wp[v] = W(wslot(gz + 1), v, ey, ex);
       }
       faces_of<2>(Wm, Wc, Wp, gz, Wl, Wh);
-      phys_flux<T, DIM, NSX, 2>(Wl, Fl, gas());
-      phys_flux<T, DIM, NSX, 2>(Wh, Fh, gas());
+      T Pl[NV], Ph[NV];
+      limited_fluxes<2>(Wl, Wh, Fl, Fh, Pl, Ph);
       const T ih = inv_h(2, gi, gj, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         dU[v] += (Fl[v] - Fh[v]) * ih;
-        if (zlo) ZR[v * NFZ + iz] = Wl[v];
-        if (zhi) zhp[v * NFZ + iz] = Wh[v];
+        if (zlo) ZR[v * NFZ + iz] = Pl[v];
+        if (zhi) zhp[v * NFZ + iz] = Ph[v];
       }
     }
 #pragma unroll
@@ -372,21 +435,27 @@ struct Sweep {
     // A face is counted (fallbacks, Newton iterations) by the one CTA that
     // owns it: its tile's faces except the upper edge, unless that is the
     // domain's last face.
-    if (xlo) finish_state(XR + ixlo, NFX, Wc, dU, px - 1 < TX || gi == n0);
-    if (xhi) finish_state(XL + ixhi, NFX, Wc, dU, px < TX || gi + 1 == n0);
+    T* ztl = ZTL + (gz & 1) * NFZ;
+    if (xlo) finish_state(XR + ixlo, NFX, Wc, dU, px - 1 < TX || gi == n0, XTR + ixlo);
+    if (xhi) finish_state(XL + ixhi, NFX, Wc, dU, px < TX || gi + 1 == n0, XTL + ixhi);
     if constexpr (DIM >= 2) {
-      if (ylo) finish_state(YR + iylo, NFY, Wc, dU, py - 1 < TY || gj == n1);
-      if (yhi) finish_state(YL + iyhi, NFY, Wc, dU, py < TY || gj + 1 == n1);
+      if (ylo) finish_state(YR + iylo, NFY, Wc, dU, py - 1 < TY || gj == n1, YTR + iylo);
+      if (yhi) finish_state(YL + iyhi, NFY, Wc, dU, py < TY || gj + 1 == n1, YTL + iyhi);
     }
     if constexpr (DIM == 3) {
-      if (zlo) finish_state(ZR + iz, NFZ, Wc, dU, gz < z1 || gz == n2);
-      if (zhi) finish_state(zhp + iz, NFZ, Wc, dU, gz + 1 < z1 || gz + 1 == n2);
+      if (zlo) finish_state(ZR + iz, NFZ, Wc, dU, gz < z1 || gz == n2, ZTR + iz);
+      if (zhi) finish_state(zhp + iz, NFZ, Wc, dU, gz + 1 < z1 || gz + 1 == n2, ztl + iz);
     }
   }
 
   template <int DIR>
-  __device__ __forceinline__ void riemann(const T* WL, const T* WR, T* F, bool owned) {
-    if constexpr (RS == RS_HLL) {
+  __device__ __forceinline__ void riemann(const T* WL, const T* WR, T* F, bool owned, T TL = T(0),
+                                          T TR = T(0)) {
+    if constexpr (EOS == 1 && RS == RS_HLL) {
+      riemann_hll_rad<T, DIM, NSX, DIR>(WL, WR, F, a.grad, TL, TR);
+    } else if constexpr (EOS == 1 && RS == RS_HLLC) {
+      riemann_hllc_rad<T, DIM, NSX, DIR>(WL, WR, F, a.grad, TL, TR);
+    } else if constexpr (RS == RS_HLL) {
       riemann_hll<T, DIM, NSX, DIR>(WL, WR, F, gas());
     } else if constexpr (RS == RS_HLLC) {
       riemann_hllc<T, DIM, NSX, DIR>(WL, WR, F, gas());
@@ -417,7 +486,7 @@ struct Sweep {
           WL[v] = XL[v * NFX + idx];
           WR[v] = XR[v * NFX + idx];
         }
-        riemann<0>(WL, WR, F, f < TX || x0 + f == n0);
+        riemann<0>(WL, WR, F, f < TX || x0 + f == n0, EOS ? XTL[idx] : T(0), EOS ? XTR[idx] : T(0));
         if constexpr (dual) dual_terms(WL, WR, F, XQ, NFX, idx);
 #pragma unroll
         for (int v = 0; v < NV; ++v) XL[v * NFX + idx] = F[v];
@@ -430,7 +499,8 @@ struct Sweep {
           WL[v] = YL[v * NFY + k];
           WR[v] = YR[v * NFY + k];
         }
-        riemann<(DIM >= 2 ? 1 : 0)>(WL, WR, F, fy < TY || y0 + fy == n1);
+        riemann<(DIM >= 2 ? 1 : 0)>(WL, WR, F, fy < TY || y0 + fy == n1, EOS ? YTL[k] : T(0),
+                                    EOS ? YTR[k] : T(0));
         if constexpr (dual) dual_terms(WL, WR, F, YQ, NFY, k);
 #pragma unroll
         for (int v = 0; v < NV; ++v) YL[v * NFY + k] = F[v];
@@ -443,7 +513,8 @@ struct Sweep {
           WL[v] = zlp[v * NFZ + k];
           WR[v] = ZR[v * NFZ + k];
         }
-        riemann<(DIM == 3 ? 2 : 0)>(WL, WR, F, gz < z1 || gz == n2);
+        riemann<(DIM == 3 ? 2 : 0)>(WL, WR, F, gz < z1 || gz == n2,
+                                    EOS ? ZTL[((gz - 1) & 1) * NFZ + k] : T(0), EOS ? ZTR[k] : T(0));
         if constexpr (dual) dual_terms(WL, WR, F, ZQ, NFZ, k);
 #pragma unroll
         for (int v = 0; v < NV; ++v) ZR[v * NFZ + k] = F[v];
@@ -780,13 +851,13 @@ cudaError_t launch_sweep(const SweepArgs<T>& a, cudaStream_t s) {
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, DIM, NSX, RS, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::smem_bytes_for(MODE & 2));
+                                         (int)S::smem_bytes_for(MODE));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 grid((a.n[0] + S::TX - 1) / S::TX, DIM >= 2 ? (a.n[1] + S::TY - 1) / S::TY : 1,
             DIM == 3 ? (a.n[2] + a.zchunk - 1) / a.zchunk : 1);
-  sweep_kernel<T, DIM, NSX, RS, MODE><<<grid, S::NT, S::smem_bytes_for(MODE & 2), s>>>(a);
+  sweep_kernel<T, DIM, NSX, RS, MODE><<<grid, S::NT, S::smem_bytes_for(MODE), s>>>(a);
   return cudaGetLastError();
 }
 
