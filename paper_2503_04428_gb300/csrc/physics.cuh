@@ -112,15 +112,24 @@ struct GasRad : Gas<T> {
   }
 };
 
+// Square roots.  The FP32 bulk takes x rsqrt(x) (about 3 ulp; x > 0 on every
+// path that uses it): the correctly rounded sqrtf sequence cost 2-3 % of the
+// FP32 step's instructions.
 template <typename T> __device__ __forceinline__ T dsqrt(T x);
 template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
-template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ float dsqrt<float>(float x) { return x * rsqrtf(x); }
+// Powers (x > 0) as exp2(y log2 x): a few ulp (FP64: relative 1e-15 at the
+// exponents of the exact solver), against the accurate pow/powf, whose
+// extended-precision logarithm is several times longer and dominated the
+// instruction stream of the exact solver.
 template <typename T> __device__ __forceinline__ T dpow(T x, T y);
-template <> __device__ __forceinline__ double dpow<double>(double x, double y) { return pow(x, y); }
-// FP32 powers (x > 0) as exp2(y log2 x): a few ulp, against the accurate
-// powf, whose extended-precision logarithm is several times longer and
-// dominated the instruction stream of the FP32 exact solver.
+template <> __device__ __forceinline__ double dpow<double>(double x, double y) { return exp2(y * log2(x)); }
 template <> __device__ __forceinline__ float dpow<float>(float x, float y) { return exp2f(y * log2f(x)); }
+// Quotient of the state conversions and wave speeds: correctly rounded in
+// FP64, the fast 2-ulp division in FP32 (the FP32 bulk's rounding error is
+// ~1e-7 per operation either way; the IEEE sequence cost ~5 % of the step).
+template <typename T> __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
 template <typename T> __device__ __forceinline__ T dexp(T x);
 template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
 template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
@@ -134,7 +143,7 @@ template <> __device__ __forceinline__ float dlog<float>(float x) { return logf(
 template <typename T, int D, int NSX, typename G>
 __device__ __forceinline__ void to_prim(const T* U, T* W, const G& gas) {
   const T rho = U[0];
-  const T ir = T(1) / rho;
+  const T ir = qdiv(T(1), rho);
   T ke = T(0);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -157,7 +166,7 @@ __device__ __forceinline__ void to_prim(const T* U, T* W, const G& gas) {
 template <typename T, int D, int NSX, typename G>
 __device__ __forceinline__ void to_prim_c2(const T* U, T* W, T& c2, const G& gas) {
   const T rho = U[0];
-  const T ir = T(1) / rho;
+  const T ir = qdiv(T(1), rho);
   T ke = T(0);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -301,7 +310,7 @@ __device__ __forceinline__ void riemann_hll_rad(const T* WL, const T* WR, T* F, 
     for (int v = 0; v < NV; ++v) F[v] = FR[v];
     return;
   }
-  const T inv = T(1) / (SR - SL);
+  const T inv = qdiv(T(1), SR - SL);
   const T sLR = SL * SR;
 #pragma unroll
   for (int v = 0; v < NV; ++v) F[v] = (SR * FL[v] - SL * FR[v] + sLR * (UR[v] - UL[v])) * inv;
@@ -361,8 +370,8 @@ __device__ __forceinline__ void riemann_hll(const T* WL, const T* WR, T* F, cons
     return;
   }
   constexpr int NV = 2 + D + NSX;
-  const T cL = dsqrt(gas.g * WL[1 + D] / WL[0]);
-  const T cR = dsqrt(gas.g * WR[1 + D] / WR[0]);
+  const T cL = dsqrt(qdiv(gas.g * WL[1 + D], WL[0]));
+  const T cR = dsqrt(qdiv(gas.g * WR[1 + D], WR[0]));
   const T SL = fmin(WL[1 + DIR] - cL, WR[1 + DIR] - cR);
   const T SR = fmax(WL[1 + DIR] + cL, WR[1 + DIR] + cR);
   T FL[NV], FR[NV];
@@ -379,7 +388,7 @@ __device__ __forceinline__ void riemann_hll(const T* WL, const T* WR, T* F, cons
   phys_flux<T, D, NSX, DIR>(WR, FR, gas);
   to_cons<T, D, NSX>(WL, UL, gas);
   to_cons<T, D, NSX>(WR, UR, gas);
-  const T inv = T(1) / (SR - SL);
+  const T inv = qdiv(T(1), SR - SL);
   const T sLR = SL * SR;
 #pragma unroll
   for (int v = 0; v < NV; ++v) F[v] = (SR * FL[v] - SL * FR[v] + sLR * (UR[v] - UL[v])) * inv;
@@ -399,7 +408,7 @@ __device__ __forceinline__ void riemann_hllc(const T* WL, const T* WR, T* F, con
   constexpr int NV = 2 + D + NSX;
   const T rL = WL[0], rR = WR[0], uL = WL[1 + DIR], uR = WR[1 + DIR];
   const T pL = WL[1 + D], pR = WR[1 + D];
-  const T cL = dsqrt(gas.g * pL / rL), cR = dsqrt(gas.g * pR / rR);
+  const T cL = dsqrt(qdiv(gas.g * pL, rL)), cR = dsqrt(qdiv(gas.g * pR, rR));
   const T SL = fmin(uL - cL, uR - cR);
   const T SR = fmax(uL + cL, uR + cR);
   if (SL >= T(0)) {
@@ -411,7 +420,7 @@ __device__ __forceinline__ void riemann_hllc(const T* WL, const T* WR, T* F, con
     return;
   }
   const T aL = rL * (SL - uL), aR = rR * (SR - uR);
-  const T Ss = (pR - pL + uL * aL - uR * aR) / (aL - aR);
+  const T Ss = qdiv(pR - pL + uL * aL - uR * aR, aL - aR);
   // pick the side of the contact
   const bool left = Ss >= T(0);
   T W[NV];
@@ -423,13 +432,13 @@ __device__ __forceinline__ void riemann_hllc(const T* WL, const T* WR, T* F, con
   T Fk[NV], Uk[NV];
   phys_flux<T, D, NSX, DIR>(W, Fk, gas);
   to_cons<T, D, NSX>(W, Uk, gas);
-  const T fac = a / (S - Ss);
+  const T fac = qdiv(a, S - Ss);
   T Us[NV];
   Us[0] = fac;
 #pragma unroll
   for (int d = 0; d < D; ++d) Us[1 + d] = fac * W[1 + d];
   Us[1 + DIR] = fac * Ss;
-  Us[1 + D] = fac * (Uk[1 + D] / rho + (Ss - un) * (Ss + p / a));
+  Us[1 + D] = fac * (qdiv(Uk[1 + D], rho) + (Ss - un) * (Ss + qdiv(p, a)));
 #pragma unroll
   for (int s = 0; s < NSX; ++s) Us[2 + D + s] = fac * W[2 + D + s];
 #pragma unroll

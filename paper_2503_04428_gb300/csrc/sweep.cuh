@@ -660,7 +660,7 @@ struct Sweep {
       to_prim_c2<T, DIM, NSX>(Un, Wn, c2n, a.grad);
     } else {
       to_prim<T, DIM, NSX>(Un, Wn, a.gas);
-      c2n = a.gas.g * Wn[1 + DIM] / Wn[0];
+      c2n = qdiv(a.gas.g * Wn[1 + DIM], Wn[0]);
     }
     bool finite = true;
 #pragma unroll
