@@ -50,6 +50,14 @@ struct BatchState {
   BatchCtrl* part_ctrl_host = nullptr;
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
   std::vector<cudaEvent_t> ev_in, ev_done;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // the host-resident run as a CUDA graph, for repeated calls on the same
+  // pinned buffers
+  cudaGraphExec_t host_graph = nullptr;
+  int hg_parts = 0, hg_nsteps = 0;
+  const void* hg_in = nullptr;
+  void* hg_out = nullptr;
+  double hg_cfl = -1.0;
   // MLP
   float* w = nullptr;
   float* m = nullptr;
@@ -107,6 +115,8 @@ static int occupancy_nw(int nw, int* blocks) {
 }
 
 // Work items (tube, first cell) of item_len cells.
+static void drop_graph(BatchState* bs);
+
 // Expected cost order of items [i0, i1) of the tube-ordered list: the waves
 // of every tube start at its interface (x = 1/2) and spread from there, so
 // items near it run the exact solver and the rest mostly take the
@@ -164,6 +174,7 @@ static int make_items(hydro_ctx* h, int item_len) {
   std::vector<int> tube(bs->nitems), start(bs->nitems);
   order_items(bs, item_len, 0, bs->nitems, tube, start);
   bs->part_items_P = 0;  // the host-resident order is rebuilt on demand
+  drop_graph(bs);
   return upload_items(tube, start, &bs->item_tube, &bs->item_start);
 }
 
@@ -179,6 +190,10 @@ static int part_items(hydro_ctx* h, const std::vector<int>& b0) {
   int st = upload_items(tube, start, &bs->part_item_tube, &bs->part_item_start);
   if (st) return st;
   bs->part_items_P = P;
+  if (bs->host_graph) {  // it points at the previous arrays
+    cudaGraphExecDestroy(bs->host_graph);
+    bs->host_graph = nullptr;
+  }
   return HYDRO_OK;
 }
 
@@ -245,6 +260,10 @@ static void drop_graph(BatchState* bs) {
   if (bs->graph) {
     cudaGraphExecDestroy(bs->graph);
     bs->graph = nullptr;
+  }
+  if (bs->host_graph) {
+    cudaGraphExecDestroy(bs->host_graph);
+    bs->host_graph = nullptr;
   }
 }
 
@@ -476,6 +495,8 @@ void hydro_batch_free_impl(hydro_ctx* h) {
   cudaFreeHost(bs->part_ctrl_host);
   cudaFree(bs->part_item_tube);
   cudaFree(bs->part_item_start);
+  if (bs->ev_fork) cudaEventDestroy(bs->ev_fork);
+  if (bs->ev_join) cudaEventDestroy(bs->ev_join);
   if (bs->s_h2d) cudaStreamDestroy(bs->s_h2d);
   if (bs->s_d2h) cudaStreamDestroy(bs->s_d2h);
   for (cudaEvent_t e : bs->ev_in) cudaEventDestroy(e);
@@ -503,56 +524,24 @@ void hydro_batch_free_impl(hydro_ctx* h) {
 // copies of one part overlap the computation of others.  Every part has its
 // own control block and work-queue range; the per-cell arithmetic is that of
 // hydro_batch_set_state + hydro_batch_run + hydro_batch_get_state.
+// Every device operation of one host-resident run, on the handle's stream
+// with the two copy streams forked from and joined back to it (so that the
+// sequence can be captured as one graph): the parts' control blocks in, then
+// per part the input copy, speeds and validity, the steps and the output
+// copy, and the control blocks back out.
 template <typename T>
-static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, double cfl, int nparts) {
+static int enqueue_host_run(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, double cfl, int P,
+                            const std::vector<int>& b0) {
   BatchState* bs = h->bs;
-  const int P = std::max(1, std::min(nparts, bs->ntubes));
-  if (bs->nparts < P) {
-    cudaFree(bs->part_ctrl);
-    cudaFreeHost(bs->part_ctrl_host);
-    bs->part_ctrl = nullptr;
-    bs->part_ctrl_host = nullptr;
-    bs->nparts = 0;
-    HCK(cudaMalloc(&bs->part_ctrl, sizeof(BatchCtrl) * P));
-    HCK(cudaMallocHost(&bs->part_ctrl_host, sizeof(BatchCtrl) * P));
-    bs->nparts = P;
-  }
-  if (!bs->s_h2d) HCK(cudaStreamCreateWithFlags(&bs->s_h2d, cudaStreamNonBlocking));
-  if (!bs->s_d2h) HCK(cudaStreamCreateWithFlags(&bs->s_d2h, cudaStreamNonBlocking));
-  while ((int)bs->ev_in.size() < P) {
-    cudaEvent_t a, b;
-    HCK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
-    HCK(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
-    bs->ev_in.push_back(a);
-    bs->ev_done.push_back(b);
-  }
-  int st = read_bctrl(h);
-  if (st) return st;
-  // part boundaries at tubes, about total/P cells each
-  std::vector<int> b0(P + 1, bs->ntubes);
-  b0[0] = 0;
-  for (int p = 1, b = 0; p < P; ++p) {
-    const long long target = bs->total * p / P;
-    while (b < bs->ntubes && bs->off[b] < target) ++b;
-    b0[p] = std::max(b, b0[p - 1] + 1);
-  }
-  for (int p = 1; p <= P; ++p) b0[p] = std::min(std::max(b0[p], b0[p - 1]), bs->ntubes);
-  b0[P] = bs->ntubes;
-  if ((st = part_items(h, b0))) return st;
-  const int slot = 0;  // input lands in buffer 0; the result is in buffer (nsteps & 1)
-  const int out_slot = nsteps & 1;
-  for (int p = 0; p < P; ++p) {
-    BatchCtrl& c = bs->part_ctrl_host[p];
-    std::memset(&c, 0, sizeof(BatchCtrl));
-    c.c.cur = slot;
-    c.c.step = bs->bctrl_host->c.step;
-    c.c.err_step = -1;
-  }
-  HCK(cudaMemcpyAsync(bs->part_ctrl, bs->part_ctrl_host, sizeof(BatchCtrl) * P, cudaMemcpyHostToDevice, h->stream));
-  HCK(cudaStreamSynchronize(h->stream));
+  int st = HYDRO_OK;
+  const int slot = 0, out_slot = nsteps & 1;
   const Gas<T> gas = make_gas<T>(h->gamma);
   T* buf_in = (T*)h->buf[slot];
   T* buf_out = (T*)h->buf[out_slot];
+  HCK(cudaMemcpyAsync(bs->part_ctrl, bs->part_ctrl_host, sizeof(BatchCtrl) * P, cudaMemcpyHostToDevice, h->stream));
+  HCK(cudaEventRecord(bs->ev_fork, h->stream));
+  HCK(cudaStreamWaitEvent(bs->s_h2d, bs->ev_fork, 0));
+  HCK(cudaStreamWaitEvent(bs->s_d2h, bs->ev_fork, 0));
   for (int p = 0; p < P; ++p) {
     const int t0 = b0[p], t1 = b0[p + 1];
     if (t1 <= t0) continue;
@@ -590,8 +579,97 @@ static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
   }
   HCK(cudaMemcpyAsync(bs->part_ctrl_host, bs->part_ctrl, sizeof(BatchCtrl) * P, cudaMemcpyDeviceToHost,
                       h->stream));
+  HCK(cudaEventRecord(bs->ev_join, bs->s_d2h));
+  HCK(cudaStreamWaitEvent(h->stream, bs->ev_join, 0));
+  return st;
+}
+
+template <typename T>
+static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, double cfl, int nparts) {
+  BatchState* bs = h->bs;
+  const int P = std::max(1, std::min(nparts, bs->ntubes));
+  if (bs->nparts < P) {
+    drop_graph(bs);  // the host-run graph refers to the old control blocks
+    cudaFree(bs->part_ctrl);
+    cudaFreeHost(bs->part_ctrl_host);
+    bs->part_ctrl = nullptr;
+    bs->part_ctrl_host = nullptr;
+    bs->nparts = 0;
+    HCK(cudaMalloc(&bs->part_ctrl, sizeof(BatchCtrl) * P));
+    HCK(cudaMallocHost(&bs->part_ctrl_host, sizeof(BatchCtrl) * P));
+    bs->nparts = P;
+  }
+  if (!bs->s_h2d) HCK(cudaStreamCreateWithFlags(&bs->s_h2d, cudaStreamNonBlocking));
+  if (!bs->s_d2h) HCK(cudaStreamCreateWithFlags(&bs->s_d2h, cudaStreamNonBlocking));
+  if (!bs->ev_fork) HCK(cudaEventCreateWithFlags(&bs->ev_fork, cudaEventDisableTiming));
+  if (!bs->ev_join) HCK(cudaEventCreateWithFlags(&bs->ev_join, cudaEventDisableTiming));
+  while ((int)bs->ev_in.size() < P) {
+    cudaEvent_t a, b;
+    HCK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    HCK(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    bs->ev_in.push_back(a);
+    bs->ev_done.push_back(b);
+  }
+  int st = read_bctrl(h);
+  if (st) return st;
+  // part boundaries at tubes, about total/P cells each
+  std::vector<int> b0(P + 1, bs->ntubes);
+  b0[0] = 0;
+  for (int p = 1, b = 0; p < P; ++p) {
+    const long long target = bs->total * p / P;
+    while (b < bs->ntubes && bs->off[b] < target) ++b;
+    b0[p] = std::max(b, b0[p - 1] + 1);
+  }
+  for (int p = 1; p <= P; ++p) b0[p] = std::min(std::max(b0[p], b0[p - 1]), bs->ntubes);
+  b0[P] = bs->ntubes;
+  if ((st = part_items(h, b0))) return st;
+  const int slot = 0;  // input lands in buffer 0; the result is in buffer (nsteps & 1)
+  const int out_slot = nsteps & 1;
+  for (int p = 0; p < P; ++p) {
+    BatchCtrl& c = bs->part_ctrl_host[p];
+    std::memset(&c, 0, sizeof(BatchCtrl));
+    c.c.cur = slot;
+    c.c.step = bs->bctrl_host->c.step;
+    c.c.err_step = -1;
+  }
+  // Reuse the captured graph for the same buffers and settings; capture one
+  // for pinned buffers; enqueue directly otherwise (a graph cannot hold
+  // copies from pageable memory).
+  const bool same = bs->host_graph && bs->hg_parts == P && bs->hg_nsteps == nsteps && bs->hg_in == U_in &&
+                    bs->hg_out == U_out && bs->hg_cfl == cfl;
+  if (!same) {
+    if (bs->host_graph) {
+      cudaGraphExecDestroy(bs->host_graph);
+      bs->host_graph = nullptr;
+    }
+    cudaPointerAttributes ai, ao;
+    const bool pinned = cudaPointerGetAttributes(&ai, U_in) == cudaSuccess && ai.type == cudaMemoryTypeHost &&
+                        cudaPointerGetAttributes(&ao, U_out) == cudaSuccess && ao.type == cudaMemoryTypeHost;
+    cudaGetLastError();  // an unregistered pointer may leave an error behind
+    if (pinned) {
+      cudaGraph_t g;
+      HCK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+      st = enqueue_host_run<T>(h, U_in, U_out, nsteps, cfl, P, b0);
+      cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+      if (st) {
+        if (e == cudaSuccess) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "hydro_batch_run_host: cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&bs->host_graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "hydro_batch_run_host: cudaGraphInstantiate");
+      bs->hg_parts = P;
+      bs->hg_nsteps = nsteps;
+      bs->hg_in = U_in;
+      bs->hg_out = U_out;
+      bs->hg_cfl = cfl;
+    } else {
+      if ((st = enqueue_host_run<T>(h, U_in, U_out, nsteps, cfl, P, b0))) return st;
+    }
+  }
+  if (bs->host_graph) HCK(cudaGraphLaunch(bs->host_graph, h->stream));
   HCK(cudaStreamSynchronize(h->stream));
-  HCK(cudaStreamSynchronize(bs->s_d2h));
   int code = 0;
   long long iters = 0, mlp = 0, fb = 0;
   for (int p = 0; p < P; ++p) {

@@ -164,6 +164,19 @@ def test_run_host_equals_set_run_get(hydro_lib, precision):
     pin_out = torch.empty_like(pin_in).pin_memory()
     b.run_host(pin_in, pin_out, 3, 0.8, nparts=100)
     assert np.array_equal(pin_out.numpy(), ref)
+    # pinned buffers again (the captured graph is replayed) and after a
+    # change of input contents, with other buffers, and with another step count
+    b.run_host(pin_in, pin_out, 3, 0.8, nparts=100)
+    assert np.array_equal(pin_out.numpy(), ref)
+    pin_in.copy_(torch.from_numpy(ref))
+    b.set_state(ref)
+    b.run(2, 0.8)
+    ref2 = b.get_state()
+    b.run_host(pin_in, pin_out, 2, 0.8, nparts=100)
+    assert np.array_equal(pin_out.numpy(), ref2)
+    pin_out2 = torch.empty_like(pin_in).pin_memory()
+    b.run_host(pin_in, pin_out2, 2, 0.8, nparts=3)
+    assert np.array_equal(pin_out2.numpy(), ref2)
     # an invalid input state is reported
     bad = U.copy()
     bad[0, 5] = -1.0
