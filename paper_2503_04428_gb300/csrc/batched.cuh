@@ -27,7 +27,7 @@
 namespace hydro {
 
 constexpr int BSEG = 28;  // cells per warp segment (32 lanes = 28 cells + 2 halo cells each side)
-constexpr int BDEPTH = 4;  // segment windows per warp in the shared-memory ring (BDEPTH-1 in flight)
+constexpr int BDEPTH = 6;  // segment windows per warp in the shared-memory ring (BDEPTH-1 in flight)
 
 // Dynamic shared memory of batched_kernel<T, NW>: one ring of BDEPTH windows
 // (3 variables x 32 cells) per warp.

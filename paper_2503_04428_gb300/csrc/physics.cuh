@@ -57,13 +57,16 @@ struct GasRad : Gas<T> {
 
   // The temperature where c1 t + c4 t^4 = y (c1 > 0, c4 >= 0).  The left side
   // is increasing and convex in t > 0, so Newton from the upper bound
-  // min(y/c1, (y/c4)^(1/4)) descends monotonically to the root; it stops when
-  // the relative step is below temp_tol and takes one more step.  y <= 0
-  // gives y/c1 <= 0, which the positivity checks reject.
-  __device__ __forceinline__ T temperature(T c1, T c4, T y) const {
+  // min(y/c1, (y/c4)^(1/4)) descends monotonically to the root; from any
+  // other positive start t0 (a nearby temperature the caller knows) the first
+  // step lands above the root and the descent follows.  It stops when the
+  // relative step is below temp_tol and takes one more step.  y <= 0 gives
+  // y/c1 <= 0, which the positivity checks reject.
+  __device__ __forceinline__ T temperature(T c1, T c4, T y, T t0 = T(0)) const {
     T t = y / c1;
     if (!(y > T(0))) return t;
-    if (c4 > T(0)) t = fmin(t, dsqrt_(dsqrt_(y / c4)));
+    if (t0 > T(0)) t = t0;
+    else if (c4 > T(0)) t = fmin(t, dsqrt_(dsqrt_(y / c4)));
     bool conv = false;
     for (int it = 0; it < 60; ++it) {
       const T t3 = t * t * t;
@@ -88,15 +91,15 @@ struct GasRad : Gas<T> {
     p = pg + pr;
     c2 = sound2(rho, pg, pr);
   }
-  // P, c^2 and the temperature from (rho, e)
-  __device__ __forceinline__ void from_e_t(T rho, T e, T& p, T& c2, T& t) const {
-    t = temperature(rho * Rg, a, e);
+  // P, c^2 and the temperature from (rho, e) (t0: a start, see temperature)
+  __device__ __forceinline__ void from_e_t(T rho, T e, T& p, T& c2, T& t, T t0 = T(0)) const {
+    t = temperature(rho * Rg, a, e, t0);
     const T pg = rho * R * t, pr = a3 * t * t * t * t;
     p = pg + pr;
     c2 = sound2(rho, pg, pr);
   }
-  // the temperature of (rho, P)
-  __device__ __forceinline__ T temp_p(T rho, T p) const { return temperature(rho * R, a3, p); }
+  // the temperature of (rho, P) (t0: a start, see temperature)
+  __device__ __forceinline__ T temp_p(T rho, T p, T t0 = T(0)) const { return temperature(rho * R, a3, p, t0); }
   // e and c^2 of a state whose temperature is known
   __device__ __forceinline__ void from_t(T rho, T t, T& e, T& c2) const {
     const T pg = rho * R * t, pr = a3 * t * t * t * t;
@@ -161,8 +164,24 @@ __device__ __forceinline__ void to_prim(const T* U, T* W, const G& gas) {
   for (int s = 0; s < NSX; ++s) W[2 + D + s] = U[2 + D + s] * ir;
 }
 
-// to_prim for the gas + radiation EoS that also returns c^2 (Eq. 7) from the
-// same temperature solve.
+// to_prim for the gas + radiation EoS that also returns c^2 (Eq. 7) and the
+// temperature of the same solve (t0: a Newton start, see GasRad::temperature).
+template <typename T, int D, int NSX, typename G>
+__device__ __forceinline__ void to_prim_ct(const T* U, T* W, T& c2, T& t, const G& gas, T t0 = T(0)) {
+  const T rho = U[0];
+  const T ir = qdiv(T(1), rho);
+  T ke = T(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    W[1 + d] = U[1 + d] * ir;
+    ke += U[1 + d] * W[1 + d];
+  }
+  W[0] = rho;
+  gas.from_e_t(rho, U[1 + D] - T(0.5) * ke, W[1 + D], c2, t, t0);
+#pragma unroll
+  for (int s = 0; s < NSX; ++s) W[2 + D + s] = U[2 + D + s] * ir;
+}
+
 template <typename T, int D, int NSX, typename G>
 __device__ __forceinline__ void to_prim_c2(const T* U, T* W, T& c2, const G& gas) {
   const T rho = U[0];

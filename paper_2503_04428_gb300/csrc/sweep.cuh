@@ -75,7 +75,8 @@ struct SweepShape {
   static constexpr size_t smem_elems = (size_t)WP * NV * WPL + (size_t)2 * NV * NFX +
                                        (size_t)2 * NV * NFY + (size_t)3 * NV * NFZ;
   static constexpr size_t dual_elems = (size_t)2 * (NFX + NFY + NFZ);  // dual-energy face terms
-  static constexpr size_t rad_elems = (size_t)2 * NFX + 2 * NFY + 3 * NFZ;  // face-state temperatures
+  // radiation EoS: face-state temperatures and those of the primitive planes
+  static constexpr size_t rad_elems = (size_t)2 * NFX + 2 * NFY + 3 * NFZ + (size_t)WP * WPL;
   static constexpr size_t smem_bytes_for(int mode) {
     return (smem_elems + ((mode & 2) ? dual_elems : 0) + ((mode & 1) ? rad_elems : 0)) * sizeof(T);
   }
@@ -134,6 +135,7 @@ struct Sweep {
   T* YTR;
   T* ZTL;
   T* ZTR;
+  T* WT;  // [slot][ey][ex] temperatures of the primitive planes
   int x0, y0, z1, n2;
   T dt, half_dt;
   const T* Uin;
@@ -168,6 +170,7 @@ struct Sweep {
     YTR = YTL + NFY;
     ZTL = YTR + NFY;
     ZTR = ZTL + 2 * NFZ;
+    WT = ZTR + NFZ;
   }
 
   // Dual energy (Sect. 2.5, reading R15): the advected internal energy
@@ -213,7 +216,13 @@ struct Sweep {
       if (fx) u[1] = -u[1];
       if (DIM >= 2 && fy) u[2] = -u[2];
       if (DIM == 3 && fz) u[3] = -u[3];
-      to_prim<T, DIM, NSX>(u, w, gas());
+      if constexpr (EOS == 1) {
+        T c2, t;
+        to_prim_ct<T, DIM, NSX>(u, w, c2, t, a.grad);
+        WT[(slot * EY + ey) * EX + ex] = t;
+      } else {
+        to_prim<T, DIM, NSX>(u, w, gas());
+      }
 #pragma unroll
       for (int v = 0; v < NV; ++v) W(slot, v, ey, ex) = w[v];
     }
@@ -284,13 +293,13 @@ struct Sweep {
       }
       w[0] = rho;
       T c2, t;
-      a.grad.from_e_t(rho, u[1 + DIM] - T(0.5) * ke, w[1 + DIM], c2, t);
+      a.grad.from_e_t(rho, u[1 + DIM] - T(0.5) * ke, w[1 + DIM], c2, t, *tp);
 #pragma unroll
       for (int s = 0; s < NSX; ++s) w[2 + DIM + s] = u[2 + DIM + s] * ir;
       if (!(w[0] > T(0)) || !(w[1 + DIM] > T(0))) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) w[v] = Wc[v];
-        t = a.grad.temp_p(Wc[0], Wc[1 + DIM]);
+        t = a.grad.temp_p(Wc[0], Wc[1 + DIM], *tp);
         if (owned) ++n_fallback;
       }
       *tp = t;
@@ -314,11 +323,20 @@ struct Sweep {
   // Physical fluxes of the two limited states of one direction and what is
   // parked in their face slots: the primitive states (ideal gas) or, for the
   // radiation EoS, the conserved states from the same temperature solve.
+  // (radiation EoS: tc = the cell's temperature, the Newton start; tl/th
+  // receive the limited states' temperatures)
   template <int DIR>
-  __device__ __forceinline__ void limited_fluxes(const T* Wl, const T* Wh, T* Fl, T* Fh, T* Pl, T* Ph) const {
+  __device__ __forceinline__ void limited_fluxes(const T* Wl, const T* Wh, T* Fl, T* Fh, T* Pl, T* Ph,
+                                                 T tc = T(0), T* tl = nullptr, T* th = nullptr) const {
     if constexpr (EOS == 1) {
-      flux_cons_e<T, DIM, NSX, DIR>(Wl, eint_of(a.grad, Wl[0], Wl[1 + DIM]), Fl, Pl);
-      flux_cons_e<T, DIM, NSX, DIR>(Wh, eint_of(a.grad, Wh[0], Wh[1 + DIM]), Fh, Ph);
+      T c2;
+      *tl = a.grad.temp_p(Wl[0], Wl[1 + DIM], tc);
+      *th = a.grad.temp_p(Wh[0], Wh[1 + DIM], tc);
+      T el, eh;
+      a.grad.from_t(Wl[0], *tl, el, c2);
+      a.grad.from_t(Wh[0], *th, eh, c2);
+      flux_cons_e<T, DIM, NSX, DIR>(Wl, el, Fl, Pl);
+      flux_cons_e<T, DIM, NSX, DIR>(Wh, eh, Fh, Ph);
     } else {
       phys_flux<T, DIM, NSX, DIR>(Wl, Fl, a.gas);
       phys_flux<T, DIM, NSX, DIR>(Wh, Fh, a.gas);
@@ -370,6 +388,7 @@ struct Sweep {
       Wc[v] = W(slot, v, ey, ex);
       dU[v] = T(0);
     }
+    const T tcell = EOS == 1 ? WT[(slot * EY + ey) * EX + ex] : T(0);
     {
       T Wm[NV], Wp[NV], Wl[NV], Wh[NV], Fl[NV], Fh[NV];
 #pragma unroll
@@ -378,8 +397,12 @@ struct Sweep {
         Wp[v] = W(slot, v, ey, ex + 1);
       }
       faces_of<0>(Wm, Wc, Wp, gi, Wl, Wh);
-      T Pl[NV], Ph[NV];
-      limited_fluxes<0>(Wl, Wh, Fl, Fh, Pl, Ph);
+      T Pl[NV], Ph[NV], tl = T(0), th = T(0);
+      limited_fluxes<0>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
+      if constexpr (EOS == 1) {
+        if (xlo) XTR[ixlo] = tl;
+        if (xhi) XTL[ixhi] = th;
+      }
       const T ih = inv_h(0, gi, gj, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -396,8 +419,12 @@ struct Sweep {
         Wp[v] = W(slot, v, ey + 1, ex);
       }
       faces_of<1>(Wm, Wc, Wp, gj, Wl, Wh);
-      T Pl[NV], Ph[NV];
-      limited_fluxes<1>(Wl, Wh, Fl, Fh, Pl, Ph);
+      T Pl[NV], Ph[NV], tl = T(0), th = T(0);
+      limited_fluxes<1>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
+      if constexpr (EOS == 1) {
+        if (ylo) YTR[iylo] = tl;
+        if (yhi) YTL[iyhi] = th;
+      }
       const T ih = inv_h(1, gi, gj, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -414,8 +441,12 @@ struct Sweep {
         Wp[v] = W(wslot(gz + 1), v, ey, ex);
       }
       faces_of<2>(Wm, Wc, Wp, gz, Wl, Wh);
-      T Pl[NV], Ph[NV];
-      limited_fluxes<2>(Wl, Wh, Fl, Fh, Pl, Ph);
+      T Pl[NV], Ph[NV], tl = T(0), th = T(0);
+      limited_fluxes<2>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
+      if constexpr (EOS == 1) {
+        if (zlo) ZTR[iz] = tl;
+        if (zhi) ZTL[(gz & 1) * NFZ + iz] = th;
+      }
       const T ih = inv_h(2, gi, gj, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -657,7 +688,8 @@ struct Sweep {
     // validity and the signal speed of the new state
     T Wn[NV], c2n;
     if constexpr (EOS == 1) {
-      to_prim_c2<T, DIM, NSX>(Un, Wn, c2n, a.grad);
+      T tn;
+      to_prim_ct<T, DIM, NSX>(Un, Wn, c2n, tn, a.grad, WT[(wslot(gz) * EY + j + HY) * EX + i + 2]);
     } else {
       to_prim<T, DIM, NSX>(Un, Wn, a.gas);
       c2n = qdiv(a.gas.g * Wn[1 + DIM], Wn[0]);

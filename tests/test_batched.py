@@ -1,4 +1,4 @@
-"""Batched tubes (config 4 form) on the GPU vs the FP64 oracle.
+"""Batched tubes (thousands of independent 1D shock tubes, exact solver) on the GPU vs the FP64 oracle.
 
 FP64: relative L1 <= 1e-11 after 20 steps (per-step 1e-12 bar, accumulated).
 FP32: per-step relative L1 <= 2e-5 with both sides restarted from the
