@@ -71,12 +71,13 @@ def alu_peaks(H):
             "source": "hydro_fma_rate: 8 independent FMA chains per thread, 8 CTAs of 256 per SM"}
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel."""
+def profiled_traffic(item_len):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this
+    kernel and the work-item length in effect (item boundaries re-fetch halos)."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     d = json.load(open(TRAFFIC_FILE))
-    if d.get("kernel_hash") != kernel_hash():
+    if d.get("kernel_hash") != kernel_hash() or d.get("item_len") != item_len:
         return None
     return float(d["dram_bytes_per_launch"])
 
@@ -492,8 +493,9 @@ def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it3
     nsteps = args.steps * args.repeats
     alg_bytes = 2 * 3 * 4 * total  # read U^n and write U^{n+1}, FP32
     achieved = alg_bytes / (t32 / nsteps) / 1e9
+    st = b32.stats()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": profiled_traffic(), "peak_kind": peak_kind, "kernel": "batched_kernel<float>",
+            "traffic": profiled_traffic(st["tile_x"]), "peak_kind": peak_kind, "kernel": "batched_kernel<float>",
             "algorithmic_bytes_per_launch": alg_bytes}
     fp64 = None
     if value64 is not None:
@@ -506,7 +508,6 @@ def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it3
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
     if rank == 0:
-        st = b32.stats()
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": nsteps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

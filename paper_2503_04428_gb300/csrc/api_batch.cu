@@ -19,7 +19,7 @@ namespace hydro {
 // Autotuner candidates: warps per CTA, cells per work item (whole 28-cell
 // segments) and persistent CTAs per SM (up to the occupancy limit).
 static const int BATCH_NW[] = {4, 8};
-static const int BATCH_ITEM[] = {28, 56, 112, 224, 448, 896};
+static const int BATCH_ITEM[] = {28, 56, 112, 224, 448, 896, 1792, 3584};
 
 struct BatchState {
   int ntubes = 0;
@@ -276,7 +276,7 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
   if (bs->tuned) return HYDRO_OK;
   bs->tuned = true;
   std::ostringstream key;
-  key << "batch4_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
+  key << "batch6_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
       << device_key();
   int cached;
   double us;
