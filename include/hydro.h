@@ -47,7 +47,7 @@ typedef enum {
   HYDRO_ERR_NEGATIVE_STATE = -3,  /* a cell reached rho <= 0 or P <= 0 */
   HYDRO_ERR_NONFINITE = -4,       /* NaN or Inf in the state */
   HYDRO_ERR_NEWTON = -5,          /* exact-solver Newton did not converge in 100 iterations */
-  HYDRO_ERR_TIMEOUT = -6,         /* reserved: a bounded device wait expired */
+  HYDRO_ERR_TIMEOUT = -6,         /* a bounded device wait expired (batched: a window copy never landed) */
   HYDRO_ERR_OOM = -7,             /* device allocation failed */
   HYDRO_ERR_VACUUM = -8,          /* exact solver: the data generate vacuum */
   HYDRO_ERR_UNSUPPORTED = -9      /* combination not built (see message) */

@@ -24,6 +24,7 @@ static const int BATCH_ITEM[] = {28, 56, 112, 224, 448, 896, 1792, 3584};
 struct BatchState {
   int ntubes = 0;
   long long total = 0;
+  long long stride = 0;  // device elements between the variables' slabs: total rounded up to 16 bytes
   long long faces_per_step = 0;
   long long* off_d = nullptr;
   std::vector<long long> off;
@@ -205,7 +206,7 @@ static BatchArgs<T> batch_args(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const 
   a.A = (const T*)h->buf[0];
   a.Aw = (T*)h->buf[0];
   a.B = (T*)h->buf[1];
-  a.total = bs->total;
+  a.stride = bs->stride;
   a.off = bs->off_d;
   a.item_tube = bs->item_tube;
   a.item_start = bs->item_start;
@@ -276,15 +277,16 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
   if (bs->tuned) return HYDRO_OK;
   bs->tuned = true;
   std::ostringstream key;
-  key << "batch6_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
+  key << "batch7_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
       << device_key();
   int cached;
   double us;
   if (tune_cache_get(key.str(), &cached, &us)) {
+    // cached = (warps * 10000 + item cells) * 100 + CTAs per SM
     bs->nw = cached / 1000000;
-    int st = make_items(h, (cached / 1000) % 1000);
+    int st = make_items(h, (cached / 100) % 10000);
     if (st) return st;
-    bs->grid = h->num_sms * (cached % 1000);
+    bs->grid = h->num_sms * (cached % 100);
     bs->tuned_us = us;
     return HYDRO_OK;
   }
@@ -360,7 +362,7 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
   if ((st = make_items(h, best_item))) return st;
   bs->grid = h->num_sms * best_mult;
   bs->tuned_us = best;
-  tune_cache_put(key.str(), best_nw * 1000000 + best_item * 1000 + best_mult, best);
+  tune_cache_put(key.str(), (best_nw * 10000 + best_item) * 100 + best_mult, best);
   return HYDRO_OK;
 }
 
@@ -371,7 +373,7 @@ static int batch_speed(hydro_ctx* h, int slot, int* status) {
   HCK(cudaMalloc(&d_status, sizeof(int)));
   HCK(cudaMemsetAsync(d_status, 0, sizeof(int), h->stream));
   HCK(cudaMemsetAsync(bs->smax_next, 0, sizeof(unsigned long long) * bs->ntubes, h->stream));
-  batch_speed_kernel<T><<<bs->ntubes, 256, 0, h->stream>>>((const T*)h->buf[slot], bs->total, bs->off_d, 0,
+  batch_speed_kernel<T><<<bs->ntubes, 256, 0, h->stream>>>((const T*)h->buf[slot], bs->stride, bs->off_d, 0,
                                                             bs->ntubes, make_gas<T>(h->gamma), bs->smax_next,
                                                             d_status);
   HCK(cudaGetLastError());
@@ -439,8 +441,10 @@ int hydro_batch_set_state_impl(hydro_ctx* h, const void* U, int where) {
   int st = read_bctrl(h);
   if (st) return st;
   const int slot = bs->bctrl_host->c.cur ^ 1;
-  HCK(cudaMemcpyAsync(h->buf[slot], U, (size_t)3 * bs->total * h->esize,
-                      where == HYDRO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  // caller layout: 3 slabs of total elements; device: slabs `stride` apart
+  HCK(cudaMemcpy2DAsync(h->buf[slot], (size_t)bs->stride * h->esize, U, (size_t)bs->total * h->esize,
+                        (size_t)bs->total * h->esize, 3,
+                        where == HYDRO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
   int status = 0;
   st = h->precision == 64 ? batch_speed<double>(h, slot, &status) : batch_speed<float>(h, slot, &status);
   if (st) return st;
@@ -464,8 +468,10 @@ int hydro_batch_set_state_impl(hydro_ctx* h, const void* U, int where) {
 int hydro_batch_get_state_impl(hydro_ctx* h, void* U, int where) {
   int st = read_bctrl(h);
   if (st) return st;
-  HCK(cudaMemcpyAsync(U, h->buf[h->bs->bctrl_host->c.cur], (size_t)3 * h->bs->total * h->esize,
-                      where == HYDRO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  const BatchState* bs = h->bs;
+  HCK(cudaMemcpy2DAsync(U, (size_t)bs->total * h->esize, h->buf[bs->bctrl_host->c.cur], (size_t)bs->stride * h->esize,
+                        (size_t)bs->total * h->esize, 3,
+                        where == HYDRO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
   HCK(cudaStreamSynchronize(h->stream));
   return HYDRO_OK;
 }
@@ -547,14 +553,14 @@ static int enqueue_host_run(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
     if (t1 <= t0) continue;
     const long long c0 = bs->off[t0], nc = bs->off[t1] - c0;
     for (int v = 0; v < 3; ++v)
-      HCK(cudaMemcpyAsync(buf_in + v * bs->total + c0, U_in + v * bs->total + c0, sizeof(T) * nc,
+      HCK(cudaMemcpyAsync(buf_in + v * bs->stride + c0, U_in + v * bs->total + c0, sizeof(T) * nc,
                           cudaMemcpyHostToDevice, bs->s_h2d));
     HCK(cudaEventRecord(bs->ev_in[p], bs->s_h2d));
     HCK(cudaStreamWaitEvent(h->stream, bs->ev_in[p], 0));
     // the part's per-tube speeds and validity (as hydro_batch_set_state)
     HCK(cudaMemsetAsync(bs->smax_next + t0, 0, sizeof(unsigned long long) * (t1 - t0), h->stream));
     HCK(cudaMemsetAsync(bs->t_tube + t0, 0, sizeof(double) * (t1 - t0), h->stream));
-    batch_speed_kernel<T><<<t1 - t0, 256, 0, h->stream>>>(buf_in, bs->total, bs->off_d, t0, t1 - t0, gas,
+    batch_speed_kernel<T><<<t1 - t0, 256, 0, h->stream>>>(buf_in, bs->stride, bs->off_d, t0, t1 - t0, gas,
                                                          bs->smax_next, &bs->part_ctrl[p].c.status);
     HCK(cudaGetLastError());
     HCK(cudaMemcpyAsync(bs->smax_cur + t0, bs->smax_next + t0, sizeof(double) * (t1 - t0),
@@ -574,7 +580,7 @@ static int enqueue_host_run(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
     HCK(cudaEventRecord(bs->ev_done[p], h->stream));
     HCK(cudaStreamWaitEvent(bs->s_d2h, bs->ev_done[p], 0));
     for (int v = 0; v < 3; ++v)
-      HCK(cudaMemcpyAsync(U_out + v * bs->total + c0, buf_out + v * bs->total + c0, sizeof(T) * nc,
+      HCK(cudaMemcpyAsync(U_out + v * bs->total + c0, buf_out + v * bs->stride + c0, sizeof(T) * nc,
                           cudaMemcpyDeviceToHost, bs->s_d2h));
   }
   HCK(cudaMemcpyAsync(bs->part_ctrl_host, bs->part_ctrl, sizeof(BatchCtrl) * P, cudaMemcpyDeviceToHost,
@@ -732,11 +738,13 @@ int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int
   h->bs = bs;
   bs->ntubes = ntubes;
   bs->total = total;
+  const long long q = 16 / h->esize;
+  bs->stride = (total + q - 1) / q * q;
   bs->limiter = limiter;
   bs->faces_per_step = total + ntubes;
   bs->off.assign(ntubes + 1, 0);
   for (int b = 0; b < ntubes; ++b) bs->off[b + 1] = bs->off[b] + lengths[b];
-  const size_t bytes = (size_t)3 * total * h->esize;
+  const size_t bytes = (size_t)3 * bs->stride * h->esize;
   for (int b = 0; b < 2; ++b)
     if ((st = h->arena.alloc(&h->buf[b], bytes))) { hydro_destroy(h); return st; }
   if (cudaMalloc(&bs->off_d, sizeof(long long) * (ntubes + 1)) != cudaSuccess ||

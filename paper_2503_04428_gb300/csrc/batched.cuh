@@ -17,40 +17,71 @@
 //     Newton to 1e-10 (FP64) and one polishing step; sample at x/t = 0;
 //   - updates cell c0+l (Eq. 19) and reduces its signal speed.
 // A segment whose whole window is one uniform state takes a short path that
-// returns exactly what the full path returns there (U + 0).  Segment windows
-// are streamed into a per-warp shared-memory ring by cp.async, several
-// segments ahead, so that enough loads are in flight to cover HBM latency.
+// returns exactly what the full path returns there (U + 0).  The windows of
+// BSPAN consecutive segments arrive together: one lane copies their aligned
+// span of every variable into a slot of the warp's shared-memory ring with
+// 1D bulk copies (cp.async.bulk, completion counted on the slot's mbarrier),
+// several spans ahead of the one in use, so that enough bytes are in flight
+// to cover HBM latency in few, large transfers.  Every variable's slab of
+// the state starts on a 16-byte boundary for this (padded stride).
 // The last CTA to finish commits the step (per-tube speeds, times, buffer).
 #pragma once
 #include "common.cuh"
 
 namespace hydro {
 
-constexpr int BSEG = 28;  // cells per warp segment (32 lanes = 28 cells + 2 halo cells each side)
-constexpr int BDEPTH = 6;  // segment windows per warp in the shared-memory ring (BDEPTH-1 in flight)
+constexpr int BSEG = 28;   // cells per warp segment (32 lanes = 28 cells + 2 halo cells each side)
+constexpr int BSPAN = 8;   // segments per ring slot
+constexpr int BVSTR = 232; // elements per variable in a slot: the span's 228 cells widened to 16-byte bounds
+constexpr int ST_TIMEOUT = -6;  // HYDRO_ERR_TIMEOUT: a bounded wait for a bulk copy expired
 
-// Dynamic shared memory of batched_kernel<T, NW>: one ring of BDEPTH windows
-// (3 variables x 32 cells) per warp.
+// Ring slots per warp (all but one in flight while one is in use).
+template <typename T>
+__host__ __device__ constexpr int bdepth() {
+  return sizeof(T) == 4 ? 3 : 2;
+}
+// Elements per 16 bytes: slabs, spans and copy sizes are multiples of this.
+template <typename T>
+__host__ __device__ constexpr int bquant() {
+  return 16 / (int)sizeof(T);
+}
+
+// Dynamic shared memory of batched_kernel<T, NW>: one ring of bdepth<T>()
+// slots (3 variables x BVSTR elements) per warp.
 template <typename T, int NW>
 constexpr size_t batched_smem_bytes() {
-  return (size_t)NW * BDEPTH * 3 * 32 * sizeof(T);
+  return (size_t)NW * bdepth<T>() * 3 * BVSTR * sizeof(T);
 }
 
-// Asynchronous 4- or 8-byte global -> shared copy (cp.async, completion
-// tracked per thread by commit/wait groups).
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gmem_src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  if constexpr (sizeof(T) == 4) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
-  } else {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
-  }
+// mbarrier and 1D bulk-copy primitives (PTX ISA: mbarrier, cp.async.bulk).
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* m) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(m)) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(m))
+               : "memory");
+}
+// Wait for phase `parity` of the mbarrier to complete, at most 2^20 polls
+// (each poll may itself suspend the thread for a bounded time); false if it
+// did not.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* m, unsigned parity) {
+  const unsigned a = smem_addr(m);
+  for (int i = 0; i < (1 << 20); ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
 }
 
 struct BatchCtrl {
@@ -64,7 +95,7 @@ struct BatchArgs {
   const T* A;
   T* B;
   T* Aw;
-  long long total;
+  long long stride;            // elements between the variables' slabs (a multiple of bquant<T>())
   const long long* off;        // ntubes + 1 cell offsets
   const int* item_tube;
   const int* item_start;
@@ -151,8 +182,13 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
   const long long step = vc->step;
   const T* Uin = cur ? a.B : a.A;
   T* Uout = cur ? a.Aw : a.B;
-  const int lane = threadIdx.x & 31;
-  T* ring = reinterpret_cast<T*>(ring_raw) + (threadIdx.x >> 5) * (BDEPTH * 96);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int BD = bdepth<T>(), Q = bquant<T>();
+  T* ring = reinterpret_cast<T*>(ring_raw) + warp * (BD * 3 * BVSTR);
+  __shared__ unsigned long long bar[NW][BD];  // one mbarrier per ring slot
+  if (lane < BD) mbar_init(&bar[warp][lane]);
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the inits, visible to the copies
+  __syncwarp();
   const Gas<T>& gas = a.gas;
   if (a.mlp_on) {
     for (int p = threadIdx.x; p < MLP_H * MLP_IN; p += NW * 32) sw.w1[p] = a.mlp_w[MW1 + p];
@@ -173,6 +209,10 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
   // the last uniform window's state and its |u| + c (warp-uniform values)
   bool have_u = false;
   T ur[3] = {T(0), T(0), T(0)}, u_spd = T(0);
+  // spans issued into / taken out of this warp's ring so far (warp-uniform);
+  // slot q % BD completes its phase (q / BD) & 1 for the q-th span
+  unsigned q_issue = 0, q_use = 0;
+  bool dead = false;  // a bounded wait expired: stop, drain, report
 
   for (;;) {
     int it = 0;
@@ -192,199 +232,241 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     const T dtdx = (T)dtd * fn;
     T smax = T(0);
 
-    // The conserved window of segment s (cells c0-2+lane, clamped to the
-    // tube: transmissive ends) streams through this warp's ring by cp.async,
-    // BDEPTH-1 segments ahead of the one being computed.  Lane l copies and
-    // later reads only its own ring entries, so its own wait suffices.
+    // The conserved windows (cells c0-2+lane, clamped to the tube:
+    // transmissive ends) of segments BSPAN*k .. BSPAN*k+BSPAN-1 arrive in
+    // ring slot q_use % BD as span k: cells lo .. hi-1 of the tube, widened
+    // to 16-byte bounds, copied by lane 0 with one bulk copy per variable,
+    // BD-1 spans ahead of the one in use.
     const int nseg = (s_end - s_beg + BSEG - 1) / BSEG;
-    auto issue = [&](int sg) {
-      if (sg < nseg) {
-        const int ca = min(max(s_beg + sg * BSEG - 2 + lane, 0), nb - 1);
-        T* dst = ring + (sg % BDEPTH) * 96 + lane;
+    const int nspan = (nseg + BSPAN - 1) / BSPAN;
+    auto span_of = [&](int k, long long& g0, int& len) {
+      const int lo = max(s_beg + k * BSPAN * BSEG - 2, 0);
+      const int hi = min(s_beg + (k + 1) * BSPAN * BSEG + 2, nb);
+      g0 = (base + lo) & ~(long long)(Q - 1);
+      len = (int)(((base + hi + Q - 1) & ~(long long)(Q - 1)) - g0);  // <= BVSTR
+    };
+    auto issue = [&](int k) {
+      if (k < nspan) {
+        if (lane == 0) {
+          long long g0;
+          int len;
+          span_of(k, g0, len);
+          const int sl = (int)(q_issue % BD);
+          const unsigned bytes = (unsigned)len * (unsigned)sizeof(T);
+          mbar_expect_tx(&bar[warp][sl], 3u * bytes);
 #pragma unroll
-        for (int v = 0; v < 3; ++v) cp_async_elem(dst + 32 * v, Uin + v * a.total + base + ca);
+          for (int v = 0; v < 3; ++v)
+            bulk_copy_g2s(ring + sl * (3 * BVSTR) + v * BVSTR, Uin + v * a.stride + g0, bytes, &bar[warp][sl]);
+        }
+        ++q_issue;
       }
-      cp_async_commit();  // (an empty group when sg is past the item)
     };
 #pragma unroll
-    for (int sg = 0; sg < BDEPTH - 1; ++sg) issue(sg);
-    for (int sg = 0; sg < nseg; ++sg) {
-      const int c0 = s_beg + sg * BSEG;
-      issue(sg + BDEPTH - 1);      // into the ring slot read one segment ago
-      cp_async_wait<BDEPTH - 1>();  // segment sg has landed
-      T Ua[3];
-#pragma unroll
-      for (int v = 0; v < 3; ++v) Ua[v] = ring[(sg % BDEPTH) * 96 + 32 * v + lane];
-      const int ncell = min(BSEG, s_end - c0);  // cells updated in this segment
-      // A window holding one state everywhere (clamped tube ends included)
-      // has zero slopes, a +0 Hancock increment, identical face states and
-      // equal fluxes, so the full path below returns U + 0 for every cell:
-      // produce exactly that without the face work.
-      // (the shuffles run on every lane before the comparison: a shuffle
-      // inside a short-circuit condition would leave lanes out of it)
-      const T r0 = __shfl_sync(0xffffffffu, Ua[0], 0);
-      const T r1 = __shfl_sync(0xffffffffu, Ua[1], 0);
-      const T r2 = __shfl_sync(0xffffffffu, Ua[2], 0);
-      const bool uniform = __all_sync(0xffffffffu, (Ua[0] == r0) & (Ua[1] == r1) & (Ua[2] == r2));
-      if (uniform) {
-        // One state (r0, r1, r2) on every lane: its validity and |u| + c are
-        // those of the last uniform window whenever the state repeats, as it
-        // does along the undisturbed stretches of a tube.
-        if (!(have_u && r0 == ur[0] && r1 == ur[1] && r2 == ur[2])) {
-          have_u = true;
-          ur[0] = r0;
-          ur[1] = r1;
-          ur[2] = r2;
-          T u[3] = {r0 + T(0), r1 + T(0), r2 + T(0)}, w[3];
-          const bool finite = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
-          to_prim<T, 1, 0>(u, w, gas);
-          if (!finite) err = err ? err : ST_NONFINITE;
-          else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
-          u_spd = fabs(w[1]) + dsqrt(gas.g * w[2] / w[0]);
-        }
-        smax = fmax(smax, u_spd * fn);
-        if (lane < ncell) {
-          const long long c = base + c0 + lane;
-          Uout[c] = r0 + T(0);
-          Uout[a.total + c] = r1 + T(0);
-          Uout[2 * a.total + c] = r2 + T(0);
-        }
-        continue;
+    for (int k = 0; k < BD - 1; ++k) issue(k);
+    for (int k = 0; k < nspan; ++k) {
+      __syncwarp();     // every lane is done with the slot refilled next (read one span ago)
+      issue(k + BD - 1);
+      const int sl = (int)(q_use % BD);
+      const bool landed = mbar_wait(&bar[warp][sl], (q_use / BD) & 1u);
+      ++q_use;
+      if (__any_sync(0xffffffffu, !landed)) {
+        dead = true;
+        err = ST_TIMEOUT;
+        break;
       }
-      // a1 + a2: primitives of the window (transmissive ends by clamping)
-      T Wa[3];
-      to_prim<T, 1, 0>(Ua, Wa, gas);
-      // a3 + a4: cell c0-1+lane -- slopes, Hancock increment, predicted face states
-      T Wc[3], Wlo[3], Whi[3];
-      {
-        T Wp[3], fl[3], fh[3];
+      long long g0;
+      int len;
+      span_of(k, g0, len);
+      const T* slot = ring + sl * (3 * BVSTR);
+#pragma unroll 1
+      for (int j = 0; j < BSPAN; ++j) {
+        const int sg = k * BSPAN + j;
+        if (sg >= nseg) break;
+        const int c0 = s_beg + sg * BSEG;
+        T Ua[3];
+        {
+          const int idx = (int)(base + min(max(c0 - 2 + lane, 0), nb - 1) - g0);
+#pragma unroll
+          for (int v = 0; v < 3; ++v) Ua[v] = slot[v * BVSTR + idx];
+        }
+        const int ncell = min(BSEG, s_end - c0);  // cells updated in this segment
+        // A window holding one state everywhere (clamped tube ends included)
+        // has zero slopes, a +0 Hancock increment, identical face states and
+        // equal fluxes, so the full path below returns U + 0 for every cell:
+        // produce exactly that without the face work.
+        // (the shuffles run on every lane before the comparison: a shuffle
+        // inside a short-circuit condition would leave lanes out of it)
+        const T r0 = __shfl_sync(0xffffffffu, Ua[0], 0);
+        const T r1 = __shfl_sync(0xffffffffu, Ua[1], 0);
+        const T r2 = __shfl_sync(0xffffffffu, Ua[2], 0);
+        const bool uniform = __all_sync(0xffffffffu, (Ua[0] == r0) & (Ua[1] == r1) & (Ua[2] == r2));
+        if (uniform) {
+          // One state (r0, r1, r2) on every lane: its validity and |u| + c are
+          // those of the last uniform window whenever the state repeats, as it
+          // does along the undisturbed stretches of a tube.
+          if (!(have_u && r0 == ur[0] && r1 == ur[1] && r2 == ur[2])) {
+            have_u = true;
+            ur[0] = r0;
+            ur[1] = r1;
+            ur[2] = r2;
+            T u[3] = {r0 + T(0), r1 + T(0), r2 + T(0)}, w[3];
+            const bool finite = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+            to_prim<T, 1, 0>(u, w, gas);
+            if (!finite) err = err ? err : ST_NONFINITE;
+            else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
+            u_spd = fabs(w[1]) + dsqrt(gas.g * w[2] / w[0]);
+          }
+          smax = fmax(smax, u_spd * fn);
+          if (lane < ncell) {
+            const long long c = base + c0 + lane;
+            Uout[c] = r0 + T(0);
+            Uout[a.stride + c] = r1 + T(0);
+            Uout[2 * a.stride + c] = r2 + T(0);
+          }
+          continue;
+        }
+        // a1 + a2: primitives of the window (transmissive ends by clamping)
+        T Wa[3];
+        to_prim<T, 1, 0>(Ua, Wa, gas);
+        // a3 + a4: cell c0-1+lane -- slopes, Hancock increment, predicted face states
+        T Wc[3], Wlo[3], Whi[3];
+        {
+          T Wp[3], fl[3], fh[3];
+#pragma unroll
+          for (int v = 0; v < 3; ++v) {
+            Wc[v] = win(Wa[v], 1);
+            Wp[v] = win(Wa[v], 2);
+            const T sig = limit<T>(a.limiter, (Wc[v] - Wa[v]) * fn, (Wp[v] - Wc[v]) * fn);
+            Wlo[v] = Wc[v] - hw * sig;
+            Whi[v] = Wc[v] + hw * sig;
+          }
+          phys_flux<T, 1, 0, 0>(Wlo, fl, gas);
+          phys_flux<T, 1, 0, 0>(Whi, fh, gas);
+          T ul[3], uh[3];
+          to_cons<T, 1, 0>(Wlo, ul, gas);
+          to_cons<T, 1, 0>(Whi, uh, gas);
+#pragma unroll
+          for (int v = 0; v < 3; ++v) {
+            const T du = T(0.5) * dtdx * (fl[v] - fh[v]);
+            ul[v] += du;
+            uh[v] += du;
+          }
+          to_prim<T, 1, 0>(ul, Wlo, gas);
+          to_prim<T, 1, 0>(uh, Whi, gas);
+          // a non-physical prediction falls back to the cell average
+          const bool own = lane >= 1 && lane <= ncell;  // cells of this segment
+          if (!(Wlo[0] > T(0)) || !(Wlo[2] > T(0))) {
+#pragma unroll
+            for (int v = 0; v < 3; ++v) Wlo[v] = Wc[v];
+            if (own) ++n_fb;
+          }
+          if (!(Whi[0] > T(0)) || !(Whi[2] > T(0))) {
+#pragma unroll
+            for (int v = 0; v < 3; ++v) Whi[v] = Wc[v];
+            if (own) ++n_fb;
+          }
+        }
+        // a5: face c0+lane between cell c0-1+lane (its high state, this lane)
+        // and cell c0+lane (its low state, next lane)
+        T WL[3], WR[3], F[3] = {T(0), T(0), T(0)};
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          Wc[v] = win(Wa[v], 1);
-          Wp[v] = win(Wa[v], 2);
-          const T sig = limit<T>(a.limiter, (Wc[v] - Wa[v]) * fn, (Wp[v] - Wc[v]) * fn);
-          Wlo[v] = Wc[v] - hw * sig;
-          Whi[v] = Wc[v] + hw * sig;
+          WL[v] = Whi[v];
+          WR[v] = __shfl_down_sync(0xffffffffu, Wlo[v], 1);
         }
-        phys_flux<T, 1, 0, 0>(Wlo, fl, gas);
-        phys_flux<T, 1, 0, 0>(Whi, fh, gas);
-        T ul[3], uh[3];
-        to_cons<T, 1, 0>(Wlo, ul, gas);
-        to_cons<T, 1, 0>(Whi, uh, gas);
+        const bool face = lane <= ncell;
+        const bool owned = face && (lane < ncell || c0 + lane == nb);
+        const bool same = WL[0] == WR[0] && WL[1] == WR[1] && WL[2] == WR[2];
+        T pg = T(0);
+        int kind = 0;
+        T cL = T(0), cR = T(0);
+        if (face && !same) {
+          cL = dsqrt(gas.g * WL[2] / WL[0]);
+          cR = dsqrt(gas.g * WR[2] / WR[0]);
+          pg = toro_guess<T>(WL[0], WL[1], WL[2], cL, WR[0], WR[1], WR[2], cR, gas, kind);
+          if (!mlp_gate<T>(kind, WL[2], WR[2])) kind = -kind;  // negative: network not used
+          if (kind == 2 && a.harvest) {
+            const unsigned long long id = (unsigned long long)(base + b + c0 + lane);
+            const unsigned long long hsh =
+                mix64(a.harvest_seed + 0x9E3779B97F4A7C15ull * (id + 1) + ((unsigned long long)step << 40));
+            if (hsh < a.harvest_thresh) {
+              const unsigned long long slot = atomicAdd(a.harvest_n, 1ull);
+              if ((long long)slot < a.harvest_cap) {
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          const T du = T(0.5) * dtdx * (fl[v] - fh[v]);
-          ul[v] += du;
-          uh[v] += du;
-        }
-        to_prim<T, 1, 0>(ul, Wlo, gas);
-        to_prim<T, 1, 0>(uh, Whi, gas);
-        // a non-physical prediction falls back to the cell average
-        const bool own = lane >= 1 && lane <= ncell;  // cells of this segment
-        if (!(Wlo[0] > T(0)) || !(Wlo[2] > T(0))) {
-#pragma unroll
-          for (int v = 0; v < 3; ++v) Wlo[v] = Wc[v];
-          if (own) ++n_fb;
-        }
-        if (!(Whi[0] > T(0)) || !(Whi[2] > T(0))) {
-#pragma unroll
-          for (int v = 0; v < 3; ++v) Whi[v] = Wc[v];
-          if (own) ++n_fb;
-        }
-      }
-      // a5: face c0+lane between cell c0-1+lane (its high state, this lane)
-      // and cell c0+lane (its low state, next lane)
-      T WL[3], WR[3], F[3] = {T(0), T(0), T(0)};
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        WL[v] = Whi[v];
-        WR[v] = __shfl_down_sync(0xffffffffu, Wlo[v], 1);
-      }
-      const bool face = lane <= ncell;
-      const bool owned = face && (lane < ncell || c0 + lane == nb);
-      const bool same = WL[0] == WR[0] && WL[1] == WR[1] && WL[2] == WR[2];
-      T pg = T(0);
-      int kind = 0;
-      T cL = T(0), cR = T(0);
-      if (face && !same) {
-        cL = dsqrt(gas.g * WL[2] / WL[0]);
-        cR = dsqrt(gas.g * WR[2] / WR[0]);
-        pg = toro_guess<T>(WL[0], WL[1], WL[2], cL, WR[0], WR[1], WR[2], cR, gas, kind);
-        if (!mlp_gate<T>(kind, WL[2], WR[2])) kind = -kind;  // negative: network not used
-        if (kind == 2 && a.harvest) {
-          const unsigned long long id = (unsigned long long)(base + b + c0 + lane);
-          const unsigned long long hsh =
-              mix64(a.harvest_seed + 0x9E3779B97F4A7C15ull * (id + 1) + ((unsigned long long)step << 40));
-          if (hsh < a.harvest_thresh) {
-            const unsigned long long slot = atomicAdd(a.harvest_n, 1ull);
-            if ((long long)slot < a.harvest_cap) {
-#pragma unroll
-              for (int v = 0; v < 3; ++v) {
-                a.harvest[slot * 6 + v] = (double)WL[v];
-                a.harvest[slot * 6 + 3 + v] = (double)WR[v];
+                for (int v = 0; v < 3; ++v) {
+                  a.harvest[slot * 6 + v] = (double)WL[v];
+                  a.harvest[slot * 6 + 3 + v] = (double)WR[v];
+                }
               }
             }
           }
         }
-      }
-      // learned guess on two-shock faces, evaluated by the whole warp
-      if (a.mlp_on) {
-        unsigned todo = __ballot_sync(0xffffffffu, face && !same && kind == 2);
-        while (todo) {
-          const int g = __ffs(todo) - 1;
-          todo &= todo - 1;
-          float q[6];
+        // learned guess on two-shock faces, evaluated by the whole warp
+        if (a.mlp_on) {
+          unsigned todo = __ballot_sync(0xffffffffu, face && !same && kind == 2);
+          while (todo) {
+            const int g = __ffs(todo) - 1;
+            todo &= todo - 1;
+            float q[6];
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+              q[v] = (float)__shfl_sync(0xffffffffu, WL[v], g);
+              q[3 + v] = (float)__shfl_sync(0xffffffffu, WR[v], g);
+            }
+            float x[6], pref;
+            mlp_features((float)gas.g, q[0], q[1], q[2], q[3], q[4], q[5], x, pref);
+            const float y = mlp_warp(sw, x, lane);
+            if (lane == g) {
+              pg = (T)((double)pref * exp((double)y));
+              if (owned) ++n_mlp;
+            }
+          }
+        }
+        if (face) {
+          if (same) {
+            phys_flux<T, 1, 0, 0>(WL, F, gas);
+          } else {
+            int its = 0, k2 = 0;
+            const int st = riemann_exact<T, 1, 0, 0>(WL, WR, F, gas, pg, its, k2);
+            if (owned) n_iters += its;
+            if (st != ST_OK && err == 0) err = st;
+          }
+        }
+        // a6: update cell c0+lane with faces c0+lane (this lane) and c0+lane+1 (next)
+        T Fh[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) Fh[v] = __shfl_down_sync(0xffffffffu, F[v], 1);
+        T Uo[3];  // conserved state of cell c0+lane, from the window (lane+2)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) Uo[v] = win(Ua[v], 2);
+        if (lane < ncell) {
+          const long long c = base + c0 + lane;
+          T u[3], w[3];
+          bool finite = true;
 #pragma unroll
           for (int v = 0; v < 3; ++v) {
-            q[v] = (float)__shfl_sync(0xffffffffu, WL[v], g);
-            q[3 + v] = (float)__shfl_sync(0xffffffffu, WR[v], g);
+            u[v] = Uo[v] + dtdx * (F[v] - Fh[v]);
+            finite = finite && isfinite(u[v]);
           }
-          float x[6], pref;
-          mlp_features((float)gas.g, q[0], q[1], q[2], q[3], q[4], q[5], x, pref);
-          const float y = mlp_warp(sw, x, lane);
-          if (lane == g) {
-            pg = (T)((double)pref * exp((double)y));
-            if (owned) ++n_mlp;
-          }
+          to_prim<T, 1, 0>(u, w, gas);
+          if (!finite) err = err ? err : ST_NONFINITE;
+          else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
+          smax = fmax(smax, (fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * fn);
+#pragma unroll
+          for (int v = 0; v < 3; ++v) Uout[v * a.stride + c] = u[v];
         }
-      }
-      if (face) {
-        if (same) {
-          phys_flux<T, 1, 0, 0>(WL, F, gas);
-        } else {
-          int its = 0, k2 = 0;
-          const int st = riemann_exact<T, 1, 0, 0>(WL, WR, F, gas, pg, its, k2);
-          if (owned) n_iters += its;
-          if (st != ST_OK && err == 0) err = st;
-        }
-      }
-      // a6: update cell c0+lane with faces c0+lane (this lane) and c0+lane+1 (next)
-      T Fh[3];
-#pragma unroll
-      for (int v = 0; v < 3; ++v) Fh[v] = __shfl_down_sync(0xffffffffu, F[v], 1);
-      T Uo[3];  // conserved state of cell c0+lane, from the window (lane+2)
-#pragma unroll
-      for (int v = 0; v < 3; ++v) Uo[v] = win(Ua[v], 2);
-      if (lane < ncell) {
-        const long long c = base + c0 + lane;
-        T u[3], w[3];
-        bool finite = true;
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          u[v] = Uo[v] + dtdx * (F[v] - Fh[v]);
-          finite = finite && isfinite(u[v]);
-        }
-        to_prim<T, 1, 0>(u, w, gas);
-        if (!finite) err = err ? err : ST_NONFINITE;
-        else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
-        smax = fmax(smax, (fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * fn);
-#pragma unroll
-        for (int v = 0; v < 3; ++v) Uout[v * a.total + c] = u[v];
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
     if (lane == 0) atomicMax(&a.smax_next[b], dbits((double)smax));
+    if (dead) break;
+  }
+  // after an expired wait, let the copies still in flight land (bounded)
+  // before the CTA's shared memory is released
+  while (q_use < q_issue) {
+    mbar_wait(&bar[warp][q_use % BD], (q_use / BD) & 1u);
+    ++q_use;
   }
 
   // block totals of the counters and the error, then the last-CTA commit
@@ -435,7 +517,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
 
 // Signal speed of the current state per tube (after set_state).
 template <typename T>
-__global__ void batch_speed_kernel(const T* U, long long total, const long long* off, int tube0,
+__global__ void batch_speed_kernel(const T* U, long long stride, const long long* off, int tube0,
                                    int ntubes, Gas<T> gas, unsigned long long* smax_bits, int* status) {
   if ((int)blockIdx.x >= ntubes) return;
   const int b = tube0 + blockIdx.x;
@@ -448,7 +530,7 @@ __global__ void batch_speed_kernel(const T* U, long long total, const long long*
     bool finite = true;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-      u[v] = U[v * total + base + i];
+      u[v] = U[v * stride + base + i];
       finite = finite && isfinite(u[v]);
     }
     if (!finite) { err = ST_NONFINITE; continue; }

@@ -87,6 +87,22 @@ def test_ragged_and_minimum_tubes(hydro_lib):
     b.set_state(U)
     b.run(10, 0.6)
     assert np.all(rel_l1(ref, b.get_state()) <= 1e-11)
+    # FP32: the same ragged set (total not a multiple of the 16-byte slab
+    # quantum, tubes shorter than one segment) per step, through the host and
+    # the device copy paths
+    torch = pytest.importorskip("torch")
+    U32 = U.astype(np.float32)
+    b32 = hydro_lib.Batch(lengths, 5 / 3, limiter=hydro_lib.HYDRO_VANLEER, precision=32)
+    for k in range(4):
+        if k % 2:
+            b32.set_state(torch.from_numpy(U32).cuda())
+        else:
+            b32.set_state(U32)
+        ref, _ = O.batch_run(lengths, U32.astype(np.float64), 5 / 3, O.EXACT, O.VANLEER, 0.6, 1)
+        b32.run(1, 0.6)
+        G = b32.get_state()
+        assert np.all(rel_l1(ref, G) <= 2e-5), rel_l1(ref, G)
+        U32 = G
 
 
 def test_full_size_sampled(hydro_lib):
@@ -183,3 +199,31 @@ def test_run_host_equals_set_run_get(hydro_lib, precision):
     with pytest.raises(hydro_lib.HydroError):
         b.run_host(bad, out, 1, 0.8)
     b.close()
+
+
+def test_tune_cache_round_trip(tmp_path):
+    """A launch shape stored in the autotuner's cache file comes back as
+    stored, including work items longer than 999 cells (HYDRO_TUNE_CACHE is
+    read when a process first tunes a batch)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    prog = ("import json, sys; sys.path.insert(0, %r)\n"
+            "from paper_2503_04428_gb300 import hydro as H, workloads as wl\n"
+            "w = wl.tubes(16, seed=5, lo=4000, hi=8000)\n"
+            "b = H.Batch(w['lengths'], w['gamma'], precision=32)\n"
+            "b.set_state(w['U']); b.run(1, 0.8)\n"
+            "import torch; sms = torch.cuda.get_device_properties(0).multi_processor_count\n"
+            "s = b.stats(); print(json.dumps([s['tile_x'], s['tile_y'], s['zchunk'], sms]))\n" % root)
+    env = dict(os.environ, HYDRO_TUNE_CACHE=str(cache))
+    run = lambda: subprocess.run([sys.executable, "-c", prog], env=env, capture_output=True, text=True,
+                                 timeout=300, check=True).stdout.strip().splitlines()[-1]
+    import json
+    json.loads(run())
+    key, _, us = cache.read_text().splitlines()[0].split()
+    # 8 warps per CTA, 3584-cell items, one CTA per SM
+    cache.write_text("%s %d %s\n" % (key, (8 * 10000 + 3584) * 100 + 1, us))
+    item, nw, grid, sms = json.loads(run())
+    assert (item, nw, grid) == (3584, 8, sms)
