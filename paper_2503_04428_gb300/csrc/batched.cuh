@@ -426,8 +426,10 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
           if (same) {
             phys_flux<T, 1, 0, 0>(WL, F, gas);
           } else {
-            int its = 0, k2 = 0;
-            const int st = riemann_exact<T, 1, 0, 0>(WL, WR, F, gas, pg, its, k2);
+            // from the guess and sound speeds chosen above (Newton starts
+            // from the same value the general entry would use)
+            int its = 0;
+            const int st = riemann_exact_from<T>(WL, WR, cL, cR, pg, F, gas, its);
             if (owned) n_iters += its;
             if (st != ST_OK && err == 0) err = st;
           }

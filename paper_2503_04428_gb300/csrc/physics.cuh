@@ -644,20 +644,29 @@ static __device__ __noinline__ int newton_star_fp64(float p0, float rL, float uL
   return st;
 }
 
+// Star state from a given initial guess p0 and the sound speeds cL, cR of
+// the two states (vacuum check, FP32 hard-face fallback, Newton).
 template <typename T>
-__device__ __forceinline__ int exact_star(T rL, T uL, T pL, T rR, T uR, T pR, const Gas<T>& gas,
-                                          T guess_in, T& ps, T& us, int& iters, int& kind) {
-  const T cL = dsqrt(gas.g * pL / rL), cR = dsqrt(gas.g * pR / rR);
+__device__ __forceinline__ int exact_star_from(T rL, T uL, T pL, T cL, T rR, T uR, T pR, T cR,
+                                               const Gas<T>& gas, T p0, T& ps, T& us, int& iters) {
   const T vac = gas.two_gm1 * (cL + cR);
   if (vac <= uR - uL) return ST_VACUUM;
-  T p0 = toro_guess(rL, uL, pL, cL, rR, uR, pR, cR, gas, kind);
-  if (guess_in > T(0)) p0 = guess_in;
   if constexpr (sizeof(T) == 4) {
     const T ratio = fmax(pL, pR) / fmin(pL, pR);
     if (ratio > T(1e6) || vac - (uR - uL) < T(0.05) * vac)
       return newton_star_fp64(p0, rL, uL, pL, rR, uR, pR, gas, ps, us, iters);
   }
   return newton_star<T>(p0, rL, uL, pL, cL, rR, uR, pR, cR, gas, newton_tol<T>(), ps, us, iters);
+}
+
+template <typename T>
+__device__ __forceinline__ int exact_star(T rL, T uL, T pL, T rR, T uR, T pR, const Gas<T>& gas,
+                                          T guess_in, T& ps, T& us, int& iters, int& kind) {
+  const T cL = dsqrt(gas.g * pL / rL), cR = dsqrt(gas.g * pR / rR);
+  if (gas.two_gm1 * (cL + cR) <= uR - uL) return ST_VACUUM;
+  T p0 = toro_guess(rL, uL, pL, cL, rR, uR, pR, cR, gas, kind);
+  if (guess_in > T(0)) p0 = guess_in;
+  return exact_star_from<T>(rL, uL, pL, cL, rR, uR, pR, cR, gas, p0, ps, us, iters);
 }
 
 // Godunov flux from the exact solution at x/t = 0; tangential velocities and
@@ -697,6 +706,26 @@ __device__ __forceinline__ int riemann_exact(const T* WL, const T* WR, T* F, con
   W[1 + DIR] = u;
   W[1 + D] = p;
   phys_flux<T, D, NSX, DIR>(W, F, gas);
+  return ST_OK;
+}
+
+// The Godunov flux of two different states (1D, no scalars) from a given
+// initial guess p0 and their sound speeds: the batched path has both in
+// hand from choosing the guess, so neither is computed twice.
+template <typename T>
+__device__ __forceinline__ int riemann_exact_from(const T* WL, const T* WR, T cL, T cR, T p0, T* F,
+                                                  const Gas<T>& gas, int& iters) {
+  T ps, us;
+  const int st = exact_star_from<T>(WL[0], WL[1], WL[2], cL, WR[0], WR[1], WR[2], cR, gas, p0, ps, us, iters);
+  if (st != ST_OK) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v) F[v] = T(0);
+    return st;
+  }
+  T W[3];
+  const bool left = sample0<T>(WL[0], WL[1], WL[2], cL, WR[0], WR[1], WR[2], cR, ps, us, gas, W[0], W[1], W[2]);
+  (void)left;
+  phys_flux<T, 1, 0, 0>(W, F, gas);
   return ST_OK;
 }
 
