@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
             to_prim<T, 1, 0>(u, w, gas);
             if (!finite) err = err ? err : ST_NONFINITE;
             else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
-            u_spd = fabs(w[1]) + dsqrt(gas.g * w[2] / w[0]);
+            u_spd = fabs(w[1]) + dsqrt(qdiv(gas.g * w[2], w[0]));
           }
           smax = fmax(smax, u_spd * fn);
           if (lane < ncell) {
@@ -381,8 +381,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
         int kind = 0;
         T cL = T(0), cR = T(0);
         if (face && !same) {
-          cL = dsqrt(gas.g * WL[2] / WL[0]);
-          cR = dsqrt(gas.g * WR[2] / WR[0]);
+          cL = dsqrt(qdiv(gas.g * WL[2], WL[0]));
+          cR = dsqrt(qdiv(gas.g * WR[2], WR[0]));
           pg = toro_guess<T>(WL[0], WL[1], WL[2], cL, WR[0], WR[1], WR[2], cR, gas, kind);
           if (!mlp_gate<T>(kind, WL[2], WR[2])) kind = -kind;  // negative: network not used
           if (kind == 2 && a.harvest) {
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
           to_prim<T, 1, 0>(u, w, gas);
           if (!finite) err = err ? err : ST_NONFINITE;
           else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
-          smax = fmax(smax, (fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * fn);
+          smax = fmax(smax, (fabs(w[1]) + dsqrt(qdiv(gas.g * w[2], w[0]))) * fn);
 #pragma unroll
           for (int v = 0; v < 3; ++v) Uout[v * a.stride + c] = u[v];
         }

@@ -128,9 +128,11 @@ template <> __device__ __forceinline__ float dsqrt<float>(float x) { return x * 
 template <typename T> __device__ __forceinline__ T dpow(T x, T y);
 template <> __device__ __forceinline__ double dpow<double>(double x, double y) { return exp2(y * log2(x)); }
 template <> __device__ __forceinline__ float dpow<float>(float x, float y) { return exp2f(y * log2f(x)); }
-// Quotient of the state conversions and wave speeds: correctly rounded in
+// Quotient of the state conversions, wave speeds and the exact solver
+// (pressure functions, guess, Newton step, sampling): correctly rounded in
 // FP64, the fast 2-ulp division in FP32 (the FP32 bulk's rounding error is
-// ~1e-7 per operation either way; the IEEE sequence cost ~5 % of the step).
+// ~1e-7 per operation either way, and Newton corrects its own iterates; the
+// IEEE sequence is several times longer).
 template <typename T> __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
 template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
 template <typename T> __device__ __forceinline__ T dexp(T x);
@@ -473,16 +475,16 @@ __device__ __forceinline__ void riemann_hllc(const T* WL, const T* WR, T* F, con
 template <typename T>
 __device__ __forceinline__ void press_fn(T p, T rK, T pK, T cK, const Gas<T>& gas, T& f, T& df) {
   if (p > pK) {
-    const T A = gas.A2 / rK, B = gas.Bq * pK;
-    const T q = dsqrt(A / (B + p));
+    const T A = qdiv(gas.A2, rK), B = gas.Bq * pK;
+    const T q = dsqrt(qdiv(A, B + p));
     f = (p - pK) * q;
-    df = q * (T(1) - T(0.5) * (p - pK) / (B + p));
+    df = q * (T(1) - T(0.5) * qdiv(p - pK, B + p));
   } else {
-    const T pr = p / pK;
+    const T pr = qdiv(p, pK);
     const T pz = dpow(pr, gas.z);  // (p/pK)^((g-1)/(2g))
     f = gas.two_gm1 * cK * (pz - T(1));
     // (p/pK)^(-(g+1)/(2g)) = (p/pK)^z / (p/pK)
-    df = pz / (pr * rK * cK);
+    df = qdiv(pz, pr * rK * cK);
   }
 }
 
@@ -495,20 +497,20 @@ __device__ __forceinline__ T toro_guess(T rL, T uL, T pL, T cL, T rR, T uR, T pR
   T ppv = T(0.5) * (pL + pR) - T(0.125) * (uR - uL) * (rL + rR) * (cL + cR);
   ppv = fmax(ppv, T(0));
   const T pmin = fmin(pL, pR), pmax = fmax(pL, pR);
-  if (pmax / pmin <= T(2) && ppv >= pmin && ppv <= pmax) {
+  if (qdiv(pmax, pmin) <= T(2) && ppv >= pmin && ppv <= pmax) {
     kind = 0;
     return ppv;
   }
   if (ppv < pmin) {
     kind = 1;
     const T num = cL + cR - T(0.5) * gas.gm1 * (uR - uL);
-    const T den = cL / dpow(pL, gas.z) + cR / dpow(pR, gas.z);
-    return dpow(num / den, gas.iz);
+    const T den = qdiv(cL, dpow(pL, gas.z)) + qdiv(cR, dpow(pR, gas.z));
+    return dpow(qdiv(num, den), gas.iz);
   }
   kind = 2;
-  const T gL = dsqrt(gas.A2 / rL / (ppv + gas.Bq * pL));
-  const T gR = dsqrt(gas.A2 / rR / (ppv + gas.Bq * pR));
-  return (gL * pL + gR * pR - (uR - uL)) / (gL + gR);
+  const T gL = dsqrt(qdiv(qdiv(gas.A2, rL), ppv + gas.Bq * pL));
+  const T gR = dsqrt(qdiv(qdiv(gas.A2, rR), ppv + gas.Bq * pR));
+  return qdiv(gL * pL + gR * pR - (uR - uL), gL + gR);
 }
 
 // Newton on f_L(p) + f_R(p) + (u_R - u_L) = 0 from p0: stop when the
@@ -526,10 +528,10 @@ __device__ __forceinline__ int newton_star(T p, T rL, T uL, T pL, T cL, T rR, T 
   while (it < 100) {
     press_fn(p, rL, pL, cL, gas, fL, dfL);
     press_fn(p, rR, pR, cR, gas, fR, dfR);
-    T pn = p - (fL + fR + du) / (dfL + dfR);
+    T pn = p - qdiv(fL + fR + du, dfL + dfR);
     if (pn < T(0)) pn = pfloor;
     ++it;
-    const T ch = T(2) * fabs(pn - p) / (pn + p);
+    const T ch = qdiv(T(2) * fabs(pn - p), pn + p);
     p = pn;
     if (conv) break;
     if (ch < tol) conv = true;
@@ -551,53 +553,53 @@ __device__ __forceinline__ bool sample_xi(T S, T rL, T uL, T pL, T cL, T rR, T u
                                           T us, const Gas<T>& gas, T& rho, T& u, T& p) {
   if (S <= us) {
     if (ps > pL) {
-      const T SL = uL - cL * dsqrt(gas.zp * ps / pL + gas.z);
+      const T SL = uL - cL * dsqrt(gas.zp * qdiv(ps, pL) + gas.z);
       if (S <= SL) { rho = rL; u = uL; p = pL; }
       else {
-        const T q = ps / pL;
-        rho = rL * (q + gas.Bq) / (gas.Bq * q + T(1));
+        const T q = qdiv(ps, pL);
+        rho = qdiv(rL * (q + gas.Bq), gas.Bq * q + T(1));
         u = us; p = ps;
       }
     } else {
       const T SHL = uL - cL;
-      const T cs = cL * dpow(ps / pL, gas.z);
+      const T cs = cL * dpow(qdiv(ps, pL), gas.z);
       const T STL = us - cs;
       if (S <= SHL) { rho = rL; u = uL; p = pL; }
       else if (S >= STL) {
-        rho = rL * dpow(ps / pL, gas.ig);
+        rho = rL * dpow(qdiv(ps, pL), gas.ig);
         u = us; p = ps;
       } else {
         // inside the left fan: c = 2/(g+1) (cL + (g-1)/2 (uL - S)), u = c + S
         const T c = gas.A2 * (cL + T(0.5) * gas.gm1 * (uL - S));
         u = c + S;
-        rho = rL * dpow(c / cL, gas.two_gm1);
-        p = pL * dpow(c / cL, gas.pow_c);
+        rho = rL * dpow(qdiv(c, cL), gas.two_gm1);
+        p = pL * dpow(qdiv(c, cL), gas.pow_c);
       }
     }
     return true;
   }
   if (ps > pR) {
-    const T SR = uR + cR * dsqrt(gas.zp * ps / pR + gas.z);
+    const T SR = uR + cR * dsqrt(gas.zp * qdiv(ps, pR) + gas.z);
     if (S >= SR) { rho = rR; u = uR; p = pR; }
     else {
-      const T q = ps / pR;
-      rho = rR * (q + gas.Bq) / (gas.Bq * q + T(1));
+      const T q = qdiv(ps, pR);
+      rho = qdiv(rR * (q + gas.Bq), gas.Bq * q + T(1));
       u = us; p = ps;
     }
   } else {
     const T SHR = uR + cR;
-    const T cs = cR * dpow(ps / pR, gas.z);
+    const T cs = cR * dpow(qdiv(ps, pR), gas.z);
     const T STR = us + cs;
     if (S >= SHR) { rho = rR; u = uR; p = pR; }
     else if (S <= STR) {
-      rho = rR * dpow(ps / pR, gas.ig);
+      rho = rR * dpow(qdiv(ps, pR), gas.ig);
       u = us; p = ps;
     } else {
       // inside the right fan: c = 2/(g+1) (cR - (g-1)/2 (uR - S)), u = S - c
       const T c = gas.A2 * (cR - T(0.5) * gas.gm1 * (uR - S));
       u = S - c;
-      rho = rR * dpow(c / cR, gas.two_gm1);
-      p = pR * dpow(c / cR, gas.pow_c);
+      rho = rR * dpow(qdiv(c, cR), gas.two_gm1);
+      p = pR * dpow(qdiv(c, cR), gas.pow_c);
     }
   }
   return false;
@@ -652,7 +654,7 @@ __device__ __forceinline__ int exact_star_from(T rL, T uL, T pL, T cL, T rR, T u
   const T vac = gas.two_gm1 * (cL + cR);
   if (vac <= uR - uL) return ST_VACUUM;
   if constexpr (sizeof(T) == 4) {
-    const T ratio = fmax(pL, pR) / fmin(pL, pR);
+    const T ratio = qdiv(fmax(pL, pR), fmin(pL, pR));
     if (ratio > T(1e6) || vac - (uR - uL) < T(0.05) * vac)
       return newton_star_fp64(p0, rL, uL, pL, rR, uR, pR, gas, ps, us, iters);
   }
@@ -662,7 +664,7 @@ __device__ __forceinline__ int exact_star_from(T rL, T uL, T pL, T cL, T rR, T u
 template <typename T>
 __device__ __forceinline__ int exact_star(T rL, T uL, T pL, T rR, T uR, T pR, const Gas<T>& gas,
                                           T guess_in, T& ps, T& us, int& iters, int& kind) {
-  const T cL = dsqrt(gas.g * pL / rL), cR = dsqrt(gas.g * pR / rR);
+  const T cL = dsqrt(qdiv(gas.g * pL, rL)), cR = dsqrt(qdiv(gas.g * pR, rR));
   if (gas.two_gm1 * (cL + cR) <= uR - uL) return ST_VACUUM;
   T p0 = toro_guess(rL, uL, pL, cL, rR, uR, pR, cR, gas, kind);
   if (guess_in > T(0)) p0 = guess_in;
@@ -696,7 +698,7 @@ __device__ __forceinline__ int riemann_exact(const T* WL, const T* WR, T* F, con
     for (int v = 0; v < NV; ++v) F[v] = T(0);
     return st;
   }
-  const T cL = dsqrt(gas.g * pL / rL), cR = dsqrt(gas.g * pR / rR);
+  const T cL = dsqrt(qdiv(gas.g * pL, rL)), cR = dsqrt(qdiv(gas.g * pR, rR));
   T rho, u, p;
   const bool left = sample0<T>(rL, uL, pL, cL, rR, uR, pR, cR, ps, us, gas, rho, u, p);
   T W[NV];
