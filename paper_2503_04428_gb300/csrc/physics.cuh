@@ -38,6 +38,28 @@ struct Gas {
   T pow_c;    // 2 gamma/(gamma - 1)
 };
 
+// Square roots.  The FP32 bulk takes x rsqrt(x) (about 3 ulp; x > 0 on every
+// path that uses it): the correctly rounded sqrtf sequence cost 2-3 % of the
+// FP32 step's instructions.
+template <typename T> __device__ __forceinline__ T dsqrt(T x);
+template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float dsqrt<float>(float x) { return x * rsqrtf(x); }
+// Powers (x > 0) as exp2(y log2 x): a few ulp (FP64: relative 1e-15 at the
+// exponents of the exact solver), against the accurate pow/powf, whose
+// extended-precision logarithm is several times longer and dominated the
+// instruction stream of the exact solver.
+template <typename T> __device__ __forceinline__ T dpow(T x, T y);
+template <> __device__ __forceinline__ double dpow<double>(double x, double y) { return exp2(y * log2(x)); }
+template <> __device__ __forceinline__ float dpow<float>(float x, float y) { return exp2f(y * log2f(x)); }
+
+// Quotient of the state conversions, wave speeds and the exact solver
+// (pressure functions, guess, Newton step, sampling): correctly rounded in
+// FP64, the fast 2-ulp division in FP32 (the FP32 bulk's rounding error is
+// ~1e-7 per operation either way, and Newton corrects its own iterates; the
+// IEEE sequence is several times longer).
+template <typename T> __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
+
 template <typename T> __device__ __forceinline__ T temp_tol();
 template <> __device__ __forceinline__ double temp_tol<double>() { return 1e-13; }
 template <> __device__ __forceinline__ float temp_tol<float>() { return 1e-6f; }
@@ -63,26 +85,25 @@ struct GasRad : Gas<T> {
   // relative step is below temp_tol and takes one more step.  y <= 0 gives
   // y/c1 <= 0, which the positivity checks reject.
   __device__ __forceinline__ T temperature(T c1, T c4, T y, T t0 = T(0)) const {
-    T t = y / c1;
+    T t = qdiv(y, c1);
     if (!(y > T(0))) return t;
     if (t0 > T(0)) t = t0;
-    else if (c4 > T(0)) t = fmin(t, dsqrt_(dsqrt_(y / c4)));
+    else if (c4 > T(0)) t = fmin(t, dsqrt(dsqrt(qdiv(y, c4))));
     bool conv = false;
     for (int it = 0; it < 60; ++it) {
       const T t3 = t * t * t;
-      const T tn = t - (c1 * t + c4 * t3 * t - y) / (c1 + T(4) * c4 * t3);
-      const T ch = fabs(tn - t) / tn;
+      const T tn = t - qdiv(c1 * t + c4 * t3 * t - y, c1 + T(4) * c4 * t3);
+      const T ch = qdiv(fabs(tn - t), tn);
       t = tn;
       if (conv) break;
       if (ch < temp_tol<T>()) conv = true;
     }
     return t;
   }
-  static __device__ __forceinline__ T dsqrt_(T x) { return sqrt(x); }
   // Eq. 7 from the gas and radiation pressures
   __device__ __forceinline__ T sound2(T rho, T pg, T pr) const {
-    const T al = pr / pg;
-    return (c_g + T(20) * al + T(16) * al * al) / (c_1 + T(12) * al) * pg / rho;
+    const T al = qdiv(pr, pg);
+    return qdiv(c_g + T(20) * al + T(16) * al * al, c_1 + T(12) * al) * qdiv(pg, rho);
   }
   // P and c^2 from (rho, e)
   __device__ __forceinline__ void from_e(T rho, T e, T& p, T& c2) const {
@@ -115,26 +136,6 @@ struct GasRad : Gas<T> {
   }
 };
 
-// Square roots.  The FP32 bulk takes x rsqrt(x) (about 3 ulp; x > 0 on every
-// path that uses it): the correctly rounded sqrtf sequence cost 2-3 % of the
-// FP32 step's instructions.
-template <typename T> __device__ __forceinline__ T dsqrt(T x);
-template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
-template <> __device__ __forceinline__ float dsqrt<float>(float x) { return x * rsqrtf(x); }
-// Powers (x > 0) as exp2(y log2 x): a few ulp (FP64: relative 1e-15 at the
-// exponents of the exact solver), against the accurate pow/powf, whose
-// extended-precision logarithm is several times longer and dominated the
-// instruction stream of the exact solver.
-template <typename T> __device__ __forceinline__ T dpow(T x, T y);
-template <> __device__ __forceinline__ double dpow<double>(double x, double y) { return exp2(y * log2(x)); }
-template <> __device__ __forceinline__ float dpow<float>(float x, float y) { return exp2f(y * log2f(x)); }
-// Quotient of the state conversions, wave speeds and the exact solver
-// (pressure functions, guess, Newton step, sampling): correctly rounded in
-// FP64, the fast 2-ulp division in FP32 (the FP32 bulk's rounding error is
-// ~1e-7 per operation either way, and Newton corrects its own iterates; the
-// IEEE sequence is several times longer).
-template <typename T> __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
-template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
 template <typename T> __device__ __forceinline__ T dexp(T x);
 template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
 template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
@@ -220,7 +221,7 @@ __device__ __forceinline__ T sound2_of(const G& gas, T rho, T p) {
     gas.from_p(rho, p, e, c2);
     return c2;
   } else {
-    return gas.g * p / rho;
+    return qdiv(gas.g * p, rho);
   }
 }
 
@@ -269,8 +270,8 @@ __device__ __forceinline__ T limit(int kind, T dm, T dp) {
   const T pr = dm * dp;
   if (kind == LIM_FIRST || !(pr > T(0))) return T(0);
   if (kind == LIM_MINMOD) return dm > T(0) ? fmin(dm, dp) : fmax(dm, dp);
-  if (kind == LIM_VANLEER) return T(2) * pr / (dm + dp);
-  return pr * (dm + dp) / (dm * dm + dp * dp);
+  if (kind == LIM_VANLEER) return qdiv(T(2) * pr, dm + dp);
+  return qdiv(pr * (dm + dp), dm * dm + dp * dp);
 }
 
 // ---------------------------------------------------------------------------
@@ -362,7 +363,7 @@ __device__ __forceinline__ void riemann_hllc_rad(const T* WL, const T* WR, T* F,
     return;
   }
   const T aL = rL * (SL - uL), aR = rR * (SR - uR);
-  const T Ss = (pR - pL + uL * aL - uR * aR) / (aL - aR);
+  const T Ss = qdiv(pR - pL + uL * aL - uR * aR, aL - aR);
   const bool left = Ss >= T(0);
   T W[NV];
 #pragma unroll
@@ -371,13 +372,13 @@ __device__ __forceinline__ void riemann_hllc_rad(const T* WL, const T* WR, T* F,
   const T a = left ? aL : aR;
   const T rho = W[0], un = W[1 + DIR], p = W[1 + D];
   flux_cons_e<T, D, NSX, DIR>(W, left ? eL : eR, Fk, Uk);
-  const T fac = a / (S - Ss);
+  const T fac = qdiv(a, S - Ss);
   T Us[NV];
   Us[0] = fac;
 #pragma unroll
   for (int d = 0; d < D; ++d) Us[1 + d] = fac * W[1 + d];
   Us[1 + DIR] = fac * Ss;
-  Us[1 + D] = fac * (Uk[1 + D] / rho + (Ss - un) * (Ss + p / a));
+  Us[1 + D] = fac * (qdiv(Uk[1 + D], rho) + (Ss - un) * (Ss + qdiv(p, a)));
 #pragma unroll
   for (int s = 0; s < NSX; ++s) Us[2 + D + s] = fac * W[2 + D + s];
 #pragma unroll
