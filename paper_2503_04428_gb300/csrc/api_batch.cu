@@ -20,6 +20,8 @@ namespace hydro {
 // segments) and persistent CTAs per SM (up to the occupancy limit).
 static const int BATCH_NW[] = {4, 8};
 static const int BATCH_ITEM[] = {28, 56, 112, 224, 448, 896, 1792, 3584};
+// Steps per captured graph on runs of many steps.
+static const int BGRAPH_STEPS = 8;
 
 struct BatchState {
   int ntubes = 0;
@@ -61,6 +63,7 @@ struct BatchState {
   double hg_cfl = -1.0;
   // MLP
   float* w = nullptr;
+  MlpSmemW* w_packed = nullptr;  // w in the batched kernel's shared-memory layout
   float* m = nullptr;
   float* v = nullptr;
   bool w_set = false;
@@ -70,8 +73,9 @@ struct BatchState {
   unsigned long long* harvest_n = nullptr;
   long long harvest_cap = 0;
   unsigned long long harvest_thresh = 0, harvest_seed = 0;
-  // graph of one step
+  // graphs of one step and of BGRAPH_STEPS steps
   cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph_k = nullptr;
   double graph_cfl = -1.0;
   bool tuned = false;
   double tuned_us = 0.0;
@@ -220,7 +224,7 @@ static BatchArgs<T> batch_args(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const 
   a.cfl = cfl;
   a.gas = make_gas<T>(h->gamma);
   a.limiter = bs->limiter;
-  a.mlp_w = bs->w;
+  a.mlp_w = bs->w_packed;
   a.mlp_on = bs->mlp_on && bs->w_set;
   a.harvest = bs->harvest;
   a.harvest_n = bs->harvest_n;
@@ -261,6 +265,10 @@ static void drop_graph(BatchState* bs) {
   if (bs->graph) {
     cudaGraphExecDestroy(bs->graph);
     bs->graph = nullptr;
+  }
+  if (bs->graph_k) {
+    cudaGraphExecDestroy(bs->graph_k);
+    bs->graph_k = nullptr;
   }
   if (bs->host_graph) {
     cudaGraphExecDestroy(bs->host_graph);
@@ -407,10 +415,19 @@ static void init_weights(std::vector<float>& w, unsigned long long seed) {
 static int ensure_mlp(hydro_ctx* h) {
   BatchState* bs = h->bs;
   if (!bs->w) {
+    HCK(cudaMalloc(&bs->w_packed, sizeof(MlpSmemW)));
     HCK(cudaMalloc(&bs->w, sizeof(float) * MLP_NPARAM));
     HCK(cudaMalloc(&bs->m, sizeof(float) * MLP_NPARAM));
     HCK(cudaMalloc(&bs->v, sizeof(float) * MLP_NPARAM));
   }
+  return HYDRO_OK;
+}
+
+// The kernel's copy of the weights, after every change of bs->w.
+static int pack_mlp(hydro_ctx* h) {
+  mlp_pack_kernel<<<1, 256, 0, h->stream>>>(h->bs->w, h->bs->w_packed);
+  HCK(cudaGetLastError());
+  HCK(cudaStreamSynchronize(h->stream));
   return HYDRO_OK;
 }
 
@@ -516,6 +533,7 @@ void hydro_batch_free_impl(hydro_ctx* h) {
   cudaFree(bs->item_tube);
   cudaFree(bs->item_start);
   cudaFree(bs->w);
+  cudaFree(bs->w_packed);
   cudaFree(bs->m);
   cudaFree(bs->v);
   cudaFree(bs->harvest);
@@ -789,18 +807,27 @@ int hydro_batch_run(hydro_t h, int nsteps, double cfl) {
   if ((st = autotune_batch(h, cfl))) return st;
   if (!bs->graph || bs->graph_cfl != cfl) {
     drop_graph(bs);
-    cudaGraph_t g;
-    HCK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
-    st = launch_batch(h, cfl, bs->bctrl, bs->smax_cur, bs->smax_next, bs->t_tube);
-    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
-    if (st) return st;
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&bs->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    // one step, and BGRAPH_STEPS steps back to back (fewer graph launches
+    // per step on long runs)
+    for (int k : {1, BGRAPH_STEPS}) {
+      cudaGraph_t g;
+      HCK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+      for (int r = 0; r < k && st == 0; ++r) st = launch_batch(h, cfl, bs->bctrl, bs->smax_cur, bs->smax_next, bs->t_tube);
+      cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+      if (st) {
+        if (e == cudaSuccess) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(k == 1 ? &bs->graph : &bs->graph_k, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    }
     bs->graph_cfl = cfl;
   }
-  for (int s = 0; s < nsteps; ++s) HCK(cudaGraphLaunch(bs->graph, h->stream));
+  int s = 0;
+  for (; s + BGRAPH_STEPS <= nsteps; s += BGRAPH_STEPS) HCK(cudaGraphLaunch(bs->graph_k, h->stream));
+  for (; s < nsteps; ++s) HCK(cudaGraphLaunch(bs->graph, h->stream));
   if ((st = read_bctrl(h))) return st;
   const int code = bs->bctrl_host->c.status;
   if (code == 0) return HYDRO_OK;
@@ -858,6 +885,7 @@ int hydro_mlp_set(hydro_t h, const float* weights, int enable) {
   if (st) return st;
   if (weights) {
     HCK(cudaMemcpy(bs->w, weights, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice));
+    if ((st = pack_mlp(h))) return st;
     bs->w_set = true;
   }
   if (enable && !bs->w_set) return berr("hydro_mlp_set: no weights to enable");
@@ -885,6 +913,7 @@ int hydro_mlp_train(hydro_t h, const double* faces6, const double* log_pstar, lo
     std::vector<float> w0;
     init_weights(w0, seed);
     HCK(cudaMemcpy(bs->w, w0.data(), sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice));
+    if ((st = pack_mlp(h))) return st;
     bs->w_set = true;
   }
   HCK(cudaMemset(bs->m, 0, sizeof(float) * MLP_NPARAM));
@@ -974,6 +1003,7 @@ int hydro_mlp_train(hydro_t h, const double* faces6, const double* log_pstar, lo
   cleanup();
   if (st) return st;
   if (e != cudaSuccess) return cuda_fail(e, "hydro_mlp_train");
+  if ((st = pack_mlp(h))) return st;
   if (loss_out) *loss_out = loss;
   drop_graph(bs);
   return HYDRO_OK;

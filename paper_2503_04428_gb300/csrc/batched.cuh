@@ -90,6 +90,8 @@ struct BatchCtrl {
   unsigned int pad2;
 };
 
+struct MlpSmemW;
+
 template <typename T>
 struct BatchArgs {
   const T* A;
@@ -109,7 +111,7 @@ struct BatchArgs {
   double cfl;
   Gas<T> gas;
   int limiter;
-  const float* mlp_w;          // 4673 weights (device) or null
+  const MlpSmemW* mlp_w;        // packed weights (device) or null
   int mlp_on;
   double* harvest;             // capacity x 6 doubles or null
   unsigned long long* harvest_n;
@@ -126,16 +128,38 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
-// Network weights staged per CTA; W2 is stored transposed (W2T[i][o]) so that
-// the 32 lanes of a warp read consecutive words.
-struct MlpSmemW {
+// Network weights as the kernel holds them in shared memory; W2 is stored
+// transposed (W2T[i][o]) so that the 32 lanes of a warp read consecutive
+// words.  The host keeps a device copy in this layout (mlp_pack_kernel, run
+// when the weights change), which every CTA loads with one bulk copy.
+struct __align__(16) MlpSmemW {
   float w1[MLP_H * MLP_IN];
   float b1[MLP_H];
   float w2t[MLP_H * MLP_H];
   float b2[MLP_H];
   float w3[MLP_H];
   float b3;
+  float pad[3];  // the size, a multiple of 16 bytes
 };
+static_assert(sizeof(MlpSmemW) % 16 == 0, "bulk-copied weights");
+
+// The 4673 weights (flat layout of mlp.cuh) into the kernel's layout.
+__global__ void mlp_pack_kernel(const float* __restrict__ w, MlpSmemW* __restrict__ out) {
+  for (int p = threadIdx.x; p < MLP_H * MLP_IN; p += blockDim.x) out->w1[p] = w[MW1 + p];
+  for (int p = threadIdx.x; p < MLP_H * MLP_H; p += blockDim.x) {
+    const int o = p / MLP_H, i = p % MLP_H;
+    out->w2t[i * MLP_H + o] = w[MW2 + p];
+  }
+  for (int p = threadIdx.x; p < MLP_H; p += blockDim.x) {
+    out->b1[p] = w[MB1 + p];
+    out->b2[p] = w[MB2 + p];
+    out->w3[p] = w[MW3 + p];
+  }
+  if (threadIdx.x == 0) {
+    out->b3 = w[MB3];
+    out->pad[0] = out->pad[1] = out->pad[2] = 0.f;
+  }
+}
 
 // The 6-64-64-1 network evaluated by a whole warp for one input x (the same
 // on every lane): lane l owns hidden units l and l+32.  Out of line: few
@@ -175,6 +199,7 @@ template <typename T, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     batched_kernel(const BatchArgs<T> a) {
   __shared__ MlpSmemW sw;
+  __shared__ unsigned long long wbar;  // completes when sw has landed
   extern __shared__ __align__(16) unsigned char ring_raw[];
   const volatile Ctrl* vc = &a.ctrl->c;
   if (vc->status != 0) return;
@@ -190,20 +215,18 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the inits, visible to the copies
   __syncwarp();
   const Gas<T>& gas = a.gas;
+  // the network's weights arrive by one bulk copy; only warps that meet a
+  // face using the network wait for them
   if (a.mlp_on) {
-    for (int p = threadIdx.x; p < MLP_H * MLP_IN; p += NW * 32) sw.w1[p] = a.mlp_w[MW1 + p];
-    for (int p = threadIdx.x; p < MLP_H * MLP_H; p += NW * 32) {
-      const int o = p / MLP_H, i = p % MLP_H;
-      sw.w2t[i * MLP_H + o] = a.mlp_w[MW2 + p];
+    if (threadIdx.x == 0) {
+      mbar_init(&wbar);
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_expect_tx(&wbar, (unsigned)sizeof(MlpSmemW));
+      bulk_copy_g2s(&sw, a.mlp_w, (unsigned)sizeof(MlpSmemW), &wbar);
     }
-    for (int p = threadIdx.x; p < MLP_H; p += NW * 32) {
-      sw.b1[p] = a.mlp_w[MB1 + p];
-      sw.b2[p] = a.mlp_w[MB2 + p];
-      sw.w3[p] = a.mlp_w[MW3 + p];
-    }
-    if (threadIdx.x == 0) sw.b3 = a.mlp_w[MB3];
-    __syncthreads();
+    __syncthreads();  // the barrier's init, visible to every warp
   }
+  bool w_ready = false;  // this warp has seen the weights land
   unsigned long long n_iters = 0, n_mlp = 0, n_fb = 0;
   int err = 0;
   // the last uniform window's state and its |u| + c (warp-uniform values)
@@ -404,6 +427,13 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
         // learned guess on two-shock faces, evaluated by the whole warp
         if (a.mlp_on) {
           unsigned todo = __ballot_sync(0xffffffffu, face && !same && kind == 2);
+          if (todo && !w_ready) {
+            w_ready = __all_sync(0xffffffffu, mbar_wait(&wbar, 0u));
+            if (!w_ready) {
+              err = ST_TIMEOUT;  // (these faces keep Toro's guess)
+              todo = 0u;
+            }
+          }
           while (todo) {
             const int g = __ffs(todo) - 1;
             todo &= todo - 1;
@@ -486,6 +516,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     if (n_fb) atomicAdd(&a.ctrl->c.fallbacks, n_fb);
     if (err && atomicCAS(&a.ctrl->c.status, 0, err) == 0) a.ctrl->c.err_step = step;
   }
+  // the weights' copy has landed before the CTA ends (bounded)
+  if (a.mlp_on && threadIdx.x == 0) mbar_wait(&wbar, 0u);
   __syncthreads();
   __shared__ int last;
   if (threadIdx.x == 0) {
@@ -498,11 +530,35 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
   volatile BatchCtrl* vb = a.ctrl;
   const bool ok = vb->c.status == 0;
   if (ok) {
+    // This CTA runs alone now (every other CTA has taken its ticket after its
+    // last atomic), so plain loads and stores do; each thread issues the
+    // loads of CU tubes before it uses them, so that the commit costs a few
+    // memory round trips rather than a few per tube.  The speeds are read
+    // past L1 (they were written by atomics at L2).
+    constexpr int CU = 8;
     double* smc = const_cast<double*>(a.smax_cur);
-    for (int t = a.tube0 + threadIdx.x; t < a.tube0 + a.ntubes; t += NW * 32) {
-      a.t_tube[t] += a.cfl / smc[t];
-      const unsigned long long nbits = atomicExch(&a.smax_next[t], 0ull);
-      smc[t] = __longlong_as_double((long long)nbits);
+    const int t_end = a.tube0 + a.ntubes;
+    for (int t0 = a.tube0 + threadIdx.x; t0 < t_end; t0 += CU * NW * 32) {
+      double sc[CU], tt[CU];
+      unsigned long long nb[CU];
+#pragma unroll
+      for (int k = 0; k < CU; ++k) {
+        const int t = t0 + k * NW * 32;
+        if (t < t_end) {
+          sc[k] = smc[t];
+          tt[k] = a.t_tube[t];
+          nb[k] = __ldcg(&a.smax_next[t]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < CU; ++k) {
+        const int t = t0 + k * NW * 32;
+        if (t < t_end) {
+          a.t_tube[t] = tt[k] + a.cfl / sc[k];
+          a.smax_next[t] = 0ull;
+          smc[t] = __longlong_as_double((long long)nb[k]);
+        }
+      }
     }
   }
   __syncthreads();
