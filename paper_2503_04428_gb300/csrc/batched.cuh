@@ -447,7 +447,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
             mlp_features((float)gas.g, q[0], q[1], q[2], q[3], q[4], q[5], x, pref);
             const float y = mlp_warp(sw, x, lane);
             if (lane == g) {
-              pg = (T)((double)pref * exp((double)y));
+              // (the guess only seeds Newton: FP32 exp in the FP32 form)
+              if constexpr (sizeof(T) == 4) pg = pref * expf(y);
+              else pg = (T)((double)pref * exp((double)y));
               if (owned) ++n_mlp;
             }
           }
