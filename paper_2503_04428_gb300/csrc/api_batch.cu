@@ -575,15 +575,12 @@ static int enqueue_host_run(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
                           cudaMemcpyHostToDevice, bs->s_h2d));
     HCK(cudaEventRecord(bs->ev_in[p], bs->s_h2d));
     HCK(cudaStreamWaitEvent(h->stream, bs->ev_in[p], 0));
-    // the part's per-tube speeds and validity (as hydro_batch_set_state)
-    HCK(cudaMemsetAsync(bs->smax_next + t0, 0, sizeof(unsigned long long) * (t1 - t0), h->stream));
-    HCK(cudaMemsetAsync(bs->t_tube + t0, 0, sizeof(double) * (t1 - t0), h->stream));
-    batch_speed_kernel<T><<<t1 - t0, 256, 0, h->stream>>>(buf_in, bs->stride, bs->off_d, t0, t1 - t0, gas,
-                                                         bs->smax_next, &bs->part_ctrl[p].c.status);
+    // the part's per-tube speeds, times and validity (as hydro_batch_set_state),
+    // in one kernel: no copy-engine work between the part's input and its step
+    batch_init_kernel<T><<<t1 - t0, 256, 0, h->stream>>>(buf_in, bs->stride, bs->off_d, t0, t1 - t0, gas,
+                                                        bs->smax_cur, bs->smax_next, bs->t_tube,
+                                                        &bs->part_ctrl[p].c.status);
     HCK(cudaGetLastError());
-    HCK(cudaMemcpyAsync(bs->smax_cur + t0, bs->smax_next + t0, sizeof(double) * (t1 - t0),
-                        cudaMemcpyDeviceToDevice, h->stream));
-    HCK(cudaMemsetAsync(bs->smax_next + t0, 0, sizeof(unsigned long long) * (t1 - t0), h->stream));
     BatchArgs<T> a = batch_args<T>(h, cfl, &bs->part_ctrl[p], bs->smax_cur, bs->smax_next, bs->t_tube);
     const int i0 = bs->item_first[t0], i1 = bs->item_first[t1];
     a.item_tube = bs->part_item_tube + i0;

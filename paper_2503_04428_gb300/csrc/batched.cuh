@@ -610,6 +610,61 @@ __global__ void batch_speed_kernel(const T* U, long long stride, const long long
   }
 }
 
+// A host-resident run's new state, one CTA per tube: smax_cur[b] = max_i
+// (|u|+c)/h of tube b (FP64), smax_next[b] = 0 (the step's atomic maximum
+// starts there) and t_tube[b] = 0, all in one pass over the tube -- no copy
+// or memset between the input copies and the step.  An invalid cell sets
+// *status.  (blockDim.x: a multiple of 32, at most 1024.)
+template <typename T>
+__global__ void batch_init_kernel(const T* U, long long stride, const long long* off, int tube0, int ntubes,
+                                  Gas<T> gas, double* smax_cur, unsigned long long* smax_next, double* t_tube,
+                                  int* status) {
+  if ((int)blockIdx.x >= ntubes) return;
+  const int b = tube0 + blockIdx.x;
+  const long long base = off[b];
+  const int nb = (int)(off[b + 1] - base);
+  double smax = 0.0;
+  int err = 0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    T u[3], w[3];
+    bool finite = true;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      u[v] = U[v * stride + base + i];
+      finite = finite && isfinite(u[v]);
+    }
+    if (!finite) { err = ST_NONFINITE; continue; }
+    to_prim<T, 1, 0>(u, w, gas);
+    if (!(w[0] > T(0)) || !(w[2] > T(0))) { err = err ? err : ST_NEG; continue; }
+    smax = fmax(smax, (double)((fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * (T)nb));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    const int e2 = __shfl_xor_sync(0xffffffffu, err, o);
+    err = err ? err : e2;
+  }
+  __shared__ double red_s[32];
+  __shared__ int red_e[32];
+  if ((threadIdx.x & 31) == 0) {
+    red_s[threadIdx.x >> 5] = smax;
+    red_e[threadIdx.x >> 5] = err;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    int e = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      m = fmax(m, red_s[k]);
+      e = e ? e : red_e[k];
+    }
+    smax_cur[b] = m;
+    smax_next[b] = 0ull;
+    t_tube[b] = 0.0;
+    if (e) atomicCAS(status, 0, e);
+  }
+}
+
 // Exact star states of independent faces (one thread per face).
 template <typename T>
 __global__ void exact_list_kernel(const double* WL, const double* WR, long long n, Gas<T> gas,
