@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     dtd = __shfl_sync(0xffffffffu, dtd, 0);
     const T dtdx = (T)dtd * fn;
     T smax = T(0);
+    T* const out = Uout + base;  // the tube's cell 0 in the output
 
     // The conserved windows (cells c0-2+lane, clamped to the tube:
     // transmissive ends) of segments BSPAN*k .. BSPAN*k+BSPAN-1 arrive in
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
       int len;
       span_of(k, g0, len);
       const T* slot = ring + sl * (3 * BVSTR);
+      const int ib = (int)(base - g0);  // slot index of the tube's cell 0
 #pragma unroll 1
       for (int j = 0; j < BSPAN; ++j) {
         const int sg = k * BSPAN + j;
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
         const int c0 = s_beg + sg * BSEG;
         T Ua[3];
         {
-          const int idx = (int)(base + min(max(c0 - 2 + lane, 0), nb - 1) - g0);
+          const int idx = ib + min(max(c0 - 2 + lane, 0), nb - 1);
 #pragma unroll
           for (int v = 0; v < 3; ++v) Ua[v] = slot[v * BVSTR + idx];
         }
@@ -316,18 +318,20 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
         // A window holding one state everywhere (clamped tube ends included)
         // has zero slopes, a +0 Hancock increment, identical face states and
         // equal fluxes, so the full path below returns U + 0 for every cell:
-        // produce exactly that without the face work.
-        // (the shuffles run on every lane before the comparison: a shuffle
-        // inside a short-circuit condition would leave lanes out of it)
-        const T r0 = __shfl_sync(0xffffffffu, Ua[0], 0);
-        const T r1 = __shfl_sync(0xffffffffu, Ua[1], 0);
-        const T r2 = __shfl_sync(0xffffffffu, Ua[2], 0);
-        const bool uniform = __all_sync(0xffffffffu, (Ua[0] == r0) & (Ua[1] == r1) & (Ua[2] == r2));
-        if (uniform) {
-          // One state (r0, r1, r2) on every lane: its validity and |u| + c are
-          // those of the last uniform window whenever the state repeats, as it
-          // does along the undisturbed stretches of a tube.
-          if (!(have_u && r0 == ur[0] && r1 == ur[1] && r2 == ur[2])) {
+        // produce exactly that without the face work.  First test against
+        // the last uniform window's state (the common case along the
+        // undisturbed stretch of a tube: no shuffles), then against lane 0.
+        // (every vote and shuffle runs on every lane: a collective inside a
+        // short-circuit condition would leave lanes out of it)
+        bool uniform = __all_sync(0xffffffffu, have_u & (Ua[0] == ur[0]) & (Ua[1] == ur[1]) & (Ua[2] == ur[2]));
+        if (!uniform) {
+          const T r0 = __shfl_sync(0xffffffffu, Ua[0], 0);
+          const T r1 = __shfl_sync(0xffffffffu, Ua[1], 0);
+          const T r2 = __shfl_sync(0xffffffffu, Ua[2], 0);
+          uniform = __all_sync(0xffffffffu, (Ua[0] == r0) & (Ua[1] == r1) & (Ua[2] == r2));
+          if (uniform) {
+            // a new uniform state: its validity and |u| + c, kept for the
+            // windows that repeat it
             have_u = true;
             ur[0] = r0;
             ur[1] = r1;
@@ -339,12 +343,16 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
             else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
             u_spd = fabs(w[1]) + dsqrt(qdiv(gas.g * w[2], w[0]));
           }
+        }
+        if (uniform) {
+          // (equal values compare equal but for the sign of zero, which
+          // U + 0 erases: the cached state's U + 0 is the window's)
           smax = fmax(smax, u_spd * fn);
           if (lane < ncell) {
-            const long long c = base + c0 + lane;
-            Uout[c] = r0 + T(0);
-            Uout[a.stride + c] = r1 + T(0);
-            Uout[2 * a.stride + c] = r2 + T(0);
+            T* o = out + c0 + lane;
+            o[0] = ur[0] + T(0);
+            o[a.stride] = ur[1] + T(0);
+            o[2 * a.stride] = ur[2] + T(0);
           }
           continue;
         }
