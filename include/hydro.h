@@ -169,9 +169,11 @@ int hydro_stats(hydro_t h, hydro_stats_t* out);
 int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int riemann,
                        int limiter, int precision, void* stream, hydro_t* out);
 
-/* nsteps steps of every tube in one persistent launch per step (replayed as a
- * CUDA graph); the first call runs the launch-shape autotuner on a scratch
- * copy of the state. */
+/* nsteps steps of every tube in one persistent launch per step (replayed from
+ * captured CUDA graphs of 8 steps and of 1 step); the first call runs the
+ * launch-shape autotuner on a scratch copy of the state.  A failing step
+ * (invalid state, Newton or a bounded device wait, HYDRO_ERR_TIMEOUT) leaves
+ * the last good state and stops the remaining steps. */
 int hydro_batch_run(hydro_t h, int nsteps, double cfl);
 
 /* Advance a batch whose state lives in host memory: U_in (3 x total cells,

@@ -23,7 +23,10 @@
 // 1D bulk copies (cp.async.bulk, completion counted on the slot's mbarrier),
 // several spans ahead of the one in use, so that enough bytes are in flight
 // to cover HBM latency in few, large transfers.  Every variable's slab of
-// the state starts on a 16-byte boundary for this (padded stride).
+// the state starts on a 16-byte boundary for this (padded stride).  The
+// network's weights arrive the same way, one bulk copy per CTA from a device
+// copy kept in the kernel's shared-memory layout; only warps that meet a face
+// using the network wait for them.
 // The last CTA to finish commits the step (per-tube speeds, times, buffer).
 #pragma once
 #include "common.cuh"
