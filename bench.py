@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import time
@@ -48,9 +49,14 @@ def load_peaks():
 
 
 def kernel_hash(sources=KERNEL_SOURCES):
+    """Hash of the kernels' code (comments and whitespace removed), so that a
+    profiled figure stays attached to the code it was measured on."""
     h = hashlib.sha256()
     for f in sources:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        src = open(os.path.join(ROOT, f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
