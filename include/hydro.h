@@ -253,6 +253,14 @@ int hydro_exact_solve(const double* WL, const double* WR, long n, double gamma, 
                       const float* weights, int precision, double* pstar, double* ustar,
                       int* iters);
 
+/* Failure-detection check of the device waits: one thread waits, with the
+ * bounded wait the batched kernel uses on its bulk copies, on an mbarrier
+ * that nothing completes.  Returns HYDRO_ERR_TIMEOUT (the expected outcome:
+ * the wait gave up and reported it, the context stays usable) and the time
+ * the wait took in *seconds_out (may be null); HYDRO_OK would mean a wait
+ * that cannot complete did. */
+int hydro_wait_probe(double* seconds_out);
+
 /* Measured arithmetic peak of the current GPU: dense fused multiply-adds in
  * FP64 (precision 64) or FP32 (32), in TFLOP/s (2 flops per FMA), the best
  * of four ~20 ms launches of eight independent FMA chains per thread.  The

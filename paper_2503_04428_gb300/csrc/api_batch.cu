@@ -449,6 +449,18 @@ static int mlp_gradient(cudaStream_t s, const float* W, const float* X, const fl
   return HYDRO_OK;
 }
 
+// A wait that cannot complete: thread 0 arms an mbarrier for 16 bytes that no
+// copy delivers (none is issued) and waits on it with the batched kernel's
+// bounded wait (mbar_wait), which must give up and report a timeout.
+__global__ void wait_probe_kernel(int* status) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar);
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  mbar_expect_tx(&bar, 16u);
+  *status = mbar_wait(&bar, 0u) ? HYDRO_OK : ST_TIMEOUT;
+}
+
 }  // namespace hydro
 
 using namespace hydro;
@@ -723,6 +735,29 @@ static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
 }
 
 extern "C" {
+
+int hydro_wait_probe(double* seconds_out) {
+  int* d_status = nullptr;
+  HCK(cudaMalloc(&d_status, sizeof(int)));
+  cudaEvent_t e0, e1;
+  HCK(cudaEventCreate(&e0));
+  HCK(cudaEventCreate(&e1));
+  HCK(cudaEventRecord(e0, 0));
+  wait_probe_kernel<<<1, 32>>>(d_status);
+  HCK(cudaGetLastError());
+  HCK(cudaEventRecord(e1, 0));
+  HCK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  int status = HYDRO_ERR_CUDA;
+  HCK(cudaMemcpy(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d_status);
+  if (seconds_out) *seconds_out = 1e-3 * ms;
+  if (status == ST_TIMEOUT) set_error("hydro_wait_probe: the bounded wait expired (the expected outcome)");
+  return status;
+}
 
 int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int riemann, int limiter,
                        int precision, void* stream, hydro_t* out) {

@@ -84,6 +84,7 @@ _SIGS = {
     "hydro_mlp_loss_grad_device": [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP],
     "hydro_destroy": [_VP],
     "hydro_fma_rate": [C.c_int, C.POINTER(C.c_double)],
+    "hydro_wait_probe": [C.POINTER(C.c_double)],
     "hydro_set_eos_radiation": [_VP, C.c_double, C.c_double],
     "hydro_set_dual_energy": [_VP, C.c_double],
     "hydro_batch_run_host": [_VP, _VP, _VP, C.c_int, C.c_double, C.c_int],
@@ -309,6 +310,14 @@ def hydro_fma_rate(precision=64):
     out = C.c_double()
     _call("hydro_fma_rate", int(precision), C.byref(out))
     return out.value
+
+
+def hydro_wait_probe():
+    """(status, seconds) of a bounded device wait on an mbarrier that nothing
+    completes: HYDRO_ERR_TIMEOUT is the expected status."""
+    out = C.c_double()
+    st = lib().hydro_wait_probe(C.byref(out))
+    return st, out.value
 
 
 def hydro_destroy(h):

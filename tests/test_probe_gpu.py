@@ -16,3 +16,20 @@ def test_fma_rates_are_plausible(hydro_lib):
 def test_fma_rate_rejects_bad_precision(hydro_lib):
     with pytest.raises(hydro_lib.HydroError):
         hydro_lib.hydro_fma_rate(16)
+
+
+def test_bounded_wait_expires_and_reports_timeout(hydro_lib):
+    """A device wait whose barrier nothing completes gives up after its bound
+    and reports HYDRO_ERR_TIMEOUT; the context stays usable afterwards (the
+    failure is detected without a fault, as the batched kernel's waits on its
+    bulk copies would report one)."""
+    import numpy as np
+    from paper_2503_04428_gb300 import workloads as wl
+    st, secs = hydro_lib.hydro_wait_probe()
+    assert st == hydro_lib.HYDRO_ERR_TIMEOUT
+    assert 0.0 < secs < 60.0, secs
+    w = wl.tubes(4, seed=3, lo=256, hi=600)
+    b = hydro_lib.Batch(w["lengths"], w["gamma"], precision=32)
+    b.set_state(w["U"])
+    b.run(2, 0.8)
+    assert np.isfinite(b.get_state()).all()
