@@ -227,9 +227,11 @@ int hydro_mlp_loss_grad(const float* weights, const double* x6, const double* ta
                         double* grad_out, double* loss_out);
 
 /* The same gradient as hydro_mlp_loss_grad, without allocating device memory.
- * The paper has no counterpart: this entry point serves callers that cannot
- * allocate while they call in -- code running inside CUDA stream capture,
- * or a host framework that owns all device memory through its own pool.
+ * The paper has no counterpart: this entry point serves callers that must
+ * not allocate while they call in -- a host framework that owns all of the
+ * GPU's memory through its own pool (an allocation behind its back can fail
+ * or fragment that pool), or a code whose device-memory budget is fixed when
+ * it starts.
  * Every pointer is a device address in the current context: weights
  * (HYDRO_MLP_NPARAM floats), x6 (n x 6 floats, the network inputs), target
  * (n floats), grad_out (HYDRO_MLP_NPARAM doubles), loss_out (1 double); work
@@ -239,8 +241,9 @@ int hydro_mlp_loss_grad(const float* weights, const double* x6, const double* ta
  * until the process exits; hence 1 <= n <= HYDRO_NOALLOC_MAX_SAMPLES, larger n
  * is rejected with HYDRO_ERR_ARG.  The array is shared by all calls: nothing
  * in it has to start at zero, but calls that overlap on the GPU race on it.
- * The first call on a device looks the array's address up (no allocation);
- * make that first call before any stream capture. */
+ * The first call on a device, with that device current, looks the array's
+ * address up and raises the gradient kernel's shared-memory limit (no
+ * allocation); make that first call before any stream capture. */
 #define HYDRO_NOALLOC_MAX_SAMPLES 16384
 int hydro_mlp_loss_grad_device(const float* weights, const float* x6, const float* target, long n,
                                double* grad_out, double* loss_out, void* stream);

@@ -87,15 +87,10 @@ static int berr(const std::string& m) {
   return HYDRO_ERR_ARG;
 }
 
-// Allow the ring's dynamic shared memory (once per instantiation).
+// Allow the ring's dynamic shared memory (once per instantiation and device).
 template <typename T, int NW>
 static int batch_attr() {
-  static bool done = false;
-  if (!done) {
-    HCK(cudaFuncSetAttribute(batched_kernel<T, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)batched_smem_bytes<T, NW>()));
-    done = true;
-  }
+  HCK(smem_attr_once((const void*)batched_kernel<T, NW>, (int)batched_smem_bytes<T, NW>()));
   return HYDRO_OK;
 }
 
@@ -435,11 +430,7 @@ static int pack_mlp(hydro_ctx* h) {
 static int mlp_gradient(cudaStream_t s, const float* W, const float* X, const float* Y, const int* idx,
                         long long first, long long count, float* partial, double* loss_partial,
                         double* grad, double* loss_acc) {
-  static bool attr = false;
-  if (!attr) {
-    HCK(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
-    attr = true;
-  }
+  HCK(smem_attr_once((const void*)mlp_grad_kernel, (int)sizeof(MlpSmem)));
   const int nblocks = (int)((count + MLP_SB - 1) / MLP_SB);
   mlp_grad_kernel<<<nblocks, 256, sizeof(MlpSmem), s>>>(W, X, Y, idx, first, count, (float)(1.0 / count),
                                                         partial, loss_partial);
@@ -996,11 +987,7 @@ int hydro_mlp_train(hydro_t h, const double* faces6, const double* log_pstar, lo
   const long long steps_per_epoch = m_use / bsz_use;
   const long long total_steps = steps_per_epoch * (long long)epochs;
   std::vector<int> perm(m_use);
-  static bool grad_attr = false;
-  if (!grad_attr) {
-    HCK(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
-    grad_attr = true;
-  }
+  HCK(smem_attr_once((const void*)mlp_grad_kernel, (int)sizeof(MlpSmem)));
   unsigned long long state = seed ^ 0xD1B54A32D192ED03ull;
   auto next = [&]() {
     state += 0x9E3779B97F4A7C15ull;
@@ -1186,10 +1173,13 @@ constexpr size_t NOALLOC_BYTES = NOALLOC_GRAD_BYTES + (size_t)NOALLOC_MAX_BLOCKS
 // to be cleared between calls; calls that overlap on the GPU race on it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
-// Device address of the array, looked up once per device (the host-side
-// symbol is only a stand-in and must not be passed to a kernel).
+// Per-device set-up, done once per device with that device current and under
+// one lock: the array's device address (the host-side symbol is only a
+// stand-in and must not be passed to a kernel) and the gradient kernel's
+// raised shared-memory limit, which is a per-device property of the kernel.
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[64] = {nullptr};
+static bool g_noalloc_attr[64] = {false};
 
 static int noalloc_scratch(void** out) {
   int dev = 0;
@@ -1204,6 +1194,12 @@ static int noalloc_scratch(void** out) {
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
     g_noalloc_ptr[dev] = p;
+  }
+  if (!g_noalloc_attr[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(MlpSmem));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mlp_grad_kernel)");
+    g_noalloc_attr[dev] = true;
   }
   *out = g_noalloc_ptr[dev];
   return HYDRO_OK;
@@ -1241,11 +1237,6 @@ extern "C" int hydro_mlp_loss_grad_device(const float* weights, const float* x6,
   void* scratch = nullptr;
   int st = hydro::noalloc_scratch(&scratch);
   if (st) return st;
-  static bool attr = false;
-  if (!attr) {
-    HCK(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
-    attr = true;
-  }
   cudaStream_t s = (cudaStream_t)stream;
   float* partial = (float*)scratch;
   double* loss_partial = (double*)((unsigned char*)scratch + hydro::NOALLOC_GRAD_BYTES);

@@ -295,12 +295,14 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
       issue(k + BD - 1);
       const int sl = (int)(q_use % BD);
       const bool landed = mbar_wait(&bar[warp][sl], (q_use / BD) & 1u);
-      ++q_use;
       if (__any_sync(0xffffffffu, !landed)) {
+        // q_use still names the span whose wait expired: the drain below
+        // waits for it again, with the later spans already issued
         dead = true;
         err = ST_TIMEOUT;
         break;
       }
+      ++q_use;
       long long g0;
       int len;
       span_of(k, g0, len);
@@ -508,7 +510,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     if (dead) break;
   }
   // after an expired wait, let the copies still in flight land (bounded)
-  // before the CTA's shared memory is released
+  // before the CTA's shared memory is released: spans q_use .. q_issue-1,
+  // the one whose wait expired first (on a normal exit q_use == q_issue)
   while (q_use < q_issue) {
     mbar_wait(&bar[warp][q_use % BD], (q_use / BD) & 1u);
     ++q_use;

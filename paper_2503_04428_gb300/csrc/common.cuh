@@ -3,6 +3,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "physics.cuh"
 
 namespace hydro {
@@ -97,6 +101,23 @@ cudaError_t sweep_dispatch_dual(const SweepArgs<T>& a, int nsx, int rs, cudaStre
 template <typename T, int DIM>
 cudaError_t sweep_dispatch_rad(const SweepArgs<T>& a, int nsx, int rs, int dual, cudaStream_t s, int* tx,
                                int* ty, int* nt);
+
+// Raise the dynamic shared-memory limit of kernel `fn` to `bytes` on the
+// current device.  The attribute is a property of the kernel on one device,
+// so it is set once per (device, kernel) pair, under a lock (host threads may
+// make their first calls at the same time).
+inline cudaError_t smem_attr_once(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, fn})) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert({dev, fn});
+  return e;
+}
 
 // Bits of a non-negative double, for an ordered atomicMax.
 __device__ __forceinline__ unsigned long long dbits(double x) {

@@ -879,14 +879,8 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
 template <typename T, int DIM, int NSX, int RS, int MODE>
 cudaError_t launch_sweep(const SweepArgs<T>& a, cudaStream_t s) {
   using S = SweepShape<T, DIM, NSX>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, DIM, NSX, RS, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::smem_bytes_for(MODE));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e = smem_attr_once((const void*)sweep_kernel<T, DIM, NSX, RS, MODE>, (int)S::smem_bytes_for(MODE));
+  if (e != cudaSuccess) return e;
   dim3 grid((a.n[0] + S::TX - 1) / S::TX, DIM >= 2 ? (a.n[1] + S::TY - 1) / S::TY : 1,
             DIM == 3 ? (a.n[2] + a.zchunk - 1) / a.zchunk : 1);
   sweep_kernel<T, DIM, NSX, RS, MODE><<<grid, S::NT, S::smem_bytes_for(MODE), s>>>(a);

@@ -23,3 +23,19 @@ def hydro_lib():
     from paper_2503_04428_gb300 import hydro
     hydro.lib()
     return hydro
+
+
+def pytest_terminal_summary(terminalreporter):
+    """The worst relative-L1 and element-wise errors of every parity test that
+    ran (tests/parity.py), beside its bars."""
+    try:
+        import parity
+    except ImportError:
+        return
+    if not parity.WORST:
+        return
+    tr = terminalreporter
+    tr.write_sep("-", "parity: worst errors against the oracle (relative L1 / element-wise, bars)")
+    for name in sorted(parity.WORST):
+        e1, em, b1, bm = parity.WORST[name]
+        tr.write_line("%-90s L1 %.2e (<= %.0e)  max %.2e (<= %.0e)" % (name[-90:], e1, b1, em, bm))

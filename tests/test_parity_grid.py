@@ -1,10 +1,11 @@
 """GPU grid path vs the FP64 oracle, element by element, one step at a time.
 
-Bar: FP64 relative L1 per conserved component <= 1e-12 per step; FP32
-relative L1 <= 2e-5 per step (the oracle is given the FP32-rounded input, so
-this measures the step's FP32 arithmetic; eps_32 = 6e-8 times the O(100)
-rounding steps on the path of one value).  Sizes span several tiles with
-ragged tails along every axis and several z-chunks in 3D.
+Bars per conserved component and step (tests/parity.py): FP64 relative L1
+<= 1e-12 and element-wise max|B - A| <= 1e-11 of the component's scale;
+FP32 relative L1 <= 2e-5 and element-wise <= 1e-4 (the oracle is given the
+FP32-rounded input, so this measures the step's FP32 arithmetic; eps_32 =
+6e-8 times the O(100) rounding steps on the path of one value).  Sizes span
+several tiles with ragged tails along every axis and several z-chunks in 3D.
 """
 import numpy as np
 import pytest
@@ -14,32 +15,16 @@ from paper_2503_04428_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {64: 1e-12, 32: 2e-5}
+from parity import ELEM_TOL, L1_TOL, check
+
+TOL = L1_TOL
 
 
 def rel_l1(A, B, dim, gamma=1.4):
-    """Relative L1 error per conserved component (B against the reference A).
-
-    Each component is measured against its own L1 norm; momenta against at
-    least sum(rho c) and scalars against at least sum(rho), so that a
-    component that is nearly zero (a momentum created in one step from a
-    near-balanced state) is measured on its physical scale."""
-    A = A.astype(np.float64)
-    B = B.astype(np.float64)
-    nv = A.shape[0]
-    rho = A[0]
-    ke = 0.5 * sum(A[1 + d] ** 2 for d in range(dim)) / rho
-    p = np.maximum((gamma - 1) * (A[1 + dim] - ke), 0.0)
-    mom_scale = np.sum(np.sqrt(gamma * p * rho))
-    out = []
-    for v in range(nv):
-        den = np.abs(A[v]).sum()
-        if 1 <= v <= dim:
-            den = max(den, mom_scale)
-        elif v > 1 + dim:
-            den = max(den, np.abs(rho).sum())
-        out.append(np.abs(B[v] - A[v]).sum() / den)
-    return np.array(out)
+    """Relative L1 error per conserved component (B against the oracle's A),
+    on the scales of tests/parity.py."""
+    from parity import errors
+    return errors(A, B, dim, gamma)[0]
 
 
 def step_compare(hydro_lib, case, precision, steps=1, tol=None, dt=None):
@@ -50,6 +35,7 @@ def step_compare(hydro_lib, case, precision, steps=1, tol=None, dt=None):
     s = O.solver_from_case(case)
     g = H.Grid.from_case(case, precision)
     tol = TOL[precision] if tol is None else tol
+    elem = ELEM_TOL[precision] * tol / TOL[precision]
     worst = 0.0
     for _ in range(steps):
         d = dt if dt is not None else s.cfl_dt(case["cfl"])
@@ -57,9 +43,8 @@ def step_compare(hydro_lib, case, precision, steps=1, tol=None, dt=None):
         g.step(d)
         A = s.get_state()
         B = g.get_state()
-        err = rel_l1(A, B, case["dim"], case["gamma"])
+        err, _ = check(A, B, case["dim"], case["gamma"], precision, l1=tol, elem=elem, label=case["name"])
         worst = max(worst, err.max())
-        assert np.all(err <= tol), (case["name"], err)
         if precision == 32:  # restart both from the oracle's state each step
             g.set_state(A.astype(np.float32))
             s.set_state(A.astype(np.float32).astype(np.float64))
@@ -148,7 +133,7 @@ def test_ni56_heating(hydro_lib):
     s.step(dt)
     g.step(dt)
     assert np.abs(s.get_state()[2] - U0[2]).max() > 1e-6 * np.abs(U0[2]).max()  # heating acts
-    assert np.all(rel_l1(s.get_state(), g.get_state(), 1, 5 / 3) <= 1e-12)
+    check(s.get_state(), g.get_state(), 1, 5 / 3, 64)
 
 
 @pytest.mark.parametrize("precision", [64, 32])
@@ -174,7 +159,9 @@ def test_device_dt_run_matches_oracle_sod(hydro_lib):
     t_gpu = g.run(k + 5, 0.8, t_end=0.2)
     assert abs(t_gpu - 0.2) < 1e-14
     assert g.stats()["steps"] == k
-    assert np.all(rel_l1(s.get_state(), g.get_state(), 1) <= 1e-10)
+    # (a whole run: the per-step bars times the ~250 steps; the shocks' cells
+    # carry the largest differences)
+    check(s.get_state(), g.get_state(), 1, 1.4, 64, l1=1e-10, elem=1e-9)
 
 
 @pytest.mark.parametrize("precision", [64, 32])
@@ -263,7 +250,7 @@ def test_sedov_full_size_window(hydro_lib, precision):
     win.step(dt)
     A = win.get_state()[:, 3:-3, 3:-3, 3:-3]
     Bw = B[:, lo + 3:hi - 3, lo + 3:hi - 3, lo + 3:hi - 3]
-    assert np.all(rel_l1(A, Bw, 3) <= TOL[precision])
+    check(A, Bw, 3, 1.4, precision)
     # far field untouched in one step, and the blast is octant-symmetric
     assert np.array_equal(B[:, :100, :100, :100], U0[:, :100, :100, :100])
     assert np.abs(B[0] - B[0][::-1, ::-1, ::-1]).max() <= (1e-12 if precision == 64 else 1e-5)
@@ -293,7 +280,7 @@ def test_wedge_full_size_window(hydro_lib):
         ri = slice(0 if r0 == 0 else 3, (r1 - r0) if r1 == 1024 else (r1 - r0 - 3))
         sl = (slice(None), slice(3, k1 - k0), slice(0, j1 - j0 - 3), ri)
         Bw = B[:, k0:k1, j0:j1, r0:r1][sl]
-        assert np.all(rel_l1(A[sl], Bw, 3, case["gamma"]) <= TOL[32])
+        check(A[sl], Bw, 3, case["gamma"], 32)
 
 
 @pytest.mark.parametrize("precision", [64, 32])
