@@ -5,16 +5,27 @@ limited reconstruction, Hancock predictor, exact Riemann solve with the
 learned or Toro guess, conservative update, per-tube CFL speed), i.e. one
 persistent launch of the batched kernel replayed from a CUDA graph.
 
+The workload runs every tube for K = 200 of its own CFL steps, and the cost
+of a step changes along that run (the waves spread from each interface, and
+with them the faces that run Newton).  So the `--steps` timed steps are
+spread evenly over the 200-step run (step j*200/steps for j < steps; the
+first `--steps` steps if that is more than 200), each timed alone with CUDA
+events; the run is advanced untimed between them.
+
 Headline (`value`): FP32 bulk + MLP star-pressure guess + batched/graph, in
-cell-updates/s over all ranks, inputs resident in HBM.  Beside it: the plain
-FP64 + Toro-guess form of the same kernel (`fp64_plain`), the end-to-end rate
-through the C ABI with host buffers (`e2e`), the HBM roofline of the kernel,
-and the FP64 CPU oracle on a bounded sample (`cpu_baseline`).
+cell-updates/s over all ranks, inputs resident in HBM, over those steps.
+Beside it, over the same steps: the plain FP64 + Toro-guess form of the same
+kernel (`fp64_plain`), the FP32 form without the network (`mlp_gain`), and
+the end-to-end rate through the C ABI with host buffers (`e2e`); then the
+HBM roofline of the kernel, the first steps alone (`early_window`), a dense
+state on which every face iterates (`dense_state`), the 3D grid sweeps, and
+the FP64 CPU oracle on a bounded sample (`cpu_baseline`).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun each rank advances its own 4096 tubes (weak scaling, no data
-exchange); timing is the max over ranks.
+Under torchrun the job is N x 4096 tubes of the workload's distribution
+(one seed), cut into N contiguous ranges of about equal cell counts, one per
+rank (weak scaling, no data exchange); timing is the max over ranks.
 """
 import argparse
 import hashlib
@@ -138,9 +149,37 @@ def dist_info():
     return ws, rank, local
 
 
-def rank_seed(rank):
-    """Each rank advances its own 4096 tubes (weak scaling): a seed per rank."""
-    return 2 + 1000 * rank
+TRAJ = 200  # steps every tube takes in the workload
+
+
+def partition_by_cells(lengths, world):
+    """Contiguous tube ranges [b0, b1) of about equal cell counts, one per
+    rank: range r starts at the first tube whose cumulative cell count
+    reaches r/world of the total."""
+    cum = np.concatenate([[0], np.cumsum(np.asarray(lengths, dtype=np.int64))])
+    total = int(cum[-1])
+    bounds = [int(np.searchsorted(cum, r * total / world, side="left")) for r in range(world)] + [len(lengths)]
+    for r in range(1, world + 1):
+        bounds[r] = max(bounds[r], bounds[r - 1])
+    return [(bounds[r], bounds[r + 1]) for r in range(world)]
+
+
+def rank_tubes(world, rank, perturb=0.0, ntubes=NTUBES):
+    """This rank's share of the job: world x ntubes tubes of the workload's
+    distribution (seed 2; at world = 1 exactly the 4096-tube workload), cut
+    by cumulative cell count."""
+    from paper_2503_04428_gb300 import workloads as wl
+    n = ntubes * world
+    b0, b1 = partition_by_cells(wl.tube_lengths(n, 2), world)[rank]
+    return wl.tubes(n, seed=2, perturb=perturb, tube_range=(b0, b1))
+
+
+def trajectory_positions(k, length=TRAJ):
+    """0-based step indices of the k timed steps within the workload's run:
+    evenly spread over its `length` steps, or the first k steps if k >= length."""
+    if k >= length:
+        return list(range(k))
+    return [j * length // k for j in range(k)]
 
 
 def job_rate(elapsed_local, cells_local, steps, dist=None, device=None):
@@ -176,6 +215,48 @@ def train_mlp(H, torch, gamma, seed):
     wts = b.mlp_get()
     b.close()
     return wts, {"faces": int(keep.sum()), "loss": loss, "train_s": round(time.time() - t0, 2)}
+
+
+def time_trajectory(torch, stream, b, U, positions, cfl=CFL):
+    """From state U, advance the batch through the run and time each step at
+    `positions` alone (CUDA events on the launching stream around one graph
+    replay of one step); untimed steps in between.  Returns the summed
+    device time in seconds and the solver counters accumulated over the whole
+    run (steps 0 .. last position)."""
+    b.set_state(U)
+    s0 = b.stats()
+    cur = 0
+    evs = []
+    torch.cuda.synchronize()
+    for p in positions:
+        if p > cur:
+            b.run(p - cur, cfl)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(1, cfl)
+        e1.record(stream)
+        evs.append((e0, e1))
+        cur = p + 1
+    torch.cuda.synchronize()
+    t = sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1000.0
+    s1 = b.stats()
+    return t, counters(s0, s1)
+
+
+def counters(s0, s1):
+    """Exact-solver counters between two stats() snapshots: iterations per
+    face (all faces), and per Newton face by guess category."""
+    faces = max(s1["faces"] - s0["faces"], 1)
+    nf = [a - b for a, b in zip(s1["newton_faces"], s0["newton_faces"])]
+    ni = [a - b for a, b in zip(s1["newton_iters_by"], s0["newton_iters_by"])]
+    out = {"steps": s1["steps"] - s0["steps"],
+           "newton_iters_per_face": (s1["newton_iters"] - s0["newton_iters"]) / faces,
+           "newton_face_fraction": sum(nf) / faces}
+    for k, name in enumerate(("toro", "mlp", "fp64_fallback")):
+        out[name] = {"faces": nf[k], "face_fraction": nf[k] / faces,
+                     "iters_per_face": (ni[k] / nf[k]) if nf[k] else None}
+    return out
 
 
 def timed_steps(torch, stream, fn, steps):
@@ -251,20 +332,23 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200, help="steps per timed pass (the workload's K = 200)")
+    ap.add_argument("--steps", type=int, default=TRAJ,
+                    help="timed steps, spread evenly over the workload's 200-step run")
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--repeats", type=int, default=5,
-                    help="timed passes, each from the initial state (the state reset is not timed)")
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tubes", type=int, default=NTUBES, help="tubes per GPU (profiling a smaller case)")
     ap.add_argument("--skip-fp64", action="store_true", help="do not time the plain FP64 form")
     ap.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer path")
     ap.add_argument("--skip-grids", action="store_true", help="do not time the 3D grid sweeps")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="time only the headline form (profiling): no FP64, no-network, e2e, dense or grids")
     ap.add_argument("--grid-only", choices=["sedov3d_fp32", "sedov3d_fp64", "wedge_fp32", "wedge_fp32_rad"],
                     help="time one grid sweep only (profiling)")
     ap.add_argument("--grid-n", type=int, default=0, help="cells per axis for --grid-only sedov3d")
     args = ap.parse_args()
+    if args.skip_extras:
+        args.skip_fp64 = args.skip_e2e = args.skip_grids = True
     if args.grid_only:
         import torch
         from paper_2503_04428_gb300 import hydro as H
@@ -281,14 +365,15 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     from paper_2503_04428_gb300 import hydro as H
-    from paper_2503_04428_gb300 import workloads as wl
 
-    seed = rank_seed(rank)
-    w = wl.tubes(args.tubes, seed=seed)
+    w = rank_tubes(ws, rank, ntubes=args.tubes)
     total = int(w["lengths"].sum())
     gamma = w["gamma"]
     stream = torch.cuda.current_stream()
-    weights, train_info = train_mlp(H, torch, gamma, seed)
+    weights, train_info = train_mlp(H, torch, gamma, 2)
+    positions = trajectory_positions(args.steps)
+    ksteps = len(positions)
+    dist_or_none = torch.distributed if ws > 1 else None
 
     def barrier():
         if ws > 1:
@@ -300,57 +385,51 @@ def main():
     b32 = H.Batch(w["lengths"], gamma, precision=32, stream=stream.cuda_stream)
     b32.mlp_set(weights, True)
     b32.set_state(U32)
-    b32.run(args.warmup, CFL)  # includes the autotuner on first use
+    b32.run(max(3, args.warmup), CFL)  # includes the autotuner on first use
     clocks = Clocks(local)
-    t32 = 0.0
-    it_acc = mlp_acc = face_acc = 0
     barrier()
     clocks.start()
-    for _ in range(args.repeats):
-        b32.set_state(U32)
-        s0 = b32.stats()
-        t32 += timed_steps(torch, stream, lambda k: b32.run(k, CFL), args.steps)
-        s1 = b32.stats()
-        face_acc += s1["faces"] - s0["faces"]
-        it_acc += s1["newton_iters"] - s0["newton_iters"]
-        mlp_acc += s1["mlp_faces"] - s0["mlp_faces"]
+    t32, c32 = time_trajectory(torch, stream, b32, U32, positions)
     clk = clocks.stop()
     barrier()
-    nsteps = args.steps * args.repeats
-    value, t32 = job_rate(t32, total, nsteps, torch.distributed if ws > 1 else None, "cuda")
-    it32 = it_acc / max(face_acc, 1)
-    mlp_frac = mlp_acc / max(face_acc, 1)
-    ms = 1000.0 * t32 / nsteps
-    out32 = b32.get_state().astype(np.float64)
-    times32 = b32.times()
-
-    value64 = t64 = it64 = rho_rel = None
-    k64 = 0
-    accuracy = {"rho_rel_l1_fp32mlp_vs_fp64": None}
+    value, t32 = job_rate(t32, total, ksteps, dist_or_none, "cuda")
+    ms = 1000.0 * t32 / ksteps
+    # the state after the workload's 200 steps, for the accuracy comparison
+    out32 = times32 = None
     if not args.skip_fp64:
-        value64, t64, k64, it64, rho_rel, out64, times64 = time_fp64(H, torch, stream, w, args, ws, total,
-                                                                       out32)
-        # equal stated accuracy: both forms' per-tube L1(rho) error against the
-        # exact solution at the final time, averaged over tubes
-        e32 = exact_l1_rho(H, w, out32[0], times32)
-        e64 = exact_l1_rho(H, w, out64[0], times64)
-        accuracy = {"rho_rel_l1_fp32mlp_vs_fp64": rho_rel,
-                    "l1_rho_vs_exact": {"fp32_mlp": e32, "fp64_toro": e64,
-                                        "relative_difference": abs(e32 - e64) / e64,
-                                        "steps": args.steps,
-                                        "definition": "mean over tubes of sum_i |rho_i - rho_exact(x_i, t_b)| / n_b"}}
+        b32.set_state(U32)
+        b32.run(TRAJ, CFL)
+        out32 = b32.get_state().astype(np.float64)
+        times32 = b32.times()
+
+    extras = {}
+    # the first steps alone (the easy regime: waves near the interfaces)
+    k0 = min(ksteps, 20)
+    te, ce = time_trajectory(torch, stream, b32, U32, list(range(k0)))
+    ve, te = job_rate(te, total, k0, dist_or_none, "cuda")
+    extras["early_window"] = {"value": ve, "unit": METRIC, "ms_per_step": 1000.0 * te / k0,
+                              "steps": "1-%d of the run" % k0, "counters": ce}
+    if not args.skip_fp64:
+        # the FP32 form without the network, same steps
+        b32.mlp_set(weights, False)
+        tn, cn = time_trajectory(torch, stream, b32, U32, positions)
+        b32.mlp_set(weights, True)
+        vn, tn = job_rate(tn, total, ksteps, dist_or_none, "cuda")
+        extras["mlp_gain"] = {"value_with_network": value, "value_without_network": vn,
+                              "gain": value / vn, "counters_without_network": cn}
+        extras["fp64_plain"], extras["accuracy"] = time_fp64(H, torch, stream, w, positions, ws, total, value,
+                                                            out32, times32)
     e2e = None
     if not args.skip_e2e:
-        e2e = time_e2e(H, torch, b32, w, args, ws, total, barrier)
-    dense = None
+        e2e = time_e2e(H, torch, b32, w, positions, ws, total, barrier)
+    alu = None
     if not args.skip_fp64:
-        dense = time_dense(H, torch, stream, args, ws, weights)
-    alu = alu_peaks(H)
-    grids = None
+        extras["dense_state"] = time_dense(H, torch, stream, args, ws, rank, weights)
+        alu = alu_peaks(H)
+        extras["alu_peaks"] = alu
     if not args.skip_grids:
-        grids = time_grids(H, torch, stream, args, alu=alu)
-    return report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it32, mlp_frac,
-                  value64, t64, k64, it64, accuracy, dense, grids, alu)
+        extras["grid_sweep"] = time_grids(H, torch, stream, args, alu=alu)
+    return report(args, ws, rank, b32, value, ms, t32, ksteps, total, e2e, clk, train_info, c32, extras)
 
 
 def time_grids(H, torch, stream, args, only=None, alu=None):
@@ -398,28 +477,29 @@ def time_grids(H, torch, stream, args, only=None, alu=None):
     return out
 
 
-def time_dense(H, torch, stream, args, ws, weights):
+def time_dense(H, torch, stream, args, ws, rank, weights):
     """The headline form on a dense state: every cell's density and pressure
     perturbed by 1 %, so that no face has two identical states and every face
-    runs the Newton iteration."""
-    from paper_2503_04428_gb300 import workloads as wl
-    w = wl.tubes(args.tubes, seed=rank_seed(dist_info()[1]), perturb=0.01)
+    runs the Newton iteration; with and without the network."""
+    w = rank_tubes(ws, rank, perturb=0.01, ntubes=args.tubes)
     total = int(w["lengths"].sum())
     U = torch.from_numpy(w["U"].astype(np.float32)).cuda()
     b = H.Batch(w["lengths"], w["gamma"], precision=32, stream=stream.cuda_stream)
     b.mlp_set(weights, True)
     b.set_state(U)
     b.run(2, CFL)
-    b.set_state(U)
-    k = max(5, args.steps // 2)
-    s0 = b.stats()
-    t = timed_steps(torch, stream, lambda n: b.run(n, CFL), k)
-    s1 = b.stats()
-    rate, t = job_rate(t, total, k, torch.distributed if ws > 1 else None, "cuda")
-    it = (s1["newton_iters"] - s0["newton_iters"]) / max(s1["faces"] - s0["faces"], 1)
+    k = min(max(5, args.steps // 4), 20)
+    out = {"state": "every cell's rho and P x (1 + 0.01 U(-1,1))", "steps": "1-%d" % k}
+    for on in (True, False):
+        b.mlp_set(weights, on)
+        t, c = time_trajectory(torch, stream, b, U, list(range(k)))
+        rate, t = job_rate(t, total, k, torch.distributed if ws > 1 else None, "cuda")
+        key = "with_network" if on else "without_network"
+        out[key] = {"value": rate, "unit": METRIC, "ms_per_step": 1000.0 * t / k, "counters": c}
+    out["value"] = out["with_network"]["value"]
+    out["mlp_gain"] = out["with_network"]["value"] / out["without_network"]["value"]
     b.close()
-    return {"value": rate, "unit": METRIC, "ms_per_step": 1000.0 * t / k, "newton_iters_per_face": it,
-            "state": "every cell's rho and P x (1 + 0.01 U(-1,1))"}
+    return out
 
 
 def exact_l1_rho(H, w, rho, times):
@@ -437,107 +517,115 @@ def exact_l1_rho(H, w, rho, times):
     return float(np.bincount(face_of, weights=err).mean())
 
 
-def time_fp64(H, torch, stream, w, args, ws, total, out32):
-    """The plain FP64 form of the same kernel (Toro guess), and the difference
-    of its density field from the headline form's after the same steps."""
+def time_fp64(H, torch, stream, w, positions, ws, total, value32, out32, times32):
+    """The plain FP64 form of the same kernel (Toro guess) over the same steps
+    of the run, and the accuracy of both forms after the workload's 200 steps."""
     gamma = w["gamma"]
     U64 = torch.from_numpy(w["U"]).cuda()
     b64 = H.Batch(w["lengths"], gamma, precision=64, stream=stream.cuda_stream)
     b64.set_state(U64)
-    b64.run(max(2, args.warmup // 2), CFL)
+    b64.run(3, CFL)
+    t64, c64 = time_trajectory(torch, stream, b64, U64, positions)
+    value64, t64 = job_rate(t64, total, len(positions), torch.distributed if ws > 1 else None, "cuda")
+    peak, _ = load_peaks()
+    ach64 = 2 * 3 * 8 * total / (t64 / len(positions)) / 1e9
+    fp64 = {"value": value64, "unit": METRIC, "ms_per_step": 1000.0 * t64 / len(positions),
+            "hbm_frac": ach64 / peak, "counters": c64, "speedup_of_headline": value32 / value64,
+            "steps": "the headline's steps of the run"}
+    # equal stated accuracy: both forms' per-tube L1(rho) error against the
+    # exact solution after the workload's 200 steps, averaged over tubes
     b64.set_state(U64)
-    k64 = max(5, args.steps // 2)  # FP64 is ~15x slower: half a pass
-    r0 = b64.stats()
-    t64 = timed_steps(torch, stream, lambda k: b64.run(k, CFL), k64)
-    r1 = b64.stats()
-    it64 = (r1["newton_iters"] - r0["newton_iters"]) / max(r1["faces"] - r0["faces"], 1)
-    value64, t64 = job_rate(t64, total, k64, torch.distributed if ws > 1 else None, "cuda")
-    # same number of steps from the same start for an accuracy comparison
-    b64.set_state(U64)
-    b64.run(args.steps, CFL)
+    b64.run(TRAJ, CFL)
     out64 = b64.get_state()
     times64 = b64.times()
-    rho_rel = float(np.abs(out32[0] - out64[0]).sum() / np.abs(out64[0]).sum())
     b64.close()
-    return value64, t64, k64, it64, rho_rel, out64, times64
+    e32 = exact_l1_rho(H, w, out32[0], times32)
+    e64 = exact_l1_rho(H, w, out64[0], times64)
+    acc = {"rho_rel_l1_fp32mlp_vs_fp64": float(np.abs(out32[0] - out64[0]).sum() / np.abs(out64[0]).sum()),
+           "l1_rho_vs_exact": {"fp32_mlp": e32, "fp64_toro": e64, "relative_difference": abs(e32 - e64) / e64,
+                               "steps": TRAJ,
+                               "definition": "mean over tubes of sum_i |rho_i - rho_exact(x_i, t_b)| / n_b"}}
+    return fp64, acc
 
 
-def time_e2e(H, torch, b32, w, args, ws, total, barrier):
-    """Same metric through the C ABI with pinned host buffers: every step
-    copies the state in from host memory, advances one step and copies it
-    out (hydro_batch_run_host: the copies of one group of tubes overlap the
-    steps of the others).  Also the unpipelined sequence set_state + run +
-    get_state for reference."""
+def time_e2e(H, torch, b32, w, positions, ws, total, barrier):
+    """Same metric through the C ABI with pinned host buffers, at the same
+    steps of the run: each timed step copies that step's state in from host
+    memory, advances one step and copies the result out
+    (hydro_batch_run_host: the copies of one group of tubes overlap the steps
+    of the others); wall-clock time of the call.  The state for the next
+    timed step is prepared untimed.  Also the unpipelined sequence set_state
+    + run + get_state at the same steps."""
     host_in = torch.from_numpy(w["U"].astype(np.float32)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    ke = max(3, args.steps // 5)
-    b32.run_host(host_in, host_out, 1, CFL)
+    U0 = host_in.clone()
+    b32.run_host(host_in, host_out, 1, CFL)  # captures the host-run graph
+    ts = tu = 0.0
+    b32.set_state(U0)
+    cur = 0
     barrier()
-    te0 = time.perf_counter()
-    for _ in range(ke):
+    for p in positions:
+        if p > cur:
+            b32.run(p - cur, CFL)
+        b32.get_state(host_in)  # this step's input, in host memory (untimed)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         b32.run_host(host_in, host_out, 1, CFL)
-    torch.cuda.synchronize()
-    te = time.perf_counter() - te0
-    rate, te = job_rate(te, total, ke, torch.distributed if ws > 1 else None, "cuda")
-    barrier()
-    ts0 = time.perf_counter()
-    for _ in range(ke):
+        ts += time.perf_counter() - t0
+        # the plain sequence on the same input (the handle then holds the same result)
+        t0 = time.perf_counter()
         b32.set_state(host_in)
         b32.run(1, CFL)
         b32.get_state(host_out)
-    torch.cuda.synchronize()
-    ts = time.perf_counter() - ts0
+        tu += time.perf_counter() - t0
+        cur = p + 1
+    barrier()
+    rate, ts = job_rate(ts, total, len(positions), torch.distributed if ws > 1 else None, "cuda")
+    rate_u, _ = job_rate(tu, total, len(positions), torch.distributed if ws > 1 else None, "cuda")
     nbytes = 3 * total * 4
     return {"value": rate, "unit": METRIC, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-            "api": "hydro_batch_run_host (8 groups of tubes, pinned buffers)",
-            "unpipelined_value": ws * total * ke / ts}
+            "api": "hydro_batch_run_host (8 groups of tubes, pinned buffers), the headline's steps of the run",
+            "unpipelined_value": rate_u}
 
 
-def report(args, ws, rank, b32, value, ms, t32, total, e2e, clk, train_info, it32, mlp_frac,
-           value64, t64, k64, it64, accuracy, dense=None, grids=None, alu=None):
+def report(args, ws, rank, b32, value, ms, t32, ksteps, total, e2e, clk, train_info, c32, extras):
     peak, peak_kind = load_peaks()
-    nsteps = args.steps * args.repeats
     alg_bytes = 2 * 3 * 4 * total  # read U^n and write U^{n+1}, FP32
-    achieved = alg_bytes / (t32 / nsteps) / 1e9
+    achieved = alg_bytes / (t32 / ksteps) / 1e9
     st = b32.stats()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": profiled_traffic(st["tile_x"]), "peak_kind": peak_kind, "kernel": "batched_kernel<float>",
-            "algorithmic_bytes_per_launch": alg_bytes}
-    fp64 = None
-    if value64 is not None:
-        ach64 = 2 * 3 * 8 * total / (t64 / k64) / 1e9
-        fp64 = {"value": value64, "unit": METRIC, "ms_per_step": 1000.0 * t64 / k64, "hbm_frac": ach64 / peak,
-                "fp64_peak_tflops": alu["fp64_tflops"] if alu else None,
-                "newton_iters_per_face": it64, "speedup_of_headline": value / value64}
-
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "window": "the headline's timed steps (one launch each)"}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
     if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": nsteps,
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": ksteps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if args.tubes == NTUBES else "%d-tube subset of: %s" % (args.tubes, WORKLOAD),
-                       "tubes_per_gpu": args.tubes, "cells_per_gpu": total,
+                       "tubes_per_gpu": len(b32.lengths), "cells_per_gpu": total,
                        "form": "FP32 bulk + MLP p* guess (two-shock faces, jump > 4) + persistent batched kernel + CUDA graph",
                        "cfl": CFL, "l2": "state 208 MB per buffer > 129 MB L2 (no flush needed)",
-                       "timing": "%d passes of %d steps from the initial state (state reset untimed)"
-                                 % (args.repeats, args.steps),
-                       "launch": {"chunk": st["tile_x"], "ctas": st["zchunk"]}},
+                       "timing": "%d steps at positions j*200/%d of the workload's 200-step run (one pass from the "
+                                 "initial state, untimed advance between them), each one graph replay timed alone "
+                                 "with CUDA events" % (ksteps, ksteps) if ksteps < TRAJ else
+                                 "steps 1-%d of the run, each timed alone with CUDA events" % ksteps,
+                       "partition": "the job is %d x 4096 tubes (seed 2) cut into %d ranges of about equal cells"
+                                    % (ws, ws),
+                       "launch": {"item_cells": st["tile_x"], "warps_per_cta": st["tile_y"], "ctas": st["zchunk"]}},
             "e2e": e2e,
-            "gpu_launches": nsteps,
+            "gpu_launches": ksteps,
             "clocks": clk,
             "roofline": roof,
             "cpu_baseline": cpu,
-            "fp64_plain": fp64,
-            "dense_state": dense,
-            "grid_sweep": grids,
-            "alu_peaks": alu,
-            "newton_iters_per_face": {"fp32_mlp": it32, "fp64_toro": it64},
-            "mlp": dict(train_info, guessed_face_fraction=mlp_frac),
-            "accuracy": accuracy,
-        }))
+            "solver": c32,
+            "mlp": train_info,
+        }
+        line.update(extras)
+        print(json.dumps(line))
     b32.close()
 
 

@@ -94,6 +94,13 @@ typedef struct {
   double last_dt;
   int tile_x, tile_y, zchunk, threads;  /* launch shape chosen by the autotuner */
   double tuned_us_per_step;            /* autotuner's best measured step time */
+  /* Batched exact solver, owned faces that ran Newton (not two identical
+   * states) and their iterations, by category: [0] started from Toro's guess,
+   * [1] from the network's guess, both in the handle's precision; [2] FP32
+   * faces solved in FP64 (pressure ratio above 1e6 or within 5 % of the
+   * vacuum limit), whatever their guess.  Zero for grid handles. */
+  long long newton_faces[3];
+  long long newton_iters_by[3];
 } hydro_stats_t;
 
 /* Create a grid solver.  precision: 64 (FP64 throughout) or 32 (FP32 bulk

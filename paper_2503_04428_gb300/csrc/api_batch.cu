@@ -506,6 +506,10 @@ int hydro_batch_stats_impl(hydro_ctx* h, hydro_stats_t* out) {
   out->newton_iters = (long long)c.iters;
   out->fallbacks = (long long)c.fallbacks;
   out->mlp_faces = (long long)c.mlp;
+  for (int k = 0; k < NCAT; ++k) {
+    out->newton_faces[k] = (long long)h->bs->bctrl_host->cat_faces[k];
+    out->newton_iters_by[k] = (long long)h->bs->bctrl_host->cat_iters[k];
+  }
   out->tile_x = h->bs->item_len;
   out->tile_y = h->bs->nw;
   out->zchunk = h->bs->grid;
@@ -696,12 +700,17 @@ static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
   HCK(cudaStreamSynchronize(h->stream));
   int code = 0;
   long long iters = 0, mlp = 0, fb = 0;
+  unsigned long long cf[NCAT] = {0, 0, 0}, ci[NCAT] = {0, 0, 0};
   for (int p = 0; p < P; ++p) {
     const Ctrl& c = bs->part_ctrl_host[p].c;
     if (c.status && !code) code = c.status;
     iters += (long long)c.iters;
     mlp += (long long)c.mlp;
     fb += (long long)c.fallbacks;
+    for (int k = 0; k < NCAT; ++k) {
+      cf[k] += bs->part_ctrl_host[p].cat_faces[k];
+      ci[k] += bs->part_ctrl_host[p].cat_iters[k];
+    }
   }
   // the handle now holds the result, as after set_state + run
   BatchCtrl& g = *bs->bctrl_host;
@@ -715,6 +724,10 @@ static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
     g.c.iters += iters;
     g.c.mlp += mlp;
     g.c.fallbacks += fb;
+    for (int k = 0; k < NCAT; ++k) {
+      g.cat_faces[k] += cf[k];
+      g.cat_iters[k] += ci[k];
+    }
   }
   if ((st = write_bctrl(h))) return st;
   if (code) {

@@ -87,10 +87,17 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* m, unsigned parity
   return false;
 }
 
+// Exact-solver faces by where Newton started and in which precision it ran:
+// Toro's guess, the network's guess (both in the form's precision), or the
+// FP64 solve of an FP32 hard face (reading R12), whatever its guess.
+enum { CAT_TORO = 0, CAT_MLP = 1, CAT_FP64 = 2, NCAT = 3 };
+
 struct BatchCtrl {
   Ctrl c;
   unsigned int next_item;  // work-queue head of the running launch
   unsigned int pad2;
+  unsigned long long cat_faces[NCAT];  // faces that ran Newton, per category
+  unsigned long long cat_iters[NCAT];  // their Newton iterations
 };
 
 struct MlpSmemW;
@@ -231,6 +238,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
   }
   bool w_ready = false;  // this warp has seen the weights land
   unsigned long long n_iters = 0, n_mlp = 0, n_fb = 0;
+  unsigned cat_f[NCAT] = {0u, 0u, 0u}, cat_i[NCAT] = {0u, 0u, 0u};  // per-lane counts of this launch
   int err = 0;
   // the last uniform window's state and its |u| + c (warp-uniform values)
   bool have_u = false;
@@ -415,6 +423,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
         const bool same = WL[0] == WR[0] && WL[1] == WR[1] && WL[2] == WR[2];
         T pg = T(0);
         int kind = 0;
+        bool by_mlp = false;  // pg came from the network
         T cL = T(0), cR = T(0);
         if (face && !same) {
           cL = dsqrt(qdiv(gas.g * WL[2], WL[0]));
@@ -463,6 +472,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
               // (the guess only seeds Newton: FP32 exp in the FP32 form)
               if constexpr (sizeof(T) == 4) pg = pref * expf(y);
               else pg = (T)((double)pref * exp((double)y));
+              by_mlp = true;
               if (owned) ++n_mlp;
             }
           }
@@ -475,7 +485,15 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
             // from the same value the general entry would use)
             int its = 0;
             const int st = riemann_exact_from<T>(WL, WR, cL, cR, pg, F, gas, its);
-            if (owned) n_iters += its;
+            if (owned) {
+              n_iters += its;
+              int cat = by_mlp ? CAT_MLP : CAT_TORO;
+              if constexpr (sizeof(T) == 4) {
+                if (hard_face<T>(WL[2], WR[2], WR[1] - WL[1], gas.two_gm1 * (cL + cR))) cat = CAT_FP64;
+              }
+              cat_f[cat] += 1u;
+              cat_i[cat] += (unsigned)its;
+            }
             if (st != ST_OK && err == 0) err = st;
           }
         }
@@ -523,10 +541,20 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     n_iters += __shfl_xor_sync(0xffffffffu, n_iters, o);
     n_mlp += __shfl_xor_sync(0xffffffffu, n_mlp, o);
     n_fb += __shfl_xor_sync(0xffffffffu, n_fb, o);
+#pragma unroll
+    for (int c = 0; c < NCAT; ++c) {
+      cat_f[c] += __shfl_xor_sync(0xffffffffu, cat_f[c], o);
+      cat_i[c] += __shfl_xor_sync(0xffffffffu, cat_i[c], o);
+    }
     const int e2 = __shfl_xor_sync(0xffffffffu, err, o);
     err = err ? err : e2;
   }
   if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < NCAT; ++c) {
+      if (cat_f[c]) atomicAdd(&a.ctrl->cat_faces[c], (unsigned long long)cat_f[c]);
+      if (cat_i[c]) atomicAdd(&a.ctrl->cat_iters[c], (unsigned long long)cat_i[c]);
+    }
     if (n_iters) atomicAdd(&a.ctrl->c.iters, n_iters);
     if (n_mlp) atomicAdd(&a.ctrl->c.mlp, n_mlp);
     if (n_fb) atomicAdd(&a.ctrl->c.fallbacks, n_fb);

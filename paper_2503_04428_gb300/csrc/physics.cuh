@@ -647,6 +647,13 @@ static __device__ __noinline__ int newton_star_fp64(float p0, float rL, float uL
   return st;
 }
 
+// An FP32 face that is solved in FP64 (reading R12): pressure ratio above
+// 1e6, or a velocity jump within 5 % of the vacuum limit vac = 2(cL+cR)/(g-1).
+template <typename T>
+__device__ __forceinline__ bool hard_face(T pL, T pR, T du, T vac) {
+  return qdiv(fmax(pL, pR), fmin(pL, pR)) > T(1e6) || vac - du < T(0.05) * vac;
+}
+
 // Star state from a given initial guess p0 and the sound speeds cL, cR of
 // the two states (vacuum check, FP32 hard-face fallback, Newton).
 template <typename T>
@@ -655,8 +662,7 @@ __device__ __forceinline__ int exact_star_from(T rL, T uL, T pL, T cL, T rR, T u
   const T vac = gas.two_gm1 * (cL + cR);
   if (vac <= uR - uL) return ST_VACUUM;
   if constexpr (sizeof(T) == 4) {
-    const T ratio = qdiv(fmax(pL, pR), fmin(pL, pR));
-    if (ratio > T(1e6) || vac - (uR - uL) < T(0.05) * vac)
+    if (hard_face<T>(pL, pR, uR - uL, vac))
       return newton_star_fp64(p0, rL, uL, pL, rR, uR, pR, gas, ps, us, iters);
   }
   return newton_star<T>(p0, rL, uL, pL, cL, rR, uR, pR, cR, gas, newton_tol<T>(), ps, us, iters);

@@ -44,7 +44,8 @@ class hydro_stats_t(C.Structure):
     _fields_ = [("steps", C.c_longlong), ("faces", C.c_longlong), ("newton_iters", C.c_longlong),
                 ("fallbacks", C.c_longlong), ("mlp_faces", C.c_longlong), ("t", C.c_double),
                 ("last_dt", C.c_double), ("tile_x", C.c_int), ("tile_y", C.c_int),
-                ("zchunk", C.c_int), ("threads", C.c_int), ("tuned_us_per_step", C.c_double)]
+                ("zchunk", C.c_int), ("threads", C.c_int), ("tuned_us_per_step", C.c_double),
+                ("newton_faces", C.c_longlong * 3), ("newton_iters_by", C.c_longlong * 3)]
 
 
 class HydroError(RuntimeError):
@@ -208,7 +209,10 @@ def hydro_totals(h, nv):
 def hydro_stats(h):
     s = hydro_stats_t()
     _call("hydro_stats", h, C.byref(s))
-    return {k: getattr(s, k) for k, _ in hydro_stats_t._fields_}
+    out = {k: getattr(s, k) for k, _ in hydro_stats_t._fields_}
+    for k in ("newton_faces", "newton_iters_by"):
+        out[k] = [int(x) for x in out[k]]
+    return out
 
 
 def hydro_batch_create(lengths, eos, riemann, limiter, precision, stream):

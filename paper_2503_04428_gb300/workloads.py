@@ -181,20 +181,25 @@ def tube_lengths(ntubes=4096, seed=2, lo=256, hi=8192):
     return (lo + np.floor(r * (hi - lo + 1))).astype(np.int32)
 
 
-def tubes(ntubes=4096, seed=2, lo=256, hi=8192, gamma=5.0 / 3.0, perturb=0.0):
+def tubes(ntubes=4096, seed=2, lo=256, hi=8192, gamma=5.0 / 3.0, perturb=0.0, tube_range=None):
     """Batched exact-Riemann workload: ragged SoA (3, total cells), interface at x=0.5 of [0,1].
 
     perturb > 0 multiplies density and pressure of every cell by
-    1 + perturb U(-1,1) (a dense state in which no two neighbours are equal)."""
+    1 + perturb U(-1,1) (a dense state in which no two neighbours are equal).
+    tube_range = (b0, b1) keeps tubes b0..b1-1 of the ntubes-tube set (the
+    same tubes and values as in the whole set)."""
     lengths = tube_lengths(ntubes, seed, lo, hi)
     WL, WR = tube_states(ntubes, seed)
-    total = int(lengths.sum())
+    b0, b1 = (0, ntubes) if tube_range is None else (int(tube_range[0]), int(tube_range[1]))
+    start = int(lengths[:b0].sum())
+    total = int(lengths[b0:b1].sum())
     noise = None
     if perturb > 0:
-        noise = 1.0 + perturb * (2.0 * uniform01(seed + 0x68E31DA4, 2 * total).reshape(2, total) - 1.0)
+        noise = 1.0 + perturb * (2.0 * uniform01(seed + 0x68E31DA4, 2 * int(lengths.sum()))
+                                 .reshape(2, -1)[:, start:start + total] - 1.0)
     U = np.empty((3, total))
     off = 0
-    for b in range(ntubes):
+    for b in range(b0, b1):
         nb = int(lengths[b])
         x = (np.arange(nb) + 0.5) / nb
         left = x < 0.5
@@ -206,7 +211,7 @@ def tubes(ntubes=4096, seed=2, lo=256, hi=8192, gamma=5.0 / 3.0, perturb=0.0):
             p = p * noise[1, off:off + nb]
         U[:, off:off + nb] = conserved(gamma, rho, [u], p)
         off += nb
-    return dict(name="tubes%d" % ntubes, lengths=lengths, U=U, gamma=gamma, WL=WL, WR=WR,
+    return dict(name="tubes%d" % ntubes, lengths=lengths[b0:b1], U=U, gamma=gamma, WL=WL[b0:b1], WR=WR[b0:b1],
                 riemann=EXACT, limiter=MINMOD, cfl=0.8)
 
 

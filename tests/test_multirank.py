@@ -1,7 +1,9 @@
 """The multi-rank bench path on CPU: world_size 2 over gloo.
 
-Each rank builds its own tube set (no data exchange); the whole-job rate uses
-the slowest rank's time and the cells of all ranks."""
+The job at N ranks is N x 4096 tubes of the workload's distribution (one
+seed), cut into N contiguous ranges of about equal cell counts; each rank
+builds only its own range (no data exchange).  The whole-job rate uses the
+slowest rank's time and the cells of all ranks."""
 import os
 import socket
 
@@ -22,28 +24,60 @@ def _worker(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
-    from paper_2503_04428_gb300 import workloads as wl
-    lengths = wl.tube_lengths(64, bench.rank_seed(rank))
-    cells = int(lengths.sum())
+    w = bench.rank_tubes(world, rank, ntubes=64)
+    cells = int(w["lengths"].sum())
     elapsed = 1.0 + rank  # rank 1 is the slow one
     rate, t = bench.job_rate(elapsed, cells, 10, dist, "cpu")
-    out[rank] = (rate, t, cells)
+    out[rank] = (rate, t, cells, w["U"][:, :5].copy(), w["lengths"].copy())
     dist.destroy_process_group()
 
 
-def test_two_ranks_weak_scaling_rate():
+def test_two_ranks_partition_and_rate():
     world = 2
     port = _free_port()
     with mp.Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
+    from paper_2503_04428_gb300 import workloads as wl
+    whole = wl.tubes(64 * world, seed=2)
     cells = [res[r][2] for r in range(world)]
-    assert cells[0] != cells[1]  # each rank has its own tubes
+    # the two ranges are the whole tube set, in order, with no tube twice
+    assert np.array_equal(np.concatenate([res[0][4], res[1][4]]), whole["lengths"])
+    assert sum(cells) == int(whole["lengths"].sum())
+    # the second range starts where the first ends, with the same values
+    assert np.array_equal(res[1][3], whole["U"][:, cells[0]:cells[0] + 5])
+    # balanced to within one tube
+    assert abs(cells[0] - cells[1]) <= int(whole["lengths"].max())
     for r in range(world):
-        rate, t, _ = res[r]
+        rate, t, _, _, _ = res[r]
         assert t == 2.0  # max over ranks
         assert np.isclose(rate, sum(cells) * 10 / 2.0)
+
+
+def test_partition_by_cells_covers_and_balances():
+    import bench
+    from paper_2503_04428_gb300 import workloads as wl
+    for world in (1, 2, 3, 4, 8):
+        ln = wl.tube_lengths(4096 * world, 2)
+        parts = bench.partition_by_cells(ln, world)
+        assert parts[0][0] == 0 and parts[-1][1] == len(ln)
+        assert all(parts[r][1] == parts[r + 1][0] for r in range(world - 1))
+        cells = [int(ln[a:b].sum()) for a, b in parts]
+        assert max(cells) - min(cells) <= 2 * int(ln.max())
+    # one rank: exactly the 4096-tube workload
+    w = bench.rank_tubes(1, 0, ntubes=4096)
+    ref = wl.tubes(4096, seed=2)
+    assert np.array_equal(w["lengths"], ref["lengths"]) and np.array_equal(w["U"], ref["U"])
+
+
+def test_trajectory_positions():
+    import bench
+    assert bench.trajectory_positions(200) == list(range(200))
+    p = bench.trajectory_positions(20)
+    assert p == list(range(0, 200, 10))
+    assert len(bench.trajectory_positions(7)) == 7 and max(bench.trajectory_positions(7)) < 200
+    assert bench.trajectory_positions(250) == list(range(250))
 
 
 def test_single_process_rate():
