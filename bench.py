@@ -219,10 +219,12 @@ def train_mlp(H, torch, gamma, seed):
 
 def time_trajectory(torch, stream, b, U, positions, cfl=CFL):
     """From state U, advance the batch through the run and time each step at
-    `positions` alone (CUDA events on the launching stream around one graph
-    replay of one step); untimed steps in between.  Returns the summed
-    device time in seconds and the solver counters accumulated over the whole
-    run (steps 0 .. last position)."""
+    `positions` alone: CUDA events on the launching stream around one graph
+    replay of one step, queued without a host round trip
+    (hydro_batch_enqueue) behind the untimed steps before it, so that the
+    events bracket the step's kernel and nothing else.  Returns the summed
+    device time in seconds and the solver counters accumulated over the
+    whole run (steps 0 .. last position)."""
     b.set_state(U)
     s0 = b.stats()
     cur = 0
@@ -230,14 +232,19 @@ def time_trajectory(torch, stream, b, U, positions, cfl=CFL):
     torch.cuda.synchronize()
     for p in positions:
         if p > cur:
-            b.run(p - cur, cfl)
+            b.enqueue(p - cur, cfl)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        if not evs and p == 0:
+            # nothing queued ahead: keep the device busy while the host
+            # queues the first timed step, so that e0 fires right before it
+            torch.cuda._sleep(100000)
         e0.record(stream)
-        b.run(1, cfl)
+        b.enqueue(1, cfl)
         e1.record(stream)
         evs.append((e0, e1))
         cur = p + 1
+    b.run(0, cfl)  # waits, and reports a failed step
     torch.cuda.synchronize()
     t = sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1000.0
     s1 = b.stats()

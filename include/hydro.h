@@ -97,7 +97,7 @@ typedef struct {
   /* Batched exact solver, owned faces that ran Newton (not two identical
    * states) and their iterations, by category: [0] started from Toro's guess,
    * [1] from the network's guess, both in the handle's precision; [2] FP32
-   * faces solved in FP64 (pressure ratio above 1e6 or within 5 % of the
+   * faces solved in FP64 (pressure ratio above 1e6 or within 20 % of the
    * vacuum limit), whatever their guess.  Zero for grid handles. */
   long long newton_faces[3];
   long long newton_iters_by[3];
@@ -146,6 +146,41 @@ int hydro_set_dual_energy(hydro_t h, double eps);
 int hydro_set_sources(hydro_t h, int gravity, const double g0[3], double G, double Mc,
                       int heating, const double* heat_params);
 
+/* Domain decomposition (Sect. 3.3.1: one subdomain per process, with ghost
+ * layers exchanged between neighbours).  A grid handle may be one slab of a
+ * larger grid: the sides of ONE axis can be marked as exchanged, and their
+ * ghost cells are then the neighbouring slabs' cells, supplied by the caller
+ * before every step, instead of a boundary condition.
+ *
+ * hydro_set_exchange: mark side `side` (0 low, 1 high) of `axis` as
+ * exchanged; ghost_faces[0..1] are the two face coordinates beyond that side,
+ * nearest first (the neighbour's cells' geometry, so that a slab gives
+ * bit for bit the arithmetic of the whole grid).  Call before
+ * hydro_set_state; sides of a second axis are rejected (HYDRO_ERR_ARG).
+ * Halos, in the state's precision, are laid out [v][layer][cross section]:
+ * layer l is the ghost at distance l+1 from the side, and the cross section
+ * runs over the two other axes, the lower one fastest ((k, j) for axis 0,
+ * (k, i) for axis 1, (j, i) for axis 2): nv * 2 * cross elements.
+ * hydro_set_halo: the ghost layers of an exchanged side (host or device
+ * memory, `where`), used by the following steps.
+ * hydro_get_boundary: the state's two boundary layers at a side in the same
+ * layout (layer l = the cell at distance l from the side) -- exactly the
+ * halo the neighbour across that side needs.
+ * hydro_shell_masses: m_i = sum_jk rho dV of every radial cell of the
+ * current state (FP64, n[0] values, host), for monopole gravity (Eq. 4) on a
+ * grid split along r; hydro_set_inner_mass: the mass of all shells inside
+ * this slab (the sum of the inner slabs' m_i), where the enclosed-mass sum
+ * M_i = Mc + (4 pi/Omega)(sum_{i'<i} m_i' + m_i/2) starts.
+ * A step of a split grid is: exchange halos, (monopole) exchange shell
+ * masses, take the minimum of every slab's hydro_cfl_dt, hydro_step.
+ * hydro_run (device-side dt, graph) returns HYDRO_ERR_UNSUPPORTED on a grid
+ * with exchanged sides. */
+int hydro_set_exchange(hydro_t h, int axis, int side, const double ghost_faces[2]);
+int hydro_set_halo(hydro_t h, int axis, int side, const void* halo, int where);
+int hydro_get_boundary(hydro_t h, int axis, int side, void* out, int where);
+int hydro_shell_masses(hydro_t h, double* m_out);
+int hydro_set_inner_mass(hydro_t h, double mass);
+
 /* Copy a state in (validated on the device: rho > 0, P > 0, finite; on
  * failure the previous state is kept) and compute its CFL signal speed. */
 int hydro_set_state(hydro_t h, const void* U, int where);
@@ -182,6 +217,16 @@ int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int
  * (invalid state, Newton or a bounded device wait, HYDRO_ERR_TIMEOUT) leaves
  * the last good state and stops the remaining steps. */
 int hydro_batch_run(hydro_t h, int nsteps, double cfl);
+
+/* The steps of hydro_batch_run, queued on the handle's stream without
+ * waiting for them (the first call still runs the autotuner, synchronously).
+ * A step that fails on the device leaves the last good state, and the later
+ * queued steps do nothing; the failure is reported by the next
+ * hydro_batch_run (hydro_batch_run(h, 0, cfl) only waits and reports).  The
+ * paper has no counterpart: this lets a caller overlap its own work with the
+ * steps, or time a single step on the device without the host round trip
+ * of the status check. */
+int hydro_batch_enqueue(hydro_t h, int nsteps, double cfl);
 
 /* Advance a batch whose state lives in host memory: U_in (3 x total cells,
  * the layout of hydro_batch_set_state) is copied in, every tube advances

@@ -76,6 +76,11 @@ def lib():
         L.orc_set_dual_energy.argtypes = [C.c_void_p, C.c_double]
         L.orc_eos_rad.argtypes = [C.c_double] * 5 + [_D, _D, _D]
         L.orc_eos_rad_eint.argtypes = [C.c_double] * 5 + [_D, _D]
+        L.orc_set_exchange.argtypes = [C.c_void_p, C.c_int, C.c_int, _D]
+        L.orc_set_halo.argtypes = [C.c_void_p, C.c_int, C.c_int, _D]
+        L.orc_get_boundary.argtypes = [C.c_void_p, C.c_int, C.c_int, _D]
+        L.orc_shell_masses.argtypes = [C.c_void_p, _D]
+        L.orc_set_inner_mass.argtypes = [C.c_void_p, C.c_double]
         _lib = L
     return _lib
 
@@ -175,6 +180,34 @@ class Solver:
         out = np.empty(self.n[0])
         _check(lib().orc_shell_mass(self._h, _dp(out)), "shell_mass")
         return out
+
+    # --- domain decomposition (Sect. 3.3.1): exchanged sides of one axis ---
+    def halo_shape(self, axis):
+        """(nv, 2, cross section) of a halo of `axis` (the two other axes, lower fastest)."""
+        other = [self.n[d] for d in range(3) if d != axis]
+        return (self.nv, 2, other[1], other[0])
+
+    def set_exchange(self, axis, side, ghost_faces):
+        gf = np.ascontiguousarray(ghost_faces, dtype=np.float64)
+        assert gf.shape == (2,)
+        _check(lib().orc_set_exchange(self._h, axis, side, _dp(gf)), "set_exchange")
+
+    def set_halo(self, axis, side, halo):
+        a = np.ascontiguousarray(halo, dtype=np.float64).reshape(self.halo_shape(axis))
+        _check(lib().orc_set_halo(self._h, axis, side, _dp(a)), "set_halo")
+
+    def get_boundary(self, axis, side):
+        out = np.empty(self.halo_shape(axis))
+        _check(lib().orc_get_boundary(self._h, axis, side, _dp(out)), "get_boundary")
+        return out
+
+    def shell_masses(self):
+        out = np.empty(self.n[0])
+        _check(lib().orc_shell_masses(self._h, _dp(out)), "shell_masses")
+        return out
+
+    def set_inner_mass(self, mass):
+        _check(lib().orc_set_inner_mass(self._h, float(mass)), "set_inner_mass")
 
 
 def solver_from_case(case):

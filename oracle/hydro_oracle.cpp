@@ -545,6 +545,30 @@ struct Solver {
   std::vector<double> xfe[3];   // face coordinates including ghosts (n+2NG+1)
   std::vector<double> U;        // interior state [v][k][j][i]
   long long st_faces = 0, st_iters = 0, st_fallback = 0, st_mlp = 0;
+  /* Domain decomposition (Sect. 3.3.1: one subdomain per process, ghost
+   * layers exchanged with the neighbouring subdomains).  The sides of one
+   * axis, xaxis, may be exchanged: their ghosts are the neighbour's cells,
+   * given by the caller as halo[side] = [v][layer][cross section] (layer l =
+   * the ghost at distance l+1 from the boundary; the cross section runs over
+   * the two other axes, the lower axis fastest), and their geometry is that
+   * of those cells, from xg[side] = the NG face coordinates beyond the side,
+   * nearest first. */
+  int xaxis = -1;
+  bool xch[2] = {false, false};
+  double xg[2][NG] = {{0.0, 0.0}, {0.0, 0.0}};
+  std::vector<double> halo[2];
+  /* Monopole of a subdomain split along r: the mass of all shells inside it
+   * (reading R9's running sum where this subdomain's shells begin). */
+  double inner_mass = 0.0;
+
+  bool exch_ghost(int d, int g) const {
+    return d == xaxis && ((g < 0 && xch[0]) || (g >= n[d] && xch[1]));
+  }
+  /* Cells of the cross section of axis a: the two other axes. */
+  long cross(int a) const { return a == 0 ? (long)n[1] * n[2] : a == 1 ? (long)n[0] * n[2] : (long)n[0] * n[1]; }
+  long cross_idx(int a, int i, int j, int k) const {
+    return a == 0 ? (long)k * n[1] + j : a == 1 ? (long)k * n[0] + i : (long)j * n[0] + i;
+  }
 
   int m(int d) const { return d < dim ? n[d] + 2 * NG : 1; }
   int off(int d) const { return d < dim ? NG : 0; }
@@ -590,6 +614,13 @@ struct Solver {
       for (int gcell = -1; gcell >= -NG; --gcell) xfe[d][gcell + NG] = xfe[d][gcell + NG + 1] - width(gcell);
       for (int gcell = nn; gcell < nn + NG; ++gcell)
         xfe[d][gcell + NG + 1] = xfe[d][gcell + NG] + width(gcell);
+      /* exchanged sides: the neighbour's own faces */
+      if (d == xaxis) {
+        for (int l = 0; l < NG; ++l) {
+          if (xch[0]) xfe[d][NG - 1 - l] = xg[0][l];
+          if (xch[1]) xfe[d][nn + NG + 1 + l] = xg[1][l];
+        }
+      }
     }
   }
   double xlo(int d, int ie) const { return xfe[d][ie]; }
@@ -639,9 +670,11 @@ struct Solver {
    * h_r = dr, h_theta = r_i dtheta, h_phi = r_i sin(theta)_j dphi with
    * r_i the mid radius and sin(theta)_j the mean of the face sines. */
   double h(int d, int ie, int je, int ke) const {
-    /* geometry of the source cells (reading R6), interior extended indices */
-    int i = src(0, ie - off(0)) + off(0), j = src(1, je - off(1)) + off(1);
-    int idx[3] = {i, j, src(2, ke - off(2)) + off(2)};
+    /* geometry of the source cells (reading R6), interior extended indices;
+     * an exchanged ghost is a real cell of the neighbour with its own */
+    auto gidx = [&](int d2, int e) { return exch_ghost(d2, e - off(d2)) ? e : src(d2, e - off(d2)) + off(d2); };
+    int i = gidx(0, ie), j = gidx(1, je);
+    int idx[3] = {i, j, gidx(2, ke)};
     double w = xhi(d, idx[d]) - xlo(d, idx[d]);
     if (coords == ORC_CARTESIAN || d == 0) return w;
     double r = xc(0, i);
@@ -660,8 +693,15 @@ struct Solver {
         for (int ie = 0; ie < m(0); ++ie) {
           int src[3] = {ie - off(0), je - off(1), ke - off(2)};
           bool flip[3] = {false, false, false};
+          int layer = -1, side = 0;  // an exchanged ghost: its halo layer and side
           for (int d = 0; d < dim; ++d) {
             int g = src[d], nn = n[d];
+            if (exch_ghost(d, g)) {
+              side = g < 0 ? 0 : 1;
+              layer = g < 0 ? -1 - g : g - nn;
+              src[d] = 0;
+              continue;
+            }
             if (g < 0) {
               if (bc[d][0] == ORC_PERIODIC) g += nn;
               else if (bc[d][0] == ORC_TRANSMISSIVE) g = 0;
@@ -673,26 +713,39 @@ struct Solver {
             }
             src[d] = g;
           }
-          long s = iidx(src[0], src[1], src[2]);
           long e = eidx(ie, je, ke);
-          for (int v = 0; v < nv; ++v) Ue[(size_t)v * ne + e] = U[(size_t)v * ncell() + s];
+          if (layer >= 0) {
+            const long nx = cross(xaxis);
+            const long q = cross_idx(xaxis, src[0], src[1], src[2]);
+            for (int v = 0; v < nv; ++v)
+              Ue[(size_t)v * ne + e] = halo[side][((size_t)v * NG + layer) * nx + q];
+          } else {
+            long s = iidx(src[0], src[1], src[2]);
+            for (int v = 0; v < nv; ++v) Ue[(size_t)v * ne + e] = U[(size_t)v * ncell() + s];
+          }
           for (int d = 0; d < dim; ++d)
             if (flip[d]) Ue[(size_t)(1 + d) * ne + e] = -Ue[(size_t)(1 + d) * ne + e];
         }
   }
 
   /* Enclosed mass per radial cell (reading R9), FP64, fixed order. */
-  void monopole_mass(std::vector<double>& M) const {
+  /* Shell masses m_i = sum_jk rho dV (FP64, fixed order). */
+  void shell_masses(std::vector<double>& shell) const {
     int nr = n[0];
-    std::vector<double> shell(nr, 0.0);
+    shell.assign(nr, 0.0);
     for (int i = 0; i < nr; ++i)
       for (int k = 0; k < n[2]; ++k)
         for (int j = 0; j < n[1]; ++j)
           shell[i] += U[iidx(i, j, k)] * dV(i + off(0), j + off(1), k + off(2));
+  }
+  void monopole_mass(std::vector<double>& M) const {
+    int nr = n[0];
+    std::vector<double> shell;
+    shell_masses(shell);
     double omega = (std::cos(th_lo(off(1))) - std::cos(th_hi(off(1) + n[1] - 1))) *
                    (ph_hi(off(2) + n[2] - 1) - ph_lo(off(2)));
     M.assign(nr, 0.0);
-    double below = 0.0;
+    double below = inner_mass;
     for (int i = 0; i < nr; ++i) {
       M[i] = Mc + 4.0 * PI / omega * (below + 0.5 * shell[i]);
       below += shell[i];
@@ -1124,6 +1177,56 @@ int orc_shell_mass(orc_t h, double* M) {
   std::vector<double> m;
   h->s.monopole_mass(m);
   for (size_t i = 0; i < m.size(); ++i) M[i] = m[i];
+  return ORC_OK;
+}
+
+int orc_set_exchange(orc_t h, int axis, int side, const double* ghost_faces) {
+  Solver& s = h->s;
+  if (axis < 0 || axis >= s.dim || side < 0 || side > 1 || !ghost_faces) return ORC_ERR_ARG;
+  if (s.xaxis >= 0 && s.xaxis != axis) return ORC_ERR_ARG;  /* slabs: one axis */
+  s.xaxis = axis;
+  s.xch[side] = true;
+  for (int l = 0; l < NG; ++l) s.xg[side][l] = ghost_faces[l];
+  s.halo[side].assign((size_t)s.eos.nv() * NG * s.cross(axis), 0.0);
+  s.build_ext_faces();
+  return ORC_OK;
+}
+
+int orc_set_halo(orc_t h, int axis, int side, const double* halo) {
+  Solver& s = h->s;
+  if (axis != s.xaxis || side < 0 || side > 1 || !s.xch[side] || !halo) return ORC_ERR_ARG;
+  std::copy(halo, halo + s.halo[side].size(), s.halo[side].begin());
+  return ORC_OK;
+}
+
+int orc_get_boundary(orc_t h, int axis, int side, double* out) {
+  Solver& s = h->s;
+  if (axis < 0 || axis >= s.dim || side < 0 || side > 1 || !out) return ORC_ERR_ARG;
+  const int nv = s.eos.nv();
+  const long nx = s.cross(axis);
+  for (int v = 0; v < nv; ++v)
+    for (int l = 0; l < NG; ++l)
+      for (int k = 0; k < s.n[2]; ++k)
+        for (int j = 0; j < s.n[1]; ++j)
+          for (int i = 0; i < s.n[0]; ++i) {
+            int g = axis == 0 ? i : axis == 1 ? j : k;
+            int want = side == 0 ? l : s.n[axis] - 1 - l;
+            if (g != want) continue;
+            out[((size_t)v * NG + l) * nx + s.cross_idx(axis, i, j, k)] =
+                s.U[(size_t)v * s.ncell() + s.iidx(i, j, k)];
+          }
+  return ORC_OK;
+}
+
+int orc_shell_masses(orc_t h, double* m) {
+  std::vector<double> sm;
+  h->s.shell_masses(sm);
+  for (size_t i = 0; i < sm.size(); ++i) m[i] = sm[i];
+  return ORC_OK;
+}
+
+int orc_set_inner_mass(orc_t h, double mass) {
+  h->s.inner_mass = mass;
   return ORC_OK;
 }
 

@@ -69,6 +69,22 @@ int  orc_totals(orc_t h, double* out);
 int  orc_stats(orc_t h, long long* out);
 int  orc_shell_mass(orc_t h, double* M_out);   /* enclosed mass per radial cell (monopole) */
 
+/* Domain decomposition (Sect. 3.3.1): the sides of one axis may be exchanged
+ * with neighbouring subdomains.  set_exchange marks (axis, side) and gives
+ * the 2 face coordinates beyond it, nearest first (the neighbour's cells'
+ * geometry); set_halo gives its 2 ghost layers [nv][2][cross] (layer l = the
+ * ghost at distance l+1; the cross section runs over the two other axes, the
+ * lower one fastest); get_boundary returns the 2 boundary layers of the
+ * state in the same layout (layer l = the cell at distance l from the side),
+ * which is the neighbour's halo.  shell_masses: m_i = sum_jk rho dV per
+ * radial cell; set_inner_mass: the mass of the shells inside this subdomain
+ * (monopole of an r-split). */
+int  orc_set_exchange(orc_t h, int axis, int side, const double* ghost_faces);
+int  orc_set_halo(orc_t h, int axis, int side, const double* halo);
+int  orc_get_boundary(orc_t h, int axis, int side, double* out);
+int  orc_shell_masses(orc_t h, double* m_out);
+int  orc_set_inner_mass(orc_t h, double mass);
+
 /* Batched 1D tubes on [0,1], transmissive ends, each advanced nsteps at its own
  * CFL time step.  U is (3 x total cells), tubes concatenated per variable. */
 int  orc_batch_run(const int* lengths, int ntubes, double* U, double gamma, int riemann,

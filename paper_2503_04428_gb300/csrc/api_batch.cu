@@ -835,9 +835,9 @@ int hydro_batch_run_host(hydro_t h, const void* U_in, void* U_out, int nsteps, d
              : batch_run_host_t<float>(h, (const float*)U_in, (float*)U_out, nsteps, cfl, nparts);
 }
 
-int hydro_batch_run(hydro_t h, int nsteps, double cfl) {
-  if (!h || !h->batched) return berr("hydro_batch_run: batched handle required");
-  if (nsteps < 0 || !(cfl > 0.0)) return berr("hydro_batch_run: bad nsteps or cfl");
+int hydro_batch_enqueue(hydro_t h, int nsteps, double cfl) {
+  if (!h || !h->batched) return berr("hydro_batch_enqueue: batched handle required");
+  if (nsteps < 0 || !(cfl > 0.0)) return berr("hydro_batch_enqueue: bad nsteps or cfl");
   BatchState* bs = h->bs;
   int st;
   if ((st = autotune_batch(h, cfl))) return st;
@@ -864,6 +864,15 @@ int hydro_batch_run(hydro_t h, int nsteps, double cfl) {
   int s = 0;
   for (; s + BGRAPH_STEPS <= nsteps; s += BGRAPH_STEPS) HCK(cudaGraphLaunch(bs->graph_k, h->stream));
   for (; s < nsteps; ++s) HCK(cudaGraphLaunch(bs->graph, h->stream));
+  return HYDRO_OK;
+}
+
+int hydro_batch_run(hydro_t h, int nsteps, double cfl) {
+  if (!h || !h->batched) return berr("hydro_batch_run: batched handle required");
+  if (nsteps < 0 || !(cfl > 0.0)) return berr("hydro_batch_run: bad nsteps or cfl");
+  BatchState* bs = h->bs;
+  int st;
+  if ((st = hydro_batch_enqueue(h, nsteps, cfl))) return st;
   if ((st = read_bctrl(h))) return st;
   const int code = bs->bctrl_host->c.status;
   if (code == 0) return HYDRO_OK;

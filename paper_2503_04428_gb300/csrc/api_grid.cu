@@ -125,8 +125,40 @@ static int build_geometry(hydro_ctx* h) {
   }
   std::vector<void*> g(G_COUNT, nullptr);
   AxisExt ax[3];
+  // per extended cell, the two faces whose mid-point is the radius or whose
+  // sines give the mean polar sine of its physical widths
+  std::vector<double> gf_lo[3], gf_hi[3];
   for (int d = 0; d < 3; ++d) {
     ax[d] = axis_ext(xf[d], d < h->dim ? h->bc[d][0] : BC_PERIODIC, d < h->dim ? h->bc[d][1] : BC_PERIODIC);
+    const int me = (int)ax[d].w.size();
+    gf_lo[d].assign(me, 0.0);
+    gf_hi[d].assign(me, 0.0);
+    for (int k = 0; k < me; ++k) {
+      const int q = ax[d].src[k];
+      gf_lo[d][k] = xf[d][q];
+      gf_hi[d][k] = xf[d][q + 1];
+    }
+    if (d == h->xaxis) {
+      // exchanged sides: the ghosts are the neighbour's cells, with their
+      // own faces (the same operations as for an interior cell)
+      const int n = (int)xf[d].size() - 1;
+      if (h->xch[0]) {
+        ax[d].lo[1] = h->xg[0][0];
+        ax[d].w[1] = xf[d][0] - h->xg[0][0];
+        ax[d].lo[0] = h->xg[0][1];
+        ax[d].w[0] = h->xg[0][0] - h->xg[0][1];
+        gf_lo[d][1] = h->xg[0][0], gf_hi[d][1] = xf[d][0];
+        gf_lo[d][0] = h->xg[0][1], gf_hi[d][0] = h->xg[0][0];
+      }
+      if (h->xch[1]) {
+        ax[d].lo[n + 2] = xf[d][n];
+        ax[d].w[n + 2] = h->xg[1][0] - xf[d][n];
+        ax[d].lo[n + 3] = h->xg[1][0];
+        ax[d].w[n + 3] = h->xg[1][1] - h->xg[1][0];
+        gf_lo[d][n + 2] = xf[d][n], gf_hi[d][n + 2] = h->xg[1][0];
+        gf_lo[d][n + 3] = h->xg[1][0], gf_hi[d][n + 3] = h->xg[1][1];
+      }
+    }
     const int m = (int)ax[d].w.size();
     std::vector<double> idxc(m, 0.0), hw(m), iw(m);
     for (int k = 0; k < m; ++k) {
@@ -148,15 +180,9 @@ static int build_geometry(hydro_ctx* h) {
     const int m0 = (int)ax[0].w.size(), m1 = (int)ax[1].w.size();
     std::vector<double> ir(m0, 1.0), is(m1, 1.0);
     if (sph) {
-      // radius and mean polar sine of the source cell
-      for (int k = 0; k < m0; ++k) {
-        const int q = ax[0].src[k];
-        ir[k] = 1.0 / (0.5 * (xf[0][q] + xf[0][q + 1]));
-      }
-      for (int k = 0; k < m1; ++k) {
-        const int q = ax[1].src[k];
-        is[k] = 1.0 / (0.5 * (std::sin(xf[1][q]) + std::sin(xf[1][q + 1])));
-      }
+      // radius and mean polar sine of the source cell (an exchanged ghost's own)
+      for (int k = 0; k < m0; ++k) ir[k] = 1.0 / (0.5 * (gf_lo[0][k] + gf_hi[0][k]));
+      for (int k = 0; k < m1; ++k) is[k] = 1.0 / (0.5 * (std::sin(gf_lo[1][k]) + std::sin(gf_hi[1][k])));
     }
     int st;
     if ((st = upload<T>(h, ir, &g[G_IR]))) return st;
@@ -330,6 +356,9 @@ static SweepArgs<T> sweep_args(hydro_ctx* h, double dt_host, double cfl, double 
   a.zchunk = h->zchunk;
   a.ctrl = ctrl;
   a.geo = geom_of<T>(h);
+  a.xaxis = h->xaxis;
+  a.halo[0] = (const T*)h->halo_d[0];
+  a.halo[1] = (const T*)h->halo_d[1];
   return a;
 }
 
@@ -344,7 +373,8 @@ static int launch_step_t(hydro_ctx* h, double dt_host, double cfl, double t_end,
     HCK(cudaGetLastError());
     monopole_kernel<T><<<1, MONO_THREADS, 0, h->stream>>>(ctrl, h->shell_partial, h->shell_nchunks, h->n[0],
                                                  h->dvol[0], h->rc_d, h->G, h->Mc,
-                                                 4.0 * PI / h->omega, h->shell, (T*)h->gmono);
+                                                 4.0 * PI / h->omega, h->inner_mass, h->shell,
+                                                 (T*)h->gmono);
     HCK(cudaGetLastError());
   }
   SweepArgs<T> a = sweep_args<T>(h, dt_host, cfl, t_end, ctrl);
@@ -753,6 +783,117 @@ int hydro_set_sources(hydro_t h, int gravity, const double g0[3], double G, doub
   return HYDRO_OK;
 }
 
+int hydro_set_exchange(hydro_t h, int axis, int side, const double ghost_faces[2]) {
+  if (!h || h->batched) return arg_error("hydro_set_exchange: grid handle required");
+  if (axis < 0 || axis >= h->dim || side < 0 || side > 1 || !ghost_faces)
+    return arg_error("hydro_set_exchange: bad axis, side or face coordinates");
+  if (h->xaxis >= 0 && h->xaxis != axis)
+    return arg_error("hydro_set_exchange: only the sides of one axis can be exchanged (slabs)");
+  const double f0 = ghost_faces[0], f1 = ghost_faces[1];
+  const std::vector<double>& xf = h->faces[axis];
+  const bool ok = side == 0 ? (f1 < f0 && f0 < xf.front()) : (xf.back() < f0 && f0 < f1);
+  if (!ok || !std::isfinite(f0) || !std::isfinite(f1))
+    return arg_error("hydro_set_exchange: the two faces beyond the side must continue the axis monotonically");
+  const long long nx = axis == 0 ? (long long)h->n[1] * h->n[2]
+                     : axis == 1 ? (long long)h->n[0] * h->n[2] : (long long)h->n[0] * h->n[1];
+  const size_t bytes = (size_t)h->nv * 2 * nx * h->esize;
+  int st;
+  if (!h->halo_d[side]) {
+    if ((st = h->arena.alloc(&h->halo_d[side], bytes))) return st;
+    HCK(cudaMemsetAsync(h->halo_d[side], 0, bytes, h->stream));
+  }
+  if (!h->pack_d && (st = h->arena.alloc(&h->pack_d, bytes))) return st;
+  h->xaxis = axis;
+  h->xch[side] = true;
+  h->xg[side][0] = f0;
+  h->xg[side][1] = f1;
+  h->bc[axis][side] = BC_EXCHANGED;
+  st = h->precision == 64 ? build_geometry<double>(h) : build_geometry<float>(h);
+  if (st) return st;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  HCK(cudaStreamSynchronize(h->stream));
+  return HYDRO_OK;
+}
+
+static long long halo_bytes(const hydro_ctx* h, int axis) {
+  const long long nx = axis == 0 ? (long long)h->n[1] * h->n[2]
+                     : axis == 1 ? (long long)h->n[0] * h->n[2] : (long long)h->n[0] * h->n[1];
+  return (long long)h->nv * 2 * nx * (long long)h->esize;
+}
+
+int hydro_set_halo(hydro_t h, int axis, int side, const void* halo, int where) {
+  if (!h || h->batched || !halo) return arg_error("hydro_set_halo: grid handle and halo required");
+  if (axis != h->xaxis || side < 0 || side > 1 || !h->xch[side])
+    return arg_error("hydro_set_halo: that side is not exchanged (hydro_set_exchange first)");
+  HCK(cudaMemcpyAsync(h->halo_d[side], halo, (size_t)halo_bytes(h, axis),
+                      where == HYDRO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  if (where != HYDRO_DEVICE) HCK(cudaStreamSynchronize(h->stream));
+  return HYDRO_OK;
+}
+
+int hydro_get_boundary(hydro_t h, int axis, int side, void* out, int where) {
+  if (!h || h->batched || !out) return arg_error("hydro_get_boundary: grid handle and output required");
+  if (axis < 0 || axis >= h->dim || side < 0 || side > 1) return arg_error("hydro_get_boundary: bad axis or side");
+  int st;
+  if (!h->pack_d && (st = h->arena.alloc(&h->pack_d, (size_t)halo_bytes(h, axis)))) return st;
+  if (h->xaxis >= 0 && axis != h->xaxis) return arg_error("hydro_get_boundary: not the exchanged axis");
+  void* dst = where == HYDRO_DEVICE ? out : h->pack_d;
+  const long long n = halo_bytes(h, axis) / (long long)h->esize;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 4LL * h->num_sms);
+  if (h->precision == 64)
+    pack_boundary_kernel<double><<<blocks, 256, 0, h->stream>>>(h->ctrl, (const double*)h->buf[0],
+                                                                (const double*)h->buf[1], h->ncell, h->n[0],
+                                                                h->n[1], h->n[2], h->nv, axis, side,
+                                                                (double*)dst);
+  else
+    pack_boundary_kernel<float><<<blocks, 256, 0, h->stream>>>(h->ctrl, (const float*)h->buf[0],
+                                                               (const float*)h->buf[1], h->ncell, h->n[0],
+                                                               h->n[1], h->n[2], h->nv, axis, side, (float*)dst);
+  HCK(cudaGetLastError());
+  if (where != HYDRO_DEVICE)
+    HCK(cudaMemcpyAsync(out, h->pack_d, (size_t)halo_bytes(h, axis), cudaMemcpyDeviceToHost, h->stream));
+  HCK(cudaStreamSynchronize(h->stream));
+  return HYDRO_OK;
+}
+
+int hydro_shell_masses(hydro_t h, double* m_out) {
+  if (!h || h->batched || !m_out) return arg_error("hydro_shell_masses: grid handle and output required");
+  if (h->gravity != HYDRO_GRAV_POINT_MONOPOLE)
+    return arg_error("hydro_shell_masses: the handle has no monopole gravity");
+  dim3 gb((h->n[0] + 31) / 32, h->shell_nchunks), tb(32, 8);
+  if (h->precision == 64)
+    shell_partial_kernel<double><<<gb, tb, 0, h->stream>>>(h->ctrl, (const double*)h->buf[0],
+                                                           (const double*)h->buf[1], h->ncell, h->n[0], h->n[1],
+                                                           h->n[2], h->shell_kchunk, h->dvol[1], h->dvol[2],
+                                                           h->shell_partial);
+  else
+    shell_partial_kernel<float><<<gb, tb, 0, h->stream>>>(h->ctrl, (const float*)h->buf[0],
+                                                          (const float*)h->buf[1], h->ncell, h->n[0], h->n[1],
+                                                          h->n[2], h->shell_kchunk, h->dvol[1], h->dvol[2],
+                                                          h->shell_partial);
+  HCK(cudaGetLastError());
+  shell_mass_kernel<<<(h->n[0] + 127) / 128, 128, 0, h->stream>>>(h->shell_partial, h->shell_nchunks, h->n[0],
+                                                                  h->dvol[0], h->shell);
+  HCK(cudaGetLastError());
+  HCK(cudaMemcpyAsync(m_out, h->shell, sizeof(double) * h->n[0], cudaMemcpyDeviceToHost, h->stream));
+  HCK(cudaStreamSynchronize(h->stream));
+  return HYDRO_OK;
+}
+
+int hydro_set_inner_mass(hydro_t h, double mass) {
+  if (!h || h->batched) return arg_error("hydro_set_inner_mass: grid handle required");
+  if (!std::isfinite(mass) || mass < 0.0) return arg_error("hydro_set_inner_mass: need a finite mass >= 0");
+  h->inner_mass = mass;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return HYDRO_OK;
+}
+
 int hydro_set_state(hydro_t h, const void* U, int where) {
   if (!h || !U) return arg_error("hydro_set_state: null argument");
   if (h->batched) return hydro_batch_set_state_impl(h, U, where);
@@ -822,6 +963,11 @@ int hydro_step(hydro_t h, double dt) {
 int hydro_run(hydro_t h, int nsteps, double cfl, double t_end, double* t_out) {
   if (!h || h->batched) return arg_error("hydro_run: grid handle required");
   if (nsteps < 0 || !(cfl > 0.0)) return arg_error("hydro_run: bad nsteps or cfl");
+  if (h->xaxis >= 0) {
+    set_error("hydro_run: a grid with exchanged sides needs its halos (and the global dt) before every step: "
+              "use hydro_step");
+    return HYDRO_ERR_UNSUPPORTED;
+  }
   int st;
   if ((st = autotune_grid(h, cfl))) return st;
   if (!h->graph || h->graph_cfl != cfl || h->graph_tend != t_end) {

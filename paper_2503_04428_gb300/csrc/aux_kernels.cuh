@@ -147,11 +147,13 @@ template <typename T>
 __global__ void __launch_bounds__(MONO_THREADS)
     monopole_kernel(const Ctrl* ctrl, const double* partial, int nchunks, int n0,
                     const double* __restrict__ da, const double* __restrict__ rc, double G,
-                    double Mc, double four_pi_over_omega, double* shell, T* gmono) {
+                    double Mc, double four_pi_over_omega, double inner, double* shell, T* gmono) {
   if (((volatile const Ctrl*)ctrl)->status != 0) return;
   __shared__ double sh[MONO_THREADS];
   const int tid = threadIdx.x;
-  double carry = 0.0;  // mass of all shells of the previous chunks
+  // mass of all shells of the previous chunks, starting from the shells
+  // inside this subdomain (0 unless the grid is one slab of an r-split)
+  double carry = inner;
   for (int base = 0; base < n0; base += MONO_THREADS) {
     const int i = base + tid;
     double m = 0.0;
@@ -176,6 +178,42 @@ __global__ void __launch_bounds__(MONO_THREADS)
     }
     carry += sh[MONO_THREADS - 1];
     __syncthreads();
+  }
+}
+
+// Shell masses m_i = (sum of the chunk partials) * a_i, summed as in
+// monopole_kernel, for the caller of a domain-decomposed run.
+__global__ void shell_mass_kernel(const double* partial, int nchunks, int n0, const double* __restrict__ da,
+                                  double* m) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n0) return;
+  double s = 0.0;
+  for (int q = 0; q < nchunks; ++q) s += partial[(long long)q * n0 + i];
+  m[i] = s * da[i];
+}
+
+// The 2 boundary layers of a state at side `side` of axis `axis`, as
+// [v][layer][cross section] (layer l = the cell at distance l from the side;
+// the cross section runs over the two other axes, the lower one fastest):
+// the halo that the neighbouring subdomain reads.
+template <typename T>
+__global__ void pack_boundary_kernel(const Ctrl* ctrl, const T* A, const T* B, long long ncell, int n0, int n1,
+                                     int n2, int nv, int axis, int side, T* out) {
+  const T* U = ((volatile const Ctrl*)ctrl)->cur ? B : A;
+  const int na = axis == 0 ? n0 : axis == 1 ? n1 : n2;
+  const long long nx = axis == 0 ? (long long)n1 * n2 : axis == 1 ? (long long)n0 * n2 : (long long)n0 * n1;
+  const long long total = (long long)nv * 2 * nx;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long q = t % nx;
+    const int l = (int)((t / nx) % 2);
+    const int v = (int)(t / (2 * nx));
+    const int g = side == 0 ? min(l, na - 1) : max(na - 1 - l, 0);
+    long long c;
+    if (axis == 0) c = q * n0 + g;                                          // q = k n1 + j
+    else if (axis == 1) c = ((q / n0) * n1 + g) * n0 + q % n0;            // q = k n0 + i
+    else c = (long long)g * n1 * n0 + q;                                   // q = j n0 + i
+    out[t] = U[(long long)v * ncell + c];
   }
 }
 

@@ -11,7 +11,9 @@
 
 namespace hydro {
 
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+// BC_EXCHANGED: a side whose ghosts are a neighbouring subdomain's cells,
+// supplied by the caller (domain decomposition, Sect. 3.3.1).
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_EXCHANGED = 3 };
 enum { GRAV_NONE = 0, GRAV_UNIFORM = 1, GRAV_POINT = 2, GRAV_MONO = 3 };
 enum { HEAT_NONE = 0, HEAT_CONST = 1, HEAT_NI56 = 2 };
 
@@ -88,6 +90,12 @@ struct SweepArgs {
   int zchunk;             // planes per CTA along axis 2 (3D)
   Ctrl* ctrl;
   Geom<T> geo;
+  // domain decomposition: the axis whose sides may be BC_EXCHANGED (-1 none)
+  // and their ghost layers [v][layer][cross section] (layer l = the ghost at
+  // distance l+1 from the side; the cross section runs over the two other
+  // axes, the lower one fastest)
+  int xaxis;
+  const T* halo[2];
 };
 
 template <typename T, int DIM>

@@ -516,7 +516,11 @@ __device__ __forceinline__ T toro_guess(T rL, T uL, T pL, T cL, T rR, T uR, T pR
 
 // Newton on f_L(p) + f_R(p) + (u_R - u_L) = 0 from p0: stop when the
 // relative change 2|dp|/(p_k + p_{k-1}) < tol, then take one more step.
-// Negative iterates are clamped to 1e-14 of the mean pressure.
+// Negative iterates are clamped to 1e-14 of the mean pressure.  In FP32 the
+// iteration also stops when the residual is within 8 ulp of the sum of the
+// magnitudes of its terms: the rounding of f_L + f_R + du then decides the
+// step, and no later iterate is better determined (near vacuum, where the
+// two rarefaction terms nearly cancel du, the 1e-6 change is never reached).
 template <typename T>
 __device__ __forceinline__ int newton_star(T p, T rL, T uL, T pL, T cL, T rR, T uR, T pR, T cR,
                                            const Gas<T>& gas, T tol, T& ps, T& us, int& iters) {
@@ -529,13 +533,17 @@ __device__ __forceinline__ int newton_star(T p, T rL, T uL, T pL, T cL, T rR, T 
   while (it < 100) {
     press_fn(p, rL, pL, cL, gas, fL, dfL);
     press_fn(p, rR, pR, cR, gas, fR, dfR);
-    T pn = p - qdiv(fL + fR + du, dfL + dfR);
+    const T res = fL + fR + du;
+    T pn = p - qdiv(res, dfL + dfR);
     if (pn < T(0)) pn = pfloor;
     ++it;
     const T ch = qdiv(T(2) * fabs(pn - p), pn + p);
     p = pn;
     if (conv) break;
     if (ch < tol) conv = true;
+    if constexpr (sizeof(T) == 4) {
+      if (fabs(res) <= T(8 * 1.1920929e-7) * (fabs(fL) + fabs(fR) + fabs(du))) conv = true;
+    }
   }
   iters = it;
   if (!conv) return ST_NEWTON;
@@ -631,7 +639,7 @@ __device__ __forceinline__ Gas<double> gas_double(const Gas<float>& g) {
 }
 
 // Star state of one face.  guess_in > 0 replaces Toro's guess (MLP).  In FP32
-// a face near vacuum (margin below 5 %) or with a pressure ratio above 1e6
+// a face near vacuum (margin below 20 %) or with a pressure ratio above 1e6
 // is solved in FP64, where the FP32 pressure function loses digits.
 // The FP64 Newton solve of an FP32 face near vacuum or with a pressure ratio
 // above 1e6 (reading R12).  Kept out of line: it is rare, and its FP64 code
@@ -648,10 +656,12 @@ static __device__ __noinline__ int newton_star_fp64(float p0, float rL, float uL
 }
 
 // An FP32 face that is solved in FP64 (reading R12): pressure ratio above
-// 1e6, or a velocity jump within 5 % of the vacuum limit vac = 2(cL+cR)/(g-1).
+// 1e6, or a velocity jump within 20 % of the vacuum limit vac =
+// 2(cL+cR)/(g-1), where the FP32 residual loses more than ~5 of its bits to
+// the cancellation of the two rarefaction terms against du.
 template <typename T>
 __device__ __forceinline__ bool hard_face(T pL, T pR, T du, T vac) {
-  return qdiv(fmax(pL, pR), fmin(pL, pR)) > T(1e6) || vac - du < T(0.05) * vac;
+  return qdiv(fmax(pL, pR), fmin(pL, pR)) > T(1e6) || vac - du < T(0.2) * vac;
 }
 
 // Star state from a given initial guess p0 and the sound speeds cL, cR of

@@ -83,6 +83,15 @@ struct hydro_ctx {
   int tile_x = 0, tile_y = 0, threads = 0;
   double tuned_us = 0.0;
   bool tuned = false;
+  // domain decomposition (Sect. 3.3.1): exchanged sides of axis xaxis, the
+  // two face coordinates beyond each (nearest first), their halo buffers
+  // [nv][2][cross section] on the device, and the monopole's inner mass
+  int xaxis = -1;
+  bool xch[2] = {false, false};
+  double xg[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  void* halo_d[2] = {nullptr, nullptr};
+  void* pack_d = nullptr;    // staging of hydro_get_boundary for host output
+  double inner_mass = 0.0;
   // graph of one device-dt step
   cudaGraphExec_t graph = nullptr;
   double graph_cfl = -1.0, graph_tend = -2.0;

@@ -84,8 +84,14 @@ struct SweepShape {
 
 // Ghost mapping of one axis (periodic wrap, transmissive copy of the edge
 // cell, reflective mirror with the normal momentum negated).  g in [-2, n+1].
-__device__ __forceinline__ int map_axis(int g, int n, int lo, int hi, bool& flip) {
+// A ghost of an exchanged side (domain decomposition) sets `layer` to its
+// distance - 1 from the side and returns 0; layer stays -1 otherwise.
+__device__ __forceinline__ int map_axis(int g, int n, int lo, int hi, bool& flip, int& layer) {
   flip = false;
+  if ((g < 0 && lo == BC_EXCHANGED) || (g >= n && hi == BC_EXCHANGED)) {
+    layer = g < 0 ? -1 - g : g - n;
+    return 0;
+  }
   if (g < 0) {
     if (lo == BC_PERIODIC) return g + n;
     if (lo == BC_TRANSMISSIVE) return 0;
@@ -199,20 +205,39 @@ struct Sweep {
   __device__ void load_plane(int gz) {
     const int n0 = a.n[0], n1 = a.n[1];
     bool fz = false;
-    const int sz = DIM == 3 ? map_axis(gz, a.n[2], a.bc[2][0], a.bc[2][1], fz) : 0;
+    int lz = -1;
+    const int sz = DIM == 3 ? map_axis(gz, a.n[2], a.bc[2][0], a.bc[2][1], fz, lz) : 0;
     const int slot = wslot(gz);
     const int nvact = 2 + DIM + a.ns;
     for (int idx = threadIdx.x; idx < S::WPL; idx += NT) {
       const int ex = idx % EX, ey = idx / EX;
       const int gi = min(x0 - 2 + ex, n0 + 1);
       bool fx, fy = false;
-      const int si = map_axis(gi, n0, a.bc[0][0], a.bc[0][1], fx);
-      int sj = 0;
-      if (DIM >= 2) sj = map_axis(min(y0 - HY + ey, n1 + 1), n1, a.bc[1][0], a.bc[1][1], fy);
-      const long long c = ((long long)sz * n1 + sj) * n0 + si;
+      int lx = -1, ly = -1;
+      const int si = map_axis(gi, n0, a.bc[0][0], a.bc[0][1], fx, lx);
+      int sj = 0, gj = 0;
+      if (DIM >= 2) {
+        gj = min(y0 - HY + ey, n1 + 1);
+        sj = map_axis(gj, n1, a.bc[1][0], a.bc[1][1], fy, ly);
+      }
       T u[NV], w[NV];
+      const int layer = max(lx, max(ly, lz));  // >= 0: a ghost of an exchanged side
+      if (layer < 0) {
+        const long long c = ((long long)sz * n1 + sj) * n0 + si;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) u[v] = v < nvact ? __ldg(Uin + (long long)v * a.ncell + c) : T(0);
+        for (int v = 0; v < NV; ++v) u[v] = v < nvact ? __ldg(Uin + (long long)v * a.ncell + c) : T(0);
+      } else {
+        // the neighbour subdomain's cell, from the halo of that side; the
+        // other axes are mapped (and flipped) as for any ghost
+        const int side = (lx >= 0 ? gi : ly >= 0 ? gj : gz) < 0 ? 0 : 1;
+        const long long nx = a.xaxis == 0 ? (long long)n1 * a.n[2] : a.xaxis == 1 ? (long long)n0 * a.n[2]
+                                                                                 : (long long)n0 * n1;
+        const long long q = a.xaxis == 0 ? (long long)sz * n1 + sj : a.xaxis == 1 ? (long long)sz * n0 + si
+                                                                                 : (long long)sj * n0 + si;
+        const T* hp = a.halo[side] + (long long)layer * nx + q;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = v < nvact ? hp[(long long)v * 2 * nx] : T(0);
+      }
       if (fx) u[1] = -u[1];
       if (DIM >= 2 && fy) u[2] = -u[2];
       if (DIM == 3 && fz) u[3] = -u[3];

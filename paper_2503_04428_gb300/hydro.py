@@ -75,6 +75,7 @@ _SIGS = {
     "hydro_batch_create": [_I, C.c_int, C.POINTER(hydro_eos), C.c_int, C.c_int, C.c_int, _VP,
                            C.POINTER(_VP)],
     "hydro_batch_run": [_VP, C.c_int, C.c_double],
+    "hydro_batch_enqueue": [_VP, C.c_int, C.c_double],
     "hydro_harvest_begin": [_VP, C.c_long, C.c_double, C.c_ulonglong],
     "hydro_harvest_get": [_VP, _D, C.c_long, C.POINTER(C.c_long)],
     "hydro_mlp_set": [_VP, _F, C.c_int],
@@ -91,6 +92,11 @@ _SIGS = {
     "hydro_batch_run_host": [_VP, _VP, _VP, C.c_int, C.c_double, C.c_int],
     "hydro_exact_sample": [_D, _D, C.c_long, C.c_double, C.POINTER(C.c_longlong), _D, C.c_long, _D],
     "hydro_batch_times": [_VP, _D],
+    "hydro_set_exchange": [_VP, C.c_int, C.c_int, _D],
+    "hydro_set_halo": [_VP, C.c_int, C.c_int, _VP, C.c_int],
+    "hydro_get_boundary": [_VP, C.c_int, C.c_int, _VP, C.c_int],
+    "hydro_shell_masses": [_VP, _D],
+    "hydro_set_inner_mass": [_VP, C.c_double],
     "hydro_last_error": [],
 }
 
@@ -418,6 +424,43 @@ class Grid:
     def stats(self):
         return hydro_stats(self.h)
 
+    # --- domain decomposition (Sect. 3.3.1): exchanged sides of one axis ---
+    def halo_shape(self, axis):
+        """(nv, 2, cross section) of a halo of `axis` (the two other axes, lower fastest)."""
+        other = [self.n[d] for d in range(3) if d != axis]
+        return (self.nv, 2, other[1], other[0])
+
+    def set_exchange(self, axis, side, ghost_faces):
+        gf = np.ascontiguousarray(ghost_faces, dtype=np.float64)
+        if gf.shape != (2,):
+            raise ValueError("ghost_faces: the two face coordinates beyond the side")
+        _call("hydro_set_exchange", self.h, axis, side, gf.ctypes.data_as(_D))
+
+    def set_halo(self, axis, side, halo):
+        if hasattr(halo, "data_ptr"):
+            p, where = _ptr(halo)
+            _call("hydro_set_halo", self.h, axis, side, p, where)
+        else:
+            a = np.ascontiguousarray(halo, dtype=self.dtype).reshape(self.halo_shape(axis))
+            _call("hydro_set_halo", self.h, axis, side, a.ctypes.data, HYDRO_HOST)
+
+    def get_boundary(self, axis, side, out=None):
+        if out is not None:
+            p, where = _ptr(out)
+            _call("hydro_get_boundary", self.h, axis, side, p, where)
+            return out
+        a = np.empty(self.halo_shape(axis), dtype=self.dtype)
+        _call("hydro_get_boundary", self.h, axis, side, a.ctypes.data, HYDRO_HOST)
+        return a
+
+    def shell_masses(self):
+        out = np.empty(self.n[0])
+        _call("hydro_shell_masses", self.h, out.ctypes.data_as(_D))
+        return out
+
+    def set_inner_mass(self, mass):
+        _call("hydro_set_inner_mass", self.h, float(mass))
+
     def close(self):
         if getattr(self, "h", None):
             hydro_destroy(self.h)
@@ -461,6 +504,11 @@ class Batch:
 
     def run(self, nsteps, cfl):
         hydro_batch_run(self.h, nsteps, cfl)
+
+    def enqueue(self, nsteps, cfl):
+        """Queue nsteps steps without waiting (hydro_batch_enqueue); a device
+        failure is reported by the next run()."""
+        _call("hydro_batch_enqueue", self.h, nsteps, cfl)
 
     def stats(self):
         return hydro_stats(self.h)

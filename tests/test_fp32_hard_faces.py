@@ -1,20 +1,25 @@
 """FP32 exact-solver faces that are solved in FP64, and their neighbourhood, against the oracle.
 
 The FP32 form solves a face in FP64 when its pressure ratio exceeds 1e6 or
-its velocity jump du = u_R - u_L comes within 5 % of the vacuum limit
+its velocity jump du = u_R - u_L comes within 20 % of the vacuum limit
 vac = 2 (c_L + c_R)/(gamma - 1), where the FP32 pressure functions lose
-their digits (reading R12).  The workload's own jumps stop at a pressure
-ratio of 1e4, so these cases are built here:
+their digits (reading R12).  The FP32 form computes with gamma rounded to
+FP32, so its star states are compared with the oracle's at that gamma (near
+vacuum p* moves by ~1e-5 between gamma = 5/3 and its FP32 rounding).  The
+workload's own jumps stop at a pressure ratio of 1e4, so these cases are
+built here:
 
 - star states of faces inside the FP64 band (ratio 2e6-1e8, or du between
-  0.95 and 0.97 of vac): the FP64 Newton solve of the FP32-rounded data, so
+  0.82 and 0.97 of vac): the FP64 Newton solve of the FP32-rounded data, so
   p* and u* must equal the oracle's solve of the same data up to the final
   rounding to FP32 (2 ulp);
-- faces just outside the band, solved in FP32 (ratio 1e4-5e5, du from 0.70
-  to 0.94 of vac), where the bound on p* follows from the rounding of the
-  data: near vacuum p* ~ (vac - du)^(1/z) with z = (gamma-1)/(2 gamma), so
-  a relative error 4 eps32 vac/(vac - du) of the margin becomes 1/z times
-  that in p*, on top of Newton's own FP32 stopping rule (1e-6, polished);
+- faces just outside the band, solved in FP32 (ratio 1e4-5e5, du from 0.40
+  to 0.78 of vac), where the bound on p* follows from the rounding of the
+  residual r(p) = f_L(p) + f_R(p) + du (Toro's pressure functions): k ulp of
+  |f_L| + |f_R| + |du| move the root by kappa = (|f_L| + |f_R| + |du|) /
+  (p* r'(p*)) times k eps32 relative (near vacuum the terms cancel to the
+  margin vac - du, and kappa ~ vac/(z (vac - du)), z = (gamma-1)/(2 gamma)),
+  on top of Newton's own FP32 stopping rule (1e-6, polished);
 - whole FP32 tubes whose interface has a pressure ratio of 2e6-1e8, stepped
   against the oracle with the per-step FP32 bars of tests/parity.py, with
   the FP64 category of the solver counters showing that the FP64 path ran.
@@ -29,6 +34,7 @@ from parity import check
 pytestmark = pytest.mark.gpu
 
 G = 5.0 / 3.0
+G32 = float(np.float32(G))  # the FP32 form's gamma
 EPS32 = 2.0 ** -24
 
 
@@ -59,13 +65,26 @@ def _faces(n, seed, ratio_lo, ratio_hi, vac_lo, vac_hi):
     return WL, WR
 
 
-def _oracle(WL, WR):
-    out = np.array([O.exact_star(G, WL[i], WR[i])[:2] for i in range(len(WL))])
+def _kappa(W, p, gamma=G32):
+    """|f_K(p)| and f_K'(p) of Toro's pressure function for the states W (n x 3)."""
+    r, pk = W[:, 0], W[:, 2]
+    c = np.sqrt(gamma * pk / r)
+    A, B = 2.0 / ((gamma + 1.0) * r), (gamma - 1.0) / (gamma + 1.0) * pk
+    shock = p > pk
+    q = np.sqrt(A / (p + B))
+    f = np.where(shock, (p - pk) * q, 2.0 * c / (gamma - 1.0) * ((p / pk) ** ((gamma - 1.0) / (2.0 * gamma)) - 1.0))
+    df = np.where(shock, q * (1.0 - 0.5 * (p - pk) / (B + p)),
+                  (p / pk) ** (-(gamma + 1.0) / (2.0 * gamma)) / (r * c))
+    return np.abs(f), df
+
+
+def _oracle(WL, WR, gamma=G32):
+    out = np.array([O.exact_star(gamma, WL[i], WR[i])[:2] for i in range(len(WL))])
     return out[:, 0], out[:, 1]
 
 
 def test_fp32_faces_in_the_fp64_band(hydro_lib):
-    WL, WR = _faces(4000, 41, 2e6, 1e8, 0.95, 0.97)
+    WL, WR = _faces(4000, 41, 2e6, 1e8, 0.82, 0.97)
     ps, us, it = hydro_lib.hydro_exact_solve(WL, WR, G, precision=32)
     po, uo = _oracle(WL, WR)
     assert np.all(it > 0) and np.all(ps > 0)
@@ -78,14 +97,15 @@ def test_fp32_faces_in_the_fp64_band(hydro_lib):
 
 
 def test_fp32_faces_next_to_the_fp64_band(hydro_lib):
-    WL, WR = _faces(4000, 42, 1e4, 5e5, 0.70, 0.94)
+    WL, WR = _faces(4000, 42, 1e4, 5e5, 0.40, 0.78)
     ps, us, it = hydro_lib.hydro_exact_solve(WL, WR, G, precision=32)
     po, uo = _oracle(WL, WR)
+    assert np.all(it > 0), "Newton failed on %d faces" % int((it <= 0).sum())
     assert np.all(ps > 0)
-    vac = 2.0 / (G - 1.0) * (_sound(WL) + _sound(WR))
-    margin = np.maximum(vac - (WR[:, 1] - WL[:, 1]), 1e-300)
-    z = (G - 1.0) / (2.0 * G)
-    bound = 1e-5 + 10.0 * (1.0 / z) * 4.0 * EPS32 * vac / margin
+    fl, dfl = _kappa(WL, po)
+    fr, dfr = _kappa(WR, po)
+    kappa = (fl + fr + np.abs(WR[:, 1] - WL[:, 1])) / (po * (dfl + dfr))
+    bound = 1e-6 + 16.0 * EPS32 * kappa
     ep = np.abs(ps - po) / po
     print("next to the band: worst p* error / bound %.2e (worst relative %.2e)" % ((ep / bound).max(), ep.max()))
     assert np.all(ep <= bound)
