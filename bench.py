@@ -217,6 +217,16 @@ def train_mlp(H, torch, gamma, seed):
     return wts, {"faces": int(keep.sum()), "loss": loss, "train_s": round(time.time() - t0, 2)}
 
 
+def work_stream(torch):
+    """A dedicated stream, made torch's current one: every handle is created
+    on it, every tensor is made on it, and the timing events are recorded on
+    it -- the stream the kernels are launched on.  (The legacy default
+    stream would not do: a handle given a null stream makes its own.)"""
+    s = torch.cuda.Stream()
+    torch.cuda.set_stream(s)
+    return s
+
+
 def time_trajectory(torch, stream, b, U, positions, cfl=CFL):
     """From state U, advance the batch through the run and time each step at
     `positions` alone: CUDA events on the launching stream around one graph
@@ -359,7 +369,7 @@ def main():
     if args.grid_only:
         import torch
         from paper_2503_04428_gb300 import hydro as H
-        print(json.dumps(time_grids(H, torch, torch.cuda.current_stream(), args, only=args.grid_only,
+        print(json.dumps(time_grids(H, torch, work_stream(torch), args, only=args.grid_only,
                                     alu=alu_peaks(H))))
         return
     if args.impl == "reference":
@@ -376,7 +386,7 @@ def main():
     w = rank_tubes(ws, rank, ntubes=args.tubes)
     total = int(w["lengths"].sum())
     gamma = w["gamma"]
-    stream = torch.cuda.current_stream()
+    stream = work_stream(torch)
     weights, train_info = train_mlp(H, torch, gamma, 2)
     positions = trajectory_positions(args.steps)
     ksteps = len(positions)

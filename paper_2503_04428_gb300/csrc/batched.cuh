@@ -316,6 +316,42 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
       span_of(k, g0, len);
       const T* slot = ring + sl * (3 * BVSTR);
       const int ib = (int)(base - g0);  // slot index of the tube's cell 0
+      // A span whose whole window (every cell any of its segments reads) is
+      // one state: each of its cells gets U + 0, what the segment paths
+      // below give there.  Tested against the span's first cell, with a few
+      // strided shared-memory reads per lane and one vote; the state's
+      // validity and |u| + c are cached like a uniform segment's.
+      {
+        const int i0 = ib + max(s_beg + k * BSPAN * BSEG - 2, 0);
+        const int i1 = ib + min(s_beg + (k + 1) * BSPAN * BSEG + 2, nb);
+        const T r0 = slot[i0], r1 = slot[BVSTR + i0], r2 = slot[2 * BVSTR + i0];
+        bool eq = true;
+        for (int i = i0 + lane; i < i1; i += 32)
+          eq = eq & (slot[i] == r0) & (slot[BVSTR + i] == r1) & (slot[2 * BVSTR + i] == r2);
+        if (__all_sync(0xffffffffu, eq)) {
+          if (!(have_u & (r0 == ur[0]) & (r1 == ur[1]) & (r2 == ur[2]))) {
+            have_u = true;
+            ur[0] = r0;
+            ur[1] = r1;
+            ur[2] = r2;
+            T u[3] = {r0 + T(0), r1 + T(0), r2 + T(0)}, w[3];
+            const bool finite = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+            to_prim<T, 1, 0>(u, w, gas);
+            if (!finite) err = err ? err : ST_NONFINITE;
+            else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
+            u_spd = fabs(w[1]) + dsqrt(qdiv(gas.g * w[2], w[0]));
+          }
+          smax = fmax(smax, u_spd * fn);
+          const int a0 = s_beg + k * BSPAN * BSEG, a1 = min(a0 + BSPAN * BSEG, s_end);
+          const T o0 = ur[0] + T(0), o1 = ur[1] + T(0), o2 = ur[2] + T(0);
+          for (int c = a0 + lane; c < a1; c += 32) {
+            out[c] = o0;
+            out[a.stride + c] = o1;
+            out[2 * a.stride + c] = o2;
+          }
+          continue;
+        }
+      }
 #pragma unroll 1
       for (int j = 0; j < BSPAN; ++j) {
         const int sg = k * BSPAN + j;

@@ -8,10 +8,14 @@ all-reduce, shell masses for the monopole as an all-gather.  No kernel waits
 on another process: every exchange happens on the host between steps.  The
 result must equal the whole grid run by the library in one handle, and the
 oracle's whole run within the per-step parity bars times the steps taken
-(tests/parity.py).  Without a monopole the slabs do the whole grid's
-arithmetic cell for cell, so the states are compared bit for bit; the
-monopole's enclosed-mass sum is associated differently in a slab (its scan
-starts from the inner slabs' total), so there the bar is 1e-14.
+(tests/parity.py).  Against the whole grid on the GPU the bar is 1e-14
+(relative L1) and 1e-13 (element-wise) in FP64, 1e-6 and 1e-5 in FP32:
+the 3D sweep's CTAs march z in chunks, which start at other planes in a
+slab than in the whole grid (the test prints whether the states still agree
+bit for bit, and their largest difference); the monopole's enclosed-mass sum
+is also associated differently in a slab (its scan starts from the inner
+slabs' total).  The oracle's slabs equal its whole grid bit for bit
+(tests/test_decomposition.py).
 """
 import os
 import socket
@@ -90,8 +94,10 @@ def test_two_slabs_along_z(hydro_lib, precision):
     nsteps = 4
     split = _split(case, 2, 2, nsteps, precision)
     whole = _whole_gpu(hydro_lib, case, nsteps, precision)
-    print("z slabs, FP%d: split == whole bit for bit: %s" % (precision, np.array_equal(split, whole)))
-    assert np.array_equal(split, whole)
+    print("z slabs, FP%d: split == whole bit for bit: %s, max |difference| %.3e"
+          % (precision, np.array_equal(split, whole), np.abs(split - whole).max()))
+    check(whole, split, 3, case["gamma"], 64, l1=1e-14 if precision == 64 else 1e-6,
+          elem=1e-13 if precision == 64 else 1e-5)
     if precision == 64:
         check(_whole_oracle(case, nsteps), split, 3, case["gamma"], 64, l1=nsteps * 1e-12, elem=nsteps * 1e-11)
 
