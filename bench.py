@@ -85,7 +85,9 @@ def sweep_fp64_flops_per_cell():
 def alu_peaks(H):
     """Dense FMA peaks of this GPU, measured now by the library's FMA-chain kernel."""
     return {"fp64_tflops": H.hydro_fma_rate(64), "fp32_tflops": H.hydro_fma_rate(32),
-            "source": "hydro_fma_rate: 8 independent FMA chains per thread, 8 CTAs of 256 per SM"}
+            "fp32x2_tflops": H.hydro_fma_rate(H.HYDRO_FMA_F32X2),
+            "source": "hydro_fma_rate: 8 independent FMA chains per thread (float2 chains of paired FMAs "
+                      "for fp32x2), 8 CTAs of 256 per SM"}
 
 
 def profiled_traffic(item_len):
@@ -256,9 +258,14 @@ def time_trajectory(torch, stream, b, U, positions, cfl=CFL):
         cur = p + 1
     b.run(0, cfl)  # waits, and reports a failed step
     torch.cuda.synchronize()
-    t = sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1000.0
+    per = [e0.elapsed_time(e1) * 1000.0 for e0, e1 in evs]  # microseconds
+    t = sum(per) / 1e6
     s1 = b.stats()
-    return t, counters(s0, s1)
+    c = counters(s0, s1)
+    c["step_us"] = {"positions": list(positions) if len(positions) <= 25 else "every step",
+                    "us": [round(x, 1) for x in per] if len(per) <= 25 else
+                    [round(x, 1) for x in per[::max(1, len(per) // 20)]]}
+    return t, c
 
 
 def counters(s0, s1):

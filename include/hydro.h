@@ -317,11 +317,13 @@ int hydro_exact_solve(const double* WL, const double* WR, long n, double gamma, 
 int hydro_wait_probe(double* seconds_out);
 
 /* Measured arithmetic peak of the current GPU: dense fused multiply-adds in
- * FP64 (precision 64) or FP32 (32), in TFLOP/s (2 flops per FMA), the best
+ * FP64 (precision 64), FP32 (32) or paired FP32 (HYDRO_FMA_F32X2: one
+ * instruction performs two FMAs on a float2), in TFLOP/s (2 flops per FMA), the best
  * of four ~20 ms launches of eight independent FMA chains per thread.  The
  * paper has no counterpart: the FP64 forms of the step are bound by this
  * rate rather than by HBM on this hardware, and their roofline needs it
  * measured on the machine at hand.  Synchronous; allocates a few bytes. */
+#define HYDRO_FMA_F32X2 2  /* precision code of hydro_fma_rate: paired FP32 FMAs (f32x2) */
 int hydro_fma_rate(int precision, double* tflops_out);
 
 /* Sample the exact Riemann solution (Toro ch. 4; the reference solution of

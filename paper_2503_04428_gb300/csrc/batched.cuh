@@ -38,10 +38,12 @@ constexpr int BSPAN = 8;   // segments per ring slot
 constexpr int BVSTR = 232; // elements per variable in a slot: the span's 228 cells widened to 16-byte bounds
 constexpr int ST_TIMEOUT = -6;  // HYDRO_ERR_TIMEOUT: a bounded wait for a bulk copy expired
 
-// Ring slots per warp (all but one in flight while one is in use).
+// Ring slots per warp (all but one in flight while one is in use): 4 in
+// FP32 (89 KB of ring per 8-warp CTA, two CTAs per SM with the network's
+// weights), 2 in FP64.
 template <typename T>
 __host__ __device__ constexpr int bdepth() {
-  return sizeof(T) == 4 ? 3 : 2;
+  return sizeof(T) == 4 ? 4 : 2;
 }
 // Elements per 16 bytes: slabs, spans and copy sizes are multiples of this.
 template <typename T>

@@ -315,8 +315,12 @@ def hydro_batch_times(h, ntubes):
     return t
 
 
+HYDRO_FMA_F32X2 = 2
+
+
 def hydro_fma_rate(precision=64):
-    """Measured dense FMA peak of the current GPU in TFLOP/s (FP64 or FP32)."""
+    """Measured dense FMA peak of the current GPU in TFLOP/s (64: FP64, 32:
+    FP32, HYDRO_FMA_F32X2: paired FP32 FMAs)."""
     out = C.c_double()
     _call("hydro_fma_rate", int(precision), C.byref(out))
     return out.value
