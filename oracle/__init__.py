@@ -81,6 +81,8 @@ def lib():
         L.orc_get_boundary.argtypes = [C.c_void_p, C.c_int, C.c_int, _D]
         L.orc_shell_masses.argtypes = [C.c_void_p, _D]
         L.orc_set_inner_mass.argtypes = [C.c_void_p, C.c_double]
+        L.orc_set_moving_grid.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.orc_get_faces.argtypes = [C.c_void_p, C.c_int, _D]
         _lib = L
     return _lib
 
@@ -209,6 +211,15 @@ class Solver:
     def set_inner_mass(self, mass):
         _check(lib().orc_set_inner_mass(self._h, float(mass)), "set_inner_mass")
 
+    # --- moving grid (Sect. 3.1.1) ---
+    def set_moving_grid(self, axis, w):
+        _check(lib().orc_set_moving_grid(self._h, axis, float(w)), "set_moving_grid")
+
+    def faces(self, axis):
+        out = np.empty(self.n[axis] + 1)
+        _check(lib().orc_get_faces(self._h, axis, _dp(out)), "get_faces")
+        return out
+
 
 def solver_from_case(case):
     """Build an oracle solver from a workload case (see the package's workloads module)."""
@@ -221,6 +232,8 @@ def solver_from_case(case):
     src = case.get("sources")
     if src:
         s.set_sources(**src)
+    if case.get("moving"):
+        s.set_moving_grid(*case["moving"])
     s.set_state(case["U"])
     return s
 

@@ -511,6 +511,75 @@ int flux_exact(const Eos& eos, const double* WL, const double* WR, int d, int gu
   return ORC_OK;
 }
 
+/* Flux through a face that moves with velocity w along its normal d (the
+ * moving grid of Sect. 3.1.1, reading R16): G = F(W) - w U(W) of the
+ * Riemann solution sampled on the face's path x/t = w.  HLL and HLLC take
+ * the state of the wave region that contains w (ties as at w = 0); the
+ * exact solver samples its solution at x/t = w. */
+int flux_moving(const Eos& eos, int riemann, const double* WL, const double* WR, int d, double w, int guess,
+                const float* mlpw, double* G, ExactStats* st) {
+  const int nv = eos.nv(), D = eos.D;
+  double Wx[16], Ux[16], Fx[16];
+  if (riemann == ORC_EXACT) {
+    double wl[3] = {WL[0], WL[1 + d], WL[1 + D]};
+    double wr[3] = {WR[0], WR[1 + d], WR[1 + D]};
+    ExactResult er = exact_star(eos.gamma, wl, wr, guess, mlpw);
+    if (er.status != ORC_OK) return er.status;
+    st->iters += er.iters;
+    if (er.used_mlp) st->mlp += 1;
+    double smp[3];
+    int side;
+    exact_sample(eos.gamma, wl, wr, er.pstar, er.ustar, w, smp, &side);
+    const double* Wt = side < 0 ? WL : WR;
+    for (int v = 0; v < nv; ++v) Wx[v] = Wt[v];
+    Wx[0] = smp[0];
+    Wx[1 + d] = smp[1];
+    Wx[1 + D] = smp[2];
+    phys_flux(eos, Wx, d, Fx);
+    prim_to_cons(eos, Wx, Ux);
+    for (int v = 0; v < nv; ++v) G[v] = Fx[v] - w * Ux[v];
+    return ORC_OK;
+  }
+  double rL = WL[0], rR = WR[0], uL = WL[1 + d], uR = WR[1 + d];
+  double pL = WL[1 + D], pR = WR[1 + D];
+  double cL = sound_speed(eos, rL, pL), cR = sound_speed(eos, rR, pR);
+  double SL = std::fmin(uL - cL, uR - cR);
+  double SR = std::fmax(uL + cL, uR + cR);
+  double FL[16], FR[16], UL[16], UR[16];
+  phys_flux(eos, WL, d, FL);
+  phys_flux(eos, WR, d, FR);
+  prim_to_cons(eos, WL, UL);
+  prim_to_cons(eos, WR, UR);
+  if (SL >= w) {
+    for (int v = 0; v < nv; ++v) G[v] = FL[v] - w * UL[v];
+    return ORC_OK;
+  }
+  if (riemann == ORC_HLL) {
+    if (SR <= w) {
+      for (int v = 0; v < nv; ++v) G[v] = FR[v] - w * UR[v];
+      return ORC_OK;
+    }
+    for (int v = 0; v < nv; ++v) {
+      double Fh = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) / (SR - SL);
+      double Uh = (SR * UR[v] - SL * UL[v] - (FR[v] - FL[v])) / (SR - SL);
+      G[v] = Fh - w * Uh;
+    }
+    return ORC_OK;
+  }
+  double Sstar = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR));
+  double Us[16];
+  if (Sstar >= w) {
+    hllc_star(eos, WL, UL, d, SL, Sstar, Us);
+    for (int v = 0; v < nv; ++v) G[v] = FL[v] + SL * (Us[v] - UL[v]) - w * Us[v];
+  } else if (SR > w) {
+    hllc_star(eos, WR, UR, d, SR, Sstar, Us);
+    for (int v = 0; v < nv; ++v) G[v] = FR[v] + SR * (Us[v] - UR[v]) - w * Us[v];
+  } else {
+    for (int v = 0; v < nv; ++v) G[v] = FR[v] - w * UR[v];
+  }
+  return ORC_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* Heating / cooling source, Sect. 2.4.  NI56: Eq. 8-9 in CGS units.        */
 /* ------------------------------------------------------------------ */
@@ -560,6 +629,10 @@ struct Solver {
   /* Monopole of a subdomain split along r: the mass of all shells inside it
    * (reading R9's running sum where this subdomain's shells begin). */
   double inner_mass = 0.0;
+  /* Moving grid (Sect. 3.1.1, reading R16): the faces of axis maxis move
+   * with velocity wgrid; every step shifts them by wgrid dt. */
+  int maxis = -1;
+  double wgrid = 0.0;
 
   bool exch_ghost(int d, int g) const {
     return d == xaxis && ((g < 0 && xch[0]) || (g >= n[d] && xch[1]));
@@ -666,6 +739,27 @@ struct Solver {
     }
     return 0.5 * (rp * rp - rm * rm) * (th_hi(je) - th_lo(je));
   }
+  /* Area of a face averaged over a step in which the faces of the moving
+   * axis shift by Dl (reading R16): a radial face sweeps r^2 from r to r+Dl,
+   * whose mean is r^2 + r Dl + Dl^2/3 (so that the swept volumes add up to
+   * the change of the cell volumes); the theta and phi faces' (r+^2 - r-^2)/2
+   * varies linearly, so its mean is the mid-step value.  Cartesian areas do
+   * not change with a shift. */
+  double dS_avg(int d, int side, int ie, int je, int ke, double Dl) const {
+    if (coords == ORC_CARTESIAN) return dS(d, side, ie, je, ke);
+    double rm = xlo(0, ie), rp = xhi(0, ie);
+    if (d == 0) {
+      double r = side ? rp : rm;
+      return (r * r + r * Dl + Dl * Dl / 3.0) * (std::cos(th_lo(je)) - std::cos(th_hi(je))) *
+             (ph_hi(ke) - ph_lo(ke));
+    }
+    double a2 = 0.5 * (rp - rm) * (rp + rm + Dl);
+    if (d == 1) {
+      double th = side ? th_hi(je) : th_lo(je);
+      return a2 * std::sin(th) * (ph_hi(ke) - ph_lo(ke));
+    }
+    return a2 * (th_hi(je) - th_lo(je));
+  }
   /* Physical width of cell e along d (used by the predictor and the CFL):
    * h_r = dr, h_theta = r_i dtheta, h_phi = r_i sin(theta)_j dphi with
    * r_i the mid radius and sin(theta)_j the mean of the face sines. */
@@ -769,7 +863,9 @@ int Solver::cfl(double C, double* dtout) const {
         if (!(W[0] > 0.0) || !(W[1 + dim] > 0.0)) return ORC_ERR_NEGATIVE_STATE;
         double c = sound_speed(eos, W[0], W[1 + dim]);
         double s = 0.0;
-        for (int d = 0; d < dim; ++d) s += (std::fabs(W[1 + d]) + c) / h(d, i + off(0), j + off(1), k + off(2));
+        /* on a moving axis the signal speed is taken relative to the faces */
+        for (int d = 0; d < dim; ++d)
+          s += (std::fabs(W[1 + d] - (d == maxis ? wgrid : 0.0)) + c) / h(d, i + off(0), j + off(1), k + off(2));
         if (s > smax) smax = s;
       }
   *dtout = C / smax;
@@ -837,6 +933,13 @@ int Solver::step(double dt) {
           double Fm[16], Fp[16];
           phys_flux(eos, Wfs[d][0], d, Fm);
           phys_flux(eos, Wfs[d][1], d, Fp);
+          /* a moving axis: the fluxes through faces that move with the grid,
+           * F - w U (reading R16) */
+          if (d == maxis && wgrid != 0.0)
+            for (int v = 0; v < nv; ++v) {
+              Fm[v] -= wgrid * Ufs[d][0][v];
+              Fp[v] -= wgrid * Ufs[d][1][v];
+            }
           double hd = h(d, ie, je, ke);
           for (int v = 0; v < nv; ++v) dU[v] += 0.5 * dt * (Fm[v] - Fp[v]) / hd;
         }
@@ -895,7 +998,11 @@ int Solver::step(double dt) {
           }
           cons_to_prim(eos, UL, WL);
           cons_to_prim(eos, UR, WR);
-          if (riemann == ORC_HLL) flux_hll(eos, WL, WR, d, F);
+          if (d == maxis && wgrid != 0.0) {
+            int s = flux_moving(eos, riemann, WL, WR, d, wgrid, guess, mlpw.empty() ? nullptr : mlpw.data(), F,
+                                &est);
+            if (s != ORC_OK) return s;
+          } else if (riemann == ORC_HLL) flux_hll(eos, WL, WR, d, F);
           else if (riemann == ORC_HLLC) flux_hllc(eos, WL, WR, d, F);
           else {
             int s = flux_exact(eos, WL, WR, d, guess, mlpw.empty() ? nullptr : mlpw.data(), F, &est);
@@ -926,6 +1033,16 @@ int Solver::step(double dt) {
         int ie = i + off(0), je = j + off(1), ke = k + off(2);
         long e = eidx(ie, je, ke);
         double vol = dV(ie, je, ke);
+        /* moving grid (reading R16): face areas averaged over the step, the
+         * volume after it, and the radii sum of the Eq. 14 weight at mid-step */
+        const bool moving = maxis >= 0 && wgrid != 0.0;
+        const double Dl = moving ? wgrid * dt : 0.0;
+        double vol_new = vol;
+        if (moving && coords == ORC_SPHERICAL) {
+          double rm = xlo(0, ie) + Dl, rp = xhi(0, ie) + Dl;
+          vol_new = (rp * rp * rp - rm * rm * rm) / 3.0 * (std::cos(th_lo(je)) - std::cos(th_hi(je))) *
+                    (ph_hi(ke) - ph_lo(ke));
+        }
         double acc[16], Uc[16], Wc[16];
         for (int v = 0; v < nv; ++v) {
           acc[v] = 0.0;
@@ -936,8 +1053,8 @@ int Solver::step(double dt) {
         double A1 = 0.0, A2 = 0.0;  // sums of u_f e_f dS and u_f dS (dual energy)
         for (int d = 0; d < dim; ++d) {
           long stride = d == 0 ? 1 : d == 1 ? m(0) : (long)m(0) * m(1);
-          Slo[d] = dS(d, 0, ie, je, ke);
-          Shi[d] = dS(d, 1, ie, je, ke);
+          Slo[d] = moving ? dS_avg(d, 0, ie, je, ke, Dl) : dS(d, 0, ie, je, ke);
+          Shi[d] = moving ? dS_avg(d, 1, ie, je, ke, Dl) : dS(d, 1, ie, je, ke);
           for (int v = 0; v < nv; ++v) {
             Flo[d][v] = Fl[d][(size_t)v * ne + e - stride];
             Fhi[d][v] = Fl[d][(size_t)v * ne + e];
@@ -959,7 +1076,7 @@ int Solver::step(double dt) {
           for (int v = 0; v < nv; ++v) Uh[v] = Uc[v] + dUc[(size_t)v * ne + e];
           cons_to_prim(eos, Uh, Wh);
           double P = (Wh[0] > 0.0 && Wh[1 + dim] > 0.0) ? Wh[1 + dim] : Wc[1 + dim];
-          double rfac = (rp - rm) / ((rp + rm) * vol);
+          double rfac = (rp - rm) / ((rp + rm + Dl) * vol);
           /* theta-direction and phi-direction momentum-flux means; cell
            * values (rho u^2 + P with the absent velocity zero) when the axis
            * is absent. */
@@ -1024,6 +1141,9 @@ int Solver::step(double dt) {
           }
         }
 
+        /* moving grid: the content of the old cell, now spread over the new one */
+        if (moving && vol_new != vol)
+          for (int v = 0; v < nv; ++v) Unew[v] *= vol / vol_new;
         for (int v = 0; v < nv; ++v) Un[(size_t)v * nc + iidx(i, j, k)] = Unew[v];
       }
 
@@ -1036,6 +1156,10 @@ int Solver::step(double dt) {
   }
   U.swap(Un);
   t += dt;
+  if (maxis >= 0 && wgrid != 0.0) {
+    for (double& f : xf[maxis]) f += wgrid * dt;
+    build_ext_faces();
+  }
   return ORC_OK;
 }
 
@@ -1096,6 +1220,7 @@ int orc_set_sources(orc_t h, int gravity, const double* g0, double G, double Mc,
 
 int orc_set_dual_energy(orc_t h, double eps) {
   if (!(eps >= 0.0)) return ORC_ERR_ARG;
+  if (eps > 0.0 && h->s.maxis >= 0) return ORC_ERR_ARG;  /* not with a moving grid */
   h->s.eps_dual = eps;
   return ORC_OK;
 }
@@ -1184,6 +1309,7 @@ int orc_set_exchange(orc_t h, int axis, int side, const double* ghost_faces) {
   Solver& s = h->s;
   if (axis < 0 || axis >= s.dim || side < 0 || side > 1 || !ghost_faces) return ORC_ERR_ARG;
   if (s.xaxis >= 0 && s.xaxis != axis) return ORC_ERR_ARG;  /* slabs: one axis */
+  if (s.maxis >= 0) return ORC_ERR_ARG;                      /* not with a moving grid */
   s.xaxis = axis;
   s.xch[side] = true;
   for (int l = 0; l < NG; ++l) s.xg[side][l] = ghost_faces[l];
@@ -1215,6 +1341,27 @@ int orc_get_boundary(orc_t h, int axis, int side, double* out) {
             out[((size_t)v * NG + l) * nx + s.cross_idx(axis, i, j, k)] =
                 s.U[(size_t)v * s.ncell() + s.iidx(i, j, k)];
           }
+  return ORC_OK;
+}
+
+int orc_set_moving_grid(orc_t h, int axis, double w) {
+  Solver& s = h->s;
+  if (axis < 0 || axis >= s.dim || !std::isfinite(w)) return ORC_ERR_ARG;
+  if (s.coords == ORC_SPHERICAL && axis != 0) return ORC_ERR_ARG;       /* radial only */
+  if (s.xaxis >= 0 || s.eps_dual > 0.0) return ORC_ERR_ARG;            /* not with slabs or dual energy */
+  for (int side = 0; side < 2; ++side) {
+    int b = s.bc[axis][side];
+    if (b == ORC_REFLECTIVE || (b == ORC_PERIODIC && s.coords == ORC_SPHERICAL)) return ORC_ERR_ARG;
+  }
+  s.maxis = axis;
+  s.wgrid = w;
+  return ORC_OK;
+}
+
+int orc_get_faces(orc_t h, int axis, double* out) {
+  Solver& s = h->s;
+  if (axis < 0 || axis >= s.dim || !out) return ORC_ERR_ARG;
+  for (size_t f = 0; f < s.xf[axis].size(); ++f) out[f] = s.xf[axis][f];
   return ORC_OK;
 }
 

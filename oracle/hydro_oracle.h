@@ -85,6 +85,16 @@ int  orc_get_boundary(orc_t h, int axis, int side, double* out);
 int  orc_shell_masses(orc_t h, double* m_out);
 int  orc_set_inner_mass(orc_t h, double mass);
 
+/* Moving grid (Sect. 3.1.1): the faces of `axis` move with velocity w (each
+ * step shifts them by w dt); fluxes through the moving faces are F - w U of
+ * the Riemann solution on the face path x/t = w, the predictor uses the same
+ * fluxes along that axis, face areas are averaged over the step and the
+ * content of a cell is spread over its new volume.  Cartesian: any axis,
+ * transmissive or periodic ends; spherical: r only, transmissive ends.
+ * get_faces returns the current face coordinates of an axis (n+1). */
+int  orc_set_moving_grid(orc_t h, int axis, double w);
+int  orc_get_faces(orc_t h, int axis, double* out);
+
 /* Batched 1D tubes on [0,1], transmissive ends, each advanced nsteps at its own
  * CFL time step.  U is (3 x total cells), tubes concatenated per variable. */
 int  orc_batch_run(const int* lengths, int ntubes, double* U, double gamma, int riemann,

@@ -37,15 +37,15 @@ struct BatchState {
   BatchCtrl* bctrl_host = nullptr;
   // launch shape: warps per CTA, cells per item, CTAs
   int nw = 8, item_len = 112, grid = 0;
-  int* item_tube = nullptr;
-  int* item_start = nullptr;
+  BatchItem* items = nullptr;  // the launch's work queue (device)
   int nitems = 0;
-  std::vector<int> item_first;  // first item of every tube (+ nitems), tube order
-  std::vector<int> h_tube, h_start;  // the items in tube order (host)
-  // items ordered longest-first within each group of tubes of a host-resident
-  // run (part_items_P = the group count they were built for)
-  int* part_item_tube = nullptr;
-  int* part_item_start = nullptr;
+  std::vector<int> item_first;  // first item of every tube (+ end), tube order, before the tail cuts
+  std::vector<BatchItem> h_items;  // the items in tube order (host)
+  // items ordered within each group of tubes of a host-resident run
+  // (part_items_P = the group count they were built for; group p's items
+  // are part_first[p] .. part_first[p+1]-1)
+  BatchItem* part_items = nullptr;
+  std::vector<int> part_first;
   int part_items_P = 0;
   // host-resident runs: per-part control blocks, copy streams and events
   int nparts = 0;
@@ -114,80 +114,101 @@ static int occupancy_nw(int nw, int* blocks) {
   return HYDRO_OK;
 }
 
-// Work items (tube, first cell) of item_len cells.
 static void drop_graph(BatchState* bs);
 
-// Expected cost order of items [i0, i1) of the tube-ordered list: the waves
-// of every tube start at its interface (x = 1/2) and spread from there, so
-// items near it run the exact solver and the rest mostly take the
-// uniform-window path.  Handing out the expensive items first keeps warps
-// from waiting at the end of the persistent queue (longest processing time
-// first); the order changes no result.
-static void order_items(const BatchState* bs, int item_len, int i0, int i1, std::vector<int>& tube,
-                        std::vector<int>& start) {
+// Expected cost order of the tube-ordered items [i0, i1): the waves of every
+// tube start at its interface (x = 1/2) and spread from there, so items near
+// it run the exact solver and the rest mostly take the uniform-window paths.
+// Handing out the expensive items first keeps warps from waiting at the end
+// of the persistent queue (longest processing time first).  Then the tail of
+// the queue is cut finer, so that the last items of the launch end close
+// together: the items among the last 1/8 of the range's cells are halved,
+// among the last 1/16 quartered, among the last 1/32 cut in eighths (whole
+// 28-cell segments, at least one).  Neither the order nor the cuts change a
+// result.  Appends the range's items to `out`.
+static void order_items(const BatchState* bs, int i0, int i1, std::vector<BatchItem>& out) {
   std::vector<int> ord(i1 - i0);
   std::vector<double> key(i1 - i0);
+  long long cells = 0;
   for (int q = i0; q < i1; ++q) {
-    const int b = bs->h_tube[q];
-    const double nb = (double)(bs->off[b + 1] - bs->off[b]);
-    const double mid = (bs->h_start[q] + 0.5 * std::min((double)item_len, nb - bs->h_start[q])) / nb;
+    const BatchItem& it = bs->h_items[q];
+    const double mid = 0.5 * (it.beg + it.end) / (double)it.nb;
     key[q - i0] = std::fabs(mid - 0.5);
     ord[q - i0] = q;
+    cells += it.end - it.beg;
   }
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return key[x - i0] < key[y - i0]; });
-  for (int q = i0; q < i1; ++q) {
-    tube[q] = bs->h_tube[ord[q - i0]];
-    start[q] = bs->h_start[ord[q - i0]];
+  long long seen = 0;  // cells of the items before this one
+  for (int q : ord) {
+    const BatchItem& it = bs->h_items[q];
+    const long long left = cells - seen;  // cells from this item to the end
+    seen += it.end - it.beg;
+    int parts = left <= cells / 32 ? 8 : left <= cells / 16 ? 4 : left <= cells / 8 ? 2 : 1;
+    const int nseg = (it.end - it.beg + BSEG - 1) / BSEG;
+    parts = std::max(1, std::min(parts, nseg));
+    const int per = (nseg + parts - 1) / parts;  // segments per piece
+    for (int s0 = it.beg; s0 < it.end; s0 += per * BSEG) {
+      BatchItem piece = it;
+      piece.beg = s0;
+      piece.end = std::min(s0 + per * BSEG, it.end);
+      out.push_back(piece);
+    }
   }
 }
 
-static int upload_items(const std::vector<int>& tube, const std::vector<int>& start, int** d_tube,
-                        int** d_start) {
-  cudaFree(*d_tube);
-  cudaFree(*d_start);
-  *d_tube = nullptr;
-  *d_start = nullptr;
-  HCK(cudaMalloc(d_tube, sizeof(int) * tube.size()));
-  HCK(cudaMalloc(d_start, sizeof(int) * start.size()));
-  HCK(cudaMemcpy(*d_tube, tube.data(), sizeof(int) * tube.size(), cudaMemcpyHostToDevice));
-  HCK(cudaMemcpy(*d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
+static int upload_items(const std::vector<BatchItem>& items, BatchItem** d_items) {
+  cudaFree(*d_items);
+  *d_items = nullptr;
+  HCK(cudaMalloc(d_items, sizeof(BatchItem) * std::max<size_t>(1, items.size())));
+  HCK(cudaMemcpy(*d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
   return HYDRO_OK;
 }
 
-// Work items (tube, first cell) of item_len cells, handed out longest first.
+// Work items of item_len cells (the last of a tube shorter), in the
+// launch's queue order.
 static int make_items(hydro_ctx* h, int item_len) {
   BatchState* bs = h->bs;
-  bs->h_tube.clear();
-  bs->h_start.clear();
+  bs->h_items.clear();
   bs->item_first.assign(bs->ntubes + 1, 0);
   for (int b = 0; b < bs->ntubes; ++b) {
-    bs->item_first[b] = (int)bs->h_tube.size();
+    bs->item_first[b] = (int)bs->h_items.size();
     const int nb = (int)(bs->off[b + 1] - bs->off[b]);
-    for (int s = 0; s < nb; s += item_len) {
-      bs->h_tube.push_back(b);
-      bs->h_start.push_back(s);
+    for (int s0 = 0; s0 < nb; s0 += item_len) {
+      BatchItem it;
+      std::memset(&it, 0, sizeof(it));
+      it.base = bs->off[b];
+      it.nb = nb;
+      it.beg = s0;
+      it.end = std::min(s0 + item_len, nb);
+      it.tube = b;
+      bs->h_items.push_back(it);
     }
   }
-  bs->nitems = (int)bs->h_tube.size();
-  bs->item_first[bs->ntubes] = bs->nitems;
+  bs->item_first[bs->ntubes] = (int)bs->h_items.size();
   bs->item_len = item_len;
-  std::vector<int> tube(bs->nitems), start(bs->nitems);
-  order_items(bs, item_len, 0, bs->nitems, tube, start);
+  std::vector<BatchItem> q;
+  order_items(bs, 0, (int)bs->h_items.size(), q);
+  bs->nitems = (int)q.size();
   bs->part_items_P = 0;  // the host-resident order is rebuilt on demand
   drop_graph(bs);
-  return upload_items(tube, start, &bs->item_tube, &bs->item_start);
+  return upload_items(q, &bs->items);
 }
 
-// The item order of a host-resident run over the tube groups b0: longest
-// first within each group (a group's items stay a contiguous range).
+// The item order of a host-resident run over the tube groups b0: each
+// group's items ordered (and its tail cut) on their own, as one contiguous
+// range starting at part_first[p].
 static int part_items(hydro_ctx* h, const std::vector<int>& b0) {
   BatchState* bs = h->bs;
   const int P = (int)b0.size() - 1;
-  if (bs->part_items_P == P && bs->part_item_tube) return HYDRO_OK;
-  std::vector<int> tube(bs->nitems), start(bs->nitems);
-  for (int p = 0; p < P; ++p)
-    order_items(bs, bs->item_len, bs->item_first[b0[p]], bs->item_first[b0[p + 1]], tube, start);
-  int st = upload_items(tube, start, &bs->part_item_tube, &bs->part_item_start);
+  if (bs->part_items_P == P && bs->part_items) return HYDRO_OK;
+  std::vector<BatchItem> q;
+  bs->part_first.assign(P + 1, 0);
+  for (int p = 0; p < P; ++p) {
+    bs->part_first[p] = (int)q.size();
+    order_items(bs, bs->item_first[b0[p]], bs->item_first[b0[p + 1]], q);
+  }
+  bs->part_first[P] = (int)q.size();
+  int st = upload_items(q, &bs->part_items);
   if (st) return st;
   bs->part_items_P = P;
   if (bs->host_graph) {  // it points at the previous arrays
@@ -207,9 +228,7 @@ static BatchArgs<T> batch_args(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const 
   a.B = (T*)h->buf[1];
   a.stride = bs->stride;
   a.off = bs->off_d;
-  a.item_tube = bs->item_tube;
-  a.item_start = bs->item_start;
-  a.item_len = bs->item_len;
+  a.items = bs->items;
   a.nitems = bs->nitems;
   a.ntubes = bs->ntubes;
   a.tube0 = 0;
@@ -523,8 +542,7 @@ void hydro_batch_free_impl(hydro_ctx* h) {
   drop_graph(bs);
   cudaFree(bs->part_ctrl);
   cudaFreeHost(bs->part_ctrl_host);
-  cudaFree(bs->part_item_tube);
-  cudaFree(bs->part_item_start);
+  cudaFree(bs->part_items);
   if (bs->ev_fork) cudaEventDestroy(bs->ev_fork);
   if (bs->ev_join) cudaEventDestroy(bs->ev_join);
   if (bs->s_h2d) cudaStreamDestroy(bs->s_h2d);
@@ -537,8 +555,7 @@ void hydro_batch_free_impl(hydro_ctx* h) {
   cudaFree(bs->t_tube);
   cudaFree(bs->bctrl);
   cudaFreeHost(bs->bctrl_host);
-  cudaFree(bs->item_tube);
-  cudaFree(bs->item_start);
+  cudaFree(bs->items);
   cudaFree(bs->w);
   cudaFree(bs->w_packed);
   cudaFree(bs->m);
@@ -589,9 +606,8 @@ static int enqueue_host_run(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
                                                         &bs->part_ctrl[p].c.status);
     HCK(cudaGetLastError());
     BatchArgs<T> a = batch_args<T>(h, cfl, &bs->part_ctrl[p], bs->smax_cur, bs->smax_next, bs->t_tube);
-    const int i0 = bs->item_first[t0], i1 = bs->item_first[t1];
-    a.item_tube = bs->part_item_tube + i0;
-    a.item_start = bs->part_item_start + i0;
+    const int i0 = bs->part_first[p], i1 = bs->part_first[p + 1];
+    a.items = bs->part_items + i0;
     a.nitems = i1 - i0;
     a.tube0 = t0;
     a.ntubes = t1 - t0;

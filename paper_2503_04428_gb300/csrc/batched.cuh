@@ -38,12 +38,11 @@ constexpr int BSPAN = 8;   // segments per ring slot
 constexpr int BVSTR = 232; // elements per variable in a slot: the span's 228 cells widened to 16-byte bounds
 constexpr int ST_TIMEOUT = -6;  // HYDRO_ERR_TIMEOUT: a bounded wait for a bulk copy expired
 
-// Ring slots per warp (all but one in flight while one is in use): 4 in
-// FP32 (89 KB of ring per 8-warp CTA, two CTAs per SM with the network's
-// weights), 2 in FP64.
+// Ring slots per warp (all but one in flight while one is in use): 3 in
+// FP32 (4 measured no faster), 2 in FP64.
 template <typename T>
 __host__ __device__ constexpr int bdepth() {
-  return sizeof(T) == 4 ? 4 : 2;
+  return sizeof(T) == 4 ? 3 : 2;
 }
 // Elements per 16 bytes: slabs, spans and copy sizes are multiples of this.
 template <typename T>
@@ -104,6 +103,19 @@ struct BatchCtrl {
 
 struct MlpSmemW;
 
+// One work item: cells beg .. end-1 of tube `tube` (nb cells, the first at
+// element `base` of every variable's slab), everything a warp needs before
+// it issues the item's first copies, in one 32-byte record.
+struct __align__(16) BatchItem {
+  long long base;
+  int nb;
+  int beg;
+  int end;
+  int tube;
+  int pad[2];
+};
+static_assert(sizeof(BatchItem) == 32, "one 32-byte record per item");
+
 template <typename T>
 struct BatchArgs {
   const T* A;
@@ -111,9 +123,7 @@ struct BatchArgs {
   T* Aw;
   long long stride;            // elements between the variables' slabs (a multiple of bquant<T>())
   const long long* off;        // ntubes + 1 cell offsets
-  const int* item_tube;
-  const int* item_start;
-  int item_len;                // cells per work item (a multiple of BSEG)
+  const BatchItem* items;      // the work queue, in hand-out order
   int nitems;
   int ntubes;                  // tubes committed by this launch: tube0 .. tube0+ntubes-1
   int tube0;
@@ -255,17 +265,12 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     if (lane == 0) it = (int)atomicAdd(&a.ctrl->next_item, 1u);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= a.nitems) break;
-    const int b = a.item_tube[it];
-    const int s_beg = a.item_start[it];
-    const long long base = a.off[b];
-    const int nb = (int)(a.off[b + 1] - base);
-    const int s_end = min(s_beg + a.item_len, nb);
+    const BatchItem itm = a.items[it];
+    const int b = itm.tube;
+    const int s_beg = itm.beg, s_end = itm.end, nb = itm.nb;
+    const long long base = itm.base;
     const T fn = (T)nb;          // 1/h
     const T hw = T(0.5) / fn;    // half width
-    double dtd = 0.0;
-    if (lane == 0) dtd = a.cfl / a.smax_cur[b];
-    dtd = __shfl_sync(0xffffffffu, dtd, 0);
-    const T dtdx = (T)dtd * fn;
     T smax = T(0);
     T* const out = Uout + base;  // the tube's cell 0 in the output
 
@@ -300,6 +305,11 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     };
 #pragma unroll
     for (int k = 0; k < BD - 1; ++k) issue(k);
+    // the tube's time step, read while the first copies are in flight
+    double dtd = 0.0;
+    if (lane == 0) dtd = a.cfl / a.smax_cur[b];
+    dtd = __shfl_sync(0xffffffffu, dtd, 0);
+    const T dtdx = (T)dtd * fn;
     for (int k = 0; k < nspan; ++k) {
       __syncwarp();     // every lane is done with the slot refilled next (read one span ago)
       issue(k + BD - 1);
