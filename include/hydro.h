@@ -181,6 +181,24 @@ int hydro_get_boundary(hydro_t h, int axis, int side, void* out, int where);
 int hydro_shell_masses(hydro_t h, double* m_out);
 int hydro_set_inner_mass(hydro_t h, double mass);
 
+/* Moving grid (Sect. 3.1.1: the grid shifted along one axis during the run,
+ * e.g. radially to follow expanding ejecta).  Every face of `axis` moves with
+ * velocity w (code units), so each step of size dt shifts them by w dt; the
+ * flux through a moving face is F - w U of the Riemann solution on the face's
+ * path x/t = w (computed as the fixed-face flux of the states seen from the
+ * frame moving with w); the Hancock predictor uses the same fluxes along that
+ * axis; on a spherical grid (r only) the face areas of a step are their
+ * averages over the step (a radial face r^2 + r D + D^2/3, D = w dt) and a
+ * cell's content is spread over its new volume, so that a uniform gas at rest
+ * stays uniform; the CFL speed is |u - w| + c along that axis.  Cartesian:
+ * any axis, transmissive or periodic ends; spherical: r, transmissive ends.
+ * Ideal gas, no dual-energy correction, no exchanged sides
+ * (HYDRO_ERR_UNSUPPORTED / HYDRO_ERR_ARG).  hydro_run then drives its steps
+ * from the host (each step's geometry follows its dt).  hydro_get_faces
+ * copies the current n[axis]+1 face coordinates of an axis to host memory. */
+int hydro_set_moving_grid(hydro_t h, int axis, double w);
+int hydro_get_faces(hydro_t h, int axis, double* out);
+
 /* Copy a state in (validated on the device: rho > 0, P > 0, finite; on
  * failure the previous state is kept) and compute its CFL signal speed. */
 int hydro_set_state(hydro_t h, const void* U, int where);

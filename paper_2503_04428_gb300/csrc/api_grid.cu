@@ -89,18 +89,24 @@ static AxisExt axis_ext(const std::vector<double>& xf, int bclo, int bchi) {
   return a;
 }
 
+// Upload a geometry array in the state precision; an array that exists
+// already (a rebuild of the same grid) is overwritten in place.
 template <typename T>
 static int upload(hydro_ctx* h, const std::vector<double>& v, void** out) {
   std::vector<T> tmp(v.begin(), v.end());
-  int st = h->arena.alloc(out, tmp.size() * sizeof(T));
-  if (st) return st;
+  if (!*out) {
+    int st = h->arena.alloc(out, tmp.size() * sizeof(T));
+    if (st) return st;
+  }
   HCK(cudaMemcpy(*out, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
   return HYDRO_OK;
 }
 
 static int upload_d(hydro_ctx* h, const std::vector<double>& v, double** out) {
-  int st = h->arena.alloc((void**)out, v.size() * sizeof(double));
-  if (st) return st;
+  if (!*out) {
+    int st = h->arena.alloc((void**)out, v.size() * sizeof(double));
+    if (st) return st;
+  }
   HCK(cudaMemcpy(*out, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
   return HYDRO_OK;
 }
@@ -123,7 +129,7 @@ static int build_geometry(hydro_ctx* h) {
     else if (d == 1) xf[d] = {0.0, PI};
     else xf[d] = {0.0, 2.0 * PI};
   }
-  std::vector<void*> g(G_COUNT, nullptr);
+  std::vector<void*> g(h->geo, h->geo + G_COUNT);  // existing arrays are reused
   AxisExt ax[3];
   // per extended cell, the two faces whose mid-point is the radius or whose
   // sines give the mean polar sine of its physical widths
@@ -257,6 +263,37 @@ static int build_geometry(hydro_ctx* h) {
   return HYDRO_OK;
 }
 
+// Moving radial grid (reading R16), for a step of size dt: the axis-0
+// factors of the update with the face areas averaged over the step (a radial
+// face sweeps r^2 from r to r + D, D = w dt, mean r^2 + r D + D^2/3; the
+// theta and phi faces' (r+^2 - r-^2)/2 at mid-step) over the old volume
+// factor a, and the volume ratio a/a' of every radial cell.  The faces
+// themselves move after the step.
+template <typename T>
+static int moving_geometry(hydro_ctx* h, double dt) {
+  const std::vector<double>& xf = h->faces[0];
+  const int n0 = (int)xf.size() - 1;
+  const double D = h->wgrid * dt;
+  std::vector<double> Af(n0 + 1), ga(n0), qr(n0), gr(n0), vr(n0);
+  for (int f = 0; f <= n0; ++f) Af[f] = xf[f] * xf[f] + xf[f] * D + D * D / 3.0;
+  for (int i = 0; i < n0; ++i) {
+    const double rm = xf[i], rp = xf[i + 1];
+    const double a = (rp * rp * rp - rm * rm * rm) / 3.0;
+    const double rm2 = rm + D, rp2 = rp + D;
+    const double an = (rp2 * rp2 * rp2 - rm2 * rm2 * rm2) / 3.0;
+    ga[i] = 0.5 * (rp - rm) * (rp + rm + D) / a;
+    qr[i] = (rp - rm) / ((rp + rm + D) * a);
+    gr[i] = (Af[i + 1] - Af[i]) / a;
+    vr[i] = a / an;
+  }
+  int st;
+  if ((st = upload<T>(h, Af, &h->geo[G_AF]))) return st;
+  if ((st = upload<T>(h, ga, &h->geo[G_GA]))) return st;
+  if ((st = upload<T>(h, qr, &h->geo[G_QR]))) return st;
+  if ((st = upload<T>(h, gr, &h->geo[G_GR]))) return st;
+  return upload<T>(h, vr, &h->vr_d);
+}
+
 template <typename T>
 static Geom<T> geom_of(const hydro_ctx* h) {
   Geom<T> g;
@@ -359,6 +396,9 @@ static SweepArgs<T> sweep_args(hydro_ctx* h, double dt_host, double cfl, double 
   a.xaxis = h->xaxis;
   a.halo[0] = (const T*)h->halo_d[0];
   a.halo[1] = (const T*)h->halo_d[1];
+  a.maxis = h->maxis;
+  a.wg = (T)h->wgrid;
+  a.vr = h->maxis >= 0 && h->coords == HYDRO_SPHERICAL ? (const T*)h->vr_d : nullptr;
   return a;
 }
 
@@ -585,15 +625,15 @@ static int validate_into(hydro_ctx* h, int slot, int* status_out, double* smax_o
   const int n0 = h->n[0], n1 = h->n[1], nv = h->nv;
   if (h->eos_rad) {
     switch (h->dim) {
-      case 1: validate_kernel<T, 1><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, grad, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
-      case 2: validate_kernel<T, 2><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, grad, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
-      default: validate_kernel<T, 3><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, grad, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
+      case 1: validate_kernel<T, 1><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, grad, sph, w0, w1, w2, ir, is, d_status, d_smax, h->maxis, (T)h->wgrid); break;
+      case 2: validate_kernel<T, 2><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, grad, sph, w0, w1, w2, ir, is, d_status, d_smax, h->maxis, (T)h->wgrid); break;
+      default: validate_kernel<T, 3><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, grad, sph, w0, w1, w2, ir, is, d_status, d_smax, h->maxis, (T)h->wgrid); break;
     }
   } else {
     switch (h->dim) {
-      case 1: validate_kernel<T, 1><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
-      case 2: validate_kernel<T, 2><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
-      default: validate_kernel<T, 3><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax); break;
+      case 1: validate_kernel<T, 1><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax, h->maxis, (T)h->wgrid); break;
+      case 2: validate_kernel<T, 2><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax, h->maxis, (T)h->wgrid); break;
+      default: validate_kernel<T, 3><<<blocks, 256, 0, h->stream>>>(U, nc, n0, n1, nv, gas, sph, w0, w1, w2, ir, is, d_status, d_smax, h->maxis, (T)h->wgrid); break;
     }
   }
   HCK(cudaGetLastError());
@@ -707,6 +747,10 @@ int hydro_create(const hydro_grid* grid, int coords, const hydro_eos* eos, int r
 int hydro_set_dual_energy(hydro_t h, double eps) {
   if (!h || h->batched) return arg_error("hydro_set_dual_energy: grid handle required");
   if (!(eps >= 0.0) || !std::isfinite(eps)) return arg_error("hydro_set_dual_energy: need eps >= 0");
+  if (eps > 0.0 && h->maxis >= 0) {
+    set_error("hydro_set_dual_energy: not built with the moving grid");
+    return HYDRO_ERR_UNSUPPORTED;
+  }
   if ((eps > 0.0) != (h->eps_dual > 0.0)) h->tuned = false;  // another kernel: tune again
   h->eps_dual = eps;
   if (h->graph) {
@@ -722,6 +766,10 @@ int hydro_set_eos_radiation(hydro_t h, double R_gas, double a_rad) {
     return arg_error("hydro_set_eos_radiation: need R_gas > 0 and a_rad >= 0");
   if (h->riemann == HYDRO_EXACT) {
     set_error("hydro_set_eos_radiation: the exact Riemann solver assumes the ideal gas; use HLL or HLLC");
+    return HYDRO_ERR_UNSUPPORTED;
+  }
+  if (h->maxis >= 0) {
+    set_error("hydro_set_eos_radiation: the moving grid is built for the ideal gas");
     return HYDRO_ERR_UNSUPPORTED;
   }
   h->eos_rad = 1;
@@ -789,6 +837,7 @@ int hydro_set_exchange(hydro_t h, int axis, int side, const double ghost_faces[2
     return arg_error("hydro_set_exchange: bad axis, side or face coordinates");
   if (h->xaxis >= 0 && h->xaxis != axis)
     return arg_error("hydro_set_exchange: only the sides of one axis can be exchanged (slabs)");
+  if (h->maxis >= 0) return arg_error("hydro_set_exchange: not with a moving grid");
   const double f0 = ghost_faces[0], f1 = ghost_faces[1];
   const std::vector<double>& xf = h->faces[axis];
   const bool ok = side == 0 ? (f1 < f0 && f0 < xf.front()) : (xf.back() < f0 && f0 < f1);
@@ -952,12 +1001,65 @@ int hydro_cfl_dt(hydro_t h, double cfl, double* dt_out) {
   return HYDRO_OK;
 }
 
+// After a step on a moving grid: the faces of the moving axis shift by w dt
+// and the geometry is rebuilt for them.
+static int move_faces(hydro_ctx* h, double dt) {
+  for (double& f : h->faces[h->maxis]) f += h->wgrid * dt;
+  return h->precision == 64 ? build_geometry<double>(h) : build_geometry<float>(h);
+}
+
 int hydro_step(hydro_t h, double dt) {
   if (!h || h->batched) return arg_error("hydro_step: grid handle required");
   if (!(dt > 0.0) || !std::isfinite(dt)) return arg_error("hydro_step: dt must be positive and finite");
-  int st = launch_step(h, dt, 0.0, 0.0, h->ctrl);
+  int st;
+  const bool moving = h->maxis >= 0 && h->wgrid != 0.0;
+  if (moving && h->coords == HYDRO_SPHERICAL) {
+    st = h->precision == 64 ? moving_geometry<double>(h, dt) : moving_geometry<float>(h, dt);
+    if (st) return st;
+  }
+  st = launch_step(h, dt, 0.0, 0.0, h->ctrl);
   if (st) return st;
-  return check_status(h, "hydro_step");
+  st = check_status(h, "hydro_step");
+  if (moving) {
+    // a failed step leaves the state and the faces as they were
+    const int mv = st == HYDRO_OK ? move_faces(h, dt)
+                   : (h->precision == 64 ? build_geometry<double>(h) : build_geometry<float>(h));
+    if (mv) return mv;
+  }
+  return st;
+}
+
+int hydro_set_moving_grid(hydro_t h, int axis, double w) {
+  if (!h || h->batched) return arg_error("hydro_set_moving_grid: grid handle required");
+  if (axis < 0 || axis >= h->dim || !std::isfinite(w)) return arg_error("hydro_set_moving_grid: bad axis or velocity");
+  if (h->coords == HYDRO_SPHERICAL && axis != 0)
+    return arg_error("hydro_set_moving_grid: a spherical grid moves along r only");
+  for (int s = 0; s < 2; ++s) {
+    const int b = h->bc[axis][s];
+    if (b == BC_REFLECTIVE || b == BC_EXCHANGED || (b == BC_PERIODIC && h->coords == HYDRO_SPHERICAL))
+      return arg_error("hydro_set_moving_grid: the moving axis needs transmissive (or, Cartesian, periodic) ends");
+  }
+  if (h->eos_rad || h->eps_dual > 0.0) {
+    set_error("hydro_set_moving_grid: built for the ideal gas without the dual-energy correction");
+    return HYDRO_ERR_UNSUPPORTED;
+  }
+  h->maxis = axis;
+  h->wgrid = w;
+  if (h->coords == HYDRO_SPHERICAL && !h->vr_d) {
+    int st = h->arena.alloc(&h->vr_d, (size_t)h->n[0] * h->esize);
+    if (st) return st;
+  }
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return HYDRO_OK;
+}
+
+int hydro_get_faces(hydro_t h, int axis, double* out) {
+  if (!h || h->batched || !out || axis < 0 || axis >= h->dim) return arg_error("hydro_get_faces: bad argument");
+  std::copy(h->faces[axis].begin(), h->faces[axis].end(), out);
+  return HYDRO_OK;
 }
 
 int hydro_run(hydro_t h, int nsteps, double cfl, double t_end, double* t_out) {
@@ -967,6 +1069,21 @@ int hydro_run(hydro_t h, int nsteps, double cfl, double t_end, double* t_out) {
     set_error("hydro_run: a grid with exchanged sides needs its halos (and the global dt) before every step: "
               "use hydro_step");
     return HYDRO_ERR_UNSUPPORTED;
+  }
+  if (h->maxis >= 0 && h->wgrid != 0.0) {
+    // a moving grid's geometry follows each step's dt: steps driven from the host
+    int st;
+    for (int s = 0; s < nsteps; ++s) {
+      if ((st = read_ctrl(h))) return st;
+      const double t0 = h->ctrl_host->t;
+      if (t_end > 0.0 && t0 >= t_end) break;
+      double dt = cfl / h->ctrl_host->smax_cur;
+      if (t_end > 0.0 && t0 + dt > t_end) dt = t_end - t0;
+      if ((st = hydro_step(h, dt))) return st;
+    }
+    if ((st = read_ctrl(h))) return st;
+    if (t_out) *t_out = h->ctrl_host->t;
+    return HYDRO_OK;
   }
   int st;
   if ((st = autotune_grid(h, cfl))) return st;

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(256)
     validate_kernel(const T* __restrict__ U, long long ncell, int n0, int n1, int nv, G gas,
                     int spherical, const T* __restrict__ w0, const T* __restrict__ w1,
                     const T* __restrict__ w2, const T* __restrict__ ir, const T* __restrict__ is,
-                    int* status, unsigned long long* smax_bits) {
+                    int* status, unsigned long long* smax_bits, int maxis, T wg) {
   double smax = 0.0;
   int err = 0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
@@ -49,14 +49,15 @@ __global__ void __launch_bounds__(256)
     }
     if (!(rho > T(0)) || !(p > T(0))) { err = err ? err : ST_NEG; continue; }
     const T cs = dsqrt(c2);
-    T sp = (fabs(u[1] / rho) + cs) * w0[i + 2];
+    // (on a moving axis the speed relative to the faces)
+    T sp = (fabs(u[1] / rho - (maxis == 0 ? wg : T(0))) + cs) * w0[i + 2];
     if (DIM >= 2) {
       const T ih = spherical ? w1[j + 2] * ir[i + 2] : w1[j + 2];
-      sp += (fabs(u[2] / rho) + cs) * ih;
+      sp += (fabs(u[2] / rho - (maxis == 1 ? wg : T(0))) + cs) * ih;
     }
     if (DIM == 3) {
       const T ih = spherical ? w2[k + 2] * ir[i + 2] * is[j + 2] : w2[k + 2];
-      sp += (fabs(u[3] / rho) + cs) * ih;
+      sp += (fabs(u[3] / rho - (maxis == 2 ? wg : T(0))) + cs) * ih;
     }
     smax = fmax(smax, (double)sp);
   }

@@ -96,6 +96,13 @@ struct SweepArgs {
   // axes, the lower one fastest)
   int xaxis;
   const T* halo[2];
+  // moving grid (Sect. 3.1.1): the faces of axis maxis (-1 none) move with
+  // velocity wg; vr (spherical radial motion, else null) = a_old/a_new per
+  // radial cell, the volume ratio that spreads a cell's content over its
+  // new volume
+  int maxis;
+  T wg;
+  const T* vr;
 };
 
 template <typename T, int DIM>

@@ -92,6 +92,10 @@ struct hydro_ctx {
   void* halo_d[2] = {nullptr, nullptr};
   void* pack_d = nullptr;    // staging of hydro_get_boundary for host output
   double inner_mass = 0.0;
+  // moving grid (Sect. 3.1.1): axis, face velocity, volume ratios (device)
+  int maxis = -1;
+  double wgrid = 0.0;
+  void* vr_d = nullptr;
   // graph of one device-dt step
   cudaGraphExec_t graph = nullptr;
   double graph_cfl = -1.0, graph_tend = -2.0;

@@ -373,6 +373,19 @@ struct Sweep {
     }
   }
 
+  // Moving grid (reading R16): along the moving axis the predictor uses the
+  // fluxes through faces that move with the grid, F - w U (ideal gas).
+  __device__ __forceinline__ void moving_fluxes(const T* Wl, const T* Wh, T* Fl, T* Fh) const {
+    T ul[NV], uh[NV];
+    to_cons<T, DIM, NSX>(Wl, ul, a.gas);
+    to_cons<T, DIM, NSX>(Wh, uh, a.gas);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Fl[v] -= a.wg * ul[v];
+      Fh[v] -= a.wg * uh[v];
+    }
+  }
+
   // a3 + a4 for plane gz: the predictor increment dU = dt/2 sum_d
   // (F_d(W_lo) - F_d(W_hi))/h_d of every needed cell, and its predicted face
   // states.  PRED_ALL: tile plus halo, every face state of the plane;
@@ -424,6 +437,7 @@ struct Sweep {
       faces_of<0>(Wm, Wc, Wp, gi, Wl, Wh);
       T Pl[NV], Ph[NV], tl = T(0), th = T(0);
       limited_fluxes<0>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
+      if (a.maxis == 0) moving_fluxes(Wl, Wh, Fl, Fh);
       if constexpr (EOS == 1) {
         if (xlo) XTR[ixlo] = tl;
         if (xhi) XTL[ixhi] = th;
@@ -446,6 +460,7 @@ struct Sweep {
       faces_of<1>(Wm, Wc, Wp, gj, Wl, Wh);
       T Pl[NV], Ph[NV], tl = T(0), th = T(0);
       limited_fluxes<1>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
+      if (a.maxis == 1) moving_fluxes(Wl, Wh, Fl, Fh);
       if constexpr (EOS == 1) {
         if (ylo) YTR[iylo] = tl;
         if (yhi) YTL[iyhi] = th;
@@ -468,6 +483,7 @@ struct Sweep {
       faces_of<2>(Wm, Wc, Wp, gz, Wl, Wh);
       T Pl[NV], Ph[NV], tl = T(0), th = T(0);
       limited_fluxes<2>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
+      if (a.maxis == 2) moving_fluxes(Wl, Wh, Fl, Fh);
       if constexpr (EOS == 1) {
         if (zlo) ZTR[iz] = tl;
         if (zhi) ZTL[(gz & 1) * NFZ + iz] = th;
@@ -504,9 +520,36 @@ struct Sweep {
     }
   }
 
+  // Riemann flux of a face along DIR.  On the moving axis (reading R16) the
+  // flux through the moving face, F - w U on the face path x/t = w, is the
+  // fixed-face flux of the same two states seen from the frame that moves
+  // with the face (normal velocities minus w; every solver here is Galilean
+  // invariant), taken back to the lab frame: mass flux unchanged, normal
+  // momentum flux + w F_rho, energy flux + w F_m + w^2/2 F_rho.
   template <int DIR>
   __device__ __forceinline__ void riemann(const T* WL, const T* WR, T* F, bool owned, T TL = T(0),
                                           T TR = T(0)) {
+    if (a.maxis == DIR) {
+      const T w = a.wg;
+      T wl[NV], wr[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        wl[v] = WL[v];
+        wr[v] = WR[v];
+      }
+      wl[1 + DIR] -= w;
+      wr[1 + DIR] -= w;
+      riemann_fixed<DIR>(wl, wr, F, owned, TL, TR);
+      F[1 + DIM] += w * F[1 + DIR] + T(0.5) * w * w * F[0];
+      F[1 + DIR] += w * F[0];
+      return;
+    }
+    riemann_fixed<DIR>(WL, WR, F, owned, TL, TR);
+  }
+
+  template <int DIR>
+  __device__ __forceinline__ void riemann_fixed(const T* WL, const T* WR, T* F, bool owned, T TL = T(0),
+                                                T TR = T(0)) {
     if constexpr (EOS == 1 && RS == RS_HLL) {
       riemann_hll_rad<T, DIM, NSX, DIR>(WL, WR, F, a.grad, TL, TR);
     } else if constexpr (EOS == 1 && RS == RS_HLLC) {
@@ -710,6 +753,13 @@ struct Sweep {
       }
     }
 
+    // moving radial grid: the old cell's content spread over the new volume
+    if (a.vr) {
+      const T q = a.vr[gi];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Un[v] *= q;
+    }
+
     // validity and the signal speed of the new state
     T Wn[NV], c2n;
     if constexpr (EOS == 1) {
@@ -727,7 +777,7 @@ struct Sweep {
     const T cs = dsqrt(c2n);
     T sp = T(0);
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) sp += (fabs(Wn[1 + d]) + cs) * inv_h(d, gi, gj, gz);
+    for (int d = 0; d < DIM; ++d) sp += (fabs(Wn[1 + d] - (d == a.maxis ? a.wg : T(0))) + cs) * inv_h(d, gi, gj, gz);
     smax = fmax(smax, (double)sp);
 #pragma unroll
     for (int v = 0; v < NV; ++v)

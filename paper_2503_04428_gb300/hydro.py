@@ -97,6 +97,8 @@ _SIGS = {
     "hydro_get_boundary": [_VP, C.c_int, C.c_int, _VP, C.c_int],
     "hydro_shell_masses": [_VP, _D],
     "hydro_set_inner_mass": [_VP, C.c_double],
+    "hydro_set_moving_grid": [_VP, C.c_int, C.c_double],
+    "hydro_get_faces": [_VP, C.c_int, _D],
     "hydro_last_error": [],
 }
 
@@ -374,6 +376,8 @@ class Grid:
         src = case.get("sources")
         if src:
             g.set_sources(**src)
+        if case.get("moving"):
+            g.set_moving_grid(*case["moving"])
         g.set_state(case["U"])
         return g
 
@@ -464,6 +468,15 @@ class Grid:
 
     def set_inner_mass(self, mass):
         _call("hydro_set_inner_mass", self.h, float(mass))
+
+    # --- moving grid (Sect. 3.1.1) ---
+    def set_moving_grid(self, axis, w):
+        _call("hydro_set_moving_grid", self.h, axis, float(w))
+
+    def faces(self, axis):
+        out = np.empty(self.n[axis] + 1)
+        _call("hydro_get_faces", self.h, axis, out.ctypes.data_as(_D))
+        return out
 
     def close(self):
         if getattr(self, "h", None):
