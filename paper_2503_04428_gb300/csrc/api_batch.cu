@@ -39,7 +39,7 @@ struct BatchState {
   int nw = 8, item_len = 112, grid = 0;
   BatchItem* items = nullptr;  // the launch's work queue (device)
   int nitems = 0;
-  std::vector<int> item_first;  // first item of every tube (+ end), tube order, before the tail cuts
+  std::vector<int> item_first;  // first item of every tube (+ end), tube order
   std::vector<BatchItem> h_items;  // the items in tube order (host)
   // items ordered within each group of tubes of a host-resident run
   // (part_items_P = the group count they were built for; group p's items
@@ -120,40 +120,19 @@ static void drop_graph(BatchState* bs);
 // tube start at its interface (x = 1/2) and spread from there, so items near
 // it run the exact solver and the rest mostly take the uniform-window paths.
 // Handing out the expensive items first keeps warps from waiting at the end
-// of the persistent queue (longest processing time first).  Then the tail of
-// the queue is cut finer, so that the last items of the launch end close
-// together: the items among the last 1/8 of the range's cells are halved,
-// among the last 1/16 quartered, among the last 1/32 cut in eighths (whole
-// 28-cell segments, at least one).  Neither the order nor the cuts change a
-// result.  Appends the range's items to `out`.
+// of the persistent queue (longest processing time first); the order changes
+// no result.  Appends the range's items to `out`.
 static void order_items(const BatchState* bs, int i0, int i1, std::vector<BatchItem>& out) {
   std::vector<int> ord(i1 - i0);
   std::vector<double> key(i1 - i0);
-  long long cells = 0;
   for (int q = i0; q < i1; ++q) {
     const BatchItem& it = bs->h_items[q];
     const double mid = 0.5 * (it.beg + it.end) / (double)it.nb;
     key[q - i0] = std::fabs(mid - 0.5);
     ord[q - i0] = q;
-    cells += it.end - it.beg;
   }
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return key[x - i0] < key[y - i0]; });
-  long long seen = 0;  // cells of the items before this one
-  for (int q : ord) {
-    const BatchItem& it = bs->h_items[q];
-    const long long left = cells - seen;  // cells from this item to the end
-    seen += it.end - it.beg;
-    int parts = left <= cells / 32 ? 8 : left <= cells / 16 ? 4 : left <= cells / 8 ? 2 : 1;
-    const int nseg = (it.end - it.beg + BSEG - 1) / BSEG;
-    parts = std::max(1, std::min(parts, nseg));
-    const int per = (nseg + parts - 1) / parts;  // segments per piece
-    for (int s0 = it.beg; s0 < it.end; s0 += per * BSEG) {
-      BatchItem piece = it;
-      piece.beg = s0;
-      piece.end = std::min(s0 + per * BSEG, it.end);
-      out.push_back(piece);
-    }
-  }
+  for (int q : ord) out.push_back(bs->h_items[q]);
 }
 
 static int upload_items(const std::vector<BatchItem>& items, BatchItem** d_items) {
@@ -195,8 +174,8 @@ static int make_items(hydro_ctx* h, int item_len) {
 }
 
 // The item order of a host-resident run over the tube groups b0: each
-// group's items ordered (and its tail cut) on their own, as one contiguous
-// range starting at part_first[p].
+// group's items ordered on their own, as one contiguous range starting at
+// part_first[p].
 static int part_items(hydro_ctx* h, const std::vector<int>& b0) {
   BatchState* bs = h->bs;
   const int P = (int)b0.size() - 1;
