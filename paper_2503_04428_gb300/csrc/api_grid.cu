@@ -274,7 +274,7 @@ static int moving_geometry(hydro_ctx* h, double dt) {
   const std::vector<double>& xf = h->faces[0];
   const int n0 = (int)xf.size() - 1;
   const double D = h->wgrid * dt;
-  std::vector<double> Af(n0 + 1), ga(n0), qr(n0), gr(n0), vr(n0);
+  std::vector<double> Af(n0 + 1), ga(n0), qr(n0), gr(n0), vr(n0), irn(n0);
   for (int f = 0; f <= n0; ++f) Af[f] = xf[f] * xf[f] + xf[f] * D + D * D / 3.0;
   for (int i = 0; i < n0; ++i) {
     const double rm = xf[i], rp = xf[i + 1];
@@ -285,12 +285,14 @@ static int moving_geometry(hydro_ctx* h, double dt) {
     qr[i] = (rp - rm) / ((rp + rm + D) * a);
     gr[i] = (Af[i + 1] - Af[i]) / a;
     vr[i] = a / an;
+    irn[i] = 1.0 / (0.5 * (rm2 + rp2));
   }
   int st;
   if ((st = upload<T>(h, Af, &h->geo[G_AF]))) return st;
   if ((st = upload<T>(h, ga, &h->geo[G_GA]))) return st;
   if ((st = upload<T>(h, qr, &h->geo[G_QR]))) return st;
   if ((st = upload<T>(h, gr, &h->geo[G_GR]))) return st;
+  if ((st = upload<T>(h, irn, &h->irn_d))) return st;
   return upload<T>(h, vr, &h->vr_d);
 }
 
@@ -398,7 +400,9 @@ static SweepArgs<T> sweep_args(hydro_ctx* h, double dt_host, double cfl, double 
   a.halo[1] = (const T*)h->halo_d[1];
   a.maxis = h->maxis;
   a.wg = (T)h->wgrid;
-  a.vr = h->maxis >= 0 && h->coords == HYDRO_SPHERICAL ? (const T*)h->vr_d : nullptr;
+  const bool mv_sph = h->maxis >= 0 && h->wgrid != 0.0 && h->coords == HYDRO_SPHERICAL;
+  a.vr = mv_sph ? (const T*)h->vr_d : nullptr;
+  a.ir_new = mv_sph && h->dim >= 2 ? (const T*)h->irn_d : nullptr;
   return a;
 }
 
@@ -1045,10 +1049,7 @@ int hydro_set_moving_grid(hydro_t h, int axis, double w) {
   }
   h->maxis = axis;
   h->wgrid = w;
-  if (h->coords == HYDRO_SPHERICAL && !h->vr_d) {
-    int st = h->arena.alloc(&h->vr_d, (size_t)h->n[0] * h->esize);
-    if (st) return st;
-  }
+
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;

@@ -103,6 +103,7 @@ struct SweepArgs {
   int maxis;
   T wg;
   const T* vr;
+  const T* ir_new;  // moving radial grid: 1/r of every radial cell after the step (its CFL widths)
 };
 
 template <typename T, int DIM>

@@ -96,6 +96,7 @@ struct hydro_ctx {
   int maxis = -1;
   double wgrid = 0.0;
   void* vr_d = nullptr;
+  void* irn_d = nullptr;  // 1/r of the radial cells after the step
   // graph of one device-dt step
   cudaGraphExec_t graph = nullptr;
   double graph_cfl = -1.0, graph_tend = -2.0;

@@ -526,25 +526,26 @@ struct Sweep {
   // with the face (normal velocities minus w; every solver here is Galilean
   // invariant), taken back to the lab frame: mass flux unchanged, normal
   // momentum flux + w F_rho, energy flux + w F_m + w^2/2 F_rho.
+  // (One call site of the solver: on a fixed axis w = 0 and the shift is
+  // exact, so the fixed grid computes what it computed without this.)
   template <int DIR>
   __device__ __forceinline__ void riemann(const T* WL, const T* WR, T* F, bool owned, T TL = T(0),
                                           T TR = T(0)) {
-    if (a.maxis == DIR) {
-      const T w = a.wg;
-      T wl[NV], wr[NV];
+    const bool mv = a.maxis == DIR;
+    const T w = mv ? a.wg : T(0);
+    T wl[NV], wr[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        wl[v] = WL[v];
-        wr[v] = WR[v];
-      }
-      wl[1 + DIR] -= w;
-      wr[1 + DIR] -= w;
-      riemann_fixed<DIR>(wl, wr, F, owned, TL, TR);
+    for (int v = 0; v < NV; ++v) {
+      wl[v] = WL[v];
+      wr[v] = WR[v];
+    }
+    wl[1 + DIR] -= w;
+    wr[1 + DIR] -= w;
+    riemann_fixed<DIR>(wl, wr, F, owned, TL, TR);
+    if (mv) {
       F[1 + DIM] += w * F[1 + DIR] + T(0.5) * w * w * F[0];
       F[1 + DIR] += w * F[0];
-      return;
     }
-    riemann_fixed<DIR>(WL, WR, F, owned, TL, TR);
   }
 
   template <int DIR>
@@ -777,7 +778,13 @@ struct Sweep {
     const T cs = dsqrt(c2n);
     T sp = T(0);
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) sp += (fabs(Wn[1 + d] - (d == a.maxis ? a.wg : T(0))) + cs) * inv_h(d, gi, gj, gz);
+    for (int d = 0; d < DIM; ++d) {
+      T ih = inv_h(d, gi, gj, gz);
+      // a moving radial grid: the new state lives in the moved cell, whose
+      // angular widths scale with its new radius
+      if (d >= 1 && a.ir_new) ih *= a.ir_new[gi] / a.geo.inv_r[gi + 2];
+      sp += (fabs(Wn[1 + d] - (d == a.maxis ? a.wg : T(0))) + cs) * ih;
+    }
     smax = fmax(smax, (double)sp);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
