@@ -479,11 +479,13 @@ def time_grids(H, torch, stream, args, only=None, alu=None):
         dt = np.float32 if prec == 32 else np.float64
         g = H.Grid.from_case(dict(case, U=case["U"].astype(dt)), prec, stream=stream.cuda_stream)
         g.run(2, case["cfl"])  # autotuner on first use
+        s0 = g.stats()
         t = timed_steps(torch, stream, lambda n: g.run(n, case["cfl"]), k)
         cells = int(np.prod(case["n"]))
         nv = case["U"].shape[0]
         bytes_cell = 2 * nv * (4 if prec == 32 else 8)
         st = g.stats()
+        t_its = (st["newton_iters"] - s0["newton_iters"]) / (cells * k) if case.get("eos_rad") else None
         g.close()
         gbs = bytes_cell * cells * k / t / 1e9
         out[name] = {"value": cells * k / t, "unit": METRIC, "ms_per_step": 1000.0 * t / k, "steps": k,
@@ -491,6 +493,11 @@ def time_grids(H, torch, stream, args, only=None, alu=None):
                      "threads": st["threads"], "zchunk": st["zchunk"],
                      "gpu_launches_per_step": 3 if name.startswith("wedge") else 1,
                      "eos": "gas + radiation (Eq. 6-7)" if case.get("eos_rad") else "ideal gas (Eq. 5)"}
+        if t_its is not None:
+            out[name]["temperature_newton"] = {
+                "iters_per_cell_update": t_its,
+                "note": "every EoS call's Newton iterations (15 calls per cell-update: the staged cells, "
+                        "6 limited and 6 predicted face states and the new state), summed by the sweep"}
         fpc = sweep_fp64_flops_per_cell() if (prec == 64 and name.startswith("sedov")) else None
         if fpc is not None and alu is not None:
             ach = fpc * cells * k / t / 1e12

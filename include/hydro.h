@@ -87,7 +87,8 @@ typedef struct {
 typedef struct {
   long long steps;         /* steps completed on this handle */
   long long faces;         /* Riemann problems solved (owned faces) */
-  long long newton_iters;  /* exact solver: Newton iterations summed over faces */
+  long long newton_iters;  /* exact solver: Newton iterations summed over faces; with the gas +
+                            * radiation EoS: the temperature Newton iterations of every EoS call */
   long long fallbacks;     /* predicted face states replaced by the cell average */
   long long mlp_faces;     /* exact solver: faces whose guess came from the MLP */
   double t;                /* simulation time (grid handles) */
@@ -174,7 +175,8 @@ int hydro_set_sources(hydro_t h, int gravity, const double g0[3], double G, doub
  * A step of a split grid is: exchange halos, (monopole) exchange shell
  * masses, take the minimum of every slab's hydro_cfl_dt, hydro_step.
  * hydro_run (device-side dt, graph) returns HYDRO_ERR_UNSUPPORTED on a grid
- * with exchanged sides. */
+ * with exchanged sides.  Slabs are built for the ideal gas without the
+ * dual-energy correction (HYDRO_ERR_UNSUPPORTED otherwise). */
 int hydro_set_exchange(hydro_t h, int axis, int side, const double ghost_faces[2]);
 int hydro_set_halo(hydro_t h, int axis, int side, const void* halo, int where);
 int hydro_get_boundary(hydro_t h, int axis, int side, void* out, int where);

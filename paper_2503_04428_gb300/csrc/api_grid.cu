@@ -433,6 +433,12 @@ static int launch_step_t(hydro_ctx* h, double dt_host, double cfl, double t_end,
       case 2: e = sweep_dispatch_rad<T, 2>(a, h->nsx, h->riemann, dual, h->stream, tx, ty, nt); break;
       default: e = sweep_dispatch_rad<T, 3>(a, h->nsx, h->riemann, dual, h->stream, tx, ty, nt); break;
     }
+  } else if (h->xaxis >= 0 || h->maxis >= 0) {
+    switch (h->dim) {
+      case 1: e = sweep_dispatch_xm<T, 1>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+      case 2: e = sweep_dispatch_xm<T, 2>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+      default: e = sweep_dispatch_xm<T, 3>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
+    }
   } else if (dual) {
     switch (h->dim) {
       case 1: e = sweep_dispatch_dual<T, 1>(a, h->nsx, h->riemann, h->stream, tx, ty, nt); break;
@@ -751,8 +757,8 @@ int hydro_create(const hydro_grid* grid, int coords, const hydro_eos* eos, int r
 int hydro_set_dual_energy(hydro_t h, double eps) {
   if (!h || h->batched) return arg_error("hydro_set_dual_energy: grid handle required");
   if (!(eps >= 0.0) || !std::isfinite(eps)) return arg_error("hydro_set_dual_energy: need eps >= 0");
-  if (eps > 0.0 && h->maxis >= 0) {
-    set_error("hydro_set_dual_energy: not built with the moving grid");
+  if (eps > 0.0 && (h->maxis >= 0 || h->xaxis >= 0)) {
+    set_error("hydro_set_dual_energy: not built with the moving grid or the slabs");
     return HYDRO_ERR_UNSUPPORTED;
   }
   if ((eps > 0.0) != (h->eps_dual > 0.0)) h->tuned = false;  // another kernel: tune again
@@ -772,8 +778,8 @@ int hydro_set_eos_radiation(hydro_t h, double R_gas, double a_rad) {
     set_error("hydro_set_eos_radiation: the exact Riemann solver assumes the ideal gas; use HLL or HLLC");
     return HYDRO_ERR_UNSUPPORTED;
   }
-  if (h->maxis >= 0) {
-    set_error("hydro_set_eos_radiation: the moving grid is built for the ideal gas");
+  if (h->maxis >= 0 || h->xaxis >= 0) {
+    set_error("hydro_set_eos_radiation: the moving grid and the slabs are built for the ideal gas");
     return HYDRO_ERR_UNSUPPORTED;
   }
   h->eos_rad = 1;
@@ -842,6 +848,10 @@ int hydro_set_exchange(hydro_t h, int axis, int side, const double ghost_faces[2
   if (h->xaxis >= 0 && h->xaxis != axis)
     return arg_error("hydro_set_exchange: only the sides of one axis can be exchanged (slabs)");
   if (h->maxis >= 0) return arg_error("hydro_set_exchange: not with a moving grid");
+  if (h->eos_rad || h->eps_dual > 0.0) {
+    set_error("hydro_set_exchange: slabs are built for the ideal gas without the dual-energy correction");
+    return HYDRO_ERR_UNSUPPORTED;
+  }
   const double f0 = ghost_faces[0], f1 = ghost_faces[1];
   const std::vector<double>& xf = h->faces[axis];
   const bool ok = side == 0 ? (f1 < f0 && f0 < xf.front()) : (xf.back() < f0 && f0 < f1);

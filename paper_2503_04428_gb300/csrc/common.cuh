@@ -113,6 +113,10 @@ cudaError_t sweep_dispatch(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t 
 template <typename T, int DIM>
 cudaError_t sweep_dispatch_dual(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s, int* tx, int* ty,
                                 int* nt);
+// A slab of a decomposed grid or a moving grid (ideal gas, no dual energy).
+template <typename T, int DIM>
+cudaError_t sweep_dispatch_xm(const SweepArgs<T>& a, int nsx, int rs, cudaStream_t s, int* tx, int* ty,
+                              int* nt);
 // The gas + radiation EoS (HLL and HLLC only), with or without dual energy.
 template <typename T, int DIM>
 cudaError_t sweep_dispatch_rad(const SweepArgs<T>& a, int nsx, int rs, int dual, cudaStream_t s, int* tx,

@@ -84,20 +84,24 @@ struct GasRad : Gas<T> {
   // step lands above the root and the descent follows.  It stops when the
   // relative step is below temp_tol and takes one more step.  y <= 0 gives
   // y/c1 <= 0, which the positivity checks reject.
-  __device__ __forceinline__ T temperature(T c1, T c4, T y, T t0 = T(0)) const {
+  // (its, if given, accumulates the Newton iterations taken.)
+  __device__ __forceinline__ T temperature(T c1, T c4, T y, T t0 = T(0), int* its = nullptr) const {
     T t = qdiv(y, c1);
     if (!(y > T(0))) return t;
     if (t0 > T(0)) t = t0;
     else if (c4 > T(0)) t = fmin(t, dsqrt(dsqrt(qdiv(y, c4))));
     bool conv = false;
-    for (int it = 0; it < 60; ++it) {
+    int it = 0;
+    while (it < 60) {
       const T t3 = t * t * t;
       const T tn = t - qdiv(c1 * t + c4 * t3 * t - y, c1 + T(4) * c4 * t3);
       const T ch = qdiv(fabs(tn - t), tn);
       t = tn;
+      ++it;
       if (conv) break;
       if (ch < temp_tol<T>()) conv = true;
     }
+    if (its) *its += it;
     return t;
   }
   // Eq. 7 from the gas and radiation pressures
@@ -113,14 +117,16 @@ struct GasRad : Gas<T> {
     c2 = sound2(rho, pg, pr);
   }
   // P, c^2 and the temperature from (rho, e) (t0: a start, see temperature)
-  __device__ __forceinline__ void from_e_t(T rho, T e, T& p, T& c2, T& t, T t0 = T(0)) const {
-    t = temperature(rho * Rg, a, e, t0);
+  __device__ __forceinline__ void from_e_t(T rho, T e, T& p, T& c2, T& t, T t0 = T(0), int* its = nullptr) const {
+    t = temperature(rho * Rg, a, e, t0, its);
     const T pg = rho * R * t, pr = a3 * t * t * t * t;
     p = pg + pr;
     c2 = sound2(rho, pg, pr);
   }
   // the temperature of (rho, P) (t0: a start, see temperature)
-  __device__ __forceinline__ T temp_p(T rho, T p, T t0 = T(0)) const { return temperature(rho * R, a3, p, t0); }
+  __device__ __forceinline__ T temp_p(T rho, T p, T t0 = T(0), int* its = nullptr) const {
+    return temperature(rho * R, a3, p, t0, its);
+  }
   // e and c^2 of a state whose temperature is known
   __device__ __forceinline__ void from_t(T rho, T t, T& e, T& c2) const {
     const T pg = rho * R * t, pr = a3 * t * t * t * t;
@@ -170,7 +176,8 @@ __device__ __forceinline__ void to_prim(const T* U, T* W, const G& gas) {
 // to_prim for the gas + radiation EoS that also returns c^2 (Eq. 7) and the
 // temperature of the same solve (t0: a Newton start, see GasRad::temperature).
 template <typename T, int D, int NSX, typename G>
-__device__ __forceinline__ void to_prim_ct(const T* U, T* W, T& c2, T& t, const G& gas, T t0 = T(0)) {
+__device__ __forceinline__ void to_prim_ct(const T* U, T* W, T& c2, T& t, const G& gas, T t0 = T(0),
+                                           int* its = nullptr) {
   const T rho = U[0];
   const T ir = qdiv(T(1), rho);
   T ke = T(0);
@@ -180,7 +187,7 @@ __device__ __forceinline__ void to_prim_ct(const T* U, T* W, T& c2, T& t, const 
     ke += U[1 + d] * W[1 + d];
   }
   W[0] = rho;
-  gas.from_e_t(rho, U[1 + D] - T(0.5) * ke, W[1 + D], c2, t, t0);
+  gas.from_e_t(rho, U[1 + D] - T(0.5) * ke, W[1 + D], c2, t, t0, its);
 #pragma unroll
   for (int s = 0; s < NSX; ++s) W[2 + D + s] = U[2 + D + s] * ir;
 }

@@ -84,8 +84,26 @@ struct SweepShape {
 
 // Ghost mapping of one axis (periodic wrap, transmissive copy of the edge
 // cell, reflective mirror with the normal momentum negated).  g in [-2, n+1].
-// A ghost of an exchanged side (domain decomposition) sets `layer` to its
-// distance - 1 from the side and returns 0; layer stays -1 otherwise.
+__device__ __forceinline__ int map_axis(int g, int n, int lo, int hi, bool& flip) {
+  flip = false;
+  if (g < 0) {
+    if (lo == BC_PERIODIC) return g + n;
+    if (lo == BC_TRANSMISSIVE) return 0;
+    flip = true;
+    return -1 - g;
+  }
+  if (g >= n) {
+    if (hi == BC_PERIODIC) return g - n;
+    if (hi == BC_TRANSMISSIVE) return n - 1;
+    flip = true;
+    return 2 * n - 1 - g;
+  }
+  return g;
+}
+
+// The same with exchanged sides (domain decomposition): a ghost of an
+// exchanged side sets `layer` to its distance - 1 from the side and returns
+// 0; layer stays -1 otherwise.
 __device__ __forceinline__ int map_axis(int g, int n, int lo, int hi, bool& flip, int& layer) {
   flip = false;
   if ((g < 0 && lo == BC_EXCHANGED) || (g >= n && hi == BC_EXCHANGED)) {
@@ -111,12 +129,14 @@ __device__ __forceinline__ int map_axis(int g, int n, int lo, int hi, bool& flip
 enum { PRED_ALL = 0, PRED_ZHI = 1, PRED_ZLO = 2 };
 
 // MODE bit 0: gas + radiation EoS (Eq. 6-7); bit 1: dual-energy correction
-// (Sect. 2.5).  Each combination is its own instantiation, so the plain step
-// carries none of the optional work.
+// (Sect. 2.5); bit 2: a slab of a decomposed grid or a moving grid (exchanged
+// ghosts, moving faces; ideal gas only).  Each combination is its own
+// instantiation, so the plain step carries none of the optional work.
 template <typename T, int DIM, int NSX, int RS, int MODE>
 struct Sweep {
   static constexpr int EOS = MODE & 1;
   static constexpr bool DUAL = (MODE & 2) != 0;
+  static constexpr bool XM = (MODE & 4) != 0;
   using S = SweepShape<T, DIM, NSX>;
   static constexpr int NV = S::NV, TX = S::TX, TY = S::TY, EX = S::EX, EY = S::EY, HY = S::HY,
                        QY = S::QY, NT = S::NT, NI = S::NI, NP = S::NP, NFX = S::NFX,
@@ -147,6 +167,7 @@ struct Sweep {
   const T* Uin;
   T* Uout;
   unsigned long long n_fallback = 0, n_iters = 0;
+  int t_iters = 0;  // radiation EoS: temperature Newton iterations of this thread (reported as n_iters)
   int err = 0;
   double smax = 0.0;
   T hfac = T(0);
@@ -206,7 +227,11 @@ struct Sweep {
     const int n0 = a.n[0], n1 = a.n[1];
     bool fz = false;
     int lz = -1;
-    const int sz = DIM == 3 ? map_axis(gz, a.n[2], a.bc[2][0], a.bc[2][1], fz, lz) : 0;
+    int sz = 0;
+    if constexpr (DIM == 3) {
+      if constexpr (XM) sz = map_axis(gz, a.n[2], a.bc[2][0], a.bc[2][1], fz, lz);
+      else sz = map_axis(gz, a.n[2], a.bc[2][0], a.bc[2][1], fz);
+    }
     const int slot = wslot(gz);
     const int nvact = 2 + DIM + a.ns;
     for (int idx = threadIdx.x; idx < S::WPL; idx += NT) {
@@ -214,14 +239,16 @@ struct Sweep {
       const int gi = min(x0 - 2 + ex, n0 + 1);
       bool fx, fy = false;
       int lx = -1, ly = -1;
-      const int si = map_axis(gi, n0, a.bc[0][0], a.bc[0][1], fx, lx);
-      int sj = 0, gj = 0;
+      int si, sj = 0, gj = 0;
+      if constexpr (XM) si = map_axis(gi, n0, a.bc[0][0], a.bc[0][1], fx, lx);
+      else si = map_axis(gi, n0, a.bc[0][0], a.bc[0][1], fx);
       if (DIM >= 2) {
         gj = min(y0 - HY + ey, n1 + 1);
-        sj = map_axis(gj, n1, a.bc[1][0], a.bc[1][1], fy, ly);
+        if constexpr (XM) sj = map_axis(gj, n1, a.bc[1][0], a.bc[1][1], fy, ly);
+        else sj = map_axis(gj, n1, a.bc[1][0], a.bc[1][1], fy);
       }
       T u[NV], w[NV];
-      const int layer = max(lx, max(ly, lz));  // >= 0: a ghost of an exchanged side
+      const int layer = XM ? max(lx, max(ly, lz)) : -1;  // >= 0: a ghost of an exchanged side
       if (layer < 0) {
         const long long c = ((long long)sz * n1 + sj) * n0 + si;
 #pragma unroll
@@ -243,7 +270,7 @@ struct Sweep {
       if (DIM == 3 && fz) u[3] = -u[3];
       if constexpr (EOS == 1) {
         T c2, t;
-        to_prim_ct<T, DIM, NSX>(u, w, c2, t, a.grad);
+        to_prim_ct<T, DIM, NSX>(u, w, c2, t, a.grad, T(0), &t_iters);
         WT[(slot * EY + ey) * EX + ex] = t;
       } else {
         to_prim<T, DIM, NSX>(u, w, gas());
@@ -318,13 +345,13 @@ struct Sweep {
       }
       w[0] = rho;
       T c2, t;
-      a.grad.from_e_t(rho, u[1 + DIM] - T(0.5) * ke, w[1 + DIM], c2, t, *tp);
+      a.grad.from_e_t(rho, u[1 + DIM] - T(0.5) * ke, w[1 + DIM], c2, t, *tp, &t_iters);
 #pragma unroll
       for (int s = 0; s < NSX; ++s) w[2 + DIM + s] = u[2 + DIM + s] * ir;
       if (!(w[0] > T(0)) || !(w[1 + DIM] > T(0))) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) w[v] = Wc[v];
-        t = a.grad.temp_p(Wc[0], Wc[1 + DIM], *tp);
+        t = a.grad.temp_p(Wc[0], Wc[1 + DIM], *tp, &t_iters);
         if (owned) ++n_fallback;
       }
       *tp = t;
@@ -352,11 +379,11 @@ struct Sweep {
   // receive the limited states' temperatures)
   template <int DIR>
   __device__ __forceinline__ void limited_fluxes(const T* Wl, const T* Wh, T* Fl, T* Fh, T* Pl, T* Ph,
-                                                 T tc = T(0), T* tl = nullptr, T* th = nullptr) const {
+                                                 T tc = T(0), T* tl = nullptr, T* th = nullptr) {
     if constexpr (EOS == 1) {
       T c2;
-      *tl = a.grad.temp_p(Wl[0], Wl[1 + DIM], tc);
-      *th = a.grad.temp_p(Wh[0], Wh[1 + DIM], tc);
+      *tl = a.grad.temp_p(Wl[0], Wl[1 + DIM], tc, &t_iters);
+      *th = a.grad.temp_p(Wh[0], Wh[1 + DIM], tc, &t_iters);
       T el, eh;
       a.grad.from_t(Wl[0], *tl, el, c2);
       a.grad.from_t(Wh[0], *th, eh, c2);
@@ -437,7 +464,9 @@ struct Sweep {
       faces_of<0>(Wm, Wc, Wp, gi, Wl, Wh);
       T Pl[NV], Ph[NV], tl = T(0), th = T(0);
       limited_fluxes<0>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
-      if (a.maxis == 0) moving_fluxes(Wl, Wh, Fl, Fh);
+      if constexpr (XM) {
+        if (a.maxis == 0) moving_fluxes(Wl, Wh, Fl, Fh);
+      }
       if constexpr (EOS == 1) {
         if (xlo) XTR[ixlo] = tl;
         if (xhi) XTL[ixhi] = th;
@@ -460,7 +489,9 @@ struct Sweep {
       faces_of<1>(Wm, Wc, Wp, gj, Wl, Wh);
       T Pl[NV], Ph[NV], tl = T(0), th = T(0);
       limited_fluxes<1>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
-      if (a.maxis == 1) moving_fluxes(Wl, Wh, Fl, Fh);
+      if constexpr (XM) {
+        if (a.maxis == 1) moving_fluxes(Wl, Wh, Fl, Fh);
+      }
       if constexpr (EOS == 1) {
         if (ylo) YTR[iylo] = tl;
         if (yhi) YTL[iyhi] = th;
@@ -483,7 +514,9 @@ struct Sweep {
       faces_of<2>(Wm, Wc, Wp, gz, Wl, Wh);
       T Pl[NV], Ph[NV], tl = T(0), th = T(0);
       limited_fluxes<2>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
-      if (a.maxis == 2) moving_fluxes(Wl, Wh, Fl, Fh);
+      if constexpr (XM) {
+        if (a.maxis == 2) moving_fluxes(Wl, Wh, Fl, Fh);
+      }
       if constexpr (EOS == 1) {
         if (zlo) ZTR[iz] = tl;
         if (zhi) ZTL[(gz & 1) * NFZ + iz] = th;
@@ -531,6 +564,10 @@ struct Sweep {
   template <int DIR>
   __device__ __forceinline__ void riemann(const T* WL, const T* WR, T* F, bool owned, T TL = T(0),
                                           T TR = T(0)) {
+    if constexpr (!XM) {
+      riemann_fixed<DIR>(WL, WR, F, owned, TL, TR);
+      return;
+    }
     const bool mv = a.maxis == DIR;
     const T w = mv ? a.wg : T(0);
     T wl[NV], wr[NV];
@@ -755,7 +792,7 @@ struct Sweep {
     }
 
     // moving radial grid: the old cell's content spread over the new volume
-    if (a.vr) {
+    if (XM && a.vr) {
       const T q = a.vr[gi];
 #pragma unroll
       for (int v = 0; v < NV; ++v) Un[v] *= q;
@@ -765,7 +802,7 @@ struct Sweep {
     T Wn[NV], c2n;
     if constexpr (EOS == 1) {
       T tn;
-      to_prim_ct<T, DIM, NSX>(Un, Wn, c2n, tn, a.grad, WT[(wslot(gz) * EY + j + HY) * EX + i + 2]);
+      to_prim_ct<T, DIM, NSX>(Un, Wn, c2n, tn, a.grad, WT[(wslot(gz) * EY + j + HY) * EX + i + 2], &t_iters);
     } else {
       to_prim<T, DIM, NSX>(Un, Wn, a.gas);
       c2n = qdiv(a.gas.g * Wn[1 + DIM], Wn[0]);
@@ -780,10 +817,15 @@ struct Sweep {
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
       T ih = inv_h(d, gi, gj, gz);
-      // a moving radial grid: the new state lives in the moved cell, whose
-      // angular widths scale with its new radius
-      if (d >= 1 && a.ir_new) ih *= a.ir_new[gi] / a.geo.inv_r[gi + 2];
-      sp += (fabs(Wn[1 + d] - (d == a.maxis ? a.wg : T(0))) + cs) * ih;
+      T ud = Wn[1 + d];
+      if constexpr (XM) {
+        // a moving radial grid: the new state lives in the moved cell, whose
+        // angular widths scale with its new radius; on the moving axis the
+        // speed counts relative to the faces
+        if (d >= 1 && a.ir_new) ih *= a.ir_new[gi] / a.geo.inv_r[gi + 2];
+        if (d == a.maxis) ud -= a.wg;
+      }
+      sp += (fabs(ud) + cs) * ih;
     }
     smax = fmax(smax, (double)sp);
 #pragma unroll
@@ -955,7 +997,8 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
     sw.owner_step(0, false, true);
   }
   __syncthreads();
-  finish_step<S::NT>(args.ctrl, sw.smax, sw.err, sw.n_fallback, sw.n_iters, 0ull, step, dtd);
+  finish_step<S::NT>(args.ctrl, sw.smax, sw.err, sw.n_fallback,
+                     (MODE & 1) ? (unsigned long long)sw.t_iters : sw.n_iters, 0ull, step, dtd);
 }
 
 template <typename T, int DIM, int NSX, int RS, int MODE>
@@ -1000,6 +1043,7 @@ cudaError_t launch_sweep_shape(const SweepArgs<T>& a, cudaStream_t s, int* tx, i
   }
 #define HYDRO_SWEEP_DISPATCH(T, DIM) HYDRO_SWEEP_DISPATCH_MODE(sweep_dispatch, T, DIM, 0)
 #define HYDRO_SWEEP_DISPATCH_DUAL(T, DIM) HYDRO_SWEEP_DISPATCH_MODE(sweep_dispatch_dual, T, DIM, 2)
+#define HYDRO_SWEEP_DISPATCH_XM(T, DIM) HYDRO_SWEEP_DISPATCH_MODE(sweep_dispatch_xm, T, DIM, 4)
 
 // The gas + radiation dispatcher (HLL, HLLC) of one (precision, dimension)
 // pair, without (MODE 1) and with (MODE 3) the dual-energy correction.
