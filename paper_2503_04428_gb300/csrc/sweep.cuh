@@ -270,7 +270,9 @@ struct Sweep {
       if (DIM == 3 && fz) u[3] = -u[3];
       if constexpr (EOS == 1) {
         T c2, t;
-        to_prim_ct<T, DIM, NSX>(u, w, c2, t, a.grad, T(0), &t_iters);
+        int k = 0;  // (a local counter: a register after inlining)
+        to_prim_ct<T, DIM, NSX>(u, w, c2, t, a.grad, T(0), &k);
+        t_iters += k;
         WT[(slot * EY + ey) * EX + ex] = t;
       } else {
         to_prim<T, DIM, NSX>(u, w, gas());
@@ -345,16 +347,18 @@ struct Sweep {
       }
       w[0] = rho;
       T c2, t;
-      a.grad.from_e_t(rho, u[1 + DIM] - T(0.5) * ke, w[1 + DIM], c2, t, *tp, &t_iters);
+      int k = 0;
+      a.grad.from_e_t(rho, u[1 + DIM] - T(0.5) * ke, w[1 + DIM], c2, t, *tp, &k);
 #pragma unroll
       for (int s = 0; s < NSX; ++s) w[2 + DIM + s] = u[2 + DIM + s] * ir;
       if (!(w[0] > T(0)) || !(w[1 + DIM] > T(0))) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) w[v] = Wc[v];
-        t = a.grad.temp_p(Wc[0], Wc[1 + DIM], *tp, &t_iters);
+        t = a.grad.temp_p(Wc[0], Wc[1 + DIM], *tp, &k);
         if (owned) ++n_fallback;
       }
       *tp = t;
+      t_iters += k;
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) w[v] = p[v * st];
@@ -382,8 +386,10 @@ struct Sweep {
                                                  T tc = T(0), T* tl = nullptr, T* th = nullptr) {
     if constexpr (EOS == 1) {
       T c2;
-      *tl = a.grad.temp_p(Wl[0], Wl[1 + DIM], tc, &t_iters);
-      *th = a.grad.temp_p(Wh[0], Wh[1 + DIM], tc, &t_iters);
+      int k = 0;
+      *tl = a.grad.temp_p(Wl[0], Wl[1 + DIM], tc, &k);
+      *th = a.grad.temp_p(Wh[0], Wh[1 + DIM], tc, &k);
+      t_iters += k;
       T el, eh;
       a.grad.from_t(Wl[0], *tl, el, c2);
       a.grad.from_t(Wh[0], *th, eh, c2);
@@ -802,7 +808,9 @@ struct Sweep {
     T Wn[NV], c2n;
     if constexpr (EOS == 1) {
       T tn;
-      to_prim_ct<T, DIM, NSX>(Un, Wn, c2n, tn, a.grad, WT[(wslot(gz) * EY + j + HY) * EX + i + 2], &t_iters);
+      int k = 0;
+      to_prim_ct<T, DIM, NSX>(Un, Wn, c2n, tn, a.grad, WT[(wslot(gz) * EY + j + HY) * EX + i + 2], &k);
+      t_iters += k;
     } else {
       to_prim<T, DIM, NSX>(Un, Wn, a.gas);
       c2n = qdiv(a.gas.g * Wn[1 + DIM], Wn[0]);
