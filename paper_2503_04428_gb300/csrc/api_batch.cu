@@ -19,7 +19,7 @@ namespace hydro {
 // Autotuner candidates: warps per CTA, cells per work item (whole 28-cell
 // segments) and persistent CTAs per SM (up to the occupancy limit).
 static const int BATCH_NW[] = {4, 8};
-static const int BATCH_ITEM[] = {28, 56, 112, 224, 448, 896, 1792, 3584};
+static const int BATCH_ITEM[] = {28, 56, 112, 224, 448, 896, 1792, 3584, 5376, 8204};  // 8204 >= the longest tube
 // Steps per captured graph on runs of many steps.
 static const int BGRAPH_STEPS = 8;
 
@@ -120,38 +120,19 @@ static void drop_graph(BatchState* bs);
 // tube start at its interface (x = 1/2) and spread from there, so items near
 // it run the exact solver and the rest mostly take the uniform-window paths.
 // Handing out the expensive items first keeps warps from waiting at the end
-// of the persistent queue (longest processing time first).  Along that order
-// the items are cut as in guided self-scheduling: a piece holds at most
-// 1/(2 nwarps) of the cells still to be handed out (whole 28-cell segments,
-// at least one), so the queue starts with whole items and ends with short
-// pieces, and the launch's warps finish close together.  Neither the order
-// nor the cuts change a result.  Appends the range's items to `out`.
-static void order_items(const BatchState* bs, int i0, int i1, int nwarps, std::vector<BatchItem>& out) {
+// of the persistent queue (longest processing time first); the order changes
+// no result.  Appends the range's items to `out`.
+static void order_items(const BatchState* bs, int i0, int i1, std::vector<BatchItem>& out) {
   std::vector<int> ord(i1 - i0);
   std::vector<double> key(i1 - i0);
-  long long left = 0;  // cells not yet handed out
   for (int q = i0; q < i1; ++q) {
     const BatchItem& it = bs->h_items[q];
     const double mid = 0.5 * (it.beg + it.end) / (double)it.nb;
     key[q - i0] = std::fabs(mid - 0.5);
     ord[q - i0] = q;
-    left += it.end - it.beg;
   }
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return key[x - i0] < key[y - i0]; });
-  const long long share = 2LL * std::max(1, nwarps);
-  for (int q : ord) {
-    const BatchItem& it = bs->h_items[q];
-    for (int s0 = it.beg; s0 < it.end;) {
-      long long cap = (left + share - 1) / share;
-      cap = std::max<long long>(BSEG, (cap + BSEG - 1) / BSEG * BSEG);
-      BatchItem piece = it;
-      piece.beg = s0;
-      piece.end = (int)std::min<long long>(it.end, s0 + cap);
-      out.push_back(piece);
-      left -= piece.end - piece.beg;
-      s0 = piece.end;
-    }
-  }
+  for (int q : ord) out.push_back(bs->h_items[q]);
 }
 
 static int upload_items(const std::vector<BatchItem>& items, BatchItem** d_items) {
@@ -162,16 +143,8 @@ static int upload_items(const std::vector<BatchItem>& items, BatchItem** d_items
   return HYDRO_OK;
 }
 
-// Warps of the persistent launch (before the launch shape is chosen: two
-// 8-warp CTAs per SM).
-static int launch_warps(const hydro_ctx* h) {
-  const BatchState* bs = h->bs;
-  return bs->grid > 0 ? bs->grid * bs->nw : 2 * 8 * std::max(1, h->num_sms);
-}
-
-// Work items of at most item_len cells, in the launch's queue order (the
-// order and the cuts follow the launch's warp count: call after setting the
-// launch shape).
+// Work items of item_len cells (the last of a tube shorter), in the
+// launch's queue order.
 static int make_items(hydro_ctx* h, int item_len) {
   BatchState* bs = h->bs;
   bs->h_items.clear();
@@ -193,7 +166,7 @@ static int make_items(hydro_ctx* h, int item_len) {
   bs->item_first[bs->ntubes] = (int)bs->h_items.size();
   bs->item_len = item_len;
   std::vector<BatchItem> q;
-  order_items(bs, 0, (int)bs->h_items.size(), launch_warps(h), q);
+  order_items(bs, 0, (int)bs->h_items.size(), q);
   bs->nitems = (int)q.size();
   bs->part_items_P = 0;  // the host-resident order is rebuilt on demand
   drop_graph(bs);
@@ -211,7 +184,7 @@ static int part_items(hydro_ctx* h, const std::vector<int>& b0) {
   bs->part_first.assign(P + 1, 0);
   for (int p = 0; p < P; ++p) {
     bs->part_first[p] = (int)q.size();
-    order_items(bs, bs->item_first[b0[p]], bs->item_first[b0[p + 1]], launch_warps(h), q);
+    order_items(bs, bs->item_first[b0[p]], bs->item_first[b0[p + 1]], q);
   }
   bs->part_first[P] = (int)q.size();
   int st = upload_items(q, &bs->part_items);

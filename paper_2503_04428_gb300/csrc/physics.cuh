@@ -92,16 +92,15 @@ struct GasRad : Gas<T> {
     else if (c4 > T(0)) t = fmin(t, dsqrt(dsqrt(qdiv(y, c4))));
     bool conv = false;
     int it = 0;
-    while (it < 60) {
+    for (; it < 60; ++it) {
       const T t3 = t * t * t;
       const T tn = t - qdiv(c1 * t + c4 * t3 * t - y, c1 + T(4) * c4 * t3);
       const T ch = qdiv(fabs(tn - t), tn);
       t = tn;
-      ++it;
       if (conv) break;
       if (ch < temp_tol<T>()) conv = true;
     }
-    if (its) *its += it;
+    if (its) *its += it < 60 ? it + 1 : 60;
     return t;
   }
   // Eq. 7 from the gas and radiation pressures
