@@ -360,11 +360,9 @@ struct Sweep {
       *tp = t;
       t_iters += k;
     } else {
+      // the slot holds the limited state's conserved form (limited_fluxes)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) w[v] = p[v * st];
-      to_cons<T, DIM, NSX>(w, u, gas());
-#pragma unroll
-      for (int v = 0; v < NV; ++v) u[v] += dU[v];
+      for (int v = 0; v < NV; ++v) u[v] = p[v * st] + dU[v];
       to_prim<T, DIM, NSX>(u, w, gas());
       if (!(w[0] > T(0)) || !(w[1 + DIM] > T(0))) {
 #pragma unroll
@@ -377,8 +375,8 @@ struct Sweep {
   }
 
   // Physical fluxes of the two limited states of one direction and what is
-  // parked in their face slots: the primitive states (ideal gas) or, for the
-  // radiation EoS, the conserved states from the same temperature solve.
+  // parked in their face slots: their conserved states (for the radiation
+  // EoS from the same temperature solve).
   // (radiation EoS: tc = the cell's temperature, the Newton start; tl/th
   // receive the limited states' temperatures)
   template <int DIR>
@@ -396,22 +394,17 @@ struct Sweep {
       flux_cons_e<T, DIM, NSX, DIR>(Wl, el, Fl, Pl);
       flux_cons_e<T, DIM, NSX, DIR>(Wh, eh, Fh, Ph);
     } else {
-      phys_flux<T, DIM, NSX, DIR>(Wl, Fl, a.gas);
-      phys_flux<T, DIM, NSX, DIR>(Wh, Fh, a.gas);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        Pl[v] = Wl[v];
-        Ph[v] = Wh[v];
-      }
+      // the fluxes and the conserved states together (the same operations
+      // as phys_flux and to_cons, each done once)
+      flux_cons_e<T, DIM, NSX, DIR>(Wl, Wl[1 + DIM] * a.gas.igm1, Fl, Pl);
+      flux_cons_e<T, DIM, NSX, DIR>(Wh, Wh[1 + DIM] * a.gas.igm1, Fh, Ph);
     }
   }
 
   // Moving grid (reading R16): along the moving axis the predictor uses the
   // fluxes through faces that move with the grid, F - w U (ideal gas).
-  __device__ __forceinline__ void moving_fluxes(const T* Wl, const T* Wh, T* Fl, T* Fh) const {
-    T ul[NV], uh[NV];
-    to_cons<T, DIM, NSX>(Wl, ul, a.gas);
-    to_cons<T, DIM, NSX>(Wh, uh, a.gas);
+  // (ul, uh: the limited states' conserved forms, as parked by limited_fluxes)
+  __device__ __forceinline__ void moving_fluxes(const T* ul, const T* uh, T* Fl, T* Fh) const {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       Fl[v] -= a.wg * ul[v];
@@ -471,7 +464,7 @@ struct Sweep {
       T Pl[NV], Ph[NV], tl = T(0), th = T(0);
       limited_fluxes<0>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
       if constexpr (XM) {
-        if (a.maxis == 0) moving_fluxes(Wl, Wh, Fl, Fh);
+        if (a.maxis == 0) moving_fluxes(Pl, Ph, Fl, Fh);
       }
       if constexpr (EOS == 1) {
         if (xlo) XTR[ixlo] = tl;
@@ -496,7 +489,7 @@ struct Sweep {
       T Pl[NV], Ph[NV], tl = T(0), th = T(0);
       limited_fluxes<1>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
       if constexpr (XM) {
-        if (a.maxis == 1) moving_fluxes(Wl, Wh, Fl, Fh);
+        if (a.maxis == 1) moving_fluxes(Pl, Ph, Fl, Fh);
       }
       if constexpr (EOS == 1) {
         if (ylo) YTR[iylo] = tl;
@@ -521,7 +514,7 @@ struct Sweep {
       T Pl[NV], Ph[NV], tl = T(0), th = T(0);
       limited_fluxes<2>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
       if constexpr (XM) {
-        if (a.maxis == 2) moving_fluxes(Wl, Wh, Fl, Fh);
+        if (a.maxis == 2) moving_fluxes(Pl, Ph, Fl, Fh);
       }
       if constexpr (EOS == 1) {
         if (zlo) ZTR[iz] = tl;
