@@ -2,24 +2,30 @@
 
 One step = one MUSCL-Hancock time step of every tube (primitive recovery,
 limited reconstruction, Hancock predictor, exact Riemann solve with the
-learned or Toro guess, conservative update, per-tube CFL speed), i.e. one
-persistent launch of the batched kernel replayed from a CUDA graph.
+learned or Toro guess, conservative update, per-tube CFL speed).  One
+persistent launch of the batched kernel runs any number of steps: a tube's
+step waits only for the tube's own previous step, so there is no grid-wide
+barrier between steps.
 
 The workload runs every tube for K = 200 of its own CFL steps, and the cost
 of a step changes along that run (the waves spread from each interface, and
 with them the faces that run Newton).  So the `--steps` timed steps are
-spread evenly over the 200-step run (step j*200/steps for j < steps; the
-first `--steps` steps if that is more than 200), each timed alone with CUDA
-events; the run is advanced untimed between them.
+windows of consecutive steps of the 200-step run, each window one launch
+timed with CUDA events: two windows centred in the two halves of the run
+(one for fewer than 10 steps; the whole run from 200 steps on), so that the
+timed steps' mean position is the run's; the run is advanced untimed (one
+launch) between them.
 
-Headline (`value`): FP32 bulk + MLP star-pressure guess + batched/graph, in
-cell-updates/s over all ranks, inputs resident in HBM, over those steps.
-Beside it, over the same steps: the plain FP64 + Toro-guess form of the same
-kernel (`fp64_plain`), the FP32 form without the network (`mlp_gain`), and
-the end-to-end rate through the C ABI with host buffers (`e2e`); then the
-HBM roofline of the kernel, the first steps alone (`early_window`), a dense
-state on which every face iterates (`dense_state`), the 3D grid sweeps, and
-the FP64 CPU oracle on a bounded sample (`cpu_baseline`).
+Headline (`value`): FP32 bulk + MLP star-pressure guess, in cell-updates/s
+over all ranks, inputs resident in HBM, over those steps.  Beside it, over
+the same steps: the plain FP64 + Toro-guess form of the same kernel
+(`fp64_plain`), the FP32 form without the network (`mlp_gain`), and the
+end-to-end rate through the C ABI with host buffers (`e2e`, every step its
+own call with its copies in and out); then the HBM roofline of the kernel,
+the whole 200-step run as one launch (`whole_run`), the first steps alone
+(`early_window`), a dense state on which every face iterates
+(`dense_state`), the 3D grid sweeps, and the FP64 CPU oracle on a bounded
+sample (`cpu_baseline`).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -176,12 +182,27 @@ def rank_tubes(world, rank, perturb=0.0, ntubes=NTUBES):
     return wl.tubes(n, seed=2, perturb=perturb, tube_range=(b0, b1))
 
 
-def trajectory_positions(k, length=TRAJ):
-    """0-based step indices of the k timed steps within the workload's run:
-    evenly spread over its `length` steps, or the first k steps if k >= length."""
+def trajectory_windows(k, length=TRAJ):
+    """The k timed steps as windows of consecutive steps of the workload's
+    run, each window one launch (a launch runs any number of steps, with no
+    grid-wide barrier between them): the whole run when k >= length, else
+    two windows (one, centred, when k < 10) about a quarter of the run either
+    side of its middle, placed so that the timed steps' mean position is the
+    run's.  [(first step, count)]."""
     if k >= length:
-        return list(range(k))
-    return [j * length // k for j in range(k)]
+        return [(0, k)]
+    mid = 0.5 * (length - 1)
+    if k < 10:
+        return [(int(round(mid - 0.5 * (k - 1))), k)]
+    w0, w1 = (k + 1) // 2, k // 2
+    # centres mid -/+ d0/d1 with w0 d0 = w1 d1 (about a quarter of the run each way)
+    c0, c1 = mid - 0.5 * length * w1 / k, mid + 0.5 * length * w0 / k
+    return [(int(round(c0 - 0.5 * (w0 - 1))), w0), (int(round(c1 - 0.5 * (w1 - 1))), w1)]
+
+
+def window_steps(windows):
+    """Every step index of the windows, in order."""
+    return [p + i for p, w in windows for i in range(w)]
 
 
 def job_rate(elapsed_local, cells_local, steps, dist=None, device=None):
@@ -229,42 +250,41 @@ def work_stream(torch):
     return s
 
 
-def time_trajectory(torch, stream, b, U, positions, cfl=CFL):
-    """From state U, advance the batch through the run and time each step at
-    `positions` alone: CUDA events on the launching stream around one graph
-    replay of one step, queued without a host round trip
-    (hydro_batch_enqueue) behind the untimed steps before it, so that the
-    events bracket the step's kernel and nothing else.  Returns the summed
-    device time in seconds and the solver counters accumulated over the
-    whole run (steps 0 .. last position)."""
+def time_trajectory(torch, stream, b, U, windows, cfl=CFL):
+    """From state U, advance the batch through the run and time each window
+    of consecutive steps (trajectory_windows) as one launch: CUDA events on
+    the launching stream around it, queued without a host round trip
+    (hydro_batch_enqueue) behind the untimed launch that advances the run to
+    the window, so that the events bracket the window's kernel and nothing
+    else.  Returns the summed device time in seconds and the solver counters
+    accumulated over the whole run (steps 0 .. the last window's end)."""
     b.set_state(U)
     s0 = b.stats()
     cur = 0
     evs = []
     torch.cuda.synchronize()
-    for p in positions:
+    for p, w in windows:
         if p > cur:
             b.enqueue(p - cur, cfl)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         if not evs and p == 0:
             # nothing queued ahead: keep the device busy while the host
-            # queues the first timed step, so that e0 fires right before it
+            # queues the first timed launch, so that e0 fires right before it
             torch.cuda._sleep(100000)
         e0.record(stream)
-        b.enqueue(1, cfl)
+        b.enqueue(w, cfl)
         e1.record(stream)
-        evs.append((e0, e1))
-        cur = p + 1
+        evs.append((e0, e1, w))
+        cur = p + w
     b.run(0, cfl)  # waits, and reports a failed step
     torch.cuda.synchronize()
-    per = [e0.elapsed_time(e1) * 1000.0 for e0, e1 in evs]  # microseconds
-    t = sum(per) / 1e6
+    ms = [e0.elapsed_time(e1) for e0, e1, _ in evs]
+    t = sum(ms) / 1000.0
     s1 = b.stats()
     c = counters(s0, s1)
-    c["step_us"] = {"positions": list(positions) if len(positions) <= 25 else "every step",
-                    "us": [round(x, 1) for x in per] if len(per) <= 25 else
-                    [round(x, 1) for x in per[::max(1, len(per) // 20)]]}
+    c["step_us"] = {"windows": [[p, w] for p, w in windows],
+                    "us_per_step": [round(1000.0 * m / w, 1) for m, (_, _, w) in zip(ms, evs)]}
     return t, c
 
 
@@ -370,6 +390,9 @@ def main():
     ap.add_argument("--grid-only", choices=["sedov3d_fp32", "sedov3d_fp64", "wedge_fp32", "wedge_fp32_rad"],
                     help="time one grid sweep only (profiling)")
     ap.add_argument("--grid-n", type=int, default=0, help="cells per axis for --grid-only sedov3d")
+    ap.add_argument("--item-len", type=int, default=0,
+                    help="fix the headline's work-item length (cells; 8 warps per CTA, 2 CTAs per SM) "
+                         "instead of autotuning it (measurements of particular shapes)")
     args = ap.parse_args()
     if args.skip_extras:
         args.skip_fp64 = args.skip_e2e = args.skip_grids = True
@@ -395,8 +418,8 @@ def main():
     gamma = w["gamma"]
     stream = work_stream(torch)
     weights, train_info = train_mlp(H, torch, gamma, 2)
-    positions = trajectory_positions(args.steps)
-    ksteps = len(positions)
+    windows = trajectory_windows(args.steps)
+    ksteps = sum(n for _, n in windows)
     dist_or_none = torch.distributed if ws > 1 else None
 
     def barrier():
@@ -404,48 +427,52 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # --- headline: FP32 + MLP guess, batched persistent launch replayed as a graph
+    # --- headline: FP32 + MLP guess, persistent batched launches of several steps
     U32 = torch.from_numpy(w["U"].astype(np.float32)).cuda()
     b32 = H.Batch(w["lengths"], gamma, precision=32, stream=stream.cuda_stream)
     b32.mlp_set(weights, True)
+    if args.item_len:
+        b32.set_launch(8, args.item_len, 2)
     b32.set_state(U32)
     b32.run(max(3, args.warmup), CFL)  # includes the autotuner on first use
     clocks = Clocks(local)
     barrier()
     clocks.start()
-    t32, c32 = time_trajectory(torch, stream, b32, U32, positions)
+    t32, c32 = time_trajectory(torch, stream, b32, U32, windows)
     clk = clocks.stop()
     barrier()
     value, t32 = job_rate(t32, total, ksteps, dist_or_none, "cuda")
     ms = 1000.0 * t32 / ksteps
-    # the state after the workload's 200 steps, for the accuracy comparison
+    extras = {}
+    # the workload's whole 200-step run as one launch (hydro_batch_run(200)),
+    # and the state it ends in, for the accuracy comparison
     out32 = times32 = None
     if not args.skip_fp64:
-        b32.set_state(U32)
-        b32.run(TRAJ, CFL)
+        tw, cw = time_trajectory(torch, stream, b32, U32, [(0, TRAJ)])
         out32 = b32.get_state().astype(np.float64)
         times32 = b32.times()
-
-    extras = {}
+        vw, tw = job_rate(tw, total, TRAJ, dist_or_none, "cuda")
+        extras["whole_run"] = {"value": vw, "unit": METRIC, "ms_per_step": 1000.0 * tw / TRAJ,
+                               "steps": "all %d steps of the run in one launch" % TRAJ, "counters": cw}
     # the first steps alone (the easy regime: waves near the interfaces)
     k0 = min(ksteps, 20)
-    te, ce = time_trajectory(torch, stream, b32, U32, list(range(k0)))
+    te, ce = time_trajectory(torch, stream, b32, U32, [(0, k0)])
     ve, te = job_rate(te, total, k0, dist_or_none, "cuda")
     extras["early_window"] = {"value": ve, "unit": METRIC, "ms_per_step": 1000.0 * te / k0,
                               "steps": "1-%d of the run" % k0, "counters": ce}
     if not args.skip_fp64:
         # the FP32 form without the network, same steps
         b32.mlp_set(weights, False)
-        tn, cn = time_trajectory(torch, stream, b32, U32, positions)
+        tn, cn = time_trajectory(torch, stream, b32, U32, windows)
         b32.mlp_set(weights, True)
         vn, tn = job_rate(tn, total, ksteps, dist_or_none, "cuda")
         extras["mlp_gain"] = {"value_with_network": value, "value_without_network": vn,
                               "gain": value / vn, "counters_without_network": cn}
-        extras["fp64_plain"], extras["accuracy"] = time_fp64(H, torch, stream, w, positions, ws, total, value,
+        extras["fp64_plain"], extras["accuracy"] = time_fp64(H, torch, stream, w, windows, ws, total, value,
                                                             out32, times32)
     e2e = None
     if not args.skip_e2e:
-        e2e = time_e2e(H, torch, b32, w, positions, ws, total, barrier)
+        e2e = time_e2e(H, torch, b32, w, window_steps(windows), ws, total, barrier)
     alu = None
     if not args.skip_fp64:
         extras["dense_state"] = time_dense(H, torch, stream, args, ws, rank, weights)
@@ -453,7 +480,7 @@ def main():
         extras["alu_peaks"] = alu
     if not args.skip_grids:
         extras["grid_sweep"] = time_grids(H, torch, stream, args, alu=alu)
-    return report(args, ws, rank, b32, value, ms, t32, ksteps, total, e2e, clk, train_info, c32, extras)
+    return report(args, ws, rank, b32, value, ms, t32, windows, total, e2e, clk, train_info, c32, extras)
 
 
 def time_grids(H, torch, stream, args, only=None, alu=None):
@@ -523,7 +550,7 @@ def time_dense(H, torch, stream, args, ws, rank, weights):
     out = {"state": "every cell's rho and P x (1 + 0.01 U(-1,1))", "steps": "1-%d" % k}
     for on in (True, False):
         b.mlp_set(weights, on)
-        t, c = time_trajectory(torch, stream, b, U, list(range(k)))
+        t, c = time_trajectory(torch, stream, b, U, [(0, k)])
         rate, t = job_rate(t, total, k, torch.distributed if ws > 1 else None, "cuda")
         key = "with_network" if on else "without_network"
         out[key] = {"value": rate, "unit": METRIC, "ms_per_step": 1000.0 * t / k, "counters": c}
@@ -548,7 +575,7 @@ def exact_l1_rho(H, w, rho, times):
     return float(np.bincount(face_of, weights=err).mean())
 
 
-def time_fp64(H, torch, stream, w, positions, ws, total, value32, out32, times32):
+def time_fp64(H, torch, stream, w, windows, ws, total, value32, out32, times32):
     """The plain FP64 form of the same kernel (Toro guess) over the same steps
     of the run, and the accuracy of both forms after the workload's 200 steps."""
     gamma = w["gamma"]
@@ -556,17 +583,19 @@ def time_fp64(H, torch, stream, w, positions, ws, total, value32, out32, times32
     b64 = H.Batch(w["lengths"], gamma, precision=64, stream=stream.cuda_stream)
     b64.set_state(U64)
     b64.run(3, CFL)
-    t64, c64 = time_trajectory(torch, stream, b64, U64, positions)
-    value64, t64 = job_rate(t64, total, len(positions), torch.distributed if ws > 1 else None, "cuda")
+    k = sum(n for _, n in windows)
+    t64, c64 = time_trajectory(torch, stream, b64, U64, windows)
+    value64, t64 = job_rate(t64, total, k, torch.distributed if ws > 1 else None, "cuda")
     peak, _ = load_peaks()
-    ach64 = 2 * 3 * 8 * total / (t64 / len(positions)) / 1e9
-    fp64 = {"value": value64, "unit": METRIC, "ms_per_step": 1000.0 * t64 / len(positions),
+    ach64 = 2 * 3 * 8 * total / (t64 / k) / 1e9
+    fp64 = {"value": value64, "unit": METRIC, "ms_per_step": 1000.0 * t64 / k,
             "hbm_frac": ach64 / peak, "counters": c64, "speedup_of_headline": value32 / value64,
             "steps": "the headline's steps of the run"}
     # equal stated accuracy: both forms' per-tube L1(rho) error against the
     # exact solution after the workload's 200 steps, averaged over tubes
-    b64.set_state(U64)
-    b64.run(TRAJ, CFL)
+    tw, _ = time_trajectory(torch, stream, b64, U64, [(0, TRAJ)])
+    vw, _ = job_rate(tw, total, TRAJ, torch.distributed if ws > 1 else None, "cuda")
+    fp64["whole_run"] = {"value": vw, "unit": METRIC, "ms_per_step": 1000.0 * tw / TRAJ}
     out64 = b64.get_state()
     times64 = b64.times()
     b64.close()
@@ -619,7 +648,8 @@ def time_e2e(H, torch, b32, w, positions, ws, total, barrier):
             "unpipelined_value": rate_u}
 
 
-def report(args, ws, rank, b32, value, ms, t32, ksteps, total, e2e, clk, train_info, c32, extras):
+def report(args, ws, rank, b32, value, ms, t32, windows, total, e2e, clk, train_info, c32, extras):
+    ksteps = sum(n for _, n in windows)
     peak, peak_kind = load_peaks()
     alg_bytes = 2 * 3 * 4 * total  # read U^n and write U^{n+1}, FP32
     achieved = alg_bytes / (t32 / ksteps) / 1e9
@@ -627,7 +657,7 @@ def report(args, ws, rank, b32, value, ms, t32, ksteps, total, e2e, clk, train_i
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": profiled_traffic(st["tile_x"]), "peak_kind": peak_kind, "kernel": "batched_kernel<float>",
             "algorithmic_bytes_per_launch": alg_bytes,
-            "window": "the headline's timed steps (one launch each)"}
+            "window": "the headline's timed windows (one launch of several steps each)"}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -638,17 +668,18 @@ def report(args, ws, rank, b32, value, ms, t32, ksteps, total, e2e, clk, train_i
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if args.tubes == NTUBES else "%d-tube subset of: %s" % (args.tubes, WORKLOAD),
                        "tubes_per_gpu": len(b32.lengths), "cells_per_gpu": total,
-                       "form": "FP32 bulk + MLP p* guess (two-shock faces, jump > 4) + persistent batched kernel + CUDA graph",
+                       "form": "FP32 bulk + MLP p* guess (two-shock faces, jump > 4) + persistent batched kernel, "
+                               "one launch per window of steps (per-tube step dependencies, no grid-wide barrier)",
                        "cfl": CFL, "l2": "state 208 MB per buffer > 129 MB L2 (no flush needed)",
-                       "timing": "%d steps at positions j*200/%d of the workload's 200-step run (one pass from the "
-                                 "initial state, untimed advance between them), each one graph replay timed alone "
-                                 "with CUDA events" % (ksteps, ksteps) if ksteps < TRAJ else
-                                 "steps 1-%d of the run, each timed alone with CUDA events" % ksteps,
+                       "timing": "%d steps of the workload's 200-step run (one pass from the initial state) in "
+                                 "windows of consecutive steps %s ([first step, count]), each window one launch "
+                                 "timed with CUDA events, an untimed launch advancing the run between them"
+                                 % (ksteps, json.dumps([[p, n] for p, n in windows])),
                        "partition": "the job is %d x 4096 tubes (seed 2) cut into %d ranges of about equal cells"
                                     % (ws, ws),
                        "launch": {"item_cells": st["tile_x"], "warps_per_cta": st["tile_y"], "ctas": st["zchunk"]}},
             "e2e": e2e,
-            "gpu_launches": ksteps,
+            "gpu_launches": len(windows),
             "clocks": clk,
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -231,18 +231,25 @@ int hydro_stats(hydro_t h, hydro_stats_t* out);
 int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int riemann,
                        int limiter, int precision, void* stream, hydro_t* out);
 
-/* nsteps steps of every tube in one persistent launch per step (replayed from
- * captured CUDA graphs of 8 steps and of 1 step); the first call runs the
- * launch-shape autotuner on a scratch copy of the state.  A failing step
- * (invalid state, Newton or a bounded device wait, HYDRO_ERR_TIMEOUT) leaves
- * the last good state and stops the remaining steps. */
+/* nsteps steps of every tube in one persistent launch: a tube's step waits
+ * only for the tube's own previous step (its CFL time step needs that
+ * step's maximum over the tube), never for the other tubes, so there is no
+ * grid-wide barrier between steps.  The launch is captured as a CUDA graph
+ * once per (nsteps, cfl) and replayed.  The first call runs the launch-shape
+ * autotuner on scratch copies of the state.  A failing step (invalid state,
+ * Newton or a bounded device wait, HYDRO_ERR_TIMEOUT) stops the run: every
+ * tube keeps the state of the last step it completed (the failing tube the
+ * state before its failing step), so the tubes may then have completed
+ * different numbers of steps (hydro_batch_times gives each tube's time; the
+ * step count of hydro_stats counts the steps every tube completed). */
 int hydro_batch_run(hydro_t h, int nsteps, double cfl);
 
-/* The steps of hydro_batch_run, queued on the handle's stream without
- * waiting for them (the first call still runs the autotuner, synchronously).
- * A step that fails on the device leaves the last good state, and the later
- * queued steps do nothing; the failure is reported by the next
- * hydro_batch_run (hydro_batch_run(h, 0, cfl) only waits and reports).  The
+/* The steps of hydro_batch_run, queued on the handle's stream (one launch)
+ * without waiting for them (the first call still runs the autotuner,
+ * synchronously).  A step that fails on the device stops its launch, and
+ * later queued launches do nothing; the next hydro_batch_run reports the
+ * failure and leaves every tube at its last good step as described there
+ * (hydro_batch_run(h, 0, cfl) only waits and reports).  The
  * paper has no counterpart: this lets a caller overlap its own work with the
  * steps, or time a single step on the device without the host round trip
  * of the status check. */
@@ -355,6 +362,14 @@ int hydro_fma_rate(int precision, double* tflops_out);
  * fails with HYDRO_ERR_NEWTON.  Host arrays. */
 int hydro_exact_sample(const double* WL, const double* WR, long nf, double gamma,
                        const long long* face_of, const double* xi, long npts, double* W_out);
+
+/* Fix the batched launch shape instead of autotuning it: warps per CTA (4 or
+ * 8), cells per work item (a positive multiple of 28, the kernel's segment;
+ * items longer than every tube make one item per tube) and persistent CTAs
+ * per SM (1 up to the kernel's occupancy).  HYDRO_ERR_ARG if out of range.
+ * The paper has no counterpart: this serves tests and measurements of
+ * particular shapes. */
+int hydro_batch_set_launch(hydro_t h, int warps_per_cta, int item_cells, int ctas_per_sm);
 
 /* Simulation time of every tube of a batch (ntubes doubles, host): the sum of
  * its own CFL steps dt_b = cfl / max_i (|u|+c)_i n_b since hydro_set_state. */

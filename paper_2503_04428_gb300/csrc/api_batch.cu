@@ -19,9 +19,10 @@ namespace hydro {
 // Autotuner candidates: warps per CTA, cells per work item (whole 28-cell
 // segments) and persistent CTAs per SM (up to the occupancy limit).
 static const int BATCH_NW[] = {4, 8};
-static const int BATCH_ITEM[] = {28, 56, 112, 224, 448, 896, 1792, 3584, 5376, 8204};  // 8204 >= the longest tube
-// Steps per captured graph on runs of many steps.
-static const int BGRAPH_STEPS = 8;
+static const int BATCH_ITEM[] = {28, 56, 112, 224, 448, 896, 1792, 2800, 3584, 4200, 5376, 8204};  // 8204 >= the longest tube
+// Steps per launch that the autotuner times (one launch runs any number of
+// steps; several let it see the steps overlap).
+static const int TUNE_STEPS = 6;
 
 struct BatchState {
   int ntubes = 0;
@@ -30,23 +31,22 @@ struct BatchState {
   long long faces_per_step = 0;
   long long* off_d = nullptr;
   std::vector<long long> off;
-  double* smax_cur = nullptr;
-  unsigned long long* smax_next = nullptr;
+  // per tube (see BatchArgs): speed slots (3 x ntubes); items completed in
+  // the running launch and the launch step of the last dt added, side by
+  // side (2 x ntubes words, zeroed before every launch by one memset); time
+  // and time before the last dt
+  unsigned long long* smax = nullptr;
+  unsigned int* tcnt = nullptr;
   double* t_tube = nullptr;
+  double* t_prev = nullptr;
   BatchCtrl* bctrl = nullptr;
   BatchCtrl* bctrl_host = nullptr;
   // launch shape: warps per CTA, cells per item, CTAs
   int nw = 8, item_len = 112, grid = 0;
-  BatchItem* items = nullptr;  // the launch's work queue (device)
+  BatchItem* items = nullptr;  // one step's work items in tube order (device)
   int nitems = 0;
-  std::vector<int> item_first;  // first item of every tube (+ end), tube order
-  std::vector<BatchItem> h_items;  // the items in tube order (host)
-  // items ordered within each group of tubes of a host-resident run
-  // (part_items_P = the group count they were built for; group p's items
-  // are part_first[p] .. part_first[p+1]-1)
-  BatchItem* part_items = nullptr;
-  std::vector<int> part_first;
-  int part_items_P = 0;
+  std::vector<int> item_first;  // first item of every tube (+ end)
+  std::vector<BatchItem> h_items;  // the items (host)
   // host-resident runs: per-part control blocks, copy streams and events
   int nparts = 0;
   BatchCtrl* part_ctrl = nullptr;
@@ -57,6 +57,9 @@ struct BatchState {
   // the host-resident run as a CUDA graph, for repeated calls on the same
   // pinned buffers
   cudaGraphExec_t host_graph = nullptr;
+  // captured step launches (counter reset + one launch of n steps), by
+  // (n, cfl); a few are kept
+  std::vector<std::pair<std::pair<int, double>, cudaGraphExec_t>> step_graphs;
   int hg_parts = 0, hg_nsteps = 0;
   const void* hg_in = nullptr;
   void* hg_out = nullptr;
@@ -73,10 +76,6 @@ struct BatchState {
   unsigned long long* harvest_n = nullptr;
   long long harvest_cap = 0;
   unsigned long long harvest_thresh = 0, harvest_seed = 0;
-  // graphs of one step and of BGRAPH_STEPS steps
-  cudaGraphExec_t graph = nullptr;
-  cudaGraphExec_t graph_k = nullptr;
-  double graph_cfl = -1.0;
   bool tuned = false;
   double tuned_us = 0.0;
   int limiter = 1;
@@ -116,25 +115,6 @@ static int occupancy_nw(int nw, int* blocks) {
 
 static void drop_graph(BatchState* bs);
 
-// Expected cost order of the tube-ordered items [i0, i1): the waves of every
-// tube start at its interface (x = 1/2) and spread from there, so items near
-// it run the exact solver and the rest mostly take the uniform-window paths.
-// Handing out the expensive items first keeps warps from waiting at the end
-// of the persistent queue (longest processing time first); the order changes
-// no result.  Appends the range's items to `out`.
-static void order_items(const BatchState* bs, int i0, int i1, std::vector<BatchItem>& out) {
-  std::vector<int> ord(i1 - i0);
-  std::vector<double> key(i1 - i0);
-  for (int q = i0; q < i1; ++q) {
-    const BatchItem& it = bs->h_items[q];
-    const double mid = 0.5 * (it.beg + it.end) / (double)it.nb;
-    key[q - i0] = std::fabs(mid - 0.5);
-    ord[q - i0] = q;
-  }
-  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return key[x - i0] < key[y - i0]; });
-  for (int q : ord) out.push_back(bs->h_items[q]);
-}
-
 static int upload_items(const std::vector<BatchItem>& items, BatchItem** d_items) {
   cudaFree(*d_items);
   *d_items = nullptr;
@@ -143,8 +123,10 @@ static int upload_items(const std::vector<BatchItem>& items, BatchItem** d_items
   return HYDRO_OK;
 }
 
-// Work items of item_len cells (the last of a tube shorter), in the
-// launch's queue order.
+// Work items of item_len cells (the last of a tube shorter), in tube order:
+// every step of a launch hands them out in this order, so a tube's items of
+// the next step come a whole step of the other tubes' items after its own
+// (the items of a group of consecutive tubes are one contiguous range).
 static int make_items(hydro_ctx* h, int item_len) {
   BatchState* bs = h->bs;
   bs->h_items.clear();
@@ -152,6 +134,7 @@ static int make_items(hydro_ctx* h, int item_len) {
   for (int b = 0; b < bs->ntubes; ++b) {
     bs->item_first[b] = (int)bs->h_items.size();
     const int nb = (int)(bs->off[b + 1] - bs->off[b]);
+    const int nit = (nb + item_len - 1) / item_len;
     for (int s0 = 0; s0 < nb; s0 += item_len) {
       BatchItem it;
       std::memset(&it, 0, sizeof(it));
@@ -160,60 +143,45 @@ static int make_items(hydro_ctx* h, int item_len) {
       it.beg = s0;
       it.end = std::min(s0 + item_len, nb);
       it.tube = b;
+      it.nit = nit;
       bs->h_items.push_back(it);
     }
   }
   bs->item_first[bs->ntubes] = (int)bs->h_items.size();
   bs->item_len = item_len;
-  std::vector<BatchItem> q;
-  order_items(bs, 0, (int)bs->h_items.size(), q);
-  bs->nitems = (int)q.size();
-  bs->part_items_P = 0;  // the host-resident order is rebuilt on demand
+  bs->nitems = (int)bs->h_items.size();
   drop_graph(bs);
-  return upload_items(q, &bs->items);
+  return upload_items(bs->h_items, &bs->items);
 }
 
-// The item order of a host-resident run over the tube groups b0: each
-// group's items ordered on their own, as one contiguous range starting at
-// part_first[p].
-static int part_items(hydro_ctx* h, const std::vector<int>& b0) {
-  BatchState* bs = h->bs;
-  const int P = (int)b0.size() - 1;
-  if (bs->part_items_P == P && bs->part_items) return HYDRO_OK;
-  std::vector<BatchItem> q;
-  bs->part_first.assign(P + 1, 0);
-  for (int p = 0; p < P; ++p) {
-    bs->part_first[p] = (int)q.size();
-    order_items(bs, bs->item_first[b0[p]], bs->item_first[b0[p + 1]], q);
-  }
-  bs->part_first[P] = (int)q.size();
-  int st = upload_items(q, &bs->part_items);
-  if (st) return st;
-  bs->part_items_P = P;
-  if (bs->host_graph) {  // it points at the previous arrays
-    cudaGraphExecDestroy(bs->host_graph);
-    bs->host_graph = nullptr;
-  }
-  return HYDRO_OK;
-}
+// Per-tube bookkeeping arrays of one run (the handle's, or the autotuner's
+// scratch copies).
+struct TubeArrays {
+  unsigned long long* smax;  // 3 x ntubes
+  unsigned int* tcnt;        // 2 x ntubes: item counts, then launch steps (tstart)
+  double* t_tube;
+  double* t_prev;
+};
+
+static TubeArrays tube_arrays(const BatchState* bs) { return {bs->smax, bs->tcnt, bs->t_tube, bs->t_prev}; }
 
 template <typename T>
-static BatchArgs<T> batch_args(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const double* smax_cur,
-                               unsigned long long* smax_next, double* t_tube) {
+static BatchArgs<T> batch_args(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const TubeArrays& ta, int nsteps) {
   BatchState* bs = h->bs;
   BatchArgs<T> a;
   a.A = (const T*)h->buf[0];
   a.Aw = (T*)h->buf[0];
   a.B = (T*)h->buf[1];
   a.stride = bs->stride;
-  a.off = bs->off_d;
   a.items = bs->items;
   a.nitems = bs->nitems;
-  a.ntubes = bs->ntubes;
-  a.tube0 = 0;
-  a.smax_cur = smax_cur;
-  a.smax_next = smax_next;
-  a.t_tube = t_tube;
+  a.nsteps = nsteps;
+  a.ntot = bs->ntubes;
+  a.smax = ta.smax;
+  a.tcnt = ta.tcnt;
+  a.tstart = reinterpret_cast<int*>(ta.tcnt + bs->ntubes);
+  a.t_tube = ta.t_tube;
+  a.t_prev = ta.t_prev;
   a.cfl = cfl;
   a.gas = make_gas<T>(h->gamma);
   a.limiter = bs->limiter;
@@ -229,17 +197,18 @@ static BatchArgs<T> batch_args(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const 
 }
 
 template <typename T>
-static int launch_batch_t(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const double* smax_cur,
-                          unsigned long long* smax_next, double* t_tube) {
-  BatchArgs<T> a = batch_args<T>(h, cfl, ctrl, smax_cur, smax_next, t_tube);
+static int launch_batch_a(hydro_ctx* h, const BatchArgs<T>& a) {
   if (h->bs->nw == 4) return launch_batch_nw<T, 4>(h, a, h->bs->grid);
   return launch_batch_nw<T, 8>(h, a, h->bs->grid);
 }
 
-static int launch_batch(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const double* smax_cur,
-                        unsigned long long* smax_next, double* t_tube) {
-  return h->precision == 64 ? launch_batch_t<double>(h, cfl, ctrl, smax_cur, smax_next, t_tube)
-                            : launch_batch_t<float>(h, cfl, ctrl, smax_cur, smax_next, t_tube);
+// One launch of nsteps steps of every tube (on the handle's buffers), after
+// clearing the per-launch item counts.
+static int launch_batch(hydro_ctx* h, double cfl, BatchCtrl* ctrl, const TubeArrays& ta, int nsteps) {
+  if (nsteps < 1) return HYDRO_OK;
+  HCK(cudaMemsetAsync(ta.tcnt, 0, sizeof(unsigned int) * 2 * h->bs->ntubes, h->stream));
+  return h->precision == 64 ? launch_batch_a<double>(h, batch_args<double>(h, cfl, ctrl, ta, nsteps))
+                            : launch_batch_a<float>(h, batch_args<float>(h, cfl, ctrl, ta, nsteps));
 }
 
 static int read_bctrl(hydro_ctx* h) {
@@ -255,30 +224,25 @@ static int write_bctrl(hydro_ctx* h) {
 }
 
 static void drop_graph(BatchState* bs) {
-  if (bs->graph) {
-    cudaGraphExecDestroy(bs->graph);
-    bs->graph = nullptr;
-  }
-  if (bs->graph_k) {
-    cudaGraphExecDestroy(bs->graph_k);
-    bs->graph_k = nullptr;
-  }
   if (bs->host_graph) {
     cudaGraphExecDestroy(bs->host_graph);
     bs->host_graph = nullptr;
   }
+  for (auto& g : bs->step_graphs) cudaGraphExecDestroy(g.second);
+  bs->step_graphs.clear();
 }
 
 // Autotuner of the batched launch: warps per CTA, cells per work item and
-// persistent CTAs per SM, each candidate timed with CUDA events on scratch
-// copies of the per-tube arrays and control block (the committed state is
-// untouched; outputs land in the non-current buffer).
+// persistent CTAs per SM, each candidate timed with CUDA events on a launch
+// of TUNE_STEPS steps from the current state, run on scratch copies of the
+// state, the per-tube arrays and the control block (the handle's state is
+// untouched).
 static int autotune_batch(hydro_ctx* h, double cfl) {
   BatchState* bs = h->bs;
   if (bs->tuned) return HYDRO_OK;
   bs->tuned = true;
   std::ostringstream key;
-  key << "batch8_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
+  key << "batchms_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
       << device_key();
   int cached;
   double us;
@@ -293,28 +257,50 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
   }
   int st = read_bctrl(h);
   if (st) return st;
+  const int n = bs->ntubes;
+  const size_t sbytes = (size_t)3 * bs->stride * h->esize;
   BatchCtrl base = *bs->bctrl_host;
+  const int cur = base.c.cur;
   base.c.status = 0;
   base.c.done = 0;
-  base.next_item = 0;
+  base.c.cur = 0;
+  base.next_entry = 0;
   BatchCtrl* sc = nullptr;
-  double* s_cur = nullptr;
-  unsigned long long* s_next = nullptr;
-  double* s_t = nullptr;
-  HCK(cudaMalloc(&sc, sizeof(BatchCtrl)));
-  HCK(cudaMalloc(&s_cur, sizeof(double) * bs->ntubes));
-  HCK(cudaMalloc(&s_next, sizeof(unsigned long long) * bs->ntubes));
-  HCK(cudaMalloc(&s_t, sizeof(double) * bs->ntubes));
+  TubeArrays sa = {nullptr, nullptr, nullptr, nullptr};
+  void* sbuf[2] = {nullptr, nullptr};
+  void* const hbuf[2] = {h->buf[0], h->buf[1]};
+  auto release = [&]() {
+    cudaStreamSynchronize(h->stream);
+    h->buf[0] = hbuf[0];
+    h->buf[1] = hbuf[1];
+    cudaFree(sc);
+    cudaFree(sa.smax);
+    cudaFree(sa.tcnt);
+    cudaFree(sa.t_tube);
+    cudaFree(sa.t_prev);
+    cudaFree(sbuf[0]);
+    cudaFree(sbuf[1]);
+  };
+  if (cudaMalloc(&sc, sizeof(BatchCtrl)) || cudaMalloc(&sa.smax, sizeof(unsigned long long) * 3 * n) ||
+      cudaMalloc(&sa.tcnt, sizeof(unsigned int) * 2 * n) || cudaMalloc(&sa.t_tube, sizeof(double) * n) ||
+      cudaMalloc(&sa.t_prev, sizeof(double) * n) || cudaMalloc(&sbuf[0], sbytes) || cudaMalloc(&sbuf[1], sbytes)) {
+    release();
+    set_error("hydro_batch_run: autotuner scratch allocation failed");
+    return HYDRO_ERR_OOM;
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best = 1e300;
-  int best_nw = 8, best_item = 120, best_mult = 1;
+  int best_nw = 8, best_item = 3584, best_mult = 1;
   auto reset = [&]() {
     cudaMemcpyAsync(sc, &base, sizeof(BatchCtrl), cudaMemcpyHostToDevice, h->stream);
-    cudaMemcpyAsync(s_cur, bs->smax_cur, sizeof(double) * bs->ntubes, cudaMemcpyDeviceToDevice, h->stream);
-    cudaMemsetAsync(s_next, 0, sizeof(unsigned long long) * bs->ntubes, h->stream);
+    cudaMemcpyAsync(sbuf[0], hbuf[cur], sbytes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(sa.smax, bs->smax, sizeof(unsigned long long) * 3 * n, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemsetAsync(sa.t_tube, 0, sizeof(double) * n, h->stream);
   };
+  h->buf[0] = sbuf[0];
+  h->buf[1] = sbuf[1];
   for (int nw : BATCH_NW) {
     bs->nw = nw;
     int occ = 1;
@@ -327,11 +313,11 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
         const int reps = 2;
         float ms = 0.f;
         reset();
-        if ((st = launch_batch(h, cfl, sc, s_cur, s_next, s_t))) break;
+        if ((st = launch_batch(h, cfl, sc, sa, TUNE_STEPS))) break;
         for (int r = 0; r < reps; ++r) {
           reset();
           cudaEventRecord(e0, h->stream);
-          if ((st = launch_batch(h, cfl, sc, s_cur, s_next, s_t))) break;
+          if ((st = launch_batch(h, cfl, sc, sa, TUNE_STEPS))) break;
           cudaEventRecord(e1, h->stream);
           cudaEventSynchronize(e1);
           float m1 = 0.f;
@@ -339,7 +325,7 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
           ms += m1;
         }
         if (st) break;
-        const double t = 1000.0 * ms / reps;
+        const double t = 1000.0 * ms / (reps * TUNE_STEPS);
         if (t < best) {
           best = t;
           best_nw = nw;
@@ -351,13 +337,9 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
     }
     if (st) break;
   }
-  cudaStreamSynchronize(h->stream);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFree(sc);
-  cudaFree(s_cur);
-  cudaFree(s_next);
-  cudaFree(s_t);
+  release();
   if (st) return st;
   bs->nw = best_nw;
   bs->grid = h->num_sms * best_mult;
@@ -367,20 +349,37 @@ static int autotune_batch(hydro_ctx* h, double cfl) {
   return HYDRO_OK;
 }
 
+// The per-tube bookkeeping of the state in buffer `slot` (speeds, step
+// counts, times 0; see batch_init_kernel) and its validity (*status).
 template <typename T>
-static int batch_speed(hydro_ctx* h, int slot, int* status) {
+static int batch_init(hydro_ctx* h, int slot, int* status) {
   BatchState* bs = h->bs;
   int* d_status = nullptr;
   HCK(cudaMalloc(&d_status, sizeof(int)));
   HCK(cudaMemsetAsync(d_status, 0, sizeof(int), h->stream));
-  HCK(cudaMemsetAsync(bs->smax_next, 0, sizeof(unsigned long long) * bs->ntubes, h->stream));
-  batch_speed_kernel<T><<<bs->ntubes, 256, 0, h->stream>>>((const T*)h->buf[slot], bs->stride, bs->off_d, 0,
-                                                            bs->ntubes, make_gas<T>(h->gamma), bs->smax_next,
-                                                            d_status);
+  batch_init_kernel<T><<<bs->ntubes, 256, 0, h->stream>>>((const T*)h->buf[slot], bs->stride, bs->off_d, 0,
+                                                           bs->ntubes, make_gas<T>(h->gamma), &bs->bctrl->c,
+                                                           bs->ntubes, bs->smax, bs->tcnt,
+                                                           reinterpret_cast<int*>(bs->tcnt + bs->ntubes),
+                                                           bs->t_tube, bs->t_prev, d_status);
   HCK(cudaGetLastError());
   HCK(cudaMemcpyAsync(status, d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   HCK(cudaStreamSynchronize(h->stream));
   cudaFree(d_status);
+  return HYDRO_OK;
+}
+
+// After a failed launch: every tube's last good state into buffer `cur` of
+// the launch's start, the bookkeeping restarted at its step count s0 (see
+// batch_settle_kernel).
+template <typename T>
+static int batch_settle(hydro_ctx* h, long long s0, int cur) {
+  BatchState* bs = h->bs;
+  batch_settle_kernel<T><<<bs->ntubes, 256, 0, h->stream>>>(
+      (T*)h->buf[0], (T*)h->buf[1], bs->stride, bs->off_d, bs->item_len, make_gas<T>(h->gamma), s0, cur,
+      bs->ntubes, bs->smax, bs->tcnt, reinterpret_cast<int*>(bs->tcnt + bs->ntubes), bs->t_tube, bs->t_prev);
+  HCK(cudaGetLastError());
+  HCK(cudaStreamSynchronize(h->stream));
   return HYDRO_OK;
 }
 
@@ -463,23 +462,36 @@ int hydro_batch_set_state_impl(hydro_ctx* h, const void* U, int where) {
   HCK(cudaMemcpy2DAsync(h->buf[slot], (size_t)bs->stride * h->esize, U, (size_t)bs->total * h->esize,
                         (size_t)bs->total * h->esize, 3,
                         where == HYDRO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  // the speeds of the new state go to the slots of the current step count
+  // (the rest of the bookkeeping is written only if the state is valid)
+  std::vector<unsigned long long> keep_smax(3 * (size_t)bs->ntubes);
+  std::vector<double> keep_t(2 * (size_t)bs->ntubes);
+  HCK(cudaMemcpyAsync(keep_smax.data(), bs->smax, sizeof(unsigned long long) * 3 * bs->ntubes,
+                      cudaMemcpyDeviceToHost, h->stream));
+  HCK(cudaMemcpyAsync(keep_t.data(), bs->t_tube, sizeof(double) * bs->ntubes, cudaMemcpyDeviceToHost, h->stream));
+  HCK(cudaMemcpyAsync(keep_t.data() + bs->ntubes, bs->t_prev, sizeof(double) * bs->ntubes, cudaMemcpyDeviceToHost,
+                      h->stream));
   int status = 0;
-  st = h->precision == 64 ? batch_speed<double>(h, slot, &status) : batch_speed<float>(h, slot, &status);
+  st = h->precision == 64 ? batch_init<double>(h, slot, &status) : batch_init<float>(h, slot, &status);
   if (st) return st;
   if (status) {
+    // the previous state and its bookkeeping stay
+    HCK(cudaMemcpyAsync(bs->smax, keep_smax.data(), sizeof(unsigned long long) * 3 * bs->ntubes,
+                        cudaMemcpyHostToDevice, h->stream));
+    HCK(cudaMemcpyAsync(bs->t_tube, keep_t.data(), sizeof(double) * bs->ntubes, cudaMemcpyHostToDevice,
+                        h->stream));
+    HCK(cudaMemcpyAsync(bs->t_prev, keep_t.data() + bs->ntubes, sizeof(double) * bs->ntubes,
+                        cudaMemcpyHostToDevice, h->stream));
+    HCK(cudaStreamSynchronize(h->stream));
     set_error(status == HYDRO_ERR_NONFINITE ? "hydro_set_state: non-finite value in the state"
                                             : "hydro_set_state: density or pressure not positive");
     return status;
   }
-  HCK(cudaMemcpyAsync(bs->smax_cur, bs->smax_next, sizeof(double) * bs->ntubes, cudaMemcpyDeviceToDevice,
-                      h->stream));
-  HCK(cudaMemsetAsync(bs->smax_next, 0, sizeof(unsigned long long) * bs->ntubes, h->stream));
-  HCK(cudaMemsetAsync(bs->t_tube, 0, sizeof(double) * bs->ntubes, h->stream));
   bs->bctrl_host->c.cur = slot;
   bs->bctrl_host->c.status = 0;
   bs->bctrl_host->c.done = 0;
   bs->bctrl_host->c.err_step = -1;
-  bs->bctrl_host->next_item = 0;
+  bs->bctrl_host->next_entry = 0;
   return write_bctrl(h);
 }
 
@@ -521,7 +533,6 @@ void hydro_batch_free_impl(hydro_ctx* h) {
   drop_graph(bs);
   cudaFree(bs->part_ctrl);
   cudaFreeHost(bs->part_ctrl_host);
-  cudaFree(bs->part_items);
   if (bs->ev_fork) cudaEventDestroy(bs->ev_fork);
   if (bs->ev_join) cudaEventDestroy(bs->ev_join);
   if (bs->s_h2d) cudaStreamDestroy(bs->s_h2d);
@@ -529,9 +540,10 @@ void hydro_batch_free_impl(hydro_ctx* h) {
   for (cudaEvent_t e : bs->ev_in) cudaEventDestroy(e);
   for (cudaEvent_t e : bs->ev_done) cudaEventDestroy(e);
   cudaFree(bs->off_d);
-  cudaFree(bs->smax_cur);
-  cudaFree(bs->smax_next);
+  cudaFree(bs->smax);
+  cudaFree(bs->tcnt);
   cudaFree(bs->t_tube);
+  cudaFree(bs->t_prev);
   cudaFree(bs->bctrl);
   cudaFreeHost(bs->bctrl_host);
   cudaFree(bs->items);
@@ -578,22 +590,20 @@ static int enqueue_host_run(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
                           cudaMemcpyHostToDevice, bs->s_h2d));
     HCK(cudaEventRecord(bs->ev_in[p], bs->s_h2d));
     HCK(cudaStreamWaitEvent(h->stream, bs->ev_in[p], 0));
-    // the part's per-tube speeds, times and validity (as hydro_batch_set_state),
-    // in one kernel: no copy-engine work between the part's input and its step
+    // the part's per-tube speeds, step counts, times and validity (as
+    // hydro_batch_set_state), in one kernel: no copy-engine work between the
+    // part's input and its steps
     batch_init_kernel<T><<<t1 - t0, 256, 0, h->stream>>>(buf_in, bs->stride, bs->off_d, t0, t1 - t0, gas,
-                                                        bs->smax_cur, bs->smax_next, bs->t_tube,
-                                                        &bs->part_ctrl[p].c.status);
+                                                        &bs->part_ctrl[p].c, bs->ntubes, bs->smax, bs->tcnt,
+                                                        reinterpret_cast<int*>(bs->tcnt + bs->ntubes), bs->t_tube,
+                                                        bs->t_prev, &bs->part_ctrl[p].c.status);
     HCK(cudaGetLastError());
-    BatchArgs<T> a = batch_args<T>(h, cfl, &bs->part_ctrl[p], bs->smax_cur, bs->smax_next, bs->t_tube);
-    const int i0 = bs->part_first[p], i1 = bs->part_first[p + 1];
-    a.items = bs->part_items + i0;
+    // the part's steps in one launch over its tubes' items
+    BatchArgs<T> a = batch_args<T>(h, cfl, &bs->part_ctrl[p], tube_arrays(bs), nsteps);
+    const int i0 = bs->item_first[t0], i1 = bs->item_first[t1];
+    a.items = bs->items + i0;
     a.nitems = i1 - i0;
-    a.tube0 = t0;
-    a.ntubes = t1 - t0;
-    for (int k = 0; k < nsteps; ++k) {
-      st = bs->nw == 4 ? launch_batch_nw<T, 4>(h, a, bs->grid) : launch_batch_nw<T, 8>(h, a, bs->grid);
-      if (st) return st;
-    }
+    if ((st = launch_batch_a<T>(h, a))) return st;
     HCK(cudaEventRecord(bs->ev_done[p], h->stream));
     HCK(cudaStreamWaitEvent(bs->s_d2h, bs->ev_done[p], 0));
     for (int v = 0; v < 3; ++v)
@@ -645,7 +655,6 @@ static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
   }
   for (int p = 1; p <= P; ++p) b0[p] = std::min(std::max(b0[p], b0[p - 1]), bs->ntubes);
   b0[P] = bs->ntubes;
-  if ((st = part_items(h, b0))) return st;
   const int slot = 0;  // input lands in buffer 0; the result is in buffer (nsteps & 1)
   const int out_slot = nsteps & 1;
   for (int p = 0; p < P; ++p) {
@@ -712,7 +721,7 @@ static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
   g.c.status = 0;
   g.c.done = 0;
   g.c.err_step = -1;
-  g.next_item = 0;
+  g.next_entry = 0;
   if (!code) {
     g.c.cur = out_slot;
     g.c.step += nsteps;
@@ -726,6 +735,9 @@ static int batch_run_host_t(hydro_ctx* h, const T* U_in, T* U_out, int nsteps, d
   }
   if ((st = write_bctrl(h))) return st;
   if (code) {
+    // consistent bookkeeping for whatever the current buffer now holds
+    int ignored = 0;
+    if ((st = batch_init<T>(h, g.c.cur, &ignored))) return st;
     set_error("hydro_batch_run_host: device status " + std::to_string(code) +
               " (the state copied in is invalid or a step failed); the output is unspecified");
     return code;
@@ -797,9 +809,10 @@ int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int
   for (int b = 0; b < 2; ++b)
     if ((st = h->arena.alloc(&h->buf[b], bytes))) { hydro_destroy(h); return st; }
   if (cudaMalloc(&bs->off_d, sizeof(long long) * (ntubes + 1)) != cudaSuccess ||
-      cudaMalloc(&bs->smax_cur, sizeof(double) * ntubes) != cudaSuccess ||
-      cudaMalloc(&bs->smax_next, sizeof(unsigned long long) * ntubes) != cudaSuccess ||
+      cudaMalloc(&bs->smax, sizeof(unsigned long long) * 3 * ntubes) != cudaSuccess ||
+      cudaMalloc(&bs->tcnt, sizeof(unsigned int) * 2 * ntubes) != cudaSuccess ||
       cudaMalloc(&bs->t_tube, sizeof(double) * ntubes) != cudaSuccess ||
+      cudaMalloc(&bs->t_prev, sizeof(double) * ntubes) != cudaSuccess ||
       cudaMalloc(&bs->bctrl, sizeof(BatchCtrl)) != cudaSuccess ||
       cudaMallocHost(&bs->bctrl_host, sizeof(BatchCtrl)) != cudaSuccess) {
     set_error("hydro_batch_create: device allocation failed");
@@ -807,9 +820,10 @@ int hydro_batch_create(const int* lengths, int ntubes, const hydro_eos* eos, int
     return HYDRO_ERR_OOM;
   }
   cudaMemcpy(bs->off_d, bs->off.data(), sizeof(long long) * (ntubes + 1), cudaMemcpyHostToDevice);
-  cudaMemset(bs->smax_cur, 0, sizeof(double) * ntubes);
-  cudaMemset(bs->smax_next, 0, sizeof(unsigned long long) * ntubes);
+  cudaMemset(bs->smax, 0, sizeof(unsigned long long) * 3 * ntubes);
+  cudaMemset(bs->tcnt, 0, sizeof(unsigned int) * 2 * ntubes);
   cudaMemset(bs->t_tube, 0, sizeof(double) * ntubes);
+  cudaMemset(bs->t_prev, 0, sizeof(double) * ntubes);
   std::memset(bs->bctrl_host, 0, sizeof(BatchCtrl));
   bs->bctrl_host->c.err_step = -1;
   if ((st = write_bctrl(h)) || (st = make_items(h, 112))) { hydro_destroy(h); return st; }
@@ -836,29 +850,36 @@ int hydro_batch_enqueue(hydro_t h, int nsteps, double cfl) {
   BatchState* bs = h->bs;
   int st;
   if ((st = autotune_batch(h, cfl))) return st;
-  if (!bs->graph || bs->graph_cfl != cfl) {
-    drop_graph(bs);
-    // one step, and BGRAPH_STEPS steps back to back (fewer graph launches
-    // per step on long runs)
-    for (int k : {1, BGRAPH_STEPS}) {
-      cudaGraph_t g;
-      HCK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
-      for (int r = 0; r < k && st == 0; ++r) st = launch_batch(h, cfl, bs->bctrl, bs->smax_cur, bs->smax_next, bs->t_tube);
-      cudaError_t e = cudaStreamEndCapture(h->stream, &g);
-      if (st) {
-        if (e == cudaSuccess) cudaGraphDestroy(g);
-        return st;
-      }
-      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-      e = cudaGraphInstantiate(k == 1 ? &bs->graph : &bs->graph_k, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  if (nsteps == 0) return HYDRO_OK;
+  // all the steps in one launch (no grid-wide barrier between them),
+  // replayed from a captured graph of that launch
+  cudaGraphExec_t ge = nullptr;
+  for (auto& g : bs->step_graphs)
+    if (g.first.first == nsteps && g.first.second == cfl) ge = g.second;
+  if (!ge) {
+    if (bs->step_graphs.size() >= 16) {
+      for (auto& g : bs->step_graphs) cudaGraphExecDestroy(g.second);
+      bs->step_graphs.clear();
     }
-    bs->graph_cfl = cfl;
+    // the kernel's shared-memory limit is raised before the capture
+    if ((st = h->precision == 64 ? (bs->nw == 4 ? batch_attr<double, 4>() : batch_attr<double, 8>())
+                                 : (bs->nw == 4 ? batch_attr<float, 4>() : batch_attr<float, 8>())))
+      return st;
+    cudaGraph_t g;
+    HCK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+    st = launch_batch(h, cfl, bs->bctrl, tube_arrays(bs), nsteps);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (st) {
+      if (e == cudaSuccess) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "hydro_batch_enqueue: cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "hydro_batch_enqueue: cudaGraphInstantiate");
+    bs->step_graphs.push_back({{nsteps, cfl}, ge});
   }
-  int s = 0;
-  for (; s + BGRAPH_STEPS <= nsteps; s += BGRAPH_STEPS) HCK(cudaGraphLaunch(bs->graph_k, h->stream));
-  for (; s < nsteps; ++s) HCK(cudaGraphLaunch(bs->graph, h->stream));
+  HCK(cudaGraphLaunch(ge, h->stream));
   return HYDRO_OK;
 }
 
@@ -873,11 +894,15 @@ int hydro_batch_run(hydro_t h, int nsteps, double cfl) {
   if (code == 0) return HYDRO_OK;
   std::ostringstream m;
   m << "hydro_batch_run: device status " << code << " at step " << bs->bctrl_host->c.err_step;
+  // the failed launch left step and buffer as at its start: every tube's
+  // last good state back into that buffer
+  st = h->precision == 64 ? batch_settle<double>(h, bs->bctrl_host->c.step, bs->bctrl_host->c.cur)
+                          : batch_settle<float>(h, bs->bctrl_host->c.step, bs->bctrl_host->c.cur);
+  if (st) return st;
   bs->bctrl_host->c.status = 0;
   bs->bctrl_host->c.done = 0;
   bs->bctrl_host->c.err_step = -1;
-  bs->bctrl_host->next_item = 0;
-  HCK(cudaMemsetAsync(bs->smax_next, 0, sizeof(unsigned long long) * bs->ntubes, h->stream));
+  bs->bctrl_host->next_entry = 0;
   if ((st = write_bctrl(h))) return st;
   set_error(m.str());
   return code;
@@ -1156,6 +1181,25 @@ int hydro_exact_sample(const double* WL, const double* WR, long nf, double gamma
   ok(cudaGetLastError()) && ok(cudaMemcpy(W_out, dw, sizeof(double) * 3 * npts, cudaMemcpyDeviceToHost));
   cleanup();
   if (e != cudaSuccess) return cuda_fail(e, "hydro_exact_sample");
+  return HYDRO_OK;
+}
+
+int hydro_batch_set_launch(hydro_t h, int warps_per_cta, int item_cells, int ctas_per_sm) {
+  if (!h || !h->batched) return berr("hydro_batch_set_launch: batched handle required");
+  if (warps_per_cta != 4 && warps_per_cta != 8) return berr("hydro_batch_set_launch: 4 or 8 warps per CTA");
+  if (item_cells < BSEG || item_cells % BSEG != 0 || item_cells > 9999)
+    return berr("hydro_batch_set_launch: item_cells must be a multiple of 28 in [28, 9996]");
+  int occ = 1;
+  int st = h->precision == 64 ? occupancy_nw<double>(warps_per_cta, &occ) : occupancy_nw<float>(warps_per_cta, &occ);
+  if (st) return st;
+  if (ctas_per_sm < 1 || ctas_per_sm > std::max(1, occ))
+    return berr("hydro_batch_set_launch: ctas_per_sm must be in [1, " + std::to_string(std::max(1, occ)) + "]");
+  BatchState* bs = h->bs;
+  bs->nw = warps_per_cta;
+  bs->grid = h->num_sms * ctas_per_sm;
+  if ((st = make_items(h, item_cells))) return st;
+  bs->tuned = true;
+  bs->tuned_us = 0.0;
   return HYDRO_OK;
 }
 

@@ -27,7 +27,14 @@
 // network's weights arrive the same way, one bulk copy per CTA from a device
 // copy kept in the kernel's shared-memory layout; only warps that meet a face
 // using the network wait for them.
-// The last CTA to finish commits the step (per-tube speeds, times, buffer).
+// One launch runs several steps.  Its queue holds every (step, item) entry,
+// step by step, the items of a step in tube order; a tube's step waits only
+// for the tube's own previous step (its time step is the tube's own CFL
+// maximum), so there is no grid-wide barrier between steps: the warp that
+// completes a tube's step commits it (time, speed slots) and releases the
+// tube's next step.  With tube order the entries of a tube's next step come
+// a whole step of other tubes' items later, so the release has normally
+// happened when a warp takes them.
 #pragma once
 #include "common.cuh"
 
@@ -88,6 +95,31 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* m, unsigned parity
   return false;
 }
 
+// A tube's count of completed items, read with acquire semantics and
+// raised with release semantics at GPU scope (PTX ISA memory consistency
+// model): what a warp wrote before it counted its item is visible to a warp
+// that has read the count.  The release follows a __syncwarp, so it covers
+// the stores of every lane of the warp.
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void add_release(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+// Wait until count *p reaches n: 1 when it has, 0 when the launch failed
+// meanwhile (status set), -1 when 2^22 polls (each with a short sleep,
+// several seconds in all) did not see it.
+__device__ __forceinline__ int tube_wait(const unsigned int* p, unsigned int n, const volatile Ctrl* vc) {
+  for (int i = 0; i < (1 << 22); ++i) {
+    if (ld_acquire(p) >= n) return 1;
+    if (vc->status != 0) return 0;
+    __nanosleep(256);
+  }
+  return -1;
+}
+
 // Exact-solver faces by where Newton started and in which precision it ran:
 // Toro's guess, the network's guess (both in the form's precision), or the
 // FP64 solve of an FP32 hard face (reading R12), whatever its guess.
@@ -95,8 +127,7 @@ enum { CAT_TORO = 0, CAT_MLP = 1, CAT_FP64 = 2, NCAT = 3 };
 
 struct BatchCtrl {
   Ctrl c;
-  unsigned int next_item;  // work-queue head of the running launch
-  unsigned int pad2;
+  unsigned long long next_entry;  // work-queue head of the running launch (entry = step x items + item)
   unsigned long long cat_faces[NCAT];  // faces that ran Newton, per category
   unsigned long long cat_iters[NCAT];  // their Newton iterations
 };
@@ -104,15 +135,17 @@ struct BatchCtrl {
 struct MlpSmemW;
 
 // One work item: cells beg .. end-1 of tube `tube` (nb cells, the first at
-// element `base` of every variable's slab), everything a warp needs before
-// it issues the item's first copies, in one 32-byte record.
+// element `base` of every variable's slab; the tube is cut into nit items),
+// everything a warp needs before it issues the item's first copies, in one
+// 32-byte record.
 struct __align__(16) BatchItem {
   long long base;
   int nb;
   int beg;
   int end;
   int tube;
-  int pad[2];
+  int nit;
+  int pad;
 };
 static_assert(sizeof(BatchItem) == 32, "one 32-byte record per item");
 
@@ -122,14 +155,23 @@ struct BatchArgs {
   T* B;
   T* Aw;
   long long stride;            // elements between the variables' slabs (a multiple of bquant<T>())
-  const long long* off;        // ntubes + 1 cell offsets
-  const BatchItem* items;      // the work queue, in hand-out order
+  const BatchItem* items;      // one step's work items, in hand-out order (tube order)
   int nitems;
-  int ntubes;                  // tubes committed by this launch: tube0 .. tube0+ntubes-1
-  int tube0;
-  const double* smax_cur;      // per tube: max (|u|+c)/h of the current state
-  unsigned long long* smax_next;
+  int nsteps;                  // steps of every tube in this launch
+  int ntot;                    // tubes of the handle (the stride of smax)
+  // Per tube b (s = the step count of a state):
+  //   smax[(s % 3) * ntot + b]: bits of max_i (|u|+c)/h of the tube's state
+  //     after s steps; step s collects its result's in slot (s + 1) % 3 and,
+  //     in the tube's first item, clears slot (s + 2) % 3 for step s + 1;
+  //   tcnt[b]: items of the tube completed in this launch (0 at its start);
+  //   tstart[b]: 1 + the launch step whose dt the tube's first item added to
+  //     t_tube (0 none; 0 at the launch's start);
+  //   t_tube[b]: its time; t_prev[b]: its time before the last dt added.
+  unsigned long long* smax;
+  unsigned int* tcnt;
+  int* tstart;
   double* t_tube;
+  double* t_prev;
   double cfl;
   Gas<T> gas;
   int limiter;
@@ -215,6 +257,33 @@ __device__ __forceinline__ T win(T va, int off) {
   return __shfl_down_sync(0xffffffffu, va, off);
 }
 
+// Span k of item r: its 8 segments' windows (cells lo .. hi-1 of the tube,
+// clamped to it: transmissive ends), widened to 16-byte bounds: elements
+// g0 .. g0+len-1 of every variable's slab (len <= BVSTR).
+template <typename T>
+__device__ __forceinline__ void span_geom(const BatchItem& r, int k, long long& g0, int& len) {
+  constexpr int Q = bquant<T>();
+  const int lo = max(r.beg + k * BSPAN * BSEG - 2, 0);
+  const int hi = min(r.beg + (k + 1) * BSPAN * BSEG + 2, r.nb);
+  g0 = (r.base + lo) & ~(long long)(Q - 1);
+  len = (int)(((r.base + hi + Q - 1) & ~(long long)(Q - 1)) - g0);
+}
+
+// Span k of item r into a ring slot (3 variables, BVSTR elements apart), one
+// bulk copy per variable completing on the slot's mbarrier (issued by one
+// lane).
+template <typename T>
+__device__ __forceinline__ void issue_span(T* slotp, unsigned long long* bar, const T* Uin, long long stride,
+                                           const BatchItem& r, int k) {
+  long long g0;
+  int len;
+  span_geom<T>(r, k, g0, len);
+  const unsigned bytes = (unsigned)len * (unsigned)sizeof(T);
+  mbar_expect_tx(bar, 3u * bytes);
+#pragma unroll
+  for (int v = 0; v < 3; ++v) bulk_copy_g2s(slotp + v * BVSTR, Uin + v * stride + g0, bytes, bar);
+}
+
 // Two register budgets for the autotuner: 8-warp CTAs with 2 resident per SM
 // (128 registers) and 4-warp CTAs with 5 per SM (about 100).
 template <typename T, int NW>
@@ -224,11 +293,18 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
   __shared__ unsigned long long wbar;  // completes when sw has landed
   extern __shared__ __align__(16) unsigned char ring_raw[];
   const volatile Ctrl* vc = &a.ctrl->c;
-  if (vc->status != 0) return;
-  const int cur = vc->cur;
-  const long long step = vc->step;
-  const T* Uin = cur ? a.B : a.A;
-  T* Uout = cur ? a.Aw : a.B;
+  // the buffer of the state at the launch's start and the steps every tube
+  // had completed then (in shared memory: read where needed); a launch
+  // behind a failed one does nothing (one read for the whole CTA)
+  __shared__ long long s_step0;
+  __shared__ int s_cur0, s_fail;
+  if (threadIdx.x == 0) {
+    s_fail = vc->status;
+    s_step0 = vc->step;
+    s_cur0 = vc->cur;
+  }
+  __syncthreads();
+  if (s_fail != 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int BD = bdepth<T>(), Q = bquant<T>();
   T* ring = reinterpret_cast<T*>(ring_raw) + warp * (BD * 3 * BVSTR);
@@ -246,8 +322,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
       mbar_expect_tx(&wbar, (unsigned)sizeof(MlpSmemW));
       bulk_copy_g2s(&sw, a.mlp_w, (unsigned)sizeof(MlpSmemW), &wbar);
     }
-    __syncthreads();  // the barrier's init, visible to every warp
   }
+  __syncthreads();  // the launch's start values (and the weights' barrier), visible to every warp
   bool w_ready = false;  // this warp has seen the weights land
   unsigned long long n_iters = 0, n_mlp = 0, n_fb = 0;
   unsigned cat_f[NCAT] = {0u, 0u, 0u}, cat_i[NCAT] = {0u, 0u, 0u};  // per-lane counts of this launch
@@ -260,13 +336,64 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
   unsigned q_issue = 0, q_use = 0;
   bool dead = false;  // a bounded wait expired: stop, drain, report
 
+  const unsigned long long nent = (unsigned long long)a.nitems * (unsigned long long)a.nsteps;
   for (;;) {
-    int it = 0;
-    if (lane == 0) it = (int)atomicAdd(&a.ctrl->next_item, 1u);
-    it = __shfl_sync(0xffffffffu, it, 0);
-    if (it >= a.nitems) break;
-    const BatchItem itm = a.items[it];
+    // Take the next entry; wait (bounded) until its tube's previous step is
+    // complete (a step of the launch after the first); a failed launch stops
+    // here.  Then the step's dt; the tube's first item also advances the
+    // tube's time by dt and clears the speed slot that the next step
+    // collects into (every item of the previous step has read it).
+    int go = 1;
+    BatchItem itm;
+    int lstep = 0;
+    double dtd = 0.0;
+    if (lane == 0) {
+      const unsigned long long e = atomicAdd(&a.ctrl->next_entry, 1ull);
+      if (e >= nent) {
+        go = 0;  // the queue is empty
+      } else if (vc->status != 0) {
+        go = 2;
+      } else {
+        lstep = (int)(e / (unsigned long long)a.nitems);
+        itm = a.items[(int)(e - (unsigned long long)lstep * (unsigned long long)a.nitems)];
+        if (lstep > 0) {
+          const int r = tube_wait(&a.tcnt[itm.tube], (unsigned int)lstep * (unsigned int)itm.nit, vc);
+          if (r != 1) go = r < 0 ? -1 : 2;
+        }
+        if (go == 1) {
+          // the writes released with the count, visible to the bulk copies
+          asm volatile("fence.proxy.async.global;\n" ::: "memory");
+          const long long sm = (s_step0 + lstep) % 3;
+          dtd = a.cfl / __longlong_as_double((long long)__ldcg(&a.smax[sm * a.ntot + itm.tube]));
+          if (itm.beg == 0) {
+            const double t = __ldcg(&a.t_tube[itm.tube]);
+            a.t_prev[itm.tube] = t;
+            a.t_tube[itm.tube] = t + dtd;
+            a.tstart[itm.tube] = lstep + 1;
+            a.smax[((sm + 2) % 3) * a.ntot + itm.tube] = 0ull;
+          }
+        }
+      }
+    }
+    go = __shfl_sync(0xffffffffu, go, 0);
+    if (go != 1) {
+      if (go < 0 && lane == 0 && atomicCAS(&a.ctrl->c.status, 0, ST_TIMEOUT) == 0)
+        a.ctrl->c.err_step = s_step0 + lstep;
+      break;
+    }
+    // the item's record, from lane 0 to the warp
+    itm.base = __shfl_sync(0xffffffffu, itm.base, 0);
+    itm.nb = __shfl_sync(0xffffffffu, itm.nb, 0);
+    itm.beg = __shfl_sync(0xffffffffu, itm.beg, 0);
+    itm.end = __shfl_sync(0xffffffffu, itm.end, 0);
+    itm.tube = __shfl_sync(0xffffffffu, itm.tube, 0);
+    lstep = __shfl_sync(0xffffffffu, lstep, 0);
+    dtd = __shfl_sync(0xffffffffu, dtd, 0);
+    const long long step = s_step0 + lstep;
     const int b = itm.tube;
+    const bool odd = ((s_cur0 ^ lstep) & 1) != 0;
+    const T* Uin = odd ? a.B : a.A;
+    T* Uout = odd ? a.Aw : a.B;
     const int s_beg = itm.beg, s_end = itm.end, nb = itm.nb;
     const long long base = itm.base;
     const T fn = (T)nb;          // 1/h
@@ -274,45 +401,24 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     T smax = T(0);
     T* const out = Uout + base;  // the tube's cell 0 in the output
 
-    // The conserved windows (cells c0-2+lane, clamped to the tube:
-    // transmissive ends) of segments BSPAN*k .. BSPAN*k+BSPAN-1 arrive in
-    // ring slot q_use % BD as span k: cells lo .. hi-1 of the tube, widened
-    // to 16-byte bounds, copied by lane 0 with one bulk copy per variable,
-    // BD-1 spans ahead of the one in use.
+    // The conserved windows (cells c0-2+lane, clamped to the tube) of
+    // segments BSPAN*k .. BSPAN*k+BSPAN-1 arrive in ring slot q_use % BD as
+    // span k (span_geom), BD-1 spans ahead of the one in use.
     const int nseg = (s_end - s_beg + BSEG - 1) / BSEG;
     const int nspan = (nseg + BSPAN - 1) / BSPAN;
-    auto span_of = [&](int k, long long& g0, int& len) {
-      const int lo = max(s_beg + k * BSPAN * BSEG - 2, 0);
-      const int hi = min(s_beg + (k + 1) * BSPAN * BSEG + 2, nb);
-      g0 = (base + lo) & ~(long long)(Q - 1);
-      len = (int)(((base + hi + Q - 1) & ~(long long)(Q - 1)) - g0);  // <= BVSTR
-    };
-    auto issue = [&](int k) {
-      if (k < nspan) {
-        if (lane == 0) {
-          long long g0;
-          int len;
-          span_of(k, g0, len);
-          const int sl = (int)(q_issue % BD);
-          const unsigned bytes = (unsigned)len * (unsigned)sizeof(T);
-          mbar_expect_tx(&bar[warp][sl], 3u * bytes);
-#pragma unroll
-          for (int v = 0; v < 3; ++v)
-            bulk_copy_g2s(ring + sl * (3 * BVSTR) + v * BVSTR, Uin + v * a.stride + g0, bytes, &bar[warp][sl]);
-        }
-        ++q_issue;
-      }
-    };
-#pragma unroll
-    for (int k = 0; k < BD - 1; ++k) issue(k);
-    // the tube's time step, read while the first copies are in flight
-    double dtd = 0.0;
-    if (lane == 0) dtd = a.cfl / a.smax_cur[b];
-    dtd = __shfl_sync(0xffffffffu, dtd, 0);
+    for (int k = 0; k < BD - 1 && k < nspan; ++k) {
+      if (lane == 0) issue_span<T>(ring + (q_issue % BD) * (3 * BVSTR), &bar[warp][q_issue % BD], Uin, a.stride,
+                                   itm, k);
+      ++q_issue;
+    }
     const T dtdx = (T)dtd * fn;
     for (int k = 0; k < nspan; ++k) {
-      __syncwarp();     // every lane is done with the slot refilled next (read one span ago)
-      issue(k + BD - 1);
+      __syncwarp();  // every lane is done with the slot refilled next (read one span ago)
+      if (k + BD - 1 < nspan) {
+        if (lane == 0) issue_span<T>(ring + (q_issue % BD) * (3 * BVSTR), &bar[warp][q_issue % BD], Uin,
+                                     a.stride, itm, k + BD - 1);
+        ++q_issue;
+      }
       const int sl = (int)(q_use % BD);
       const bool landed = mbar_wait(&bar[warp][sl], (q_use / BD) & 1u);
       if (__any_sync(0xffffffffu, !landed)) {
@@ -325,7 +431,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
       ++q_use;
       long long g0;
       int len;
-      span_of(k, g0, len);
+      span_geom<T>(itm, k, g0, len);
       const T* slot = ring + sl * (3 * BVSTR);
       const int ib = (int)(base - g0);  // slot index of the tube's cell 0
       // A span whose whole window (every cell any of its segments reads) is
@@ -572,8 +678,25 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-    if (lane == 0) atomicMax(&a.smax_next[b], dbits((double)smax));
-    if (dead) break;
+    // A failure stops the launch before the tube completes the step: its
+    // state stays that of the previous step.
+    int ferr = err;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int e2 = __shfl_xor_sync(0xffffffffu, ferr, o);
+      ferr = ferr ? ferr : e2;
+    }
+    if (dead || ferr) {
+      if (lane == 0 && atomicCAS(&a.ctrl->c.status, 0, ferr ? ferr : ST_TIMEOUT) == 0) a.ctrl->c.err_step = step;
+      break;
+    }
+    // The item is complete: its speed maximum, then its count (a release:
+    // every lane's stores of the item come first).
+    __syncwarp();
+    if (lane == 0) {
+      atomicMax(&a.smax[((step + 1) % 3) * a.ntot + b], dbits((double)smax));
+      add_release(&a.tcnt[b], 1u);
+    }
   }
   // after an expired wait, let the copies still in flight land (bounded)
   // before the CTA's shared memory is released: spans q_use .. q_issue-1,
@@ -606,7 +729,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     if (n_iters) atomicAdd(&a.ctrl->c.iters, n_iters);
     if (n_mlp) atomicAdd(&a.ctrl->c.mlp, n_mlp);
     if (n_fb) atomicAdd(&a.ctrl->c.fallbacks, n_fb);
-    if (err && atomicCAS(&a.ctrl->c.status, 0, err) == 0) a.ctrl->c.err_step = step;
+    if (err && atomicCAS(&a.ctrl->c.status, 0, err) == 0) a.ctrl->c.err_step = -1;
   }
   // the weights' copy has landed before the CTA ends (bounded)
   if (a.mlp_on && threadIdx.x == 0) mbar_wait(&wbar, 0u);
@@ -617,116 +740,40 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
     last = atomicAdd(&a.ctrl->c.done, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last) return;
+  if (!last || threadIdx.x != 0) return;
+  // the last CTA: every tube has completed the launch's steps (or the launch
+  // failed, and the host settles the tubes)
   __threadfence();
   volatile BatchCtrl* vb = a.ctrl;
-  const bool ok = vb->c.status == 0;
-  if (ok) {
-    // This CTA runs alone now (every other CTA has taken its ticket after its
-    // last atomic), so plain loads and stores do; each thread issues the
-    // loads of CU tubes before it uses them, so that the commit costs a few
-    // memory round trips rather than a few per tube.  The speeds are read
-    // past L1 (they were written by atomics at L2).
-    constexpr int CU = 8;
-    double* smc = const_cast<double*>(a.smax_cur);
-    const int t_end = a.tube0 + a.ntubes;
-    for (int t0 = a.tube0 + threadIdx.x; t0 < t_end; t0 += CU * NW * 32) {
-      double sc[CU], tt[CU];
-      unsigned long long nb[CU];
-#pragma unroll
-      for (int k = 0; k < CU; ++k) {
-        const int t = t0 + k * NW * 32;
-        if (t < t_end) {
-          sc[k] = smc[t];
-          tt[k] = a.t_tube[t];
-          nb[k] = __ldcg(&a.smax_next[t]);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < CU; ++k) {
-        const int t = t0 + k * NW * 32;
-        if (t < t_end) {
-          a.t_tube[t] = tt[k] + a.cfl / sc[k];
-          a.smax_next[t] = 0ull;
-          smc[t] = __longlong_as_double((long long)nb[k]);
-        }
-      }
-    }
+  if (vb->c.status == 0) {
+    vb->c.step = s_step0 + a.nsteps;
+    vb->c.cur = s_cur0 ^ (a.nsteps & 1);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (ok) {
-      vb->c.step = step + 1;
-      vb->c.cur = cur ^ 1;
-    }
-    vb->c.done = 0;
-    vb->next_item = 0;
-    __threadfence();
-  }
+  vb->c.done = 0;
+  vb->next_entry = 0ull;
+  __threadfence();
 }
 
-// Signal speed of the current state per tube (after set_state).
+// max_i (|u|+c)/h over cells lo .. lo+n-1 of slab-strided state U (this
+// thread's share, strided by blockDim.x), reduced over the CTA (FP64);
+// thread 0 receives the maximum and the first invalid cell's status.
 template <typename T>
-__global__ void batch_speed_kernel(const T* U, long long stride, const long long* off, int tube0,
-                                   int ntubes, Gas<T> gas, unsigned long long* smax_bits, int* status) {
-  if ((int)blockIdx.x >= ntubes) return;
-  const int b = tube0 + blockIdx.x;
-  const long long base = off[b];
-  const int nb = (int)(off[b + 1] - base);
+__device__ void tube_speed(const T* U, long long stride, long long lo, int n, const Gas<T>& gas, double& m,
+                           int& e) {
   double smax = 0.0;
   int err = 0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     T u[3], w[3];
     bool finite = true;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-      u[v] = U[v * stride + base + i];
+      u[v] = U[v * stride + lo + i];
       finite = finite && isfinite(u[v]);
     }
     if (!finite) { err = ST_NONFINITE; continue; }
     to_prim<T, 1, 0>(u, w, gas);
     if (!(w[0] > T(0)) || !(w[2] > T(0))) { err = err ? err : ST_NEG; continue; }
-    smax = fmax(smax, (double)((fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * (T)nb));
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-    const int e2 = __shfl_xor_sync(0xffffffffu, err, o);
-    err = err ? err : e2;
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&smax_bits[b], dbits(smax));
-    if (err) atomicCAS(status, 0, err);
-  }
-}
-
-// A host-resident run's new state, one CTA per tube: smax_cur[b] = max_i
-// (|u|+c)/h of tube b (FP64), smax_next[b] = 0 (the step's atomic maximum
-// starts there) and t_tube[b] = 0, all in one pass over the tube -- no copy
-// or memset between the input copies and the step.  An invalid cell sets
-// *status.  (blockDim.x: a multiple of 32, at most 1024.)
-template <typename T>
-__global__ void batch_init_kernel(const T* U, long long stride, const long long* off, int tube0, int ntubes,
-                                  Gas<T> gas, double* smax_cur, unsigned long long* smax_next, double* t_tube,
-                                  int* status) {
-  if ((int)blockIdx.x >= ntubes) return;
-  const int b = tube0 + blockIdx.x;
-  const long long base = off[b];
-  const int nb = (int)(off[b + 1] - base);
-  double smax = 0.0;
-  int err = 0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    T u[3], w[3];
-    bool finite = true;
-#pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      u[v] = U[v * stride + base + i];
-      finite = finite && isfinite(u[v]);
-    }
-    if (!finite) { err = ST_NONFINITE; continue; }
-    to_prim<T, 1, 0>(u, w, gas);
-    if (!(w[0] > T(0)) || !(w[2] > T(0))) { err = err ? err : ST_NEG; continue; }
-    smax = fmax(smax, (double)((fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * (T)nb));
+    smax = fmax(smax, (double)((fabs(w[1]) + dsqrt(gas.g * w[2] / w[0])) * (T)n));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -741,17 +788,76 @@ __global__ void batch_init_kernel(const T* U, long long stride, const long long*
     red_e[threadIdx.x >> 5] = err;
   }
   __syncthreads();
+  m = 0.0;
+  e = 0;
   if (threadIdx.x == 0) {
-    double m = 0.0;
-    int e = 0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
       m = fmax(m, red_s[k]);
       e = e ? e : red_e[k];
     }
-    smax_cur[b] = m;
-    smax_next[b] = 0ull;
+  }
+}
+
+// A new state's per-tube bookkeeping, one CTA per tube (tubes tube0 ..
+// tube0+ntubes-1): with s = ctrl->step, speed slot s % 3 gets max_i
+// (|u|+c)/h (FP64 bits) and the other two slots 0; the tube has no item of
+// a launch completed and its time is 0.  An invalid cell sets *status.  In
+// one pass over the tube, so a host-resident run needs no copy or memset
+// between its input copy and its steps.  (blockDim.x: a multiple of 32, at
+// most 1024.)
+template <typename T>
+__global__ void batch_init_kernel(const T* U, long long stride, const long long* off, int tube0, int ntubes,
+                                  Gas<T> gas, const Ctrl* ctrl, int ntot, unsigned long long* smax,
+                                  unsigned int* tcnt, int* tstart, double* t_tube, double* t_prev, int* status) {
+  if ((int)blockIdx.x >= ntubes) return;
+  const int b = tube0 + blockIdx.x;
+  const long long base = off[b];
+  double m;
+  int e;
+  tube_speed<T>(U, stride, base, (int)(off[b + 1] - base), gas, m, e);
+  if (threadIdx.x == 0) {
+    const long long s = ctrl->step;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) smax[((s + k) % 3) * ntot + b] = k == 0 ? dbits(m) : 0ull;
+    tcnt[b] = 0u;
+    tstart[b] = 0;
     t_tube[b] = 0.0;
+    t_prev[b] = 0.0;
     if (e) atomicCAS(status, 0, e);
+  }
+}
+
+// After a failed launch that started at step count s0 with the state in
+// buffer cur0 (items of item_len cells): tube b completed k = tcnt[b] / nit
+// of its steps, so its last good state is in buffer cur0 ^ (k & 1).  Move it
+// to buffer cur0, where every tube's state then is; take back the dt of a
+// step that started but did not complete (tstart); restart the speed slots
+// at step count s0 with the tube's speed recomputed.
+template <typename T>
+__global__ void batch_settle_kernel(T* A, T* B, long long stride, const long long* off, int item_len, Gas<T> gas,
+                                    long long s0, int cur0, int ntot, unsigned long long* smax, unsigned int* tcnt,
+                                    int* tstart, double* t_tube, const double* t_prev) {
+  const int b = blockIdx.x;
+  const long long base = off[b];
+  const int nb = (int)(off[b + 1] - base);
+  T* dst = cur0 ? B : A;
+  const T* src = cur0 ? A : B;
+  const int nit = (nb + item_len - 1) / item_len;
+  const int k = (int)(tcnt[b] / (unsigned int)nit);
+  if (k & 1) {
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) dst[v * stride + base + i] = src[v * stride + base + i];
+  }
+  double m;
+  int e;
+  tube_speed<T>(dst, stride, base, nb, gas, m, e);  // (each thread reads the cells it copied)
+  if (threadIdx.x == 0) {
+    if (tstart[b] - 1 >= k) t_tube[b] = t_prev[b];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) smax[((s0 + j) % 3) * ntot + b] = j == 0 ? dbits(m) : 0ull;
+    tcnt[b] = 0u;
+    tstart[b] = 0;
   }
 }
 

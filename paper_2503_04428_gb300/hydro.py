@@ -92,6 +92,7 @@ _SIGS = {
     "hydro_batch_run_host": [_VP, _VP, _VP, C.c_int, C.c_double, C.c_int],
     "hydro_exact_sample": [_D, _D, C.c_long, C.c_double, C.POINTER(C.c_longlong), _D, C.c_long, _D],
     "hydro_batch_times": [_VP, _D],
+    "hydro_batch_set_launch": [_VP, C.c_int, C.c_int, C.c_int],
     "hydro_set_exchange": [_VP, C.c_int, C.c_int, _D],
     "hydro_set_halo": [_VP, C.c_int, C.c_int, _VP, C.c_int],
     "hydro_get_boundary": [_VP, C.c_int, C.c_int, _VP, C.c_int],
@@ -536,6 +537,10 @@ class Batch:
         pin = _host_address(U_in, self.dtype, (3, self.total))
         pout = _host_address(U_out, self.dtype, (3, self.total))
         _call("hydro_batch_run_host", self.h, pin, pout, int(nsteps), float(cfl), int(nparts))
+
+    def set_launch(self, warps_per_cta, item_cells, ctas_per_sm):
+        """Fix the launch shape instead of autotuning it (hydro_batch_set_launch)."""
+        _call("hydro_batch_set_launch", self.h, int(warps_per_cta), int(item_cells), int(ctas_per_sm))
 
     def times(self):
         """Simulation time of every tube (each advances at its own CFL step)."""

@@ -232,3 +232,81 @@ def test_tune_cache_round_trip(tmp_path):
     cache.write_text("%s %d %s\n" % (key, (8 * 10000 + 3584) * 100 + 1, us))
     item, nw, grid, sms = json.loads(run())
     assert (item, nw, grid) == (3584, 8, sms)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_one_launch_equals_single_steps(hydro_lib, precision):
+    """A launch of several steps (a tube's step waits only for its own previous
+    step) gives exactly what one-step launches give, with and without the
+    network; two queued launches equal one."""
+    w = small_tubes(10, seed=31)
+    U = w["U"].astype(np.float32) if precision == 32 else w["U"]
+    rng = np.random.default_rng(3)
+    weights = (0.1 * rng.standard_normal(O.MLP_NPARAM)).astype(np.float32)
+    for mlp in (False, True):
+        runs = []
+        for mode in ("one", "single", "queued"):
+            b = hydro_lib.Batch(w["lengths"], w["gamma"], precision=precision)
+            if mlp:
+                b.mlp_set(weights, True)
+            b.set_state(U)
+            if mode == "one":
+                b.run(9, 0.8)
+            elif mode == "single":
+                for _ in range(9):
+                    b.run(1, 0.8)
+            else:
+                b.enqueue(4, 0.8)
+                b.enqueue(5, 0.8)
+                b.run(0, 0.8)
+            assert b.stats()["steps"] == 9
+            runs.append((b.get_state(), b.times()))
+            b.close()
+        for G, T in runs[1:]:
+            assert np.array_equal(G, runs[0][0]) and np.array_equal(T, runs[0][1])
+
+
+def test_failed_step_leaves_each_tube_at_its_last_good_step(hydro_lib):
+    """One tube whose Riemann problem generates vacuum fails its first step;
+    the launch stops, and every tube is left at the last step it completed:
+    the failing tube at its initial state and time 0, each other tube at the
+    oracle's state after the k steps it completed (k may differ between tubes,
+    0..6), its time 0 exactly when k = 0.  The handle then runs on."""
+    H = hydro_lib
+    w = small_tubes(8, seed=33)
+    n_vac = 300
+    x = (np.arange(n_vac) + 0.5) / n_vac
+    Uv = wl.conserved(w["gamma"], np.ones(n_vac), [np.where(x < 0.5, -5.0, 5.0)], np.full(n_vac, 0.1))
+    lengths = list(w["lengths"][:3]) + [n_vac] + list(w["lengths"][3:])
+    sl = tube_slices(w["lengths"])
+    U = np.concatenate([w["U"][:, sl[t]] for t in range(3)] + [Uv] + [w["U"][:, sl[t]] for t in range(3, 8)],
+                       axis=1)
+    b = H.Batch(lengths, w["gamma"], precision=64)
+    b.set_state(U)
+    with pytest.raises(H.HydroError) as e:
+        b.run(6, 0.8)
+    assert e.value.status == H.HYDRO_ERR_VACUUM
+    G, T = b.get_state(), b.times()
+    slb = tube_slices(lengths)
+    assert np.array_equal(G[:, slb[3]], U[:, slb[3]]) and T[3] == 0.0
+    assert b.stats()["steps"] == 0
+    for t in range(len(lengths)):
+        if t == 3:
+            continue
+        Ut = U[:, slb[t]]
+        best, kbest = np.inf, -1
+        for k in range(7):
+            ref = Ut if k == 0 else O.batch_run([lengths[t]], Ut, w["gamma"], O.EXACT, O.MINMOD, 0.8, k)[0]
+            err = max(errors(ref, G[:, slb[t]], 1, G53)[0])
+            if err < best:
+                best, kbest = err, k
+        assert best <= 1e-11, (t, kbest, best)
+        assert (T[t] == 0.0) == (kbest == 0), (t, kbest, T[t])
+    # with the vacuum tube replaced, the handle runs on from the new state
+    U2 = U.copy()
+    U2[:, slb[3]] = wl.conserved(w["gamma"], np.ones(n_vac), [np.zeros(n_vac)], np.ones(n_vac))
+    b.set_state(U2)
+    b.run(3, 0.8)
+    ref, _ = O.batch_run(lengths, U2, w["gamma"], O.EXACT, O.MINMOD, 0.8, 3)
+    check(ref, b.get_state(), 1, G53, 64, **RUN64)
+    b.close()

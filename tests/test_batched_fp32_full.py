@@ -1,9 +1,9 @@
 """The FP32 batched form in the configuration the benchmark times, against the FP64 oracle.
 
 All 4096 tubes (256-8192 cells, 1.73e7 cells), the autotuned launch shape
-(work items of several thousand cells, so most tubes span several items),
-and a network trained by the benchmark's own recipe (bench.train_mlp): the
-form whose rate is the headline.  Tubes are independent, so the oracle
+and a fixed shape of 1792-cell work items (so that most tubes span several
+items), and a network trained by the benchmark's own recipe
+(bench.train_mlp): the form whose rate is the headline.  Tubes are independent, so the oracle
 recomputes a sample of them: the longest and the shortest tube and tubes
 that span two or three work items.  Three regimes, each compared step by
 step with both sides restarted from the oracle's state (FP32-rounded):
@@ -84,17 +84,24 @@ def _compare_steps(H, b, w, U32, picks, nsteps, label):
     return worst
 
 
-def test_fp32_full_size_sampled(hydro_lib, trained_weights):
+@pytest.mark.parametrize("shape", ["tuned", "items_1792"])
+def test_fp32_full_size_sampled(hydro_lib, trained_weights, shape):
+    """The autotuned launch shape (as in the benchmark), and a fixed shape of
+    1792-cell items (8 warps per CTA, 2 CTAs per SM) under which the long
+    tubes span several items whichever shape the autotuner picks."""
     H = hydro_lib
     w = wl.tubes()
     U0 = w["U"].astype(np.float32)
     b = H.Batch(w["lengths"], G53, precision=32)
     b.mlp_set(trained_weights, True)
+    if shape != "tuned":
+        b.set_launch(8, 1792, 2)
     b.set_state(U0)
-    b.run(1, CFL)  # autotunes the launch shape, as in the benchmark
+    b.run(1, CFL)  # autotunes the launch shape (unless fixed), as in the benchmark
     item_len = b.stats()["tile_x"]
     picks = _sample(w["lengths"], item_len)
-    assert max(w["lengths"][picks]) > 2 * item_len, (item_len, picks)
+    if shape != "tuned":
+        assert item_len == 1792 and max(w["lengths"][picks]) > 2 * item_len, (item_len, picks)
     s0 = b.stats()
     # (i) from the initial state
     worst_i = _compare_steps(H, b, w, U0, picks, 3, "initial")

@@ -71,13 +71,20 @@ def test_partition_by_cells_covers_and_balances():
     assert np.array_equal(w["lengths"], ref["lengths"]) and np.array_equal(w["U"], ref["U"])
 
 
-def test_trajectory_positions():
+def test_trajectory_windows():
+    """The timed steps: windows of consecutive steps inside the 200-step run,
+    k steps in all, whose mean step is the run's mean step (99.5)."""
     import bench
-    assert bench.trajectory_positions(200) == list(range(200))
-    p = bench.trajectory_positions(20)
-    assert p == list(range(0, 200, 10))
-    assert len(bench.trajectory_positions(7)) == 7 and max(bench.trajectory_positions(7)) < 200
-    assert bench.trajectory_positions(250) == list(range(250))
+    assert bench.trajectory_windows(200) == [(0, 200)]
+    assert bench.trajectory_windows(250) == [(0, 250)]
+    assert bench.trajectory_windows(20) == [(45, 10), (145, 10)]
+    for k in (1, 5, 7, 9, 10, 11, 20, 33, 150, 199):
+        win = bench.trajectory_windows(k)
+        steps = bench.window_steps(win)
+        assert len(steps) == k and len(set(steps)) == k
+        assert min(steps) >= 0 and max(steps) < 200
+        assert abs(np.mean(steps) - 99.5) <= 0.5, (k, win)
+        assert all(win[i][0] + win[i][1] <= win[i + 1][0] for i in range(len(win) - 1))
 
 
 def test_single_process_rate():
