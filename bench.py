@@ -97,14 +97,15 @@ def alu_peaks(H):
 
 
 def profiled_traffic(item_len):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this
-    kernel and the work-item length in effect (item boundaries re-fetch halos)."""
+    """DRAM bytes per step from the committed ncu summary (the captured
+    launch's bytes over its steps), if it matches this kernel and the
+    work-item length in effect (item boundaries re-fetch halos)."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     d = json.load(open(TRAFFIC_FILE))
     if d.get("kernel_hash") != kernel_hash() or d.get("item_len") != item_len:
         return None
-    return float(d["dram_bytes_per_launch"])
+    return float(d["dram_bytes_per_launch"]) / float(d.get("steps_per_launch", 1))
 
 
 class Clocks:
@@ -651,12 +652,15 @@ def time_e2e(H, torch, b32, w, positions, ws, total, barrier):
 def report(args, ws, rank, b32, value, ms, t32, windows, total, e2e, clk, train_info, c32, extras):
     ksteps = sum(n for _, n in windows)
     peak, peak_kind = load_peaks()
-    alg_bytes = 2 * 3 * 4 * total  # read U^n and write U^{n+1}, FP32
+    alg_bytes = 2 * 3 * 4 * total  # read U^n and write U^{n+1} every step, FP32
+    per_launch = ksteps / len(windows)  # steps per timed launch
     achieved = alg_bytes / (t32 / ksteps) / 1e9
     st = b32.stats()
+    tr = profiled_traffic(st["tile_x"])
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": profiled_traffic(st["tile_x"]), "peak_kind": peak_kind, "kernel": "batched_kernel<float>",
-            "algorithmic_bytes_per_launch": alg_bytes,
+            "traffic": None if tr is None else tr * per_launch, "peak_kind": peak_kind,
+            "kernel": "batched_kernel<float>", "algorithmic_bytes_per_launch": alg_bytes * per_launch,
+            "steps_per_launch": per_launch,
             "window": "the headline's timed windows (one launch of several steps each)"}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

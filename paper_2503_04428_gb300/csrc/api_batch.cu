@@ -237,13 +237,44 @@ static void drop_graph(BatchState* bs) {
 // of TUNE_STEPS steps from the current state, run on scratch copies of the
 // state, the per-tube arrays and the control block (the handle's state is
 // untouched).
+// Share of the current state's interior faces whose two cells differ: 0
+// (below a quarter), 1 (below three quarters) or 2.  The best launch shape
+// depends on it (long work items pay where most cells take the uniform
+// shortcut, short ones where every face runs the solver), so it is part of
+// the autotuner's cache key.
+static int state_roughness(hydro_ctx* h, int* cls) {
+  BatchState* bs = h->bs;
+  int st = read_bctrl(h);
+  if (st) return st;
+  unsigned long long* d = nullptr;
+  HCK(cudaMalloc(&d, sizeof(unsigned long long)));
+  HCK(cudaMemsetAsync(d, 0, sizeof(unsigned long long), h->stream));
+  if (h->precision == 64)
+    batch_rough_kernel<double><<<bs->ntubes, 256, 0, h->stream>>>((const double*)h->buf[bs->bctrl_host->c.cur],
+                                                                   bs->stride, bs->off_d, d);
+  else
+    batch_rough_kernel<float><<<bs->ntubes, 256, 0, h->stream>>>((const float*)h->buf[bs->bctrl_host->c.cur],
+                                                                  bs->stride, bs->off_d, d);
+  HCK(cudaGetLastError());
+  unsigned long long c = 0;
+  HCK(cudaMemcpyAsync(&c, d, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+  HCK(cudaStreamSynchronize(h->stream));
+  cudaFree(d);
+  const double f = (double)c / (double)std::max<long long>(1, bs->total - bs->ntubes);
+  *cls = f < 0.25 ? 0 : (f < 0.75 ? 1 : 2);
+  return HYDRO_OK;
+}
+
 static int autotune_batch(hydro_ctx* h, double cfl) {
   BatchState* bs = h->bs;
   if (bs->tuned) return HYDRO_OK;
   bs->tuned = true;
+  int rough = 0;
+  int st0 = state_roughness(h, &rough);
+  if (st0) return st0;
   std::ostringstream key;
-  key << "batchms_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_"
-      << device_key();
+  key << "batchms_p" << h->precision << "_t" << bs->ntubes << "_c" << bs->total << "_m" << bs->mlp_on << "_r"
+      << rough << "_" << device_key();
   int cached;
   double us;
   if (tune_cache_get(key.str(), &cached, &us)) {

@@ -110,8 +110,9 @@ __device__ __forceinline__ void add_release(unsigned int* p, unsigned int v) {
 }
 // Wait until count *p reaches n: 1 when it has, 0 when the launch failed
 // meanwhile (status set), -1 when 2^22 polls (each with a short sleep,
-// several seconds in all) did not see it.
-__device__ __forceinline__ int tube_wait(const unsigned int* p, unsigned int n, const volatile Ctrl* vc) {
+// several seconds in all) did not see it.  (Out of line: a tube is normally
+// ready when its item is taken; callers test the count first.)
+static __device__ __noinline__ int tube_wait(const unsigned int* p, unsigned int n, const volatile Ctrl* vc) {
   for (int i = 0; i < (1 << 22); ++i) {
     if (ld_acquire(p) >= n) return 1;
     if (vc->status != 0) return 0;
@@ -300,6 +301,38 @@ __device__ __forceinline__ void issue_span(T* slotp, unsigned long long* bar, co
   for (int v = 0; v < 3; ++v) bulk_copy_g2s(slotp + v * BVSTR, Uin + v * stride + g0, bytes, bar);
 }
 
+// A state that repeats over a whole window (the uniform shortcut): its |u|
+// + c, and its validity into *err (first error kept).  Out of line: it runs
+// once per new uniform state, and the kernel's hot code stays shorter.
+template <typename T>
+static __device__ __noinline__ T uniform_speed(T r0, T r1, T r2, Gas<T> gas, int* err) {
+  T u[3] = {r0 + T(0), r1 + T(0), r2 + T(0)}, w[3];
+  const bool finite = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+  to_prim<T, 1, 0>(u, w, gas);
+  if (!finite) *err = *err ? *err : ST_NONFINITE;
+  else if (!(w[0] > T(0)) || !(w[2] > T(0))) *err = *err ? *err : ST_NEG;
+  return fabs(w[1]) + dsqrt(qdiv(gas.g * w[2], w[0]));
+}
+
+// Record a gated face's states (network training data) with probability
+// thresh / 2^64, counter-based per face id and step.  Out of line: it runs
+// only while harvesting.
+template <typename T, typename A>
+static __device__ __noinline__ void harvest_face(const A& a, unsigned long long id, long long step, const T* WL,
+                                                 const T* WR) {
+  const unsigned long long hsh =
+      mix64(a.harvest_seed + 0x9E3779B97F4A7C15ull * (id + 1) + ((unsigned long long)step << 40));
+  if (hsh < a.harvest_thresh) {
+    const unsigned long long slot = atomicAdd(a.harvest_n, 1ull);
+    if ((long long)slot < a.harvest_cap) {
+      for (int v = 0; v < 3; ++v) {
+        a.harvest[slot * 6 + v] = (double)WL[v];
+        a.harvest[slot * 6 + 3 + v] = (double)WR[v];
+      }
+    }
+  }
+}
+
 // Two register budgets for the autotuner: 8-warp CTAs with 2 resident per SM
 // (128 registers) and 4-warp CTAs with 5 per SM (about 100).
 template <typename T, int NW>
@@ -372,8 +405,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
       } else {
         lstep = (int)(e / (unsigned long long)a.nitems);
         itm = a.items[(int)(e - (unsigned long long)lstep * (unsigned long long)a.nitems)];
-        if (lstep > 0) {
-          const int r = tube_wait(&a.tcnt[itm.tube], (unsigned int)lstep * (unsigned int)itm.nit, vc);
+        const unsigned int need = (unsigned int)lstep * (unsigned int)itm.nit;
+        if (lstep > 0 && ld_acquire(&a.tcnt[itm.tube]) < need) {
+          const int r = tube_wait(&a.tcnt[itm.tube], need, vc);
           if (r != 1) go = r < 0 ? -1 : 2;
         }
         if (go == 1) {
@@ -468,12 +502,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
             ur[0] = r0;
             ur[1] = r1;
             ur[2] = r2;
-            T u[3] = {r0 + T(0), r1 + T(0), r2 + T(0)}, w[3];
-            const bool finite = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
-            to_prim<T, 1, 0>(u, w, gas);
-            if (!finite) err = err ? err : ST_NONFINITE;
-            else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
-            u_spd = fabs(w[1]) + dsqrt(qdiv(gas.g * w[2], w[0]));
+            u_spd = uniform_speed<T>(r0, r1, r2, gas, &err);
           }
           smax = fmax(smax, u_spd * fn);
           const int a0 = s_beg + k * BSPAN * BSEG, a1 = min(a0 + BSPAN * BSEG, s_end);
@@ -519,12 +548,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
             ur[0] = r0;
             ur[1] = r1;
             ur[2] = r2;
-            T u[3] = {r0 + T(0), r1 + T(0), r2 + T(0)}, w[3];
-            const bool finite = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
-            to_prim<T, 1, 0>(u, w, gas);
-            if (!finite) err = err ? err : ST_NONFINITE;
-            else if (!(w[0] > T(0)) || !(w[2] > T(0))) err = err ? err : ST_NEG;
-            u_spd = fabs(w[1]) + dsqrt(qdiv(gas.g * w[2], w[0]));
+            u_spd = uniform_speed<T>(r0, r1, r2, gas, &err);
           }
         }
         if (uniform) {
@@ -600,21 +624,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
           cR = dsqrt(qdiv(gas.g * WR[2], WR[0]));
           pg = toro_guess<T>(WL[0], WL[1], WL[2], cL, WR[0], WR[1], WR[2], cR, gas, kind);
           if (!mlp_gate<T>(kind, WL[2], WR[2])) kind = -kind;  // negative: network not used
-          if (kind == 2 && a.harvest) {
-            const unsigned long long id = (unsigned long long)(base + b + c0 + lane);
-            const unsigned long long hsh =
-                mix64(a.harvest_seed + 0x9E3779B97F4A7C15ull * (id + 1) + ((unsigned long long)step << 40));
-            if (hsh < a.harvest_thresh) {
-              const unsigned long long slot = atomicAdd(a.harvest_n, 1ull);
-              if ((long long)slot < a.harvest_cap) {
-#pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                  a.harvest[slot * 6 + v] = (double)WL[v];
-                  a.harvest[slot * 6 + 3 + v] = (double)WR[v];
-                }
-              }
-            }
-          }
+          if (kind == 2 && a.harvest)
+            harvest_face<T, BatchArgs<T>>(a, (unsigned long long)(base + b + c0 + lane), step, WL, WR);
         }
         // learned guess on two-shock faces, evaluated by the whole warp
         if (a.mlp_on) {
@@ -873,6 +884,26 @@ __global__ void batch_settle_kernel(T* A, T* B, long long stride, const long lon
     tcnt[b] = 0u;
     tstart[b] = 0;
   }
+}
+
+// Interior faces of the tubes whose two cells hold different states (those
+// that need the Riemann solver), counted into *count; one CTA per tube.
+// (blockDim.x: a multiple of 32, at most 1024.)
+template <typename T>
+__global__ void batch_rough_kernel(const T* U, long long stride, const long long* off, unsigned long long* count) {
+  const int b = blockIdx.x;
+  const long long base = off[b];
+  const int nb = (int)(off[b + 1] - base);
+  unsigned int c = 0;
+  for (int i = 1 + threadIdx.x; i < nb; i += blockDim.x) {
+    bool same = true;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) same = same && U[v * stride + base + i] == U[v * stride + base + i - 1];
+    c += same ? 0u : 1u;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
 }
 
 // Exact star states of independent faces (one thread per face).

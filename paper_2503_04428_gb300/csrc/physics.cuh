@@ -560,6 +560,20 @@ __device__ __forceinline__ int newton_star(T p, T rL, T uL, T pL, T cL, T rR, T 
   return ST_OK;
 }
 
+// The state inside a rarefaction fan at x/t = S (Toro ch. 4.5): sign = +1
+// for the left fan (c = 2/(g+1) (cK + (g-1)/2 (uK - S)), u = c + S), -1 for
+// the right one (c = 2/(g+1) (cK - (g-1)/2 (uK - S)), u = S - c); rho and P
+// from the isentrope through (rK, pK).  Out of line: x/t = S lies inside a
+// fan only near sonic points, and the hot solver code stays shorter.
+template <typename T>
+static __device__ __noinline__ void fan_state(T S, T sign, T rK, T uK, T pK, T cK, Gas<T> gas, T& rho, T& u,
+                                              T& p) {
+  const T c = gas.A2 * (cK + sign * T(0.5) * gas.gm1 * (uK - S));
+  u = S + sign * c;
+  rho = rK * dpow(qdiv(c, cK), gas.two_gm1);
+  p = pK * dpow(qdiv(c, cK), gas.pow_c);
+}
+
 // Sample the exact solution at x/t = S given the star state (Toro ch. 4.5);
 // returns the (rho, u, P) there and whether it lies left of the contact
 // (ties left).
@@ -584,11 +598,7 @@ __device__ __forceinline__ bool sample_xi(T S, T rL, T uL, T pL, T cL, T rR, T u
         rho = rL * dpow(qdiv(ps, pL), gas.ig);
         u = us; p = ps;
       } else {
-        // inside the left fan: c = 2/(g+1) (cL + (g-1)/2 (uL - S)), u = c + S
-        const T c = gas.A2 * (cL + T(0.5) * gas.gm1 * (uL - S));
-        u = c + S;
-        rho = rL * dpow(qdiv(c, cL), gas.two_gm1);
-        p = pL * dpow(qdiv(c, cL), gas.pow_c);
+        fan_state<T>(S, T(1), rL, uL, pL, cL, gas, rho, u, p);  // inside the left fan
       }
     }
     return true;
@@ -610,11 +620,7 @@ __device__ __forceinline__ bool sample_xi(T S, T rL, T uL, T pL, T cL, T rR, T u
       rho = rR * dpow(qdiv(ps, pR), gas.ig);
       u = us; p = ps;
     } else {
-      // inside the right fan: c = 2/(g+1) (cR - (g-1)/2 (uR - S)), u = S - c
-      const T c = gas.A2 * (cR - T(0.5) * gas.gm1 * (uR - S));
-      u = S - c;
-      rho = rR * dpow(qdiv(c, cR), gas.two_gm1);
-      p = pR * dpow(qdiv(c, cR), gas.pow_c);
+      fan_state<T>(S, T(-1), rR, uR, pR, cR, gas, rho, u, p);  // inside the right fan
     }
   }
   return false;
