@@ -533,19 +533,25 @@ __device__ __forceinline__ int newton_star(T p, T rL, T uL, T pL, T cL, T rR, T 
   const T du = uR - uL;
   const T pfloor = T(1e-14) * T(0.5) * (pL + pR);
   if (!(p > pfloor)) p = pfloor;
-  bool conv = false;
+  // One evaluation site for the pressure functions (the iterates and the
+  // final p): the solver's code stays short.
+  bool conv = false, fin = false;
   int it = 0;
   T fL, dfL, fR, dfR;
-  while (it < 100) {
+  for (;;) {
     press_fn(p, rL, pL, cL, gas, fL, dfL);
     press_fn(p, rR, pR, cR, gas, fR, dfR);
+    if (fin || it >= 100) break;  // f at the final p (or the iteration limit)
     const T res = fL + fR + du;
     T pn = p - qdiv(res, dfL + dfR);
     if (pn < T(0)) pn = pfloor;
     ++it;
     const T ch = qdiv(T(2) * fabs(pn - p), pn + p);
     p = pn;
-    if (conv) break;
+    if (conv) {
+      fin = true;  // the extra step after convergence is done
+      continue;
+    }
     if (ch < tol) conv = true;
     if constexpr (sizeof(T) == 4) {
       if (fabs(res) <= T(8 * 1.1920929e-7) * (fabs(fL) + fabs(fR) + fabs(du))) conv = true;
@@ -553,8 +559,6 @@ __device__ __forceinline__ int newton_star(T p, T rL, T uL, T pL, T cL, T rR, T 
   }
   iters = it;
   if (!conv) return ST_NEWTON;
-  press_fn(p, rL, pL, cL, gas, fL, dfL);
-  press_fn(p, rR, pR, cR, gas, fR, dfR);
   ps = p;
   us = T(0.5) * (uL + uR) + T(0.5) * (fR - fL);
   return ST_OK;
