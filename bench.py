@@ -521,6 +521,16 @@ def time_grids(H, torch, stream, args, only=None, alu=None):
                      "threads": st["threads"], "zchunk": st["zchunk"],
                      "gpu_launches_per_step": 3 if name.startswith("wedge") else 1,
                      "eos": "gas + radiation (Eq. 6-7)" if case.get("eos_rad") else "ideal gas (Eq. 5)"}
+        if name.startswith("sedov") and prec == 32 and not only:
+            # the same steps with the conserved totals accumulated in the step
+            g = H.Grid.from_case(dict(case, U=case["U"].astype(dt)), prec, stream=stream.cuda_stream)
+            g.set_step_totals(True)
+            g.run(2, case["cfl"])
+            tt = timed_steps(torch, stream, lambda n: g.run(n, case["cfl"]), k)
+            tot = g.step_totals()
+            g.close()
+            out[name]["with_step_totals"] = {"ms_per_step": 1000.0 * tt / k, "cost": tt / t - 1.0,
+                                             "totals_fp64": [float(x) for x in tot]}
         if t_its is not None:
             out[name]["temperature_newton"] = {
                 "iters_per_cell_update": t_its,

@@ -223,6 +223,21 @@ int hydro_run(hydro_t h, int nsteps, double cfl, double t_end, double* t_out);
 
 /* Conserved totals sum_cells U dV, FP64, deterministic order; out has nv entries. */
 int hydro_totals(hydro_t h, double* out_nv);
+
+/* Conserved totals accumulated inside the step (spec form (1): FP32
+ * bulk arithmetic, FP64 conservation sums).  With on != 0 every later step
+ * (hydro_step, hydro_run) also sums U dV of the cells it updates in FP64:
+ * each CTA of the fused sweep in a fixed order over its cells, into its own
+ * partial; hydro_step_totals then sums the partials in a fixed order, so the
+ * totals of the new state cost no second pass over it and are deterministic.
+ * The partials take nv x (the most CTAs of any launch shape) doubles, and a
+ * step with totals uses 8 nv bytes more shared memory per updated cell of a
+ * CTA.  Rejected on a moving grid (HYDRO_ERR_UNSUPPORTED). */
+int hydro_set_step_totals(hydro_t h, int on);
+/* The totals (nv doubles, host) of the current state from the last step's
+ * partials; HYDRO_ERR_ARG if the totals are off, or no step has completed
+ * since they were turned on or the state was set. */
+int hydro_step_totals(hydro_t h, double* out_nv);
 int hydro_stats(hydro_t h, hydro_stats_t* out);
 
 /* Batched form: ntubes independent 1D tubes on [0,1] with lengths[b] uniform

@@ -403,6 +403,8 @@ static SweepArgs<T> sweep_args(hydro_ctx* h, double dt_host, double cfl, double 
   const bool mv_sph = h->maxis >= 0 && h->wgrid != 0.0 && h->coords == HYDRO_SPHERICAL;
   a.vr = mv_sph ? (const T*)h->vr_d : nullptr;
   a.ir_new = mv_sph && h->dim >= 2 ? (const T*)h->irn_d : nullptr;
+  a.tot_part = h->step_tot ? h->step_tot_part : nullptr;
+  for (int d = 0; d < 3; ++d) a.dvol[d] = h->dvol[d];
   return a;
 }
 
@@ -982,6 +984,7 @@ int hydro_set_state(hydro_t h, const void* U, int where) {
   h->ctrl_host->status = 0;
   h->ctrl_host->done = 0;
   h->ctrl_host->err_step = -1;
+  h->step_tot_ok = false;  // the step totals describe an earlier state
   return write_ctrl(h);
 }
 
@@ -1034,6 +1037,7 @@ int hydro_step(hydro_t h, double dt) {
   st = launch_step(h, dt, 0.0, 0.0, h->ctrl);
   if (st) return st;
   st = check_status(h, "hydro_step");
+  h->step_tot_ok = h->step_tot && st == HYDRO_OK;
   if (moving) {
     // a failed step leaves the state and the faces as they were
     const int mv = st == HYDRO_OK ? move_faces(h, dt)
@@ -1055,6 +1059,10 @@ int hydro_set_moving_grid(hydro_t h, int axis, double w) {
   }
   if (h->eos_rad || h->eps_dual > 0.0) {
     set_error("hydro_set_moving_grid: built for the ideal gas without the dual-energy correction");
+    return HYDRO_ERR_UNSUPPORTED;
+  }
+  if (h->step_tot) {
+    set_error("hydro_set_moving_grid: turn the step totals off first (the cell volumes change in the step)");
     return HYDRO_ERR_UNSUPPORTED;
   }
   h->maxis = axis;
@@ -1116,10 +1124,49 @@ int hydro_run(hydro_t h, int nsteps, double cfl, double t_end, double* t_out) {
     h->graph_cfl = cfl;
     h->graph_tend = t_end;
   }
+  const long long step0 = h->ctrl_host->step;
   for (int s = 0; s < nsteps; ++s) HCK(cudaGraphLaunch(h->graph, h->stream));
   st = check_status(h, "hydro_run");
+  if (st != HYDRO_OK) h->step_tot_ok = false;
+  else if (h->ctrl_host->step > step0) h->step_tot_ok = h->step_tot;
   if (t_out) *t_out = h->ctrl_host->t;
   return st;
+}
+
+int hydro_set_step_totals(hydro_t h, int on) {
+  if (!h || h->batched) return arg_error("hydro_set_step_totals: grid handle required");
+  if (on && h->maxis >= 0) {
+    set_error("hydro_set_step_totals: not on a moving grid (its cell volumes change in the step)");
+    return HYDRO_ERR_UNSUPPORTED;
+  }
+  if (on && !h->step_tot_part) {
+    // partials for the most CTAs any launch shape gives (tiles of at least
+    // 16 x 8 cells, z chunks of at least one plane)
+    const long long ctas = (long long)((h->n[0] + 15) / 16) * ((h->n[1] + 7) / 8) * h->n[2];
+    int st = h->arena.alloc((void**)&h->step_tot_part, sizeof(double) * h->nv * ctas);
+    if (st) return st;
+  }
+  h->step_tot = on != 0;
+  h->step_tot_ok = false;
+  if (h->graph) {  // the captured step's arguments change
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return HYDRO_OK;
+}
+
+int hydro_step_totals(hydro_t h, double* out_nv) {
+  if (!h || h->batched || !out_nv) return arg_error("hydro_step_totals: bad argument");
+  if (!h->step_tot || !h->step_tot_ok)
+    return arg_error("hydro_step_totals: no step with totals since they were turned on or the state was set");
+  const long long ctas = (long long)((h->n[0] + h->tile_x - 1) / h->tile_x) *
+                         (h->dim >= 2 ? (h->n[1] + h->tile_y - 1) / h->tile_y : 1) *
+                         (h->dim == 3 ? (h->n[2] + h->zchunk - 1) / h->zchunk : 1);
+  totals_final_kernel<<<1, 32, 0, h->stream>>>(h->step_tot_part, (int)ctas, h->nv, h->tot_out);
+  HCK(cudaGetLastError());
+  HCK(cudaMemcpyAsync(out_nv, h->tot_out, sizeof(double) * h->nv, cudaMemcpyDeviceToHost, h->stream));
+  HCK(cudaStreamSynchronize(h->stream));
+  return HYDRO_OK;
 }
 
 int hydro_totals(hydro_t h, double* out_nv) {

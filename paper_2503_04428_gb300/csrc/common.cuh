@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <map>
 #include <set>
 #include <utility>
 
@@ -104,6 +105,12 @@ struct SweepArgs {
   T wg;
   const T* vr;
   const T* ir_new;  // moving radial grid: 1/r of every radial cell after the step (its CFL widths)
+  // conserved totals of the new state, accumulated in the step (a10): per
+  // CTA and variable, sum over the CTA's cells of U dV in FP64, stored
+  // [v][cta] (cta = blockIdx.x + gridDim.x (blockIdx.y + gridDim.y
+  // blockIdx.z)); null: not accumulated
+  double* tot_part;
+  const double* dvol[3];  // dV of cell (i, j, k) = dvol[0][i] dvol[1][j] dvol[2][k] (FP64)
 };
 
 template <typename T, int DIM>
@@ -122,20 +129,22 @@ template <typename T, int DIM>
 cudaError_t sweep_dispatch_rad(const SweepArgs<T>& a, int nsx, int rs, int dual, cudaStream_t s, int* tx,
                                int* ty, int* nt);
 
-// Raise the dynamic shared-memory limit of kernel `fn` to `bytes` on the
-// current device.  The attribute is a property of the kernel on one device,
-// so it is set once per (device, kernel) pair, under a lock (host threads may
-// make their first calls at the same time).
+// Raise the dynamic shared-memory limit of kernel `fn` to at least `bytes`
+// on the current device.  The attribute is a property of the kernel on one
+// device, so it is set per (device, kernel) pair when a launch needs more
+// than was set before, under a lock (host threads may make their first calls
+// at the same time).
 inline cudaError_t smem_attr_once(const void* fn, int bytes) {
   static std::mutex mu;
-  static std::set<std::pair<int, const void*>> done;
+  static std::map<std::pair<int, const void*>, int> done;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(mu);
-  if (done.count({dev, fn})) return cudaSuccess;
+  auto it = done.find({dev, fn});
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done.insert({dev, fn});
+  if (e == cudaSuccess) done[{dev, fn}] = bytes;
   return e;
 }
 

@@ -78,6 +78,10 @@ struct hydro_ctx {
   double* tot_partial = nullptr;
   double* tot_out = nullptr;
   int tot_blocks = 0;
+  // totals accumulated in the step: on, valid for the current state, the
+  // per-CTA partials [nv][ctas]
+  bool step_tot = false, step_tot_ok = false;
+  double* step_tot_part = nullptr;
   // launch shape
   int zchunk = 32;
   int tile_x = 0, tile_y = 0, threads = 0;

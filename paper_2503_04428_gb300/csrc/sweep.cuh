@@ -54,6 +54,9 @@ template <> struct TileCfg<double, 3, 0> { static constexpr int TX = 16, TY = 16
 template <> struct TileCfg<double, 3, 1> { static constexpr int TX = 16, TY = 16, MB = 1; };
 template <> struct TileCfg<double, 3, 3> { static constexpr int TX = 16, TY = 8, MB = 1; };
 
+// The smallest power of two >= n (n >= 1).
+__host__ __device__ constexpr int pow2_ceil(int n) { return n <= 1 ? 1 : 2 * pow2_ceil((n + 1) / 2); }
+
 template <typename T, int DIM, int NSX>
 struct SweepShape {
   static constexpr int NV = 2 + DIM + NSX;
@@ -77,9 +80,13 @@ struct SweepShape {
   static constexpr size_t dual_elems = (size_t)2 * (NFX + NFY + NFZ);  // dual-energy face terms
   // radiation EoS: face-state temperatures and those of the primitive planes
   static constexpr size_t rad_elems = (size_t)2 * NFX + 2 * NFY + 3 * NFZ + (size_t)WP * WPL;
-  static constexpr size_t smem_bytes_for(int mode) {
+  __host__ __device__ static constexpr size_t smem_bytes_for(int mode) {
     return (smem_elems + ((mode & 2) ? dual_elems : 0) + ((mode & 1) ? rad_elems : 0)) * sizeof(T);
   }
+  // conserved totals accumulated in the step: one FP64 sum per owner and
+  // variable, after the rest (16-byte aligned)
+  __host__ __device__ static constexpr size_t tot_offset(int mode) { return (smem_bytes_for(mode) + 15) / 16 * 16; }
+  static constexpr size_t tot_bytes = (size_t)NI * NV * sizeof(double);
 };
 
 // Ghost mapping of one axis (periodic wrap, transmissive copy of the edge
@@ -162,6 +169,7 @@ struct Sweep {
   T* ZTL;
   T* ZTR;
   T* WT;  // [slot][ey][ex] temperatures of the primitive planes
+  double* tsum;  // [v][owner] FP64 sums of U dV of the owner's new cells, or null (totals off)
   int x0, y0, z1, n2;
   T dt, half_dt;
   const T* Uin;
@@ -180,6 +188,8 @@ struct Sweep {
 
   __device__ Sweep(const SweepArgs<T>& args, T* smem) : a(args) {
     Ws = smem;
+    tsum = args.tot_part ? reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(smem) + S::tot_offset(MODE))
+                         : nullptr;
     XL = Ws + S::WP * NV * S::WPL;
     XR = XL + NV * NFX;
     YL = XR + NV * NFX;
@@ -797,6 +807,17 @@ struct Sweep {
       for (int v = 0; v < NV; ++v) Un[v] *= q;
     }
 
+    // the new cell's share of the conserved totals (FP64, in the owner's sum)
+    if (tsum) {
+      double dV = a.dvol[0][gi];
+      if constexpr (DIM >= 2) dV *= a.dvol[1][gj];
+      if constexpr (DIM == 3) dV *= a.dvol[2][gz];
+      const int o = j * TX + i;
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        if (v < nvact) tsum[v * NI + o] += (double)Un[v] * dV;
+    }
+
     // validity and the signal speed of the new state
     T Wn[NV], c2n;
     if constexpr (EOS == 1) {
@@ -954,6 +975,8 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
   if (!step_begin(args.ctrl, args.dt_host, args.cfl, args.t_end, dtd, t, step, cur)) return;
 
   Sweep<T, DIM, NSX, RS, MODE> sw(args, reinterpret_cast<T*>(smem_raw));
+  if (sw.tsum)
+    for (int q = threadIdx.x; q < S::NI * S::NV; q += S::NT) sw.tsum[q] = 0.0;  // (read after later barriers)
   sw.x0 = blockIdx.x * S::TX;
   sw.y0 = blockIdx.y * S::TY;
   sw.n2 = DIM == 3 ? args.n[2] : 1;
@@ -998,6 +1021,21 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
     sw.owner_step(0, false, true);
   }
   __syncthreads();
+  if (sw.tsum) {
+    // the CTA's totals: the owners' sums by a tree in a fixed order, per
+    // variable, so the result does not depend on scheduling
+    constexpr int P2 = pow2_ceil(S::NI);
+    for (int w = P2 / 2; w > 0; w >>= 1) {
+      for (int q = threadIdx.x; q < S::NV * w; q += S::NT) {
+        const int v = q / w, o = q - v * w;
+        if (o + w < S::NI) sw.tsum[v * S::NI + o] += sw.tsum[v * S::NI + o + w];
+      }
+      __syncthreads();
+    }
+    const long long ncta = (long long)gridDim.x * gridDim.y * gridDim.z;
+    const long long cta = blockIdx.x + gridDim.x * ((long long)blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    if (threadIdx.x < S::NV) args.tot_part[threadIdx.x * ncta + cta] = sw.tsum[threadIdx.x * S::NI];
+  }
   finish_step<S::NT>(args.ctrl, sw.smax, sw.err, sw.n_fallback,
                      (MODE & 1) ? (unsigned long long)sw.t_iters : sw.n_iters, 0ull, step, dtd);
 }
@@ -1005,11 +1043,12 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
 template <typename T, int DIM, int NSX, int RS, int MODE>
 cudaError_t launch_sweep(const SweepArgs<T>& a, cudaStream_t s) {
   using S = SweepShape<T, DIM, NSX>;
-  cudaError_t e = smem_attr_once((const void*)sweep_kernel<T, DIM, NSX, RS, MODE>, (int)S::smem_bytes_for(MODE));
+  const size_t smem = a.tot_part ? S::tot_offset(MODE) + S::tot_bytes : S::smem_bytes_for(MODE);
+  cudaError_t e = smem_attr_once((const void*)sweep_kernel<T, DIM, NSX, RS, MODE>, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.n[0] + S::TX - 1) / S::TX, DIM >= 2 ? (a.n[1] + S::TY - 1) / S::TY : 1,
             DIM == 3 ? (a.n[2] + a.zchunk - 1) / a.zchunk : 1);
-  sweep_kernel<T, DIM, NSX, RS, MODE><<<grid, S::NT, S::smem_bytes_for(MODE), s>>>(a);
+  sweep_kernel<T, DIM, NSX, RS, MODE><<<grid, S::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

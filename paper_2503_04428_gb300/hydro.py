@@ -92,6 +92,8 @@ _SIGS = {
     "hydro_batch_run_host": [_VP, _VP, _VP, C.c_int, C.c_double, C.c_int],
     "hydro_exact_sample": [_D, _D, C.c_long, C.c_double, C.POINTER(C.c_longlong), _D, C.c_long, _D],
     "hydro_batch_times": [_VP, _D],
+    "hydro_set_step_totals": [_VP, C.c_int],
+    "hydro_step_totals": [_VP, _D],
     "hydro_batch_set_launch": [_VP, C.c_int, C.c_int, C.c_int],
     "hydro_set_exchange": [_VP, C.c_int, C.c_int, _D],
     "hydro_set_halo": [_VP, C.c_int, C.c_int, _VP, C.c_int],
@@ -429,6 +431,16 @@ class Grid:
 
     def totals(self):
         return hydro_totals(self.h, self.nv)
+
+    def set_step_totals(self, on=True):
+        """Accumulate the conserved totals inside every later step (hydro_set_step_totals)."""
+        _call("hydro_set_step_totals", self.h, 1 if on else 0)
+
+    def step_totals(self):
+        """Totals of the current state from the last step's in-step partials (hydro_step_totals)."""
+        out = np.empty(self.nv)
+        _call("hydro_step_totals", self.h, out.ctypes.data_as(_D))
+        return out
 
     def stats(self):
         return hydro_stats(self.h)
