@@ -254,6 +254,17 @@ static int build_geometry(hydro_ctx* h) {
   if ((st = upload_d(h, a, &h->dvol[0]))) return st;
   if ((st = upload_d(h, b, &h->dvol[1]))) return st;
   if ((st = upload_d(h, c, &h->dvol[2]))) return st;
+  {
+    // the axis-2 factors split into FP32 pairs for the FP32 form's
+    // compensated in-step totals
+    std::vector<float> hl(2 * c.size());
+    for (size_t k = 0; k < c.size(); ++k) {
+      hl[2 * k] = (float)c[k];
+      hl[2 * k + 1] = (float)(c[k] - (double)hl[2 * k]);
+    }
+    if (!h->dvz32 && (st = h->arena.alloc((void**)&h->dvz32, hl.size() * sizeof(float)))) return st;
+    HCK(cudaMemcpy(h->dvz32, hl.data(), hl.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   if ((st = upload_d(h, rc, &h->rc_d))) return st;
   double bsum = 0.0, csum = 0.0;
   for (double v : b) bsum += v;
@@ -405,6 +416,7 @@ static SweepArgs<T> sweep_args(hydro_ctx* h, double dt_host, double cfl, double 
   a.ir_new = mv_sph && h->dim >= 2 ? (const T*)h->irn_d : nullptr;
   a.tot_part = h->step_tot ? h->step_tot_part : nullptr;
   for (int d = 0; d < 3; ++d) a.dvol[d] = h->dvol[d];
+  a.dvz32 = reinterpret_cast<const float2*>(h->dvz32);
   return a;
 }
 

@@ -111,6 +111,7 @@ struct SweepArgs {
   // blockIdx.z)); null: not accumulated
   double* tot_part;
   const double* dvol[3];  // dV of cell (i, j, k) = dvol[0][i] dvol[1][j] dvol[2][k] (FP64)
+  const float2* dvz32;    // dvol[2][k] as an FP32 pair (hi, lo) with hi + lo = dvol[2][k] to ~2^-48
 };
 
 template <typename T, int DIM>

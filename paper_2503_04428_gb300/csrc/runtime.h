@@ -65,6 +65,7 @@ struct hydro_ctx {
   hydro::Ctrl* ctrl_host = nullptr;  // pinned mirror
   void* geo[32] = {nullptr};         // device geometry arrays (precision T)
   double* dvol[3] = {nullptr, nullptr, nullptr};  // FP64 volume factors a, b, c
+  float* dvz32 = nullptr;            // c as FP32 pairs (hi, lo), hi + lo = c to ~2^-48 (FP32 in-step totals)
   double* rc_d = nullptr;            // FP64 radial centres
   double omega = 4.0 * 3.14159265358979323846;
   // sources

@@ -40,7 +40,7 @@ template <> struct TileCfg<float, 1, 3> { static constexpr int TX = 254, TY = 1,
 template <> struct TileCfg<float, 2, 0> { static constexpr int TX = 32, TY = 16, MB = 1; };
 template <> struct TileCfg<float, 2, 1> { static constexpr int TX = 32, TY = 16, MB = 1; };
 template <> struct TileCfg<float, 2, 3> { static constexpr int TX = 32, TY = 8, MB = 1; };
-template <> struct TileCfg<float, 3, 0> { static constexpr int TX = 16, TY = 16, MB = 2; };
+template <> struct TileCfg<float, 3, 0> { static constexpr int TX = 16, TY = 16, MB = 3; };
 template <> struct TileCfg<float, 3, 1> { static constexpr int TX = 16, TY = 16, MB = 2; };
 template <> struct TileCfg<float, 3, 3> { static constexpr int TX = 16, TY = 16, MB = 2; };
 // double
@@ -144,6 +144,8 @@ struct Sweep {
   static constexpr int EOS = MODE & 1;
   static constexpr bool DUAL = (MODE & 2) != 0;
   static constexpr bool XM = (MODE & 4) != 0;
+  // in-step totals as compensated FP32 column sums (FP32, 3D) instead of FP64 sums per cell
+  static constexpr bool COLSUM = sizeof(T) == 4 && DIM == 3;
   using S = SweepShape<T, DIM, NSX>;
   static constexpr int NV = S::NV, TX = S::TX, TY = S::TY, EX = S::EX, EY = S::EY, HY = S::HY,
                        QY = S::QY, NT = S::NT, NI = S::NI, NP = S::NP, NFX = S::NFX,
@@ -169,7 +171,8 @@ struct Sweep {
   T* ZTL;
   T* ZTR;
   T* WT;  // [slot][ey][ex] temperatures of the primitive planes
-  double* tsum;  // [v][owner] FP64 sums of U dV of the owner's new cells, or null (totals off)
+  double* tsum;  // [v][owner] sums of U dV of the owner's new cells (FP32 3D: float2 column sums
+                 // until the end of the CTA, see close_cell), or null (totals off)
   int x0, y0, z1, n2;
   T dt, half_dt;
   const T* Uin;
@@ -177,7 +180,8 @@ struct Sweep {
   unsigned long long n_fallback = 0, n_iters = 0;
   int t_iters = 0;  // radiation EoS: temperature Newton iterations of this thread (reported as n_iters)
   int err = 0;
-  double smax = 0.0;
+  T smax = T(0);  // max of the new states' signal speeds (FP32: the FP64 max of
+                  // the same values, converted once at the end: the conversion is exact)
   T hfac = T(0);
   // owner registers: partial update of the owned cell, its predictor
   // increment (1D/2D) and the spherical partial sums of Eq. 13-16
@@ -244,6 +248,31 @@ struct Sweep {
     }
     const int slot = wslot(gz);
     const int nvact = 2 + DIM + a.ns;
+    // a staged region inside the domain on every axis: no ghost mapping
+    const bool inner = !XM && x0 >= 2 && x0 + TX + 2 <= n0 &&
+                       (DIM < 2 || (y0 >= HY && y0 + TY + HY <= n1)) && (DIM < 3 || (gz >= 0 && gz < a.n[2]));
+    if (inner) {
+      const long long zoff = (long long)gz * n1 * n0;
+      for (int idx = threadIdx.x; idx < S::WPL; idx += NT) {
+        const int ex = idx % EX, ey = idx / EX;
+        const long long c = zoff + (long long)(y0 - HY + ey) * n0 + (x0 - 2 + ex);
+        T u[NV], w[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = v < nvact ? __ldg(Uin + (long long)v * a.ncell + c) : T(0);
+        if constexpr (EOS == 1) {
+          T c2, t;
+          int k = 0;
+          to_prim_ct<T, DIM, NSX>(u, w, c2, t, a.grad, T(0), &k);
+          t_iters += k;
+          WT[(slot * EY + ey) * EX + ex] = t;
+        } else {
+          to_prim<T, DIM, NSX>(u, w, gas());
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) W(slot, v, ey, ex) = w[v];
+      }
+      return;
+    }
     for (int idx = threadIdx.x; idx < S::WPL; idx += NT) {
       const int ex = idx % EX, ey = idx / EX;
       const int gi = min(x0 - 2 + ex, n0 + 1);
@@ -807,15 +836,43 @@ struct Sweep {
       for (int v = 0; v < NV; ++v) Un[v] *= q;
     }
 
-    // the new cell's share of the conserved totals (FP64, in the owner's sum)
+    // the new cell's share of the conserved totals, in the owner's sum
     if (tsum) {
-      double dV = a.dvol[0][gi];
-      if constexpr (DIM >= 2) dV *= a.dvol[1][gj];
-      if constexpr (DIM == 3) dV *= a.dvol[2][gz];
       const int o = j * TX + i;
+      if constexpr (COLSUM) {
+        // FP32 3D: per owner and variable a compensated FP32 sum (hi, lo) of
+        // U dz along the owner's column, dz = dvol[2][gz] given as the FP32
+        // pair hi + lo.  Each product is split exactly by an FMA, the sum
+        // kept as an unevaluated pair (TwoSum, then renormalised), so each
+        // term costs ~2^-48 of the sum; the column's sum is multiplied by
+        // dvol[0] dvol[1] in FP64 at the end of the CTA.  (The _rn
+        // intrinsics keep the compiler from fusing these operations.)
+        const float2 z = a.dvz32[gz];
+        float2* ts = reinterpret_cast<float2*>(tsum);
 #pragma unroll
-      for (int v = 0; v < NV; ++v)
-        if (v < nvact) tsum[v * NI + o] += (double)Un[v] * dV;
+        for (int v = 0; v < NV; ++v)
+          if (v < nvact) {
+            const float x = Un[v];
+            const float p = __fmul_rn(x, z.x);
+            const float e = fmaf(x, z.y, fmaf(x, z.x, -p));
+            float2 sv = ts[v * NI + o];
+            const float t = __fadd_rn(sv.x, p);
+            const float bb = __fsub_rn(t, sv.x);
+            const float r = __fadd_rn(__fsub_rn(sv.x, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+            const float lo = __fadd_rn(sv.y, __fadd_rn(r, e));
+            sv.x = __fadd_rn(t, lo);
+            sv.y = __fsub_rn(lo, __fsub_rn(sv.x, t));
+            ts[v * NI + o] = sv;
+          }
+      } else {
+        // FP64 sums of U dV
+        double dV = a.dvol[0][gi];
+        if constexpr (DIM >= 2) dV *= a.dvol[1][gj];
+        if constexpr (DIM == 3) dV *= a.dvol[2][gz];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          if (v < nvact) tsum[v * NI + o] += (double)Un[v] * dV;
+      }
     }
 
     // validity and the signal speed of the new state
@@ -849,7 +906,7 @@ struct Sweep {
       }
       sp += (fabs(ud) + cs) * ih;
     }
-    smax = fmax(smax, (double)sp);
+    smax = fmax(smax, sp);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
       if (v < nvact) Uout[(long long)v * a.ncell + c] = Un[v];
@@ -1022,6 +1079,18 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
   }
   __syncthreads();
   if (sw.tsum) {
+    if constexpr (decltype(sw)::COLSUM) {
+      // each owner's compensated column sums, times its column's dvol[0]
+      // dvol[1], in FP64 and in place
+      for (int q = threadIdx.x; q < S::NI * S::NV; q += S::NT) {
+        const int o = q % S::NI;
+        const int gi = sw.x0 + o % S::TX, gj = sw.y0 + o / S::TX;
+        const float2 c = reinterpret_cast<const float2*>(sw.tsum)[q];
+        const double w = (gi < args.n[0] && gj < args.n[1]) ? args.dvol[0][gi] * args.dvol[1][gj] : 0.0;
+        sw.tsum[q] = ((double)c.x + (double)c.y) * w;
+      }
+      __syncthreads();
+    }
     // the CTA's totals: the owners' sums by a tree in a fixed order, per
     // variable, so the result does not depend on scheduling
     constexpr int P2 = pow2_ceil(S::NI);
@@ -1036,7 +1105,7 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
     const long long cta = blockIdx.x + gridDim.x * ((long long)blockIdx.y + (long long)gridDim.y * blockIdx.z);
     if (threadIdx.x < S::NV) args.tot_part[threadIdx.x * ncta + cta] = sw.tsum[threadIdx.x * S::NI];
   }
-  finish_step<S::NT>(args.ctrl, sw.smax, sw.err, sw.n_fallback,
+  finish_step<S::NT>(args.ctrl, (double)sw.smax, sw.err, sw.n_fallback,
                      (MODE & 1) ? (unsigned long long)sw.t_iters : sw.n_iters, 0ull, step, dtd);
 }
 
