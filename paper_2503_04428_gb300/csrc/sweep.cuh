@@ -80,8 +80,13 @@ struct SweepShape {
   static constexpr size_t dual_elems = (size_t)2 * (NFX + NFY + NFZ);  // dual-energy face terms
   // radiation EoS: face-state temperatures and those of the primitive planes
   static constexpr size_t rad_elems = (size_t)2 * NFX + 2 * NFY + 3 * NFZ + (size_t)WP * WPL;
+  // the x and y geometry factors of the CTA's cells, staged once per CTA
+  // (GX_N arrays over the TX + 2 predictor columns, GY_N over the TY + 2 rows)
+  enum { GX_IDM, GX_IDP, GX_HW, GX_IW, GX_IR, GX_AF, GX_INVA, GX_GA, GX_QR, GX_GR, GX_G, GX_N };
+  enum { GY_IDM, GY_IDP, GY_HW, GY_IW, GY_IS, GY_BF, GY_INVB, GY_ZC, GY_GT, GY_QT, GY_N };
+  static constexpr size_t geo_elems = (size_t)GX_N * (TX + 2) + (DIM >= 2 ? (size_t)GY_N * (TY + 2) : 0);
   __host__ __device__ static constexpr size_t smem_bytes_for(int mode) {
-    return (smem_elems + ((mode & 2) ? dual_elems : 0) + ((mode & 1) ? rad_elems : 0)) * sizeof(T);
+    return (smem_elems + ((mode & 2) ? dual_elems : 0) + ((mode & 1) ? rad_elems : 0) + geo_elems) * sizeof(T);
   }
   // conserved totals accumulated in the step: one FP64 sum per owner and
   // variable, after the rest (16-byte aligned)
@@ -171,6 +176,8 @@ struct Sweep {
   T* ZTL;
   T* ZTR;
   T* WT;  // [slot][ey][ex] temperatures of the primitive planes
+  T* GXs;  // [GX_*][px] geometry of predictor column px (cell x0 - 1 + px)
+  T* GYs;  // [GY_*][py] geometry of predictor row py (cell y0 - 1 + py)
   double* tsum;  // [v][owner] sums of U dV of the owner's new cells (FP32 3D: float2 column sums
                  // until the end of the CTA, see close_cell), or null (totals off)
   int x0, y0, z1, n2;
@@ -212,6 +219,60 @@ struct Sweep {
     ZTL = YTR + NFY;
     ZTR = ZTL + 2 * NFZ;
     WT = ZTR + NFZ;
+    GXs = Ws + S::smem_elems + (DUAL ? S::dual_elems : 0) + (EOS == 1 ? S::rad_elems : 0);
+    GYs = GXs + S::GX_N * (TX + 2);
+  }
+
+  __device__ __forceinline__ T gx(int k, int px) const { return GXs[k * (TX + 2) + px]; }
+  __device__ __forceinline__ T gy(int k, int py) const { return GYs[k * (TY + 2) + py]; }
+
+  // Stage the x and y geometry factors of the CTA's cells (constant over
+  // the march; read after the first barrier).  Indices are clamped to the
+  // arrays' ranges: entries of columns or rows beyond the domain are never
+  // used.
+  __device__ void stage_geometry() {
+    const int n0 = a.n[0], n1 = a.n[1];
+    for (int p = threadIdx.x; p < TX + 2; p += NT) {
+      const int gi = x0 - 1 + p;              // >= -1
+      const int ge = min(gi, n0 + 1) + 2;     // extended (ghost) index
+      const int gp = min(gi, n0) + 3;         // the face above, extended
+      const int gc = min(max(gi, 0), n0 - 1);  // interior cell
+      const int gf = min(max(gi, 0), n0);      // interior face
+      T* g = GXs + p;
+      constexpr int st = TX + 2;
+      g[S::GX_IDM * st] = a.geo.inv_dxc[0][ge];
+      g[S::GX_IDP * st] = a.geo.inv_dxc[0][gp];
+      g[S::GX_HW * st] = a.geo.hw[0][ge];
+      g[S::GX_IW * st] = a.geo.inv_w[0][ge];
+      g[S::GX_IR * st] = a.spherical ? a.geo.inv_r[ge] : T(1);
+      g[S::GX_AF * st] = a.geo.Af[gf];
+      g[S::GX_INVA * st] = a.geo.inva[gc];
+      g[S::GX_GA * st] = a.geo.ga[gc];
+      g[S::GX_QR * st] = a.geo.qr[gc];
+      g[S::GX_GR * st] = a.geo.gr[gc];
+      g[S::GX_G * st] = a.gravity == GRAV_POINT ? a.geo.gpt[gc] : a.gravity == GRAV_MONO ? a.gmono[gc] : T(0);
+    }
+    if constexpr (DIM >= 2) {
+      for (int p = threadIdx.x; p < TY + 2; p += NT) {
+        const int gj = y0 - 1 + p;
+        const int ge = min(gj, n1 + 1) + 2;
+        const int gp = min(gj, n1) + 3;
+        const int gc = min(max(gj, 0), n1 - 1);
+        const int gf = min(max(gj, 0), n1);
+        T* g = GYs + p;
+        constexpr int st = TY + 2;
+        g[S::GY_IDM * st] = a.geo.inv_dxc[1][ge];
+        g[S::GY_IDP * st] = a.geo.inv_dxc[1][gp];
+        g[S::GY_HW * st] = a.geo.hw[1][ge];
+        g[S::GY_IW * st] = a.geo.inv_w[1][ge];
+        g[S::GY_IS * st] = a.spherical ? a.geo.inv_s[ge] : T(1);
+        g[S::GY_BF * st] = a.geo.Bf[gf];
+        g[S::GY_INVB * st] = a.geo.invb[gc];
+        g[S::GY_ZC * st] = a.geo.zc[gc];
+        g[S::GY_GT * st] = a.geo.gt[gc];
+        g[S::GY_QT * st] = a.geo.qt[gc];
+      }
+    }
   }
 
   // Dual energy (Sect. 2.5, reading R15): the advected internal energy
@@ -321,24 +382,39 @@ struct Sweep {
     }
   }
 
-  // 1/h_d of a cell (physical width: h_r = dr, h_th = r dth, h_ph = r s dph).
-  __device__ __forceinline__ T inv_h(int d, int gi, int gj, int gk) const {
-    if (d == 0) return a.geo.inv_w[0][gi + 2];
+  // 1/h_d of the cell in predictor column px, row py, plane gk (physical
+  // width: h_r = dr, h_th = r dth, h_ph = r s dph).
+  __device__ __forceinline__ T inv_h(int d, int px, int py, int gk) const {
+    if (d == 0) return gx(S::GX_IW, px);
     if (d == 1) {
-      const T w = a.geo.inv_w[1][gj + 2];
-      return a.spherical ? w * a.geo.inv_r[gi + 2] : w;
+      const T w = gy(S::GY_IW, py);
+      return a.spherical ? w * gx(S::GX_IR, px) : w;
     }
     const T w = a.geo.inv_w[2][gk + 2];
-    return a.spherical ? w * a.geo.inv_r[gi + 2] * a.geo.inv_s[gj + 2] : w;
+    if constexpr (DIM >= 2) return a.spherical ? w * gx(S::GX_IR, px) * gy(S::GY_IS, py) : w;
+    else return w;
   }
 
   // Limited low/high face states along DIR of the cell with centre Wc and
-  // neighbours Wm/Wp; g = the cell's index along DIR.
+  // neighbours Wm/Wp; l = the cell's predictor column (DIR 0), row (DIR 1)
+  // or plane index (DIR 2).
   template <int DIR>
-  __device__ __forceinline__ void faces_of(const T* Wm, const T* Wc, const T* Wp, int g, T* Wlo,
+  __device__ __forceinline__ void faces_of(const T* Wm, const T* Wc, const T* Wp, int l, T* Wlo,
                                            T* Whi) const {
-    const T idm = a.geo.inv_dxc[DIR][g + 2], idp = a.geo.inv_dxc[DIR][g + 3];
-    const T h = a.geo.hw[DIR][g + 2];
+    T idm, idp, h;
+    if constexpr (DIR == 0) {
+      idm = gx(S::GX_IDM, l);
+      idp = gx(S::GX_IDP, l);
+      h = gx(S::GX_HW, l);
+    } else if constexpr (DIR == 1) {
+      idm = gy(S::GY_IDM, l);
+      idp = gy(S::GY_IDP, l);
+      h = gy(S::GY_HW, l);
+    } else {
+      idm = a.geo.inv_dxc[DIR][l + 2];
+      idp = a.geo.inv_dxc[DIR][l + 3];
+      h = a.geo.hw[DIR][l + 2];
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const T sig = limit<T>(a.limiter, (Wc[v] - Wm[v]) * idm, (Wp[v] - Wc[v]) * idp);
@@ -499,7 +575,7 @@ struct Sweep {
         Wm[v] = W(slot, v, ey, ex - 1);
         Wp[v] = W(slot, v, ey, ex + 1);
       }
-      faces_of<0>(Wm, Wc, Wp, gi, Wl, Wh);
+      faces_of<0>(Wm, Wc, Wp, px, Wl, Wh);
       T Pl[NV], Ph[NV], tl = T(0), th = T(0);
       limited_fluxes<0>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
       if constexpr (XM) {
@@ -509,7 +585,7 @@ struct Sweep {
         if (xlo) XTR[ixlo] = tl;
         if (xhi) XTL[ixhi] = th;
       }
-      const T ih = inv_h(0, gi, gj, gz);
+      const T ih = inv_h(0, px, py, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         dU[v] += (Fl[v] - Fh[v]) * ih;
@@ -524,7 +600,7 @@ struct Sweep {
         Wm[v] = W(slot, v, ey - 1, ex);
         Wp[v] = W(slot, v, ey + 1, ex);
       }
-      faces_of<1>(Wm, Wc, Wp, gj, Wl, Wh);
+      faces_of<1>(Wm, Wc, Wp, py, Wl, Wh);
       T Pl[NV], Ph[NV], tl = T(0), th = T(0);
       limited_fluxes<1>(Wl, Wh, Fl, Fh, Pl, Ph, tcell, &tl, &th);
       if constexpr (XM) {
@@ -534,7 +610,7 @@ struct Sweep {
         if (ylo) YTR[iylo] = tl;
         if (yhi) YTL[iyhi] = th;
       }
-      const T ih = inv_h(1, gi, gj, gz);
+      const T ih = inv_h(1, px, py, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         dU[v] += (Fl[v] - Fh[v]) * ih;
@@ -559,7 +635,7 @@ struct Sweep {
         if (zlo) ZTR[iz] = tl;
         if (zhi) ZTL[(gz & 1) * NFZ + iz] = th;
       }
-      const T ih = inv_h(2, gi, gj, gz);
+      const T ih = inv_h(2, px, py, gz);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         dU[v] += (Fl[v] - Fh[v]) * ih;
@@ -702,7 +778,7 @@ struct Sweep {
   // spherical partial sums that use these fluxes.
   __device__ __forceinline__ void open_cell(int gz, int i, int j, int gi, int gj) {
     const int fx = j * (TX + 1) + i;
-    const T Afl = a.geo.Af[gi], Afh = a.geo.Af[gi + 1], ia = a.geo.inva[gi];
+    const T Afl = gx(S::GX_AF, i + 1), Afh = gx(S::GX_AF, i + 2), ia = gx(S::GX_INVA, i + 1);
     constexpr bool dual = DUAL;
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = (XL[v * NFX + fx] * Afl - XL[v * NFX + fx + 1] * Afh) * ia;
@@ -711,8 +787,8 @@ struct Sweep {
       aq2 = (XQ[NFX + fx] * Afl - XQ[NFX + fx + 1] * Afh) * ia;
     }
     if constexpr (DIM >= 2) {
-      const T Bfl = a.geo.Bf[gj], Bfh = a.geo.Bf[gj + 1];
-      const T cy = a.geo.ga[gi] * a.geo.invb[gj];
+      const T Bfl = gy(S::GY_BF, j + 1), Bfh = gy(S::GY_BF, j + 2);
+      const T cy = gx(S::GX_GA, i + 1) * gy(S::GY_INVB, j + 1);
       const int fy = j * TX + i;
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += (YL[v * NFY + fy] * Bfl - YL[v * NFY + fy + TX] * Bfh) * cy;
@@ -726,13 +802,14 @@ struct Sweep {
         if constexpr (DIM == 3) {
           const T frl = XL[3 * NFX + fx], frh = XL[3 * NFX + fx + 1];
           const T ftl = YL[3 * NFY + fy], fth = YL[3 * NFY + fy + TX];
-          s3 = -a.geo.qr[gi] * (frh * Afh + frl * Afl) - a.geo.ga[gi] * a.geo.qt[gj] * (fth * Bfh + ftl * Bfl);
+          s3 = -gx(S::GX_QR, i + 1) * (frh * Afh + frl * Afl) -
+               gx(S::GX_GA, i + 1) * gy(S::GY_QT, j + 1) * (fth * Bfh + ftl * Bfl);
         }
       }
     }
     if constexpr (DIM == 3) {
       const int iz = j * TX + i;
-      const T cz = a.geo.ga[gi] * a.geo.zc[gj] * a.geo.invc[gz];
+      const T cz = gx(S::GX_GA, i + 1) * gy(S::GY_ZC, j + 1) * a.geo.invc[gz];
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += ZR[v * NFZ + iz] * cz;
       fzb3 = ZR[3 * NFZ + iz];
@@ -772,8 +849,9 @@ struct Sweep {
       T Tth = P, Tph = P;
       if constexpr (DIM >= 2) Tth = tth;
       if constexpr (DIM == 3) Tph = T(0.5) * (fzb3 + fzt3);
-      Un[1] += dt * T(0.5) * (Tth + Tph) * a.geo.gr[gi];
-      if constexpr (DIM >= 2) Un[2] += dt * (-a.geo.qr[gi] * x2 + Tph * a.geo.ga[gi] * a.geo.gt[gj]);
+      Un[1] += dt * T(0.5) * (Tth + Tph) * gx(S::GX_GR, i + 1);
+      if constexpr (DIM >= 2)
+        Un[2] += dt * (-gx(S::GX_QR, i + 1) * x2 + Tph * gx(S::GX_GA, i + 1) * gy(S::GY_GT, j + 1));
       if constexpr (DIM == 3) Un[3] += dt * s3;
     }
     if (a.gravity != GRAV_NONE) {
@@ -781,10 +859,8 @@ struct Sweep {
       if (a.gravity == GRAV_UNIFORM) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) g[d] = a.g0[d];
-      } else if (a.gravity == GRAV_POINT) {
-        g[0] = a.geo.gpt[gi];
       } else {
-        g[0] = a.gmono[gi];
+        g[0] = gx(S::GX_G, i + 1);  // point mass or monopole
       }
       T work = T(0);
 #pragma unroll
@@ -895,7 +971,7 @@ struct Sweep {
     T sp = T(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      T ih = inv_h(d, gi, gj, gz);
+      T ih = inv_h(d, i + 1, j + 1, gz);
       T ud = Wn[1 + d];
       if constexpr (XM) {
         // a moving radial grid: the new state lives in the moved cell, whose
@@ -923,7 +999,7 @@ struct Sweep {
     if (gi >= a.n[0] || (DIM >= 2 && gj >= a.n[1])) return;
     if constexpr (DIM == 3) {
       if (close_prev) {
-        const T cz = a.geo.ga[gi] * a.geo.zc[gj] * a.geo.invc[gz - 1];
+        const T cz = gx(S::GX_GA, i + 1) * gy(S::GY_ZC, j + 1) * a.geo.invc[gz - 1];
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc[v] -= ZR[v * NFZ + t] * cz;
         if constexpr (DUAL) {
@@ -1036,6 +1112,7 @@ __global__ void __launch_bounds__(SweepShape<T, DIM, NSX>::NT,
     for (int q = threadIdx.x; q < S::NI * S::NV; q += S::NT) sw.tsum[q] = 0.0;  // (read after later barriers)
   sw.x0 = blockIdx.x * S::TX;
   sw.y0 = blockIdx.y * S::TY;
+  sw.stage_geometry();  // (read after the first barrier below)
   sw.n2 = DIM == 3 ? args.n[2] : 1;
   sw.dt = (T)dtd;
   sw.half_dt = T(0.5) * sw.dt;
