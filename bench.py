@@ -391,6 +391,12 @@ def main():
     ap.add_argument("--grid-only", choices=["sedov3d_fp32", "sedov3d_fp64", "wedge_fp32", "wedge_fp32_rad"],
                     help="time one grid sweep only (profiling)")
     ap.add_argument("--grid-n", type=int, default=0, help="cells per axis for --grid-only sedov3d")
+    ap.add_argument("--dense-only", action="store_true",
+                    help="time only the headline form on the dense state (every face iterates), without the "
+                         "network (profiling)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="with --grid-only or --dense-only: after the timing, run one more step between "
+                         "cudaProfilerStart and cudaProfilerStop (for ncu --profile-from-start off)")
     ap.add_argument("--item-len", type=int, default=0,
                     help="fix the headline's work-item length (cells; 8 warps per CTA, 2 CTAs per SM) "
                          "instead of autotuning it (measurements of particular shapes)")
@@ -402,6 +408,11 @@ def main():
         from paper_2503_04428_gb300 import hydro as H
         print(json.dumps(time_grids(H, torch, work_stream(torch), args, only=args.grid_only,
                                     alu=alu_peaks(H))))
+        return
+    if args.dense_only:
+        import torch
+        from paper_2503_04428_gb300 import hydro as H
+        print(json.dumps(time_dense(H, torch, work_stream(torch), args, 1, 0, None)))
         return
     if args.impl == "reference":
         run_reference(args)
@@ -509,6 +520,8 @@ def time_grids(H, torch, stream, args, only=None, alu=None):
         g.run(2, case["cfl"])  # autotuner on first use
         s0 = g.stats()
         t = timed_steps(torch, stream, lambda n: g.run(n, case["cfl"]), k)
+        if only and args.profile_range:
+            profiled_step(torch, lambda: g.run(1, case["cfl"]))
         cells = int(np.prod(case["n"]))
         nv = case["U"].shape[0]
         bytes_cell = 2 * nv * (4 if prec == 32 else 8)
@@ -546,19 +559,41 @@ def time_grids(H, torch, stream, args, only=None, alu=None):
     return out
 
 
+def profiled_step(torch, fn):
+    """One more step between cudaProfilerStart and cudaProfilerStop, so that
+    ncu --profile-from-start off captures exactly this launch."""
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    fn()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+
+
 def time_dense(H, torch, stream, args, ws, rank, weights):
     """The headline form on a dense state: every cell's density and pressure
     perturbed by 1 %, so that no face has two identical states and every face
-    runs the Newton iteration; with and without the network."""
+    runs the Newton iteration; with and without the network (weights None:
+    without only)."""
     w = rank_tubes(ws, rank, perturb=0.01, ntubes=args.tubes)
     total = int(w["lengths"].sum())
     U = torch.from_numpy(w["U"].astype(np.float32)).cuda()
     b = H.Batch(w["lengths"], w["gamma"], precision=32, stream=stream.cuda_stream)
-    b.mlp_set(weights, True)
+    if weights is not None:
+        b.mlp_set(weights, True)
     b.set_state(U)
     b.run(2, CFL)
     k = min(max(5, args.steps // 4), 20)
     out = {"state": "every cell's rho and P x (1 + 0.01 U(-1,1))", "steps": "1-%d" % k}
+    if weights is None:
+        t, c = time_trajectory(torch, stream, b, U, [(0, k)])
+        rate, t = job_rate(t, total, k, None, "cuda")
+        out.update({"value": rate, "unit": METRIC, "ms_per_step": 1000.0 * t / k, "counters": c,
+                    "tubes": args.tubes, "cells": total})
+        if args.profile_range:
+            b.set_state(U)
+            profiled_step(torch, lambda: b.run(1, CFL))
+        b.close()
+        return out
     for on in (True, False):
         b.mlp_set(weights, on)
         t, c = time_trajectory(torch, stream, b, U, [(0, k)])
