@@ -523,10 +523,14 @@ __device__ __forceinline__ T toro_guess(T rL, T uL, T pL, T cL, T rR, T uR, T pR
 // Newton on f_L(p) + f_R(p) + (u_R - u_L) = 0 from p0: stop when the
 // relative change 2|dp|/(p_k + p_{k-1}) < tol, then take one more step.
 // Negative iterates are clamped to 1e-14 of the mean pressure.  In FP32 the
-// iteration also stops when the residual is within 8 ulp of the sum of the
-// magnitudes of its terms: the rounding of f_L + f_R + du then decides the
-// step, and no later iterate is better determined (near vacuum, where the
-// two rarefaction terms nearly cancel du, the 1e-6 change is never reached).
+// step whose change is below tol (1e-6) is the last: Newton converges
+// quadratically, so the iterate it gives is ~1e-12 from the root, far below
+// FP32 resolution, and a further step would only move it within its own
+// rounding.  The FP32 iteration also stops when the residual is within 8 ulp
+// of the sum of the magnitudes of its terms (then with one more step): the
+// rounding of f_L + f_R + du then decides the step, and no later iterate is
+// better determined (near vacuum, where the two rarefaction terms nearly
+// cancel du, the 1e-6 change is never reached).
 template <typename T>
 __device__ __forceinline__ int newton_star(T p, T rL, T uL, T pL, T cL, T rR, T uR, T pR, T cR,
                                            const Gas<T>& gas, T tol, T& ps, T& us, int& iters) {
@@ -552,7 +556,10 @@ __device__ __forceinline__ int newton_star(T p, T rL, T uL, T pL, T cL, T rR, T 
       fin = true;  // the extra step after convergence is done
       continue;
     }
-    if (ch < tol) conv = true;
+    if (ch < tol) {
+      conv = true;
+      if constexpr (sizeof(T) == 4) fin = true;  // FP32: this step was the last
+    }
     if constexpr (sizeof(T) == 4) {
       if (fabs(res) <= T(8 * 1.1920929e-7) * (fabs(fL) + fabs(fR) + fabs(du))) conv = true;
     }
