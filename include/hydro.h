@@ -300,7 +300,9 @@ int hydro_harvest_get(hydro_t h, double* faces6, long cap, long* n);
  * (TSRS) estimate and max(P_L,P_R) > 4 min(P_L,P_R) (PVRS serves nearby
  * states, the two-rarefaction estimate is exact when both waves are
  * rarefactions, the two-shock estimate is good for mild jumps).  Newton
- * still runs to 1e-10 relative and polishes once.  weights:
+ * still runs to convergence: to 1e-10 relative and one polishing step in
+ * FP64; in FP32 to 1e-6 relative, the step that reaches it being the last
+ * (its iterate is ~1e-12 from the root, below FP32 resolution).  weights:
  * HYDRO_MLP_NPARAM floats (host). */
 int hydro_mlp_set(hydro_t h, const float* weights, int enable);
 int hydro_mlp_get(hydro_t h, float* weights_out);
