@@ -226,9 +226,12 @@ int hydro_totals(hydro_t h, double* out_nv);
 
 /* Conserved totals accumulated inside the step (spec form (1): FP32
  * bulk arithmetic, FP64 conservation sums).  With on != 0 every later step
- * (hydro_step, hydro_run) also sums U dV of the cells it updates in FP64:
- * each CTA of the fused sweep in a fixed order over its cells, into its own
- * partial; hydro_step_totals then sums the partials in a fixed order, so the
+ * (hydro_step, hydro_run) also sums U dV of the cells it updates: each CTA
+ * of the fused sweep in a fixed order over its cells, into its own FP64
+ * partial (the FP32 3D form sums each column of cells as a compensated FP32
+ * pair of exact products and converts the column's sum to FP64; its totals
+ * equal the FP64 sums of the FP32 state to ~1e-14 relative);
+ * hydro_step_totals then sums the partials in a fixed order, so the
  * totals of the new state cost no second pass over it and are deterministic.
  * The partials take nv x (the most CTAs of any launch shape) doubles, and a
  * step with totals uses 8 nv bytes more shared memory per updated cell of a
