@@ -82,7 +82,9 @@ struct GasRad : Gas<T> {
   // min(y/c1, (y/c4)^(1/4)) descends monotonically to the root; from any
   // other positive start t0 (a nearby temperature the caller knows) the first
   // step lands above the root and the descent follows.  It stops when the
-  // relative step is below temp_tol and takes one more step.  y <= 0 gives
+  // relative step is below temp_tol and takes one more step; in FP32 the step
+  // below temp_tol (1e-6) is the last (quadratic convergence leaves that
+  // iterate ~1e-12 from the root, below FP32 resolution).  y <= 0 gives
   // y/c1 <= 0, which the positivity checks reject.
   // (its, if given, accumulates the Newton iterations taken.)
   __device__ __forceinline__ T temperature(T c1, T c4, T y, T t0 = T(0), int* its = nullptr) const {
@@ -98,7 +100,10 @@ struct GasRad : Gas<T> {
       const T ch = qdiv(fabs(tn - t), tn);
       t = tn;
       if (conv) break;
-      if (ch < temp_tol<T>()) conv = true;
+      if (ch < temp_tol<T>()) {
+        if constexpr (sizeof(T) == 4) break;  // FP32: this step was the last
+        conv = true;
+      }
     }
     if (its) *its += it < 60 ? it + 1 : 60;
     return t;
