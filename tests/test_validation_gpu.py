@@ -204,3 +204,56 @@ def test_spherical_sedov_2d_restart_from_1d(hydro_lib):
     assert abs(r_shock2 - r_exact) <= 4 * dr, (r_shock2, r_exact)
     g1.close()
     g2.close()
+
+
+def test_sedov3d_cartesian_radius_conservation_symmetry(hydro_lib):
+    """The 3D Sedov blast of the benchmark (256^3 on [-1,1]^3, gamma = 1.4, HLL,
+    FP32 bulk with the conserved totals accumulated in the step) run to
+    t = 0.05: the shock radius follows Eq. 25 with the gamma = 1.4 constant
+    (xi0 = 1.033, tests/golden/sedov_xi0.txt: 0.3116) within 2 cells; mass and
+    energy stay what they were (the shock is far from the boundary), and the
+    blast stays mirror-symmetric about the three coordinate planes."""
+    case = wl.sedov3d(256)
+    n = 256
+    g = hydro_lib.Grid.from_case(dict(case, U=case["U"].astype(np.float32)), 32)
+    t0 = g.totals()
+    g.set_step_totals(True)
+    t_end = case["t_end"]
+    t = 0.0
+    for _ in range(20):
+        t = g.run(1000, case["cfl"], t_end=t_end)
+        if t >= t_end:
+            break
+    assert abs(t - t_end) < 1e-12
+    t1 = g.step_totals()
+    rho = g.get_state()[0].astype(np.float64)  # (z, y, x)
+    g.close()
+    # conservation: mass (index 0) and total energy (index 4), FP32 bulk
+    for v in (0, 4):
+        assert abs(t1[v] - t0[v]) <= 1e-6 * abs(t0[v]), (v, t0[v], t1[v])
+    # shock radius: outer half-height crossing of the angle-averaged density
+    xc = 0.5 * (np.linspace(-1, 1, n + 1)[1:] + np.linspace(-1, 1, n + 1)[:-1])
+    Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    dx = 2.0 / n
+    bins = np.arange(0.0, 0.6 + 0.5 * dx, 0.5 * dx)
+    k = np.digitize(r.ravel(), bins) - 1
+    inside = (k >= 0) & (k < len(bins) - 1)
+    cnt = np.bincount(k[inside], minlength=len(bins) - 1)
+    tot = np.bincount(k[inside], weights=rho.ravel()[inside], minlength=len(bins) - 1)
+    prof = np.where(cnt > 0, tot / np.maximum(cnt, 1), 1.0)
+    rb = 0.5 * (bins[1:] + bins[:-1])
+    ip = int(np.argmax(prof))
+    half = 0.5 * (prof[ip] + 1.0)
+    j = ip + int(np.argmax(prof[ip:] < half))
+    # linear interpolation of the crossing between bins j-1 and j
+    r_half = rb[j - 1] + (rb[j] - rb[j - 1]) * (prof[j - 1] - half) / (prof[j - 1] - prof[j])
+    xi0 = 1.033
+    r_exact = xi0 * (1.0 * t_end ** 2 / 1.0) ** 0.2
+    print("Sedov 256^3 FP32: peak at %.4f, half-height front at %.4f, Eq. 25 %.4f (dx %.4f), peak density %.2f"
+          % (rb[ip], r_half, r_exact, dx, prof[ip]))
+    assert abs(r_half - r_exact) <= 2 * dx, (r_half, r_exact)
+    # mirror symmetry about x = 0, y = 0, z = 0 and the diagonal x <-> y
+    peak = rho.max()
+    for sym in (rho[:, :, ::-1], rho[:, ::-1, :], rho[::-1, :, :], rho.transpose(0, 2, 1)):
+        assert np.abs(rho - sym).max() <= 1e-4 * peak
