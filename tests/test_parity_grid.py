@@ -307,3 +307,22 @@ def test_fp32_periodic_conservation(hydro_lib):
     T1 = g.totals()
     scale = np.abs(T0).max()
     assert np.all(np.abs(T1 - T0) <= 2e-6 * scale), (T1 - T0) / scale
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_runs_with_totals_and_monopole_are_deterministic(hydro_lib, precision):
+    """Also with the conserved totals accumulated in the step and with the
+    monopole's FP64 shell sums (a spherical wedge): two runs of the same
+    device-side CFL steps give the same state and totals, bit for bit."""
+    cases = [wl.sedov3d(48), dict(wl.sphere_state(40, 12, 10, dim=3, rotating=True, n_scalars=3),
+                                  sources=dict(gravity=O.GRAV_POINT_MONOPOLE, G=0.01, Mc=2.0))]
+    for case in cases:
+        out = []
+        for _ in range(2):
+            g = hydro_lib.Grid.from_case(case, precision)
+            g.set_step_totals(True)
+            g.run(6, case.get("cfl", 0.4))
+            out.append((g.get_state(), g.step_totals(), g.stats()["steps"]))
+            g.close()
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+        assert out[0][2] == out[1][2] == 6
