@@ -326,3 +326,52 @@ def test_runs_with_totals_and_monopole_are_deterministic(hydro_lib, precision):
             g.close()
         assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
         assert out[0][2] == out[1][2] == 6
+
+
+def test_beyond_32bit_element_offsets(hydro_lib):
+    """Maximum sizes: a 256 x 256 x 6600 FP32 grid (4.3e8 cells, 2.2e9 state
+    values per buffer, past 32-bit element offsets) whose state varies along
+    z only, periodic everywhere, so that every one of its columns must
+    advance exactly like the column of a 16 x 16 x 6600 grid with the same
+    face spacing (8.4e6 values); one step with the same dt gives the same
+    bits in all 65536 columns, and that column agrees with the oracle's
+    2 x 2 x 6600 step."""
+    import torch
+    H = hydro_lib
+    n2, nb = 6600, 256
+    z = (np.arange(n2) + 0.5) / n2
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * z)
+    p = 1.0 + 0.1 * np.cos(2 * np.pi * z)
+    vel = [np.full(n2, 0.05), np.full(n2, -0.02), 0.3 * np.sin(4 * np.pi * z)]
+    col = wl.conserved(1.4, rho, vel, p).astype(np.float32)  # (5, n2)
+    per = [(wl.PERIODIC, wl.PERIODIC)] * 3
+
+    def case(nxy, U):
+        f = np.arange(nxy + 1) / nb
+        return dict(dim=3, n=[nxy, nxy, n2], faces=[f, f, np.linspace(0.0, 1.0, n2 + 1)], bc=per,
+                    coords=wl.CARTESIAN, gamma=1.4, n_scalars=0, riemann=wl.HLL, limiter=wl.MINMOD,
+                    sources=None, U=U)
+
+    small = H.Grid.from_case(case(16, np.ascontiguousarray(
+        np.broadcast_to(col[:, :, None, None], (5, n2, 16, 16)))), 32)
+    dt = small.cfl_dt(0.4)
+    small.step(dt)
+    ref = small.get_state()[:, :, 0, 0]
+    small.close()
+    Ub = torch.from_numpy(col).cuda().view(5, n2, 1, 1).expand(5, n2, nb, nb).contiguous()
+    big = H.Grid.from_case(case(nb, Ub), 32)
+    assert big.cfl_dt(0.4) == dt
+    big.step(dt)
+    out = torch.empty_like(Ub)
+    big.get_state(out)
+    big.close()
+    del Ub
+    refd = torch.from_numpy(np.ascontiguousarray(ref)).cuda().view(5, n2, 1, 1)
+    same = bool(torch.eq(out, refd).all())
+    worst = float((out - refd).abs().max()) if not same else 0.0
+    del out
+    assert same, worst
+    o = O.solver_from_case(case(2, np.ascontiguousarray(
+        np.broadcast_to(col.astype(np.float64)[:, :, None, None], (5, n2, 2, 2)))))
+    o.step(dt)
+    check(o.get_state()[:, :, 0, 0], ref.astype(np.float64), 3, 1.4, 32)
