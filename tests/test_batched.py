@@ -310,3 +310,42 @@ def test_failed_step_leaves_each_tube_at_its_last_good_step(hydro_lib):
     ref, _ = O.batch_run(lengths, U2, w["gamma"], O.EXACT, O.MINMOD, 0.8, 3)
     check(ref, b.get_state(), 1, G53, 64, **RUN64)
     b.close()
+
+
+def test_beyond_32bit_element_offsets(hydro_lib):
+    """Maximum sizes: 100000 tubes of 7200 cells (7.2e8 cells, 2.16e9 values
+    per buffer, past 32-bit element offsets), FP32, two steps: the first,
+    middle and last tubes equal, bit for bit, the same tubes advanced in a
+    batch of their own (tubes are independent, and the kernel's results do
+    not depend on the launch shape or on which warp takes which segment)."""
+    import torch
+    H = hydro_lib
+    nt, n, g = 100000, 7200, 5.0 / 3.0
+    WL, WR = wl.tube_states(nt, seed=17)
+    UL = wl.conserved(g, WL[:, 0], [WL[:, 1]], WL[:, 2]).astype(np.float32)  # (3, nt)
+    UR = wl.conserved(g, WR[:, 0], [WR[:, 1]], WR[:, 2]).astype(np.float32)
+    left = torch.from_numpy((np.arange(n) + 0.5) / n < 0.5).cuda()
+    U = torch.where(left[None, None, :], torch.from_numpy(UL).cuda()[:, :, None],
+                    torch.from_numpy(UR).cuda()[:, :, None]).reshape(3, nt * n)
+    big = H.Batch(np.full(nt, n, dtype=np.int32), g, precision=32)
+    big.set_launch(8, 7224, 2)  # whole-tube items, no autotuning (the small batch autotunes)
+    big.set_state(U)
+    big.run(2, 0.8)
+    out = torch.empty_like(U)
+    big.get_state(out)
+    times = big.times()
+    big.close()
+    del U
+    sample = [0, 1, nt // 2, nt - 2, nt - 1]
+    Us = np.concatenate([np.where(((np.arange(n) + 0.5) / n < 0.5)[None, :], UL[:, t, None], UR[:, t, None])
+                         for t in sample], axis=1)
+    small = H.Batch(np.full(len(sample), n, dtype=np.int32), g, precision=32)
+    small.set_state(np.ascontiguousarray(Us))
+    small.run(2, 0.8)
+    ref = small.get_state()
+    tref = small.times()
+    small.close()
+    for q, t in enumerate(sample):
+        got = out[:, t * n:(t + 1) * n].cpu().numpy()
+        assert np.array_equal(got, ref[:, q * n:(q + 1) * n]), (t, np.abs(got - ref[:, q * n:(q + 1) * n]).max())
+        assert times[t] == tref[q]
