@@ -236,7 +236,12 @@ __global__ void mlp_pack_kernel(const float* __restrict__ w, MlpSmemW* __restric
 // warp of the SM shares (measured: the cache's hit rate fell from 97 % to
 // 87 % with the accurate forms inlined).  The guess only seeds Newton.
 static __device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
-static __device__ __noinline__ float2 mlp_guess_warp(const MlpSmemW& s, float g, const float* q, int lane) {
+// (The face's six values come by value: an array passed to an out-of-line
+// function lives in local memory, which cost the kernel spills in its hot
+// loop; by value the loop needs none.)
+static __device__ __noinline__ float2 mlp_guess_warp(const MlpSmemW& s, float g, float q0, float q1, float q2,
+                                                     float q3, float q4, float q5, int lane) {
+  const float q[6] = {q0, q1, q2, q3, q4, q5};
   float x[MLP_IN];
   const float rref = sqrtf(q[0] * q[3]), pref = sqrtf(q[2] * q[5]);
   const float icref = rsqrtf(g * __fdividef(pref, rref));
@@ -302,24 +307,33 @@ __device__ __forceinline__ void issue_span(T* slotp, unsigned long long* bar, co
 }
 
 // A state that repeats over a whole window (the uniform shortcut): its |u|
-// + c, and its validity into *err (first error kept).  Out of line: it runs
-// once per new uniform state, and the kernel's hot code stays shorter.
+// + c and its validity (0 or a status).  Out of line: it runs once per new
+// uniform state, and the kernel's hot code stays shorter.  (Results come by
+// value: a local whose address an out-of-line function takes lives in local
+// memory.)
 template <typename T>
-static __device__ __noinline__ T uniform_speed(T r0, T r1, T r2, Gas<T> gas, int* err) {
+struct SpeedSt {
+  T s;
+  int st;
+};
+template <typename T>
+static __device__ __noinline__ SpeedSt<T> uniform_speed(T r0, T r1, T r2, Gas<T> gas) {
   T u[3] = {r0 + T(0), r1 + T(0), r2 + T(0)}, w[3];
   const bool finite = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
   to_prim<T, 1, 0>(u, w, gas);
-  if (!finite) *err = *err ? *err : ST_NONFINITE;
-  else if (!(w[0] > T(0)) || !(w[2] > T(0))) *err = *err ? *err : ST_NEG;
-  return fabs(w[1]) + dsqrt(qdiv(gas.g * w[2], w[0]));
+  SpeedSt<T> r;
+  r.st = !finite ? ST_NONFINITE : (!(w[0] > T(0)) || !(w[2] > T(0))) ? ST_NEG : 0;
+  r.s = fabs(w[1]) + dsqrt(qdiv(gas.g * w[2], w[0]));
+  return r;
 }
 
 // Record a gated face's states (network training data) with probability
 // thresh / 2^64, counter-based per face id and step.  Out of line: it runs
 // only while harvesting.
 template <typename T, typename A>
-static __device__ __noinline__ void harvest_face(const A& a, unsigned long long id, long long step, const T* WL,
-                                                 const T* WR) {
+static __device__ __noinline__ void harvest_face(const A& a, unsigned long long id, long long step, T l0, T l1,
+                                                 T l2, T r0, T r1, T r2) {
+  const T WL[3] = {l0, l1, l2}, WR[3] = {r0, r1, r2};
   const unsigned long long hsh =
       mix64(a.harvest_seed + 0x9E3779B97F4A7C15ull * (id + 1) + ((unsigned long long)step << 40));
   if (hsh < a.harvest_thresh) {
@@ -502,7 +516,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
             ur[0] = r0;
             ur[1] = r1;
             ur[2] = r2;
-            u_spd = uniform_speed<T>(r0, r1, r2, gas, &err);
+            const SpeedSt<T> us = uniform_speed<T>(r0, r1, r2, gas);
+            u_spd = us.s;
+            if (err == 0) err = us.st;
           }
           smax = fmax(smax, u_spd * fn);
           const int a0 = s_beg + k * BSPAN * BSEG, a1 = min(a0 + BSPAN * BSEG, s_end);
@@ -548,7 +564,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
             ur[0] = r0;
             ur[1] = r1;
             ur[2] = r2;
-            u_spd = uniform_speed<T>(r0, r1, r2, gas, &err);
+            const SpeedSt<T> us = uniform_speed<T>(r0, r1, r2, gas);
+            u_spd = us.s;
+            if (err == 0) err = us.st;
           }
         }
         if (uniform) {
@@ -625,7 +643,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
           pg = toro_guess<T>(WL[0], WL[1], WL[2], cL, WR[0], WR[1], WR[2], cR, gas, kind);
           if (!mlp_gate<T>(kind, WL[2], WR[2])) kind = -kind;  // negative: network not used
           if (kind == 2 && a.harvest)
-            harvest_face<T, BatchArgs<T>>(a, (unsigned long long)(base + b + c0 + lane), step, WL, WR);
+            harvest_face<T, BatchArgs<T>>(a, (unsigned long long)(base + b + c0 + lane), step, WL[0], WL[1], WL[2],
+                                          WR[0], WR[1], WR[2]);
         }
         // learned guess on two-shock faces, evaluated by the whole warp
         if (a.mlp_on) {
@@ -646,7 +665,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 5)
               q[v] = (float)__shfl_sync(0xffffffffu, WL[v], g);
               q[3 + v] = (float)__shfl_sync(0xffffffffu, WR[v], g);
             }
-            const float2 yp = mlp_guess_warp(sw, (float)gas.g, q, lane);
+            const float2 yp = mlp_guess_warp(sw, (float)gas.g, q[0], q[1], q[2], q[3], q[4], q[5], lane);
             if (lane == g) {
               // (the guess only seeds Newton: FP32 exp in the FP32 form)
               if constexpr (sizeof(T) == 4) pg = yp.y * __expf(yp.x);

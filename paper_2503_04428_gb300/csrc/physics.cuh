@@ -576,18 +576,26 @@ __device__ __forceinline__ int newton_star(T p, T rL, T uL, T pL, T cL, T rR, T 
   return ST_OK;
 }
 
+// A primitive 1D state returned by value (a local whose address an
+// out-of-line function takes lives in local memory).
+template <typename T>
+struct Prim3 {
+  T rho, u, p;
+};
+
 // The state inside a rarefaction fan at x/t = S (Toro ch. 4.5): sign = +1
 // for the left fan (c = 2/(g+1) (cK + (g-1)/2 (uK - S)), u = c + S), -1 for
 // the right one (c = 2/(g+1) (cK - (g-1)/2 (uK - S)), u = S - c); rho and P
 // from the isentrope through (rK, pK).  Out of line: x/t = S lies inside a
 // fan only near sonic points, and the hot solver code stays shorter.
 template <typename T>
-static __device__ __noinline__ void fan_state(T S, T sign, T rK, T uK, T pK, T cK, Gas<T> gas, T& rho, T& u,
-                                              T& p) {
+static __device__ __noinline__ Prim3<T> fan_state(T S, T sign, T rK, T uK, T pK, T cK, Gas<T> gas) {
   const T c = gas.A2 * (cK + sign * T(0.5) * gas.gm1 * (uK - S));
-  u = S + sign * c;
-  rho = rK * dpow(qdiv(c, cK), gas.two_gm1);
-  p = pK * dpow(qdiv(c, cK), gas.pow_c);
+  Prim3<T> w;
+  w.u = S + sign * c;
+  w.rho = rK * dpow(qdiv(c, cK), gas.two_gm1);
+  w.p = pK * dpow(qdiv(c, cK), gas.pow_c);
+  return w;
 }
 
 // Sample the exact solution at x/t = S given the star state (Toro ch. 4.5);
@@ -614,7 +622,12 @@ __device__ __forceinline__ bool sample_xi(T S, T rL, T uL, T pL, T cL, T rR, T u
         rho = rL * dpow(qdiv(ps, pL), gas.ig);
         u = us; p = ps;
       } else {
-        fan_state<T>(S, T(1), rL, uL, pL, cL, gas, rho, u, p);  // inside the left fan
+        {
+          const Prim3<T> f = fan_state<T>(S, T(1), rL, uL, pL, cL, gas);
+          rho = f.rho;
+          u = f.u;
+          p = f.p;
+        }  // inside the left fan
       }
     }
     return true;
@@ -636,7 +649,12 @@ __device__ __forceinline__ bool sample_xi(T S, T rL, T uL, T pL, T cL, T rR, T u
       rho = rR * dpow(qdiv(ps, pR), gas.ig);
       u = us; p = ps;
     } else {
-      fan_state<T>(S, T(-1), rR, uR, pR, cR, gas, rho, u, p);  // inside the right fan
+      {
+          const Prim3<T> f = fan_state<T>(S, T(-1), rR, uR, pR, cR, gas);
+          rho = f.rho;
+          u = f.u;
+          p = f.p;
+        }  // inside the right fan
     }
   }
   return false;
@@ -672,15 +690,21 @@ __device__ __forceinline__ Gas<double> gas_double(const Gas<float>& g) {
 // The FP64 Newton solve of an FP32 face near vacuum or with a pressure ratio
 // above 1e6 (reading R12).  Kept out of line: it is rare, and its FP64 code
 // would crowd the instruction cache of the FP32 kernels.
-static __device__ __noinline__ int newton_star_fp64(float p0, float rL, float uL, float pL, float rR, float uR,
-                                             float pR, Gas<float> gas, float& ps, float& us, int& iters) {
+struct Star32 {
+  float ps, us;
+  int iters, st;
+};
+static __device__ __noinline__ Star32 newton_star_fp64(float p0, float rL, float uL, float pL, float rR, float uR,
+                                                float pR, Gas<float> gas) {
   const Gas<double> g2 = gas_double(gas);
-  double ps2, us2;
+  double ps2 = 0.0, us2 = 0.0;
   const double cL2 = sqrt(g2.g * (double)pL / (double)rL), cR2 = sqrt(g2.g * (double)pR / (double)rR);
-  const int st = newton_star<double>((double)p0, rL, uL, pL, cL2, rR, uR, pR, cR2, g2, 1e-10, ps2, us2, iters);
-  ps = (float)ps2;
-  us = (float)us2;
-  return st;
+  Star32 r;
+  r.iters = 0;
+  r.st = newton_star<double>((double)p0, rL, uL, pL, cL2, rR, uR, pR, cR2, g2, 1e-10, ps2, us2, r.iters);
+  r.ps = (float)ps2;
+  r.us = (float)us2;
+  return r;
 }
 
 // An FP32 face that is solved in FP64 (reading R12): pressure ratio above
@@ -700,8 +724,13 @@ __device__ __forceinline__ int exact_star_from(T rL, T uL, T pL, T cL, T rR, T u
   const T vac = gas.two_gm1 * (cL + cR);
   if (vac <= uR - uL) return ST_VACUUM;
   if constexpr (sizeof(T) == 4) {
-    if (hard_face<T>(pL, pR, uR - uL, vac))
-      return newton_star_fp64(p0, rL, uL, pL, rR, uR, pR, gas, ps, us, iters);
+    if (hard_face<T>(pL, pR, uR - uL, vac)) {
+      const Star32 r = newton_star_fp64(p0, rL, uL, pL, rR, uR, pR, gas);
+      ps = r.ps;
+      us = r.us;
+      iters = r.iters;
+      return r.st;
+    }
   }
   return newton_star<T>(p0, rL, uL, pL, cL, rR, uR, pR, cR, gas, newton_tol<T>(), ps, us, iters);
 }
