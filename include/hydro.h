@@ -224,9 +224,10 @@ int hydro_run(hydro_t h, int nsteps, double cfl, double t_end, double* t_out);
 /* Conserved totals sum_cells U dV, FP64, deterministic order; out has nv entries. */
 int hydro_totals(hydro_t h, double* out_nv);
 
-/* Conserved totals accumulated inside the step (spec form (1): FP32
- * bulk arithmetic, FP64 conservation sums).  With on != 0 every later step
- * (hydro_step, hydro_run) also sums U dV of the cells it updates: each CTA
+/* Conserved totals accumulated inside the step (the FP32 form keeps its
+ * bulk arithmetic in FP32 and its conservation sums in FP64).  With on != 0
+ * every later step (hydro_step, hydro_run) also sums U dV of the cells it
+ * updates: each CTA
  * of the fused sweep in a fixed order over its cells, into its own FP64
  * partial (the FP32 3D form sums each column of cells as a compensated FP32
  * pair of exact products and converts the column's sum to FP64; its totals

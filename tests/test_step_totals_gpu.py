@@ -1,4 +1,4 @@
-"""Conserved totals accumulated inside the step (a10; spec form (1)).
+"""Conserved totals accumulated inside the step (FP32 bulk, FP64 conservation sums).
 
 With hydro_set_step_totals on, every CTA of the fused sweep sums U dV of the
 cells it updates in FP64 into its own partial, and hydro_step_totals sums the
