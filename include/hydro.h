@@ -227,11 +227,11 @@ int hydro_totals(hydro_t h, double* out_nv);
 /* Conserved totals accumulated inside the step (the FP32 form keeps its
  * bulk arithmetic in FP32 and its conservation sums in FP64).  With on != 0
  * every later step (hydro_step, hydro_run) also sums U dV of the cells it
- * updates: each CTA
- * of the fused sweep in a fixed order over its cells, into its own FP64
- * partial (the FP32 3D form sums each column of cells as a compensated FP32
- * pair of exact products and converts the column's sum to FP64; its totals
- * equal the FP64 sums of the FP32 state to ~1e-14 relative);
+ * updates: each CTA of the fused sweep in a fixed order over its cells,
+ * into its own FP64 partial (the FP32 3D form sums each column of cells as
+ * a compensated FP32 pair of exact products and converts the column's sum
+ * to FP64; its totals equal the FP64 sums of the FP32 state to ~1e-14
+ * relative);
  * hydro_step_totals then sums the partials in a fixed order, so the
  * totals of the new state cost no second pass over it and are deterministic.
  * The partials take nv x (the most CTAs of any launch shape) doubles, and a
